@@ -1,0 +1,155 @@
+/*
+ * dd.h -- C-ABI of the GB300 damage-diffusion field library (libdd.so).
+ *
+ * The library evaluates the cumulative damage field of a scanned Gaussian electron
+ * probe (Javadi Rad et al., "Fast Simulation of Damage Diffusion Distribution in
+ * STEM", Sec. 2):
+ *
+ *   phi_i(r,t) = Q0/(4 pi D) [E1(|r-r_i|^2/(2Ds+4D(t-t_i))) - E1(|r-r_i|^2/w0)]
+ *       w0 = 2Ds                     while the beam is on,  t_i <= t <= t_i+tau_i  (Eq. 1)
+ *       w0 = 2Ds + 4D(t-t_i-tau_i)   after it,              t > t_i+tau_i          (Eq. 2)
+ *       with Ds = r_s^2 (r_s = probe sigma) and the ln forms of Eq. 3/4 at r = r_i;
+ *   psi(r,t)   = sum over visits i, in visit order, of phi_i(r,t)             (Eq. 5)
+ *       (a visit that has not started, t <= t_i, adds nothing).
+ *
+ * Conventions shared by every entry point:
+ *   - Units are SI: metres, seconds, m^2/s, u/s; fields are returned in u/m^2.
+ *   - Every call returns a dd_status; on failure dd_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread).  No C++
+ *     exception crosses this boundary.
+ *   - The caller owns every input and output buffer.  dd_create_scan deep-copies
+ *     the arrays it is given.  A dd_scan is immutable after creation and may be
+ *     used from several threads; calls that write the same output race.
+ *   - Pointers marked "host or device" may point to host memory or to CUDA device
+ *     memory of the current device (detected with cudaPointerGetAttributes).
+ *     Host outputs are written before the call returns (the call synchronises
+ *     the stream).  With device inputs and outputs the call only enqueues work on
+ *     `cuda_stream` (NULL = the legacy default stream) and returns.
+ *   - Device scratch is taken with cudaMallocAsync on the call's stream and
+ *     returned with cudaFreeAsync; a scan caches its probe list per device.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_scan dd_scan;          /* opaque, library-owned */
+
+typedef enum {
+    DD_OK = 0,
+    DD_EINVAL = -1,     /* an argument is out of range, NULL where not allowed, or not finite */
+    DD_ENOMEM = -2,     /* host or device allocation failed */
+    DD_ECUDA = -3,      /* a CUDA runtime call failed (message names it) */
+    DD_ETIMEOUT = -4,   /* a bounded device wait ran out (status word set by a kernel) */
+    DD_ENOTSUP = -5     /* valid request that this build does not implement */
+} dd_status;
+
+/* Scan strategies of Sec. 1: raster; alternating (serpentine); interleaved, which
+   skips fixed grid points; random; or an explicit list of grid positions. */
+typedef enum {
+    DD_RASTER = 0,       /* rows in order, each left to right */
+    DD_SERPENTINE = 1,   /* even rows left to right, odd rows right to left */
+    DD_INTERLEAVED = 2,  /* stride S: S*S passes over the sub-lattices (iy%S, ix%S), in
+                            raster order of the sub-lattice, each pass in raster order */
+    DD_RANDOM = 3,       /* Fisher-Yates permutation driven by SplitMix64(seed) */
+    DD_CUSTOM = 4        /* custom_visit[] lists grid indices in visit order */
+} dd_order;
+
+typedef enum {
+    DD_FP64 = 0,         /* every step in FP64 */
+    DD_MIXED = 1         /* per-pair terms in FP32; per-(visit, snapshot) coefficients,
+                            per-block sums and the output in FP64 */
+} dd_precision;
+
+/* Problem statement of Sec. 2 (assumptions) and Sec. 1 (scan strategies).
+   Probe (ix, iy) sits at (ix * pitch_m, iy * pitch_m); its grid index is iy*nx + ix. */
+typedef struct {
+    int32_t nx, ny;               /* probe grid, each >= 1, nx*ny <= 2^26 */
+    double pitch_m;               /* probe pitch [m], > 0 */
+    double sigma_m;               /* Gaussian probe sigma r_s [m], > 0; Ds = sigma^2 */
+    double D_m2s;                 /* diffusion coefficient D [m^2/s], > 0 */
+    double Q0;                    /* deposition rate [u/s], finite */
+    double dwell_s;               /* dwell tau [s], > 0 (also the time unit used inside) */
+    double flyback_s;             /* dead time when a raster/serpentine scan changes row, >= 0;
+                                     must be 0 for the other orders */
+    int32_t order;                /* dd_order */
+    int32_t interleave_stride;    /* S >= 1 for DD_INTERLEAVED, ignored otherwise */
+    uint64_t seed;                /* seed of the random order / kept subset */
+    double keep_fraction;         /* in (0, 1]; < 1 keeps round(f*nx*ny) positions: the first
+                                     ones of the seeded permutation (visited in that order for
+                                     DD_RANDOM, in the order's own sequence otherwise) */
+    const uint8_t *mask;          /* host, nx*ny, row-major; NULL = all; 0 = not visited.
+                                     Must be NULL when keep_fraction < 1 or order is CUSTOM */
+    const int32_t *custom_visit;  /* host, n_custom grid indices for DD_CUSTOM, NULL otherwise */
+    int32_t n_custom;
+    const double *dwell_per_visit;/* host, optional per-visit dwell tau_i [s] (Eq. 1/2 allow a
+                                     different tau_i per probe); NULL = dwell_s for all */
+} dd_scan_desc;
+
+/* Build a scan: the visit list in visit order and each visit's start time
+   t_k = k*dwell (uniform dwell, no flyback), otherwise t_{k+1} = t_k + tau_k
+   (+ flyback_s when a raster/serpentine scan changes row).  Host-only; touches
+   no GPU.  *out is set to a new scan owned by the caller (free with dd_destroy).
+   Errors: DD_EINVAL (bad description; *out untouched), DD_ENOMEM. */
+dd_status dd_create_scan(const dd_scan_desc *desc, dd_scan **out);
+
+/* Number of visits of the scan. */
+dd_status dd_scan_size(const dd_scan *scan, int64_t *n_visits);
+
+/* Copy the visit list out: grid_index[k] (may be NULL), t_start_s[k] and
+   dwell_s[k] (each may be NULL), k < n_visits.  Host pointers. */
+dd_status dd_scan_visits(const dd_scan *scan, int32_t *grid_index, double *t_start_s,
+                         double *dwell_s);
+
+/* Cumulative field psi (Eq. 5) at n_pts points and n_t snapshot times:
+     out[it * n_pts + ip] = psi((pts_xy_m[2*ip], pts_xy_m[2*ip+1]), times_s[it])   [u/m^2]
+   pts_xy_m: host or device, 2*n_pts doubles (x, y interleaved) [m].
+   times_s:  host or device, n_t doubles [s], any order (a device array is copied
+             to the host first, which synchronises the stream).
+   out:      host or device, n_t*n_pts doubles, row = snapshot.
+   n_pts == 0 or n_t == 0 is a no-op.  Times at or before the first visit give 0.
+   Errors: DD_EINVAL (NULL scan/buffer with a non-zero size, negative sizes,
+   non-finite times, bad precision), DD_ENOMEM, DD_ECUDA. */
+dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
+                            const double *times_s, int64_t n_t, dd_precision prec,
+                            double *out, void *cuda_stream);
+
+/* Dwell-start dose of every visit: the field at the probe's own position when
+   its dwell starts, from the visits before it,
+     out[j] = psi_{j-1}(r_j, t_j) = sum_{i<j} phi_i(r_j, t_j)   (Eq. 5 at r_j, t_j)
+   in visit order.  out: host or device, n_visits doubles.  The current build
+   needs a uniform dwell without flyback (t_k = k*tau); otherwise DD_ENOTSUP.
+   Errors: DD_EINVAL, DD_ENOTSUP, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, double *out,
+                            void *cuda_stream);
+
+/* Many independent scans in one persistent launch (the paper's task partition
+   over probe subsets, Sec. 3, applied across scans).  Scan k is evaluated at
+   points pts_xy_m[2*pt_offsets[k] .. 2*pt_offsets[k+1]) and the single time
+   times_s[k]; its field goes to out[pt_offsets[k] .. pt_offsets[k+1]).
+   scans: host array of n_scans handles.  pt_offsets: host, n_scans+1 entries,
+   non-decreasing, pt_offsets[0] == 0.  times_s: host, n_scans.  pts_xy_m and out:
+   host or device.  Work items are cost-sorted and claimed by an atomic counter.
+   Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_field_batch(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
+                         const double *pts_xy_m, const double *times_s, dd_precision prec,
+                         double *out, void *cuda_stream);
+
+/* Free a scan and its per-device caches (device caches are freed on their own
+   devices).  NULL is a no-op.  The scan must not be in use by an enqueued call. */
+void dd_destroy(dd_scan *scan);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dd_last_error(void);
+
+/* Library version string. */
+const char *dd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_H */

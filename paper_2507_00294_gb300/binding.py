@@ -1,0 +1,223 @@
+"""Python binding of libdd.so (include/dd.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts numpy arrays and
+torch tensors to pointers, calls the C entry point of the same name and raises on a
+non-zero status.  If libdd.so cannot be built or loaded the import fails loudly:
+there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DD_OK, DD_EINVAL, DD_ENOMEM, DD_ECUDA, DD_ETIMEOUT, DD_ENOTSUP = 0, -1, -2, -3, -4, -5
+DD_RASTER, DD_SERPENTINE, DD_INTERLEAVED, DD_RANDOM, DD_CUSTOM = 0, 1, 2, 3, 4
+DD_FP64, DD_MIXED = 0, 1
+PRECISIONS = {"fp64": DD_FP64, "mixed": DD_MIXED, DD_FP64: DD_FP64, DD_MIXED: DD_MIXED}
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("dd status %d: %s" % (status, msg))
+        self.status = status
+
+
+class dd_scan_desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("pitch_m", ctypes.c_double), ("sigma_m", ctypes.c_double), ("D_m2s", ctypes.c_double),
+        ("Q0", ctypes.c_double), ("dwell_s", ctypes.c_double), ("flyback_s", ctypes.c_double),
+        ("order", ctypes.c_int32), ("interleave_stride", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("keep_fraction", ctypes.c_double),
+        ("mask", ctypes.POINTER(ctypes.c_uint8)),
+        ("custom_visit", ctypes.POINTER(ctypes.c_int32)), ("n_custom", ctypes.c_int32),
+        ("dwell_per_visit", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libdd.so (building it first if needed) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libdd.so not found at %s: build it with paper_2507_00294_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    lib.dd_create_scan.argtypes = [ctypes.POINTER(dd_scan_desc), ctypes.POINTER(_VP)]
+    lib.dd_scan_size.argtypes = [_VP, ctypes.POINTER(_I64)]
+    lib.dd_scan_visits.argtypes = [_VP, _VP, _VP, _VP]
+    lib.dd_field_at_times.argtypes = [_VP, _VP, _I64, _VP, _I64, ctypes.c_int, _VP, _VP]
+    lib.dd_per_probe_dose.argtypes = [_VP, ctypes.c_int, _VP, _VP]
+    lib.dd_field_batch.argtypes = [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
+    lib.dd_destroy.argtypes = [_VP]
+    lib.dd_destroy.restype = None
+    lib.dd_last_error.restype = ctypes.c_char_p
+    lib.dd_version.restype = ctypes.c_char_p
+    for name in ("dd_create_scan", "dd_scan_size", "dd_scan_visits", "dd_field_at_times",
+                 "dd_per_probe_dose", "dd_field_batch"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, what):
+    if status != DD_OK:
+        raise DDError(status, "%s: %s" % (what, load().dd_last_error().decode()))
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) for a numpy array / torch tensor of the given dtype."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError("expected a contiguous %s tensor" % want)
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    for t in tensors:
+        if t is not None and _is_torch(t) and t.is_cuda:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Scan:
+    """A dd_scan built from a workloads.ScanSpec (or anything with the same fields)."""
+
+    def __init__(self, spec):
+        lib = load()
+        d = dd_scan_desc()
+        d.nx, d.ny = int(spec.nx), int(spec.ny)
+        d.pitch_m, d.sigma_m, d.D_m2s = spec.pitch_m, spec.sigma_m, spec.D_m2s
+        d.Q0, d.dwell_s, d.flyback_s = spec.Q0, spec.dwell_s, spec.flyback_s
+        d.order, d.interleave_stride = int(spec.order), int(spec.interleave_stride)
+        d.seed, d.keep_fraction = int(spec.seed) & ((1 << 64) - 1), float(spec.keep_fraction)
+        self._keep = []
+        if spec.mask is not None:
+            m = np.ascontiguousarray(np.asarray(spec.mask, dtype=np.uint8).reshape(-1))
+            self._keep.append(m)
+            d.mask = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        if spec.custom_visit is not None:
+            c = np.ascontiguousarray(np.asarray(spec.custom_visit, dtype=np.int32))
+            self._keep.append(c)
+            d.custom_visit = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            d.n_custom = len(c)
+        if spec.dwell_per_visit is not None:
+            w = np.ascontiguousarray(np.asarray(spec.dwell_per_visit, dtype=np.float64))
+            self._keep.append(w)
+            d.dwell_per_visit = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        _check(lib.dd_create_scan(ctypes.byref(d), ctypes.byref(h)), "dd_create_scan")
+        self._keep = None
+        self.handle = h
+        self.spec = spec
+
+    def __len__(self):
+        n = ctypes.c_int64()
+        _check(load().dd_scan_size(self.handle, ctypes.byref(n)), "dd_scan_size")
+        return n.value
+
+    def visits(self):
+        """(grid_index int32, t_start_s, dwell_s) in visit order."""
+        n = len(self)
+        g = np.empty(n, np.int32)
+        t = np.empty(n, np.float64)
+        w = np.empty(n, np.float64)
+        _check(load().dd_scan_visits(self.handle, g.ctypes.data, t.ctypes.data, w.ctypes.data),
+               "dd_scan_visits")
+        return g, t, w
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def dd_create_scan(spec):
+    return Scan(spec)
+
+
+def dd_field_at_times(scan, pts_xy_m, times_s, prec="mixed", out=None, stream=None):
+    """psi at every (time, point); returns `out` ([n_t, n_pts] float64, numpy or torch)."""
+    n_pts = (pts_xy_m.shape[0] if hasattr(pts_xy_m, "shape") else len(pts_xy_m))
+    n_t = len(times_s)
+    if out is None:
+        if _is_torch(pts_xy_m) and pts_xy_m.is_cuda:
+            import torch
+            out = torch.empty((n_t, n_pts), dtype=torch.float64, device=pts_xy_m.device)
+        else:
+            out = np.empty((n_t, n_pts), dtype=np.float64)
+    p, kp = _ptr(pts_xy_m, np.float64)
+    t, kt = _ptr(times_s, np.float64)
+    o, ko = _ptr(out, np.float64)
+    st = load().dd_field_at_times(scan.handle, p, n_pts, t, n_t, PRECISIONS[prec], o,
+                                  _stream(stream, pts_xy_m, out))
+    _check(st, "dd_field_at_times")
+    return out
+
+
+def dd_per_probe_dose(scan, prec="mixed", out=None, stream=None, device=None):
+    """Dwell-start dose of every visit, in visit order."""
+    n = len(scan)
+    if out is None:
+        if device is not None:
+            import torch
+            out = torch.empty(n, dtype=torch.float64, device=device)
+        else:
+            out = np.empty(n, dtype=np.float64)
+    o, ko = _ptr(out, np.float64)
+    _check(load().dd_per_probe_dose(scan.handle, PRECISIONS[prec], o, _stream(stream, out)),
+           "dd_per_probe_dose")
+    return out
+
+
+def dd_field_batch(scans, pt_offsets, pts_xy_m, times_s, prec="mixed", out=None, stream=None):
+    """Field of many scans, each at its own points and single time; out[pt_offsets[k]:...]."""
+    n_scans = len(scans)
+    handles = (ctypes.c_void_p * n_scans)(*[s.handle.value for s in scans])
+    offs = np.ascontiguousarray(np.asarray(pt_offsets, dtype=np.int64))
+    times = np.ascontiguousarray(np.asarray(times_s, dtype=np.float64))
+    total = int(offs[-1])
+    if out is None:
+        if _is_torch(pts_xy_m) and pts_xy_m.is_cuda:
+            import torch
+            out = torch.empty(total, dtype=torch.float64, device=pts_xy_m.device)
+        else:
+            out = np.empty(total, dtype=np.float64)
+    p, kp = _ptr(pts_xy_m, np.float64)
+    o, ko = _ptr(out, np.float64)
+    st = load().dd_field_batch(handles, n_scans, offs.ctypes.data, p, times.ctypes.data,
+                               PRECISIONS[prec], o, _stream(stream, pts_xy_m, out))
+    _check(st, "dd_field_batch")
+    return out
+
+
+def version():
+    return load().dd_version().decode()

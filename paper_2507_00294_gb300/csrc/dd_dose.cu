@@ -1,0 +1,193 @@
+// dd_dose.cu -- dwell-start dose of every visit: out[j] = psi_{j-1}(r_j, t_j)
+// = sum_{i<j} phi_i(r_j, t_j)  (Eq. 5 evaluated at the probe position when its dwell
+// starts; the paper's psi_j of Eq. 5 with j-1 visits).
+//
+// With a uniform dwell and no flyback the visit start times are t_k = k tau, so the
+// pair (i, j) only depends on the lag k = j - i through w0, w1 (Eq. 1 at k = 1, where
+// the beam of visit i switches off exactly at t_j, Eq. 2 for k > 1): one coefficient
+// record per lag.  The kernel walks lags outermost, so all lanes of a warp read the
+// same record (a shared-memory broadcast) while each lane's source index j - k is
+// different and contiguous.  Work items are (target tile, lag block), cost-sorted;
+// per-block partial sums are reduced in block order (deterministic).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "dd_coef.cuh"
+#include "dd_e1.cuh"
+#include "dd_field_impl.cuh"
+#include "dd_internal.h"
+
+namespace ddk {
+
+template <typename Cfg>
+__global__ void __launch_bounds__(Cfg::kThreads)
+dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, int64_t n,
+            const typename Cfg::Rec *__restrict__ lagrec, const int2 *__restrict__ items, int lb,
+            double *__restrict__ partial) {
+    using Rec = typename Cfg::Rec;
+    using Real = typename Cfg::Real;
+    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, TILE = NT * PPT, LBMAX = Cfg::kSB;
+    constexpr int RV = sizeof(Rec) / 16;
+    __shared__ Real s_x[TILE + LBMAX], s_y[TILE + LBMAX];
+    __shared__ __align__(16) Rec s_rec[Cfg::kSTILE];
+
+    const int2 item = items[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int64_t t0 = (int64_t)item.x * TILE;             // first target of the tile
+    const int64_t t1 = min((int64_t)n, t0 + TILE);
+    const int k0 = 1 + item.y * lb;                        // lags [k0, k1)
+    const int k1 = (int)min((int64_t)k0 + lb, t1);         // lag < target index <= t1 - 1
+    // sources needed: i = j - k for j in [t0, t1), k in [k0, k1): i in [t0 - k1 + 1, t1 - k0)
+    const int64_t w0 = t0 - k1 + 1;
+    const int64_t w1 = t1 - k0;
+    const double cx = srcX[t0], cy = srcY[t0];
+    for (int64_t i = w0 + tid; i < w1; i += NT) {
+        const int64_t ic = i < 0 ? 0 : i;                  // i < 0 never used
+        s_x[i - w0] = (Real)(srcX[ic] - cx);
+        s_y[i - w0] = (Real)(srcY[ic] - cy);
+    }
+    Real px[PPT], py[PPT];
+    int64_t jt[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        jt[q] = t0 + q * NT + tid;
+        const int64_t jj = jt[q] < n ? jt[q] : t0;
+        px[q] = (Real)(srcX[jj] - cx);
+        py[q] = (Real)(srcY[jj] - cy);
+    }
+    Real acc[PPT];
+    double tot[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) { acc[q] = 0; tot[q] = 0.0; }
+
+    for (int kk = k0; kk < k1; kk += Cfg::kSTILE) {
+        const int cnt = min(Cfg::kSTILE, k1 - kk);
+        __syncthreads();
+        {
+            const float4 *row = reinterpret_cast<const float4 *>(lagrec + kk);
+            float4 *dst = reinterpret_cast<float4 *>(&s_rec[0]);
+            for (int v = tid; v < cnt * RV; v += NT) dst[v] = row[v];
+        }
+        __syncthreads();
+        for (int c = 0; c < cnt; ++c) {
+            const int k = kk + c;
+            const Rec &R = s_rec[c];
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                const int64_t i = jt[q] - k;
+                if (i >= 0 && jt[q] < n) {
+                    const Real dx = px[q] - s_x[i - w0], dy = py[q] - s_y[i - w0];
+                    acc[q] += pair_term(dx * dx + dy * dy, R);
+                }
+            }
+            if (Cfg::kFlush < Cfg::kSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) { tot[q] += (double)acc[q]; acc[q] = 0; }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) { tot[q] += (double)acc[q]; acc[q] = 0; }
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q)
+        if (jt[q] < n) partial[(int64_t)item.y * n + jt[q]] = tot[q];
+}
+
+__global__ void dose_reduce_kernel(const double *__restrict__ partial, int64_t n, int tile, int lb,
+                                   double pref, double *__restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    // blocks written for target j: every lag block that starts below the tile's last target
+    const int64_t tile_last = min(n, (j / tile + 1) * tile) - 1;
+    const int64_t nb = tile_last >= 1 ? (tile_last - 1) / lb + 1 : 0;
+    double acc = 0.0;
+    for (int64_t b = 0; b < nb; ++b) acc += partial[b * n + j];
+    out[j] = pref * acc;
+}
+
+}  // namespace ddk
+
+namespace {
+
+template <typename Cfg>
+dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
+    using Rec = typename Cfg::Rec;
+    const int64_t n = scan->n;
+    const bool out_host = !dd::is_device_pointer(out);
+    constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
+    const int lb = Cfg::kSB;
+    const int64_t n_tiles = (n + TILE - 1) / TILE;
+    std::vector<std::pair<int64_t, int2>> its;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const int64_t t0 = t * TILE, t1 = std::min(n, t0 + TILE);
+        if (t1 - 1 < 1) continue;                                    // target 0 has no source
+        const int64_t nb = (t1 - 1 - 1) / lb + 1;                    // lags 1 .. t1-1
+        for (int64_t b = 0; b < nb; ++b) {
+            const int64_t k0 = 1 + b * lb, k1 = std::min(k0 + lb, t1);
+            int64_t cost = 0;                                        // valid (j, k) pairs
+            for (int64_t k = k0; k < k1; ++k) cost += std::max<int64_t>(0, t1 - std::max(t0, k));
+            its.push_back({cost, make_int2((int)t, (int)b)});
+        }
+    }
+    std::stable_sort(its.begin(), its.end(),
+                     [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
+    const int64_t nblk = n >= 2 ? (n - 2) / lb + 1 : 0;
+    size_t bytes = 0;
+    auto add = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
+    add((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
+    add(its.size() * sizeof(int2) + 16);
+    add((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(double));
+    if (out_host) add((size_t)n * sizeof(double));
+    bytes += 256;
+
+    dd_status st = DD_OK;
+    const double *src = dd::device_sources(scan, &st);
+    if (!src) return st;
+    void *ws = nullptr;
+    cudaError_t err = cudaMallocAsync(&ws, bytes, stream);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return dd::fail(err == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,
+                        std::string("cudaMallocAsync(dose workspace): ") + cudaGetErrorString(err));
+    }
+    char *base = (char *)ws;
+    size_t off = 0;
+    auto take = [&](size_t b) { off = (off + 255) & ~size_t(255); char *p = base + off; off += b; return p; };
+    Rec *d_rec = (Rec *)take((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
+    int2 *d_items = (int2 *)take(its.size() * sizeof(int2) + 16);
+    double *d_part = (double *)take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(double));
+    double *out_dev = out_host ? (double *)take((size_t)n * sizeof(double)) : out;
+
+    auto *keep = new std::vector<int2>(its.size());
+    for (size_t k = 0; k < its.size(); ++k) (*keep)[k] = its[k].second;
+    if (n >= 2) {
+        ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
+        DD_CUDA_TRY(cudaGetLastError());
+        DD_CUDA_TRY(cudaMemcpyAsync(d_items, keep->data(), keep->size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
+        ddk::dose_kernel<Cfg><<<(unsigned)keep->size(), Cfg::kThreads, 0, stream>>>(
+            src, src + n, n, d_rec, d_items, lb, d_part);
+        DD_CUDA_TRY(cudaGetLastError());
+    }
+    ddk::dose_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev);
+    DD_CUDA_TRY(cudaGetLastError());
+    if (out_host)
+        DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    DD_CUDA_TRY(cudaFreeAsync(ws, stream));
+    DD_CUDA_TRY(cudaLaunchHostFunc(stream, [](void *p) { delete static_cast<std::vector<int2> *>(p); }, keep));
+    if (out_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    return DD_OK;
+}
+
+}  // namespace
+
+extern "C" dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, double *out, void *cuda_stream) {
+    dd::clear_error();
+    if (!scan || !out) return dd::fail(DD_EINVAL, "dd_per_probe_dose: NULL argument");
+    if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_per_probe_dose: unknown precision");
+    if (!scan->uniform)
+        return dd::fail(DD_ENOTSUP, "dd_per_probe_dose: needs a uniform dwell without flyback");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    if (prec == DD_MIXED) return run_dose<ddk::CfgMixed>(scan, out, stream);
+    return run_dose<ddk::CfgF64>(scan, out, stream);
+}

@@ -1,0 +1,258 @@
+// dd_field.cu -- cumulative damage field psi(r, t) of Eq. 5 on the GPU.
+//
+//   psi(r,t) = Q0/(4 pi D) sum_{i : t_i < t} [E1(rho_i^2 / w1) - E1(rho_i^2 / w0)]
+//   w1 = 2s + 4 kappa (t - t_i),  w0 = 2s (beam on, Eq. 1) or 2s + 4 kappa (t - t_i - tau_i)
+//   (beam off, Eq. 2), in units of the pitch and the reference dwell (dd_internal.h).
+//
+// Pipeline of one dd_field_at_times call (all on the caller's stream):
+//   1. points SI -> pitch units (prep_points_kernel);
+//   2. per (snapshot, visit) FP64 coefficients: q1 = 1/w1, dq = 1/w0 - 1/w1 and the
+//      moment coefficients c_0..c_M of dd_e1.cuh (coef_kernel);
+//   3. work items (point tile, snapshot chunk, visit block), sorted by cost, one CTA
+//      each (field_kernel): the block's visits are staged in shared memory in visit
+//      order, every thread keeps PPT points x TCH snapshots in registers, and each
+//      snapshot only sums the visits that have started (causal prefix n_active(t));
+//   4. deterministic reduce of the per-block partial sums in block order, times
+//      Q0/(4 pi D), into out[snapshot][point] (reduce_kernel).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "dd_coef.cuh"
+#include "dd_e1.cuh"
+#include "dd_field_impl.cuh"
+#include "dd_internal.h"
+
+namespace ddk {
+
+__global__ void prep_points_kernel(const double *__restrict__ xy, int64_t n, double inv_p,
+                                   double *__restrict__ X, double *__restrict__ Y) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    X[k] = xy[2 * k] * inv_p;
+    Y[k] = xy[2 * k + 1] * inv_p;
+}
+
+// out[row[j] * n_pts + p] = pref * sum_{k < nblk[chunk(j)]} partial[(k * n_tg + j) * n_pts + p]
+__global__ void reduce_kernel(const double *__restrict__ partial, const int *__restrict__ nblk_of_snap,
+                              const int *__restrict__ row, int n_tg, int64_t n_pts, double pref,
+                              double *__restrict__ out) {
+    const int j = blockIdx.y;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pts) return;
+    const int nb = nblk_of_snap[j];
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) acc += partial[((int64_t)k * n_tg + j) * n_pts + p];
+    out[(int64_t)row[j] * n_pts + p] = pref * acc;
+}
+
+}  // namespace ddk
+
+// ============================================================== host dispatcher
+namespace {
+
+using ddk::RecF32;
+using ddk::RecF64;
+
+struct Carve {
+    char *base;
+    size_t off = 0;
+    explicit Carve(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = (T *)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Host-side tables uploaded with cudaMemcpyAsync; freed from a stream callback.
+struct HostTables {
+    std::vector<std::vector<int4>> items;
+    std::vector<std::vector<int>> ints;
+    std::vector<std::vector<double>> reals;
+    static void CUDART_CB release(void *p) { delete static_cast<HostTables *>(p); }
+};
+
+// Sizes of the workspace a call needs (the same function drives the carve).
+template <typename Cfg>
+size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out_host, bool pts_host,
+                       int n_t) {
+    using Rec = typename Cfg::Rec;
+    const int tile = Cfg::kThreads * Cfg::kPPT;
+    const int64_t n_tiles = (n_pts + tile - 1) / tile;
+    const int nblk_max = (int)((n_src + sb - 1) / sb);
+    const int n_chunks = (group + Cfg::kTCH - 1) / Cfg::kTCH;
+    size_t b = 0;
+    auto add = [&](size_t bytes) { b = ((b + 255) & ~size_t(255)) + bytes; };
+    if (pts_host) add(2 * (size_t)n_pts * sizeof(double));
+    if (out_host) add((size_t)n_t * n_pts * sizeof(double));
+    add(2 * (size_t)n_pts * sizeof(double));                  // X, Y in pitch units
+    add((size_t)group * sizeof(double));                      // snapshot times
+    add((size_t)group * sizeof(int) * 3);                     // nact, row, nblk per snapshot
+    add((size_t)n_tiles * n_chunks * nblk_max * sizeof(int4));  // items
+    add((size_t)group * n_src * sizeof(Rec));                 // coefficient records
+    add((size_t)nblk_max * group * n_pts * sizeof(double));   // partial sums
+    return b + 256;
+}
+
+template <typename Cfg>
+dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
+                    const std::vector<double> &times, double *out, cudaStream_t stream) {
+    using Rec = typename Cfg::Rec;
+    const int64_t n_src = scan->n;
+    const int n_t = (int)times.size();
+    const bool pts_host = !dd::is_device_pointer(pts_xy_m);
+    const bool out_host = !dd::is_device_pointer(out);
+
+    // sort snapshots by time; n_active(t) = #{i : T_i < t} over the increasing T_i
+    std::vector<int> order(n_t);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
+    std::vector<double> tdim(n_t);
+    std::vector<int> nact(n_t);
+    for (int k = 0; k < n_t; ++k) {
+        tdim[k] = times[order[k]] / scan->dwell;
+        nact[k] = (int)(std::lower_bound(scan->T.begin(), scan->T.end(), tdim[k]) - scan->T.begin());
+    }
+
+    // visit block size and snapshot groups bound the partial and record buffers
+    const int tile = Cfg::kThreads * Cfg::kPPT;
+    const int64_t n_tiles = (n_pts + tile - 1) / tile;
+    int sb = Cfg::kSB;
+    int group = n_t;
+    const size_t budget = size_t(1) << 30;
+    while (group > Cfg::kTCH &&
+           (size_t)group * n_src * sizeof(Rec) + (size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget)
+        group = std::max(Cfg::kTCH, group / 2);
+    while ((size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget && sb < (1 << 20)) sb *= 2;
+    const int nblk_max = (int)((n_src + sb - 1) / sb);
+    const int n_chunks_max = (group + Cfg::kTCH - 1) / Cfg::kTCH;
+
+    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_host, pts_host, n_t);
+    dd_status st = DD_OK;
+    const double *src = dd::device_sources(scan, &st);
+    if (!src) return st;
+    void *ws = nullptr;
+    cudaError_t err = cudaMallocAsync(&ws, ws_bytes, stream);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return dd::fail(err == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,
+                        std::string("cudaMallocAsync(field workspace): ") + cudaGetErrorString(err));
+    }
+    Carve cv(ws);
+    const double *pts_dev = pts_xy_m;
+    if (pts_host) {
+        double *p = cv.take<double>(2 * (size_t)n_pts);
+        DD_CUDA_TRY(cudaMemcpyAsync(p, pts_xy_m, 2 * (size_t)n_pts * sizeof(double), cudaMemcpyHostToDevice, stream));
+        pts_dev = p;
+    }
+    double *out_dev = out_host ? cv.take<double>((size_t)n_t * n_pts) : out;
+    double *X = cv.take<double>(2 * (size_t)n_pts);
+    double *Y = X + n_pts;
+    double *d_t = cv.take<double>(group);
+    int *d_nact = cv.take<int>(3 * (size_t)group);
+    int *d_row = d_nact + group;
+    int *d_nblk = d_row + group;
+    int4 *d_items = cv.take<int4>((size_t)n_tiles * n_chunks_max * nblk_max);
+    Rec *d_rec = cv.take<Rec>((size_t)group * n_src);
+    double *d_part = cv.take<double>((size_t)nblk_max * group * n_pts);
+
+    ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y);
+    DD_CUDA_TRY(cudaGetLastError());
+
+    const double *srcX = src, *srcY = src + n_src, *srcT = src + 2 * n_src, *srcTAU = src + 3 * n_src;
+    // host staging for the per-group tables, released by a host callback once the
+    // stream has consumed them (the copies below may read pageable memory late)
+    HostTables *keep = new HostTables();
+    for (int g0 = 0; g0 < n_t; g0 += group) {
+        const int ng = std::min(group, n_t - g0);
+        const int n_chunks = (ng + Cfg::kTCH - 1) / Cfg::kTCH;
+        std::vector<int> tabs(3 * (size_t)ng);
+        std::vector<double> tg(ng);
+        int max_nact = 0;
+        for (int j = 0; j < ng; ++j) {
+            tg[j] = tdim[g0 + j];
+            tabs[j] = nact[g0 + j];
+            tabs[ng + j] = order[g0 + j];
+            max_nact = std::max(max_nact, nact[g0 + j]);
+        }
+        // work items: (tile, chunk, block) for every block below the chunk's largest n_active
+        std::vector<std::pair<int64_t, int4>> items;
+        for (int c = 0; c < n_chunks; ++c) {
+            const int j0 = c * Cfg::kTCH, j1 = std::min(ng, j0 + Cfg::kTCH);
+            int cmax = 0;
+            for (int j = j0; j < j1; ++j) cmax = std::max(cmax, nact[g0 + j]);
+            const int nb = (cmax + sb - 1) / sb;
+            for (int j = j0; j < j1; ++j) tabs[2 * ng + j] = nb;
+            for (int k = 0; k < nb; ++k) {
+                int64_t cost = 0;
+                for (int j = j0; j < j1; ++j)
+                    cost += std::max(0, std::min(nact[g0 + j], (k + 1) * sb) - k * sb);
+                for (int64_t t = 0; t < n_tiles; ++t)
+                    items.push_back({cost, make_int4((int)t, c, k, 0)});
+            }
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const std::pair<int64_t, int4> &a, const std::pair<int64_t, int4> &b) { return a.first > b.first; });
+        std::vector<int4> it(items.size());
+        for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
+
+        DD_CUDA_TRY(cudaMemcpyAsync(d_t, tg.data(), ng * sizeof(double), cudaMemcpyHostToDevice, stream));
+        DD_CUDA_TRY(cudaMemcpyAsync(d_nact, tabs.data(), 3 * (size_t)ng * sizeof(int), cudaMemcpyHostToDevice, stream));
+        if (!it.empty())
+            DD_CUDA_TRY(cudaMemcpyAsync(d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
+        if (max_nact > 0) {
+            dim3 cg((unsigned)((max_nact + 127) / 128), (unsigned)ng);
+            ddk::coef_kernel<Rec><<<cg, 128, 0, stream>>>(srcT, srcTAU, d_t, d_nact, scan->s, scan->kappa, d_rec, n_src);
+            DD_CUDA_TRY(cudaGetLastError());
+        }
+        if (!it.empty()) {
+            ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
+                srcX, srcY, X, Y, n_pts, d_rec, n_src, d_nact, d_items, ng, sb, d_part);
+            DD_CUDA_TRY(cudaGetLastError());
+        }
+        dim3 rg((unsigned)((n_pts + 255) / 256), (unsigned)ng);
+        ddk::reduce_kernel<<<rg, 256, 0, stream>>>(d_part, d_nblk, d_row, ng, n_pts, scan->pref, out_dev);
+        DD_CUDA_TRY(cudaGetLastError());
+        keep->items.push_back(std::move(it));
+        keep->ints.push_back(std::move(tabs));
+        keep->reals.push_back(std::move(tg));
+    }
+    if (out_host)
+        DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n_t * n_pts * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    DD_CUDA_TRY(cudaFreeAsync(ws, stream));
+    DD_CUDA_TRY(cudaLaunchHostFunc(stream, HostTables::release, keep));
+    if (out_host || pts_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    return DD_OK;
+}
+
+}  // namespace
+
+extern "C" dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
+                                       const double *times_s, int64_t n_t, dd_precision prec,
+                                       double *out, void *cuda_stream) {
+    dd::clear_error();
+    if (!scan) return dd::fail(DD_EINVAL, "dd_field_at_times: NULL scan");
+    if (n_pts < 0 || n_t < 0) return dd::fail(DD_EINVAL, "dd_field_at_times: negative size");
+    if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_field_at_times: unknown precision");
+    if (n_pts == 0 || n_t == 0) return DD_OK;
+    if (!pts_xy_m || !times_s || !out) return dd::fail(DD_EINVAL, "dd_field_at_times: NULL buffer");
+    if (n_t > (int64_t(1) << 24) || n_pts > (int64_t(1) << 31))
+        return dd::fail(DD_EINVAL, "dd_field_at_times: too many points or snapshots");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    std::vector<double> times((size_t)n_t);
+    if (dd::is_device_pointer(times_s)) {
+        DD_CUDA_TRY(cudaMemcpyAsync(times.data(), times_s, n_t * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    } else {
+        std::memcpy(times.data(), times_s, n_t * sizeof(double));
+    }
+    for (double t : times)
+        if (!std::isfinite(t)) return dd::fail(DD_EINVAL, "dd_field_at_times: non-finite time");
+    if (prec == DD_MIXED) return run_field<ddk::CfgMixed>(scan, pts_xy_m, n_pts, times, out, stream);
+    return run_field<ddk::CfgF64>(scan, pts_xy_m, n_pts, times, out, stream);
+}

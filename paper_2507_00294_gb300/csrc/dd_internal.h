@@ -1,0 +1,58 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dd.h"
+
+// A scan after dd_create_scan: visit list and times (SI) plus the dimensionless
+// form used on the device.  Lengths are in units of the pitch p, times in units of
+// the reference dwell tau_ref = desc.dwell_s.  With w(dt) = 2Ds + 4D dt (Eq. 1/2):
+//   w / p^2 = 2 s + 4 kappa (dt / tau_ref),  s = Ds / p^2,  kappa = D tau_ref / p^2,
+// and the arguments rho^2 / w are unchanged by the scaling.
+struct dd_scan {
+    int32_t nx = 0, ny = 0;
+    double pitch = 0, sigma = 0, D = 0, Q0 = 0, dwell = 0, flyback = 0;
+    int32_t order = 0, stride = 1;
+    uint64_t seed = 0;
+    double keep_fraction = 1.0;
+
+    int64_t n = 0;                       // visits
+    std::vector<int32_t> visit;          // grid index per visit
+    std::vector<double> t_start, tau;    // SI seconds
+    bool uniform = false;                // t_k = k * dwell and tau_k = dwell for all k
+
+    double s = 0, kappa = 0, pref = 0;   // dimensionless Ds, D, and Q0/(4 pi D) [u/m^2]
+    std::vector<double> X, Y, T, TAU;    // dimensionless, visit order
+
+    struct DevCache { int device; double *src; };   // 4n doubles: X | Y | T | TAU
+    mutable std::mutex mu;
+    mutable std::vector<DevCache> dev;
+};
+
+namespace dd {
+
+// Record `msg` as this thread's last error and return `st`.
+dd_status fail(dd_status st, const std::string &msg);
+dd_status fail_cuda(cudaError_t err, const char *what);
+void clear_error();
+
+// Device copy of the scan's dimensionless visit arrays on the current device
+// (created on first use with cudaMalloc, synchronously).  Returns NULL on failure
+// after recording the error in *st.
+const double *device_sources(const dd_scan *scan, dd_status *st);
+
+// True if `p` is device-accessible memory of the current device.
+bool is_device_pointer(const void *p);
+
+}  // namespace dd
+
+#define DD_CUDA_TRY(expr)                                              \
+    do {                                                               \
+        cudaError_t dd_err_ = (expr);                                  \
+        if (dd_err_ != cudaSuccess) return dd::fail_cuda(dd_err_, #expr); \
+    } while (0)

@@ -1,0 +1,276 @@
+// Host runtime: scan construction (visit order and times), validation, error state
+// and the per-device cache of the visit list.
+//
+// Scan strategies follow Sec. 1 of Javadi Rad et al. (raster, alternating,
+// interleaved, random, subsampled); the visit order feeds the cumulative sum of
+// Eq. 5, each visit starting when the previous dwell ends (Sec. 2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+static thread_local std::string g_last_error;
+
+dd_status fail(dd_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+dd_status fail_cuda(cudaError_t err, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+    return DD_ECUDA;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();   // unregistered host memory on old runtimes
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+const double *device_sources(const dd_scan *scan, dd_status *st) {
+    int device = 0;
+    cudaError_t err = cudaGetDevice(&device);
+    if (err != cudaSuccess) { *st = fail_cuda(err, "cudaGetDevice"); return nullptr; }
+    std::lock_guard<std::mutex> lock(scan->mu);
+    for (auto &c : scan->dev)
+        if (c.device == device) return c.src;
+    const size_t n = (size_t)scan->n;
+    std::vector<double> host(4 * n);
+    std::memcpy(host.data(), scan->X.data(), n * sizeof(double));
+    std::memcpy(host.data() + n, scan->Y.data(), n * sizeof(double));
+    std::memcpy(host.data() + 2 * n, scan->T.data(), n * sizeof(double));
+    std::memcpy(host.data() + 3 * n, scan->TAU.data(), n * sizeof(double));
+    double *d = nullptr;
+    err = cudaMalloc(&d, 4 * n * sizeof(double));
+    if (err != cudaSuccess) { *st = fail_cuda(err, "cudaMalloc(scan visit cache)"); cudaGetLastError(); return nullptr; }
+    err = cudaMemcpy(d, host.data(), 4 * n * sizeof(double), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) { cudaFree(d); *st = fail_cuda(err, "cudaMemcpy(scan visit cache)"); return nullptr; }
+    scan->dev.push_back({device, d});
+    return d;
+}
+
+}  // namespace dd
+
+namespace {
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): add the golden-gamma increment,
+// then two xor-shift-multiply rounds and a final xor-shift.
+struct SplitMix64 {
+    uint64_t state;
+    explicit SplitMix64(uint64_t seed) : state(seed) {}
+    uint64_t next() {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+
+// Fisher-Yates from the top; the swap partner of slot i is floor(u (i+1) / 2^64).
+std::vector<int32_t> seeded_permutation(int64_t n, uint64_t seed) {
+    std::vector<int32_t> p((size_t)n);
+    for (int64_t i = 0; i < n; ++i) p[(size_t)i] = (int32_t)i;
+    SplitMix64 rng(seed);
+    for (int64_t i = n - 1; i > 0; --i) {
+        unsigned __int128 prod = (unsigned __int128)rng.next() * (unsigned __int128)(uint64_t)(i + 1);
+        int64_t j = (int64_t)(uint64_t)(prod >> 64);
+        std::swap(p[(size_t)i], p[(size_t)j]);
+    }
+    return p;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *dd_last_error(void) { return dd::g_last_error.c_str(); }
+
+const char *dd_version(void) { return "dd-gb300 0.1 (sm_103a)"; }
+
+dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
+    dd::clear_error();
+    if (!d || !out) return dd::fail(DD_EINVAL, "dd_create_scan: NULL argument");
+    if (d->nx < 1 || d->ny < 1 || (int64_t)d->nx * d->ny > (int64_t(1) << 26))
+        return dd::fail(DD_EINVAL, "dd_create_scan: grid must be >= 1x1 and at most 2^26 positions");
+    if (!finite_pos(d->pitch_m) || !finite_pos(d->sigma_m) || !finite_pos(d->D_m2s) ||
+        !finite_pos(d->dwell_s) || !std::isfinite(d->Q0))
+        return dd::fail(DD_EINVAL, "dd_create_scan: pitch, sigma, D, dwell must be finite and > 0; Q0 finite");
+    if (!std::isfinite(d->flyback_s) || d->flyback_s < 0.0)
+        return dd::fail(DD_EINVAL, "dd_create_scan: flyback must be finite and >= 0");
+    if (d->order < DD_RASTER || d->order > DD_CUSTOM)
+        return dd::fail(DD_EINVAL, "dd_create_scan: unknown order");
+    if (d->flyback_s != 0.0 && d->order != DD_RASTER && d->order != DD_SERPENTINE)
+        return dd::fail(DD_EINVAL, "dd_create_scan: flyback applies to raster and serpentine scans only");
+    if (d->order == DD_INTERLEAVED && d->interleave_stride < 1)
+        return dd::fail(DD_EINVAL, "dd_create_scan: interleave stride must be >= 1");
+    if (!(d->keep_fraction > 0.0 && d->keep_fraction <= 1.0))
+        return dd::fail(DD_EINVAL, "dd_create_scan: keep_fraction must be in (0, 1]");
+    if (d->mask && (d->keep_fraction < 1.0 || d->order == DD_CUSTOM))
+        return dd::fail(DD_EINVAL, "dd_create_scan: a mask cannot be combined with keep_fraction < 1 or a custom order");
+    if (d->order == DD_CUSTOM && (!d->custom_visit || d->n_custom < 1))
+        return dd::fail(DD_EINVAL, "dd_create_scan: custom order needs custom_visit and n_custom >= 1");
+    if (d->order == DD_CUSTOM && d->keep_fraction < 1.0)
+        return dd::fail(DD_EINVAL, "dd_create_scan: keep_fraction < 1 cannot be combined with a custom order");
+
+    const int64_t nx = d->nx, ny = d->ny, ngrid = nx * ny;
+    dd_scan *s = new (std::nothrow) dd_scan();
+    if (!s) return dd::fail(DD_ENOMEM, "dd_create_scan: out of host memory");
+    try {
+        std::vector<int32_t> seq;
+        switch (d->order) {
+        case DD_RASTER:
+            seq.resize((size_t)ngrid);
+            for (int64_t g = 0; g < ngrid; ++g) seq[(size_t)g] = (int32_t)g;
+            break;
+        case DD_SERPENTINE:
+            seq.reserve((size_t)ngrid);
+            for (int64_t iy = 0; iy < ny; ++iy)
+                for (int64_t k = 0; k < nx; ++k)
+                    seq.push_back((int32_t)(iy * nx + ((iy & 1) ? nx - 1 - k : k)));
+            break;
+        case DD_INTERLEAVED: {
+            const int64_t S = d->interleave_stride;
+            seq.reserve((size_t)ngrid);
+            for (int64_t py = 0; py < S; ++py)
+                for (int64_t px = 0; px < S; ++px)
+                    for (int64_t iy = py; iy < ny; iy += S)
+                        for (int64_t ix = px; ix < nx; ix += S)
+                            seq.push_back((int32_t)(iy * nx + ix));
+            break;
+        }
+        case DD_RANDOM:
+            seq = seeded_permutation(ngrid, d->seed);
+            break;
+        case DD_CUSTOM:
+            seq.assign(d->custom_visit, d->custom_visit + d->n_custom);
+            for (int32_t g : seq)
+                if (g < 0 || g >= ngrid) {
+                    delete s;
+                    return dd::fail(DD_EINVAL, "dd_create_scan: custom_visit index outside the grid");
+                }
+            break;
+        }
+        if (d->mask) {
+            std::vector<int32_t> kept;
+            kept.reserve(seq.size());
+            for (int32_t g : seq)
+                if (d->mask[g]) kept.push_back(g);
+            seq.swap(kept);
+        }
+        if (d->keep_fraction < 1.0) {
+            int64_t k = (int64_t)std::floor(d->keep_fraction * (double)ngrid + 0.5);
+            if (k < 1) k = 1;
+            std::vector<int32_t> perm = seeded_permutation(ngrid, d->seed);
+            if (d->order == DD_RANDOM) {
+                seq.assign(perm.begin(), perm.begin() + k);
+            } else {
+                std::vector<uint8_t> keep((size_t)ngrid, 0);
+                for (int64_t i = 0; i < k; ++i) keep[(size_t)perm[(size_t)i]] = 1;
+                std::vector<int32_t> kept;
+                kept.reserve((size_t)k);
+                for (int32_t g : seq)
+                    if (keep[(size_t)g]) kept.push_back(g);
+                seq.swap(kept);
+            }
+        }
+        if (seq.empty()) {
+            delete s;
+            return dd::fail(DD_EINVAL, "dd_create_scan: the scan visits no position");
+        }
+        const int64_t n = (int64_t)seq.size();
+        s->nx = d->nx; s->ny = d->ny; s->pitch = d->pitch_m; s->sigma = d->sigma_m;
+        s->D = d->D_m2s; s->Q0 = d->Q0; s->dwell = d->dwell_s; s->flyback = d->flyback_s;
+        s->order = d->order; s->stride = d->interleave_stride; s->seed = d->seed;
+        s->keep_fraction = d->keep_fraction;
+        s->n = n;
+        s->visit = seq;
+        s->t_start.resize((size_t)n);
+        s->tau.resize((size_t)n);
+        if (d->dwell_per_visit) {
+            for (int64_t k = 0; k < n; ++k) {
+                double tk = d->dwell_per_visit[k];
+                if (!finite_pos(tk)) {
+                    delete s;
+                    return dd::fail(DD_EINVAL, "dd_create_scan: dwell_per_visit entries must be finite and > 0");
+                }
+                s->tau[(size_t)k] = tk;
+            }
+        } else {
+            for (int64_t k = 0; k < n; ++k) s->tau[(size_t)k] = d->dwell_s;
+        }
+        s->uniform = !d->dwell_per_visit && d->flyback_s == 0.0;
+        if (s->uniform) {
+            for (int64_t k = 0; k < n; ++k) s->t_start[(size_t)k] = (double)k * d->dwell_s;
+        } else {
+            double t = 0.0;
+            for (int64_t k = 0; k < n; ++k) {
+                s->t_start[(size_t)k] = t;
+                t = t + s->tau[(size_t)k];
+                if (d->flyback_s != 0.0 && k + 1 < n && seq[(size_t)k] / nx != seq[(size_t)k + 1] / nx)
+                    t = t + d->flyback_s;
+            }
+        }
+        // dimensionless form
+        const double p = d->pitch_m, tref = d->dwell_s;
+        s->s = (d->sigma_m / p) * (d->sigma_m / p);
+        s->kappa = d->D_m2s * tref / (p * p);
+        s->pref = d->Q0 / (4.0 * 3.14159265358979323846 * d->D_m2s);
+        s->X.resize((size_t)n); s->Y.resize((size_t)n); s->T.resize((size_t)n); s->TAU.resize((size_t)n);
+        for (int64_t k = 0; k < n; ++k) {
+            const int32_t g = seq[(size_t)k];
+            s->X[(size_t)k] = (double)(g % nx);
+            s->Y[(size_t)k] = (double)(g / nx);
+            s->T[(size_t)k] = s->uniform ? (double)k : s->t_start[(size_t)k] / tref;
+            s->TAU[(size_t)k] = s->uniform ? 1.0 : s->tau[(size_t)k] / tref;
+        }
+    } catch (const std::bad_alloc &) {
+        delete s;
+        return dd::fail(DD_ENOMEM, "dd_create_scan: out of host memory");
+    }
+    *out = s;
+    return DD_OK;
+}
+
+dd_status dd_scan_size(const dd_scan *scan, int64_t *n_visits) {
+    dd::clear_error();
+    if (!scan || !n_visits) return dd::fail(DD_EINVAL, "dd_scan_size: NULL argument");
+    *n_visits = scan->n;
+    return DD_OK;
+}
+
+dd_status dd_scan_visits(const dd_scan *scan, int32_t *grid_index, double *t_start_s, double *dwell_s) {
+    dd::clear_error();
+    if (!scan) return dd::fail(DD_EINVAL, "dd_scan_visits: NULL scan");
+    const size_t n = (size_t)scan->n;
+    if (grid_index) std::memcpy(grid_index, scan->visit.data(), n * sizeof(int32_t));
+    if (t_start_s) std::memcpy(t_start_s, scan->t_start.data(), n * sizeof(double));
+    if (dwell_s) std::memcpy(dwell_s, scan->tau.data(), n * sizeof(double));
+    return DD_OK;
+}
+
+void dd_destroy(dd_scan *scan) {
+    if (!scan) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    for (auto &c : scan->dev) {
+        if (cudaSetDevice(c.device) == cudaSuccess) cudaFree(c.src);
+    }
+    if (!scan->dev.empty() && prev >= 0) cudaSetDevice(prev);
+    cudaGetLastError();
+    delete scan;
+}
+
+}  // extern "C"

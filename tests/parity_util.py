@@ -1,0 +1,63 @@
+"""Helpers for the GPU-vs-oracle parity tests (inputs come from workloads.py; expected
+values only from oracle/)."""
+import numpy as np
+
+import oracle
+from oracle import scan as oscan
+
+FP64_RTOL = 1e-12          # GPU FP64 vs oracle, every point with |psi| >= 1e-290
+MIXED_RTOL = 1e-5          # GPU FP32-mixed vs oracle where psi >= 1e-6 of the map's peak
+
+
+def oracle_sources(spec):
+    xs, ys, ts, taus, _ = oscan.sources(
+        spec.nx, spec.ny, spec.pitch_m, spec.dwell_s, order=spec.order,
+        stride=spec.interleave_stride, seed=spec.seed, keep_fraction=spec.keep_fraction,
+        mask=spec.mask, custom=spec.custom_visit, flyback=spec.flyback_s,
+        dwell_per_visit=spec.dwell_per_visit)
+    return oracle.Sources(xs, ys, ts, taus)
+
+
+def oracle_field(spec, pts, times):
+    return oracle.field(oracle_sources(spec), spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
+                        pts[:, 0], pts[:, 1], times)
+
+
+def oracle_pairs(spec, pts, times, ip, it):
+    return oracle.field_pairs(oracle_sources(spec), spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
+                              pts[ip, 0], pts[ip, 1], times[it])
+
+
+def peak_lower_bound(spec, times):
+    """Oracle field at the probe visited last before each time: <= that map's peak."""
+    src = oracle_sources(spec)
+    idx = np.clip(np.searchsorted(src.ts, times, side="left") - 1, 0, src.n - 1)
+    return oracle.field_pairs(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
+                              src.xs[idx], src.ys[idx], times)
+
+
+def assert_fp64(got, ref, what=""):
+    got = np.asarray(got); ref = np.asarray(ref)
+    assert got.shape == ref.shape
+    zero = ref == 0.0
+    assert np.all(got[zero] == 0.0), what + ": nonzero where the oracle is exactly 0"
+    m = np.abs(ref) >= 1e-290
+    rel = np.abs(got[m] - ref[m]) / np.abs(ref[m])
+    worst = rel.max() if rel.size else 0.0
+    assert worst <= FP64_RTOL, "%s: FP64 max rel err %.3e" % (what, worst)
+    return worst
+
+
+def assert_mixed(got, ref, peak, what=""):
+    """peak: per-row (snapshot) peak or a lower bound of it, shape [n_t] or scalar."""
+    got = np.asarray(got); ref = np.asarray(ref)
+    thr = 1e-6 * np.asarray(peak)
+    if ref.ndim == 2:
+        thr = np.broadcast_to(np.reshape(thr, (-1, 1)), ref.shape)
+    assert np.all(got[ref == 0.0] == 0.0), what + ": nonzero where the oracle is exactly 0"
+    m = (ref >= thr) & (ref > 0.0)
+    assert m.sum() > 0
+    rel = np.abs(got[m] - ref[m]) / ref[m]
+    worst = rel.max()
+    assert worst <= MIXED_RTOL, "%s: mixed max rel err %.3e (median %.3e)" % (what, worst, np.median(rel))
+    return worst

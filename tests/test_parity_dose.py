@@ -1,0 +1,46 @@
+"""GPU dwell-start dose (dd_per_probe_dose) against the CPU oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_00294_gb300 import binding as b
+from paper_2507_00294_gb300 import workloads as w
+from parity_util import assert_fp64, assert_mixed, oracle_sources
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_dose(spec, prec):
+    import torch
+    scan = b.Scan(spec)
+    out = b.dd_per_probe_dose(scan, prec, device="cuda")
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("spec", [w.ScanSpec(16, 16), w.ScanSpec(64, 64),
+                                  w.ScanSpec(23, 19, order=w.RANDOM, seed=8, keep_fraction=0.7),
+                                  w.ScanSpec(1, 1), w.ScanSpec(2, 1)])
+def test_dose_full(cuda, spec):
+    src = oracle_sources(spec)
+    ref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0)
+    g64 = gpu_dose(spec, "fp64")
+    assert g64[0] == 0.0
+    assert_fp64(g64, ref, "dose fp64")
+    gm = gpu_dose(spec, "mixed")
+    if len(ref) > 1:
+        assert_mixed(gm[1:], ref[1:], ref.max(), "dose mixed")
+
+
+def test_dose_grid256_sampled(cuda):
+    job = w.precision_study(w.INTERLEAVED, 0)
+    spec = job.scan
+    rng = np.random.default_rng(31)
+    targets = np.sort(rng.choice(np.arange(1, 256 * 256), 128, replace=False))
+    targets = np.concatenate([[1, 2, 255, 256, 65535], targets])
+    src = oracle_sources(spec)
+    ref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0, targets=targets)
+    g64 = gpu_dose(spec, "fp64")
+    assert_fp64(g64[targets], ref, "dose256 fp64")
+    gm = gpu_dose(spec, "mixed")
+    assert_mixed(gm[targets], ref, ref.max(), "dose256 mixed")

@@ -1,0 +1,98 @@
+"""GPU field (dd_field_at_times, Eq. 5) against the CPU oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+from paper_2507_00294_gb300 import binding as b
+from paper_2507_00294_gb300 import workloads as w
+from parity_util import (assert_fp64, assert_mixed, oracle_field, oracle_pairs,
+                         peak_lower_bound)
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_field(spec, pts, times, prec, device=True):
+    import torch
+    scan = b.Scan(spec)
+    if device:
+        p = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+        out = b.dd_field_at_times(scan, p, np.asarray(times), prec)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    return b.dd_field_at_times(scan, np.ascontiguousarray(pts), np.asarray(times), prec)
+
+
+def test_raster16_every_dwell_full(cuda):
+    job = w.small_raster_16()
+    ref = oracle_field(job.scan, job.pts_xy, job.times)
+    g64 = gpu_field(job.scan, job.pts_xy, job.times, "fp64")
+    assert_fp64(g64, ref, "raster16 fp64")
+    gm = gpu_field(job.scan, job.pts_xy, job.times, "mixed")
+    assert_mixed(gm, ref, ref.max(axis=1), "raster16 mixed")
+
+
+def test_raster64_supersampled_sampled_pairs(cuda):
+    job = w.raster_64_supersampled()
+    ip, it = w.sample_pairs(len(job.pts_xy), len(job.times), 4096, seed=2)
+    ref = oracle_pairs(job.scan, job.pts_xy, job.times, ip, it)
+    peak = peak_lower_bound(job.scan, job.times)
+    g64 = gpu_field(job.scan, job.pts_xy, job.times, "fp64")
+    assert_fp64(g64[it, ip], ref, "raster64 fp64")
+    gm = gpu_field(job.scan, job.pts_xy, job.times, "mixed")
+    assert_mixed(gm[it, ip], ref, peak[it], "raster64 mixed")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ragged_unsorted_times_and_orders(cuda, prec):
+    rng = np.random.default_rng(17)
+    spec = w.ScanSpec(9, 7, order=w.SERPENTINE, keep_fraction=0.6, seed=4)
+    nv = w.n_visits(spec)
+    pts = np.column_stack([rng.uniform(-2e-9, 6e-9, 1000), rng.uniform(-1e-9, 4e-9, 1000)])
+    pts[:5] = [[0, 0], [0.5e-9, 0], [1e-9, 1e-9], [4e-9, 3e-9], [2.5e-9, 0.5e-9]]
+    # unsorted, before the scan, exactly at visit starts, mid-dwell, long after
+    times = np.array([7.5e-6, 0.0, -1e-6, 3e-6, (nv - 1) * 1e-6, 0.5e-6, 40 * nv * 1e-6])
+    ref = oracle_field(spec, pts, times)
+    got = gpu_field(spec, pts, times, prec)
+    assert np.all(got[[1, 2]] == 0.0)           # no visit has started
+    if prec == "fp64":
+        assert_fp64(got, ref, "ragged fp64")
+    else:
+        assert_mixed(got, ref, ref.max(axis=1), "ragged mixed")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_interleaved_random_flyback_dwell_and_extreme_D(cuda, prec):
+    rng = np.random.default_rng(5)
+    specs = [
+        w.ScanSpec(12, 12, order=w.INTERLEAVED, interleave_stride=4, D_m2s=1e-12),
+        w.ScanSpec(12, 12, order=w.RANDOM, seed=77, D_m2s=1e-15, sigma_m=0.2e-9),
+        w.ScanSpec(10, 8, order=w.RASTER, flyback_s=2.5e-6, D_m2s=3e-14),
+        w.ScanSpec(8, 8, order=w.RANDOM, seed=3, dwell_per_visit=10 ** rng.uniform(-7, -5, 64),
+                   sigma_m=0.05e-9),
+    ]
+    for spec in specs:
+        pts = w.grid_points(2 * spec.nx, spec.pitch_m / 2)
+        _, ts, taus = b.Scan(spec).visits()
+        end = ts[-1] + taus[-1]
+        times = np.array([0.3 * end, end, 1.0001 * end, 25 * end])
+        ref = oracle_field(spec, pts, times)
+        got = gpu_field(spec, pts, times, prec)
+        if prec == "fp64":
+            assert_fp64(got, ref, "orders fp64 D=%g" % spec.D_m2s)
+        else:
+            assert_mixed(got, ref, ref.max(axis=1), "orders mixed D=%g" % spec.D_m2s)
+
+
+def test_host_and_device_buffers_agree(cuda):
+    job = w.small_raster_16()
+    times = job.times[::17]
+    for prec in ("fp64", "mixed"):
+        host = gpu_field(job.scan, job.pts_xy, times, prec, device=False)
+        dev = gpu_field(job.scan, job.pts_xy, times, prec, device=True)
+        np.testing.assert_array_equal(host, dev)
+
+
+def test_deterministic_repeat(cuda):
+    job = w.raster_64_supersampled()
+    a = gpu_field(job.scan, job.pts_xy, job.times[-4:], "mixed")
+    c = gpu_field(job.scan, job.pts_xy, job.times[-4:], "mixed")
+    np.testing.assert_array_equal(a, c)
