@@ -139,12 +139,46 @@ dd_status dd_field_batch(const dd_scan *const *scans, int32_t n_scans, const int
                          const double *pts_xy_m, const double *times_s, dd_precision prec,
                          double *out, void *cuda_stream);
 
+/* Reusable plan of a batch (same arguments as dd_field_batch without the buffers):
+   validates, builds the cost-sorted work list, uploads the tables and allocates its
+   device buffers (cudaMalloc; synchronous).  The scans must outlive the plan.
+   dd_batch_run evaluates it: the launch sequence is captured into a CUDA graph on
+   the first run (and again when the point/output pointers or the kernel variant
+   change) and replayed with cudaGraphLaunch on `cuda_stream`; with device buffers the
+   call only enqueues.  pts_xy_m/out: host or device, as in dd_field_batch.
+   dd_batch_tune times each kernel variant once on device points pts_xy_m, keeps the
+   fastest for this plan and records it for (GPU, precision, batch size) in-process and
+   in the JSON file named by the environment variable DD_TUNE_CACHE, if set; plans
+   created later with the same key start from the recorded variant.
+   dd_batch_info: work items, causal pair-terms per run and the kernel variant.
+   dd_batch_destroy synchronises the device and frees the plan (NULL is a no-op). */
+typedef struct dd_batch dd_batch;
+dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
+                          const double *times_s, dd_precision prec, dd_batch **out);
+dd_status dd_batch_run(dd_batch *batch, const double *pts_xy_m, double *out, void *cuda_stream);
+dd_status dd_batch_tune(dd_batch *batch, const double *pts_xy_m, int32_t *chosen_variant);
+dd_status dd_batch_info(const dd_batch *batch, int64_t *n_items, int64_t *pair_terms,
+                        int32_t *variant);
+void dd_batch_destroy(dd_batch *batch);
+
 /* Free a scan and its per-device caches (device caches are freed on their own
    devices).  NULL is a no-op.  The scan must not be in use by an enqueued call. */
 void dd_destroy(dd_scan *scan);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *dd_last_error(void);
+
+/* Tracing (no counterpart in the paper): per-kernel device time of this library's
+   own launches.  While enabled, each launch is bracketed by two CUDA events on its
+   stream (do not enable it while a stream is being captured into a graph).
+   dd_profile_read waits for the recorded events and fills up to max_entries rows:
+   names[64*k] is the NUL-terminated kernel name (at most 63 chars), launches[k]
+   the count and total_ms[k] the summed device time since the last reset;
+   *n_entries receives the number of distinct kernels.  Host pointers. */
+dd_status dd_profile_enable(int32_t on);
+dd_status dd_profile_reset(void);
+dd_status dd_profile_read(char *names, int64_t *launches, double *total_ms, int32_t max_entries,
+                          int32_t *n_entries);
 
 /* Library version string. */
 const char *dd_version(void);

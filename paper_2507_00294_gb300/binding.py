@@ -61,6 +61,19 @@ def load(build_if_missing=True):
     lib.dd_field_at_times.argtypes = [_VP, _VP, _I64, _VP, _I64, ctypes.c_int, _VP, _VP]
     lib.dd_per_probe_dose.argtypes = [_VP, ctypes.c_int, _VP, _VP]
     lib.dd_field_batch.argtypes = [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
+    lib.dd_batch_create.argtypes = [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)]
+    lib.dd_batch_run.argtypes = [_VP, _VP, _VP, _VP]
+    lib.dd_batch_tune.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32)]
+    lib.dd_batch_info.argtypes = [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)]
+    for name in ("dd_batch_create", "dd_batch_run", "dd_batch_tune", "dd_batch_info"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.dd_batch_destroy.argtypes = [_VP]
+    lib.dd_batch_destroy.restype = None
+    lib.dd_profile_enable.argtypes = [ctypes.c_int32]
+    lib.dd_profile_reset.argtypes = []
+    lib.dd_profile_read.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    for name in ("dd_profile_enable", "dd_profile_reset", "dd_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.dd_destroy.argtypes = [_VP]
     lib.dd_destroy.restype = None
     lib.dd_last_error.restype = ctypes.c_char_p
@@ -216,6 +229,78 @@ def dd_field_batch(scans, pt_offsets, pts_xy_m, times_s, prec="mixed", out=None,
     st = load().dd_field_batch(handles, n_scans, offs.ctypes.data, p, times.ctypes.data,
                                PRECISIONS[prec], o, _stream(stream, pts_xy_m, out))
     _check(st, "dd_field_batch")
+    return out
+
+
+class Batch:
+    """A dd_batch plan: many scans, each at its own points and one time, one graph launch."""
+
+    def __init__(self, scans, pt_offsets, times_s, prec="mixed"):
+        lib = load()
+        self.scans = list(scans)                  # the plan reads them: keep them alive
+        n = len(self.scans)
+        self._handles = (ctypes.c_void_p * n)(*[s.handle.value for s in self.scans])
+        self.offsets = np.ascontiguousarray(np.asarray(pt_offsets, dtype=np.int64))
+        times = np.ascontiguousarray(np.asarray(times_s, dtype=np.float64))
+        h = ctypes.c_void_p()
+        _check(lib.dd_batch_create(self._handles, n, self.offsets.ctypes.data, times.ctypes.data,
+                                   PRECISIONS[prec], ctypes.byref(h)), "dd_batch_create")
+        self.handle = h
+        self.total = int(self.offsets[-1])
+
+    def run(self, pts_xy_m, out=None, stream=None):
+        if out is None:
+            if _is_torch(pts_xy_m) and pts_xy_m.is_cuda:
+                import torch
+                out = torch.empty(self.total, dtype=torch.float64, device=pts_xy_m.device)
+            else:
+                out = np.empty(self.total, dtype=np.float64)
+        p, kp = _ptr(pts_xy_m, np.float64)
+        o, ko = _ptr(out, np.float64)
+        _check(load().dd_batch_run(self.handle, p, o, _stream(stream, pts_xy_m, out)), "dd_batch_run")
+        return out
+
+    def tune(self, pts_xy_m):
+        p, kp = _ptr(pts_xy_m, np.float64)
+        v = ctypes.c_int32()
+        _check(load().dd_batch_tune(self.handle, p, ctypes.byref(v)), "dd_batch_tune")
+        return v.value
+
+    def info(self):
+        n, pairs, v = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(load().dd_batch_info(self.handle, ctypes.byref(n), ctypes.byref(pairs), ctypes.byref(v)),
+               "dd_batch_info")
+        return {"items": n.value, "pairs": pairs.value, "variant": v.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def dd_profile_enable(on=True):
+    _check(load().dd_profile_enable(1 if on else 0), "dd_profile_enable")
+
+
+def dd_profile_reset():
+    _check(load().dd_profile_reset(), "dd_profile_reset")
+
+
+def dd_profile_read(max_entries=64):
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    names = ctypes.create_string_buffer(64 * max_entries)
+    launches = np.zeros(max_entries, np.int64)
+    ms = np.zeros(max_entries, np.float64)
+    n = ctypes.c_int32()
+    _check(load().dd_profile_read(names, launches.ctypes.data, ms.ctypes.data, max_entries,
+                                  ctypes.byref(n)), "dd_profile_read")
+    out = {}
+    for k in range(min(n.value, max_entries)):
+        nm = names.raw[64 * k:64 * k + 64].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[k]), float(ms[k]))
     return out
 
 

@@ -1,11 +1,477 @@
-// dd_batch.cu -- many scans in one launch (placeholder until the persistent kernel lands).
+// dd_batch.cu -- many independent scans in one persistent, graph-captured launch.
+//
+// The paper balances its CPU tasks over subsets of the probe positions (Sec. 3); on the
+// GPU the same idea spans scans: every (scan, point tile, visit block) is one work item,
+// the items of all scans are sorted by cost (longest first) and a persistent grid of
+// CTAs claims them with an atomic counter, so scans of very different size share the
+// machine without a tail.  Each scan is evaluated at one snapshot time.  The launch
+// sequence (counter reset, point scaling, coefficients, persistent field kernel,
+// fixed-order reduce) is captured once into a CUDA graph and replayed.
+//
+// A tile-shape autotuner picks, per (GPU, precision, batch size), the fastest of
+// several kernel variants that share the same work list (same tile size, different
+// threads x points-per-thread) by timing each once; choices are cached in-process and,
+// when DD_TUNE_CACHE names a file, in that JSON file.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "dd_coef.cuh"
+#include "dd_e1.cuh"
+#include "dd_field_impl.cuh"
 #include "dd_internal.h"
 
-extern "C" dd_status dd_field_batch(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
-                                    const double *pts_xy_m, const double *times_s, dd_precision prec,
-                                    double *out, void *cuda_stream) {
-    (void)scans; (void)n_scans; (void)pt_offsets; (void)pts_xy_m; (void)times_s; (void)prec; (void)out;
-    (void)cuda_stream;
-    dd::clear_error();
-    return dd::fail(DD_ENOTSUP, "dd_field_batch: not built yet");
+namespace ddk {
+
+struct BScan {
+    const double *src;          // X | Y | T | TAU of the scan, n each (dimensionless)
+    int64_t n;                  // visits
+    int64_t pt_off, n_pts;      // points of the scan in the global arrays
+    int64_t rec_off;            // first record of the scan
+    int64_t part_off;           // first partial of the scan (nblk * n_pts of them)
+    double s, kappa, pref, tdim, inv_pitch;
+    int nact, nblk;
+};
+
+__device__ __forceinline__ int find_segment(const int64_t *__restrict__ offs, int n, int64_t g) {
+    int lo = 0, hi = n - 1;                     // largest k with offs[k] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
+
+__global__ void batch_prep_kernel(const BScan *__restrict__ sc, const int64_t *__restrict__ pt_offs, int n_scans,
+                                  const double *__restrict__ xy, int64_t total, double *__restrict__ X,
+                                  double *__restrict__ Y) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const double ip = sc[find_segment(pt_offs, n_scans, g)].inv_pitch;
+    X[g] = xy[2 * g] * ip;
+    Y[g] = xy[2 * g + 1] * ip;
+}
+
+template <typename Rec>
+__global__ void batch_coef_kernel(const BScan *__restrict__ sc, const int64_t *__restrict__ rec_offs, int n_scans,
+                                  int64_t total, Rec *__restrict__ rec) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const BScan &S = sc[find_segment(rec_offs, n_scans, g)];
+    const int64_t i = g - S.rec_off;
+    if (i >= S.nact) return;
+    double q1, dq, r, ell;
+    pair_geometry(S.tdim - S.src[2 * S.n + i], S.src[3 * S.n + i], S.s, S.kappa, q1, dq, r, ell);
+    Rec out;
+    RecTraits<Rec>::fill(out, q1, dq, r, ell);
+    rec[g] = out;
+}
+
+// Persistent CTAs: claim item indices from *counter until the list is exhausted.
+template <typename Cfg>
+__global__ void __launch_bounds__(Cfg::kThreads)
+batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items, int n_items,
+                   unsigned *__restrict__ counter, const double *__restrict__ X, const double *__restrict__ Y,
+                   const typename Cfg::Rec *__restrict__ rec, int sb, double *__restrict__ partial) {
+    __shared__ TileSmem<Cfg, 1> sm;
+    __shared__ int s_item;
+    constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const int4 item = items[it];
+        const BScan &S = sc[item.x];
+        const int na[1] = {S.nact};
+        const int s_begin = item.z * sb;
+        const int s_end = min(s_begin + sb, S.nact);
+        field_tile<Cfg, 1>(sm, S.src, S.src + S.n, X + S.pt_off, Y + S.pt_off, S.n_pts, (int64_t)item.y * TILE,
+                           rec + S.rec_off, 0, na, 1, s_begin, s_end,
+                           partial + S.part_off + (int64_t)item.z * S.n_pts, S.n_pts);
+    }
+}
+
+__global__ void batch_reduce_kernel(const BScan *__restrict__ sc, const int64_t *__restrict__ pt_offs, int n_scans,
+                                    int64_t total, const double *__restrict__ partial, double *__restrict__ out) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const BScan &S = sc[find_segment(pt_offs, n_scans, g)];
+    const int64_t p = g - S.pt_off;
+    double acc = 0.0;
+    for (int b = 0; b < S.nblk; ++b) acc += partial[S.part_off + (int64_t)b * S.n_pts + p];
+    out[g] = S.pref * acc;
+}
+
+// Kernel variants with the same 512-point tile (so they share one work list).
+struct CfgMixed256 : CfgMixed {
+    static constexpr int kThreads = 256, kPPT = 2;
+};
+struct CfgMixed64 : CfgMixed {
+    static constexpr int kThreads = 64, kPPT = 8;
+};
+struct CfgF64x256 : CfgF64 {
+    static constexpr int kThreads = 256, kPPT = 1;
+};
+
+}  // namespace ddk
+
+// =================================================================== plan object
+struct dd_batch {
+    int device = 0;
+    dd_precision prec = DD_MIXED;
+    int n_scans = 0;
+    int64_t total_pts = 0, total_rec = 0, total_part = 0, pairs = 0;
+    int n_items = 0, sb = 512;
+    int variant = 0;
+    std::vector<int> grid;              // persistent grid size per variant
+    void *ws = nullptr;                 // device tables and buffers (cudaMalloc)
+    ddk::BScan *d_sc = nullptr;
+    int64_t *d_pt_offs = nullptr, *d_rec_offs = nullptr;
+    int4 *d_items = nullptr;
+    unsigned *d_counter = nullptr;
+    double *d_X = nullptr, *d_Y = nullptr, *d_part = nullptr;
+    void *d_rec = nullptr;
+    double *d_pts = nullptr, *d_out = nullptr;   // staging for host buffers
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const double *g_pts = nullptr;
+    double *g_out = nullptr;
+    int g_variant = -1;
+    std::string tune_key;
+};
+
+namespace {
+
+constexpr int kTile = 512;
+constexpr int kVariants = 3;
+
+const char *variant_name(dd_precision prec, int v) {
+    static const char *mixed[kVariants] = {"batch_field_mixed_128x4", "batch_field_mixed_256x2", "batch_field_mixed_64x8"};
+    static const char *f64[kVariants] = {"batch_field_fp64_128x4", "batch_field_fp64_256x2", "batch_field_fp64_64x8"};
+    return prec == DD_MIXED ? mixed[v] : f64[v];
+}
+
+template <typename Cfg>
+int persistent_grid() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ddk::batch_field_kernel<Cfg>, Cfg::kThreads, 0);
+    return std::max(1, sms * std::max(1, per));
+}
+
+template <typename Cfg>
+void launch_field(dd_batch *b, int grid, cudaStream_t st) {
+    ddk::batch_field_kernel<Cfg><<<grid, Cfg::kThreads, 0, st>>>(
+        b->d_sc, b->d_items, b->n_items, b->d_counter, b->d_X, b->d_Y,
+        (const typename Cfg::Rec *)b->d_rec, b->sb, b->d_part);
+}
+
+// Enqueue the whole batch evaluation on `st` (used for capture and for tuning).
+dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cudaStream_t st) {
+    const unsigned nb_pts = (unsigned)((b->total_pts + 255) / 256);
+    DD_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st));
+    ddk::batch_prep_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, pts, b->total_pts, b->d_X, b->d_Y);
+    if (b->total_rec > 0) {
+        const unsigned nb = (unsigned)((b->total_rec + 127) / 128);
+        if (b->prec == DD_MIXED)
+            ddk::batch_coef_kernel<ddk::RecF32><<<nb, 128, 0, st>>>(b->d_sc, b->d_rec_offs, b->n_scans, b->total_rec,
+                                                                  (ddk::RecF32 *)b->d_rec);
+        else
+            ddk::batch_coef_kernel<ddk::RecF64><<<nb, 128, 0, st>>>(b->d_sc, b->d_rec_offs, b->n_scans, b->total_rec,
+                                                                  (ddk::RecF64 *)b->d_rec);
+    }
+    if (b->n_items > 0) {
+        const int g = b->grid[variant];
+        if (b->prec == DD_MIXED) {
+            if (variant == 0) launch_field<ddk::CfgMixed>(b, g, st);
+            else if (variant == 1) launch_field<ddk::CfgMixed256>(b, g, st);
+            else launch_field<ddk::CfgMixed64>(b, g, st);
+        } else {
+            if (variant == 0) launch_field<ddk::CfgF64>(b, g, st);   // 128 x 2 (256-point tile)
+            else if (variant == 1) launch_field<ddk::CfgF64x256>(b, g, st);
+            else launch_field<ddk::CfgF64>(b, g, st);
+        }
+    }
+    ddk::batch_reduce_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, b->total_pts, b->d_part, out);
+    DD_CUDA_TRY(cudaGetLastError());
+    return DD_OK;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+
+void tune_cache_load() {
+    static bool loaded = false;
+    if (loaded) return;
+    loaded = true;
+    const char *path = std::getenv("DD_TUNE_CACHE");
+    if (!path) return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {      // one "key": variant pair per line
+        const size_t a = line.find('"'), b = line.find('"', a + 1), c = line.find(':', b);
+        if (a == std::string::npos || b == std::string::npos || c == std::string::npos) continue;
+        g_tune[line.substr(a + 1, b - a - 1)] = std::atoi(line.c_str() + c + 1);
+    }
+}
+
+void tune_cache_store() {
+    const char *path = std::getenv("DD_TUNE_CACHE");
+    if (!path) return;
+    std::ofstream f(path);
+    f << "{\n";
+    size_t k = 0;
+    for (auto &kv : g_tune) f << "  \"" << kv.first << "\": " << kv.second << (++k < g_tune.size() ? ",\n" : "\n");
+    f << "}\n";
+}
+
+}  // namespace
+
+extern "C" {
+
+dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
+                          const double *times_s, dd_precision prec, dd_batch **out) {
+    dd::clear_error();
+    if (!scans || !pt_offsets || !times_s || !out || n_scans < 1)
+        return dd::fail(DD_EINVAL, "dd_batch_create: NULL argument or no scans");
+    if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_batch_create: unknown precision");
+    if (pt_offsets[0] != 0) return dd::fail(DD_EINVAL, "dd_batch_create: pt_offsets[0] must be 0");
+    for (int k = 0; k < n_scans; ++k) {
+        if (!scans[k]) return dd::fail(DD_EINVAL, "dd_batch_create: NULL scan");
+        if (pt_offsets[k + 1] < pt_offsets[k]) return dd::fail(DD_EINVAL, "dd_batch_create: pt_offsets must not decrease");
+        if (!std::isfinite(times_s[k])) return dd::fail(DD_EINVAL, "dd_batch_create: non-finite time");
+    }
+    std::unique_ptr<dd_batch> b(new dd_batch());
+    b->prec = prec;
+    b->n_scans = n_scans;
+    DD_CUDA_TRY(cudaGetDevice(&b->device));
+    const int tile = prec == DD_MIXED ? kTile : ddk::CfgF64::kThreads * ddk::CfgF64::kPPT;
+    std::vector<ddk::BScan> sc((size_t)n_scans);
+    std::vector<int64_t> pt_offs((size_t)n_scans), rec_offs((size_t)n_scans);
+    std::vector<std::pair<int64_t, int4>> items;
+    int64_t rec = 0, part = 0;
+    for (int k = 0; k < n_scans; ++k) {
+        const dd_scan *s = scans[k];
+        dd_status st = DD_OK;
+        const double *src = dd::device_sources(s, &st);
+        if (!src) return st;
+        ddk::BScan &S = sc[(size_t)k];
+        S.src = src;
+        S.n = s->n;
+        S.pt_off = pt_offsets[k];
+        S.n_pts = pt_offsets[k + 1] - pt_offsets[k];
+        S.s = s->s; S.kappa = s->kappa; S.pref = s->pref; S.inv_pitch = 1.0 / s->pitch;
+        S.tdim = times_s[k] / s->dwell;
+        S.nact = (int)(std::lower_bound(s->T.begin(), s->T.end(), S.tdim) - s->T.begin());
+        if (S.n_pts == 0) S.nact = 0;
+        S.nblk = (S.nact + b->sb - 1) / b->sb;
+        S.rec_off = rec;
+        S.part_off = part;
+        pt_offs[(size_t)k] = S.pt_off;
+        rec_offs[(size_t)k] = rec;
+        rec += S.nact;
+        part += (int64_t)S.nblk * S.n_pts;
+        const int64_t tiles = (S.n_pts + tile - 1) / tile;
+        for (int blk = 0; blk < S.nblk; ++blk) {
+            const int64_t nsrc = std::min<int64_t>(S.nact, (int64_t)(blk + 1) * b->sb) - (int64_t)blk * b->sb;
+            for (int64_t t = 0; t < tiles; ++t) {
+                const int64_t npt = std::min<int64_t>(tile, S.n_pts - t * tile);
+                items.push_back({nsrc * npt, make_int4(k, (int)t, blk, 0)});
+            }
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<int64_t, int4> &x, const std::pair<int64_t, int4> &y) { return x.first > y.first; });
+    b->total_pts = pt_offsets[n_scans];
+    b->total_rec = rec;
+    b->total_part = part;
+    b->n_items = (int)items.size();
+    const size_t rec_size = prec == DD_MIXED ? sizeof(ddk::RecF32) : sizeof(ddk::RecF64);
+    size_t bytes = 0;
+    auto add = [&](size_t x) { size_t o = (bytes + 255) & ~size_t(255); bytes = o + x; return o; };
+    const size_t o_sc = add(sc.size() * sizeof(ddk::BScan));
+    const size_t o_pt = add(pt_offs.size() * sizeof(int64_t));
+    const size_t o_ro = add(rec_offs.size() * sizeof(int64_t));
+    const size_t o_it = add(std::max<size_t>(1, items.size()) * sizeof(int4));
+    const size_t o_ct = add(sizeof(unsigned));
+    const size_t o_x = add(2 * (size_t)std::max<int64_t>(1, b->total_pts) * sizeof(double));
+    const size_t o_rec = add((size_t)std::max<int64_t>(1, rec) * rec_size);
+    const size_t o_part = add((size_t)std::max<int64_t>(1, part) * sizeof(double));
+    cudaError_t err = cudaMalloc(&b->ws, bytes);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return dd::fail(DD_ENOMEM, std::string("dd_batch_create: cudaMalloc: ") + cudaGetErrorString(err));
+    }
+    char *base = (char *)b->ws;
+    b->d_sc = (ddk::BScan *)(base + o_sc);
+    b->d_pt_offs = (int64_t *)(base + o_pt);
+    b->d_rec_offs = (int64_t *)(base + o_ro);
+    b->d_items = (int4 *)(base + o_it);
+    b->d_counter = (unsigned *)(base + o_ct);
+    b->d_X = (double *)(base + o_x);
+    b->d_Y = b->d_X + std::max<int64_t>(1, b->total_pts);
+    b->d_rec = base + o_rec;
+    b->d_part = (double *)(base + o_part);
+    std::vector<int4> it(items.size());
+    for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
+    DD_CUDA_TRY(cudaMemcpy(b->d_sc, sc.data(), sc.size() * sizeof(ddk::BScan), cudaMemcpyHostToDevice));
+    DD_CUDA_TRY(cudaMemcpy(b->d_pt_offs, pt_offs.data(), pt_offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    DD_CUDA_TRY(cudaMemcpy(b->d_rec_offs, rec_offs.data(), rec_offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (!it.empty()) DD_CUDA_TRY(cudaMemcpy(b->d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    DD_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    if (prec == DD_MIXED)
+        b->grid = {persistent_grid<ddk::CfgMixed>(), persistent_grid<ddk::CfgMixed256>(), persistent_grid<ddk::CfgMixed64>()};
+    else
+        b->grid = {persistent_grid<ddk::CfgF64>(), persistent_grid<ddk::CfgF64x256>(), persistent_grid<ddk::CfgF64>()};
+    // tuning key: device name, precision and a log2 bucket of the pair count
+    cudaDeviceProp prop;
+    DD_CUDA_TRY(cudaGetDeviceProperties(&prop, b->device));
+    int64_t pairs = 0;
+    for (auto &S : sc) pairs += (int64_t)S.nact * S.n_pts;
+    b->pairs = pairs;
+    int bucket = 0;
+    while ((int64_t(1) << bucket) < pairs && bucket < 62) ++bucket;
+    std::ostringstream key;
+    key << prop.name << "/sm" << prop.major << prop.minor << "/" << (prec == DD_MIXED ? "mixed" : "fp64") << "/2^" << bucket;
+    b->tune_key = key.str();
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_cache_load();
+        auto f = g_tune.find(b->tune_key);
+        b->variant = f != g_tune.end() ? std::min(std::max(f->second, 0), kVariants - 1) : 0;
+    }
+    *out = b.release();
+    return DD_OK;
+}
+
+dd_status dd_batch_tune(dd_batch *b, const double *pts_xy_m, int32_t *chosen) {
+    dd::clear_error();
+    if (!b || !pts_xy_m) return dd::fail(DD_EINVAL, "dd_batch_tune: NULL argument");
+    if (!dd::is_device_pointer(pts_xy_m)) return dd::fail(DD_EINVAL, "dd_batch_tune: points must be on the device");
+    double *tmp = nullptr;
+    DD_CUDA_TRY(cudaMalloc(&tmp, (size_t)std::max<int64_t>(1, b->total_pts) * sizeof(double)));
+    cudaEvent_t e0, e1;
+    DD_CUDA_TRY(cudaEventCreate(&e0));
+    DD_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = 0;
+    const int nv = b->prec == DD_MIXED ? kVariants : 2;
+    for (int v = 0; v < nv; ++v) {
+        dd_status st = enqueue(b, pts_xy_m, tmp, v, b->cap);           // warm
+        if (st != DD_OK) { cudaFree(tmp); return st; }
+        cudaEventRecord(e0, b->cap);
+        enqueue(b, pts_xy_m, tmp, v, b->cap);
+        cudaEventRecord(e1, b->cap);
+        DD_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(tmp);
+    b->variant = best_v;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[b->tune_key] = best_v;
+        tune_cache_store();
+    }
+    if (chosen) *chosen = best_v;
+    return DD_OK;
+}
+
+dd_status dd_batch_run(dd_batch *b, const double *pts_xy_m, double *out, void *cuda_stream) {
+    dd::clear_error();
+    if (!b || !pts_xy_m || !out) return dd::fail(DD_EINVAL, "dd_batch_run: NULL argument");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const bool pts_host = !dd::is_device_pointer(pts_xy_m);
+    const bool out_host = !dd::is_device_pointer(out);
+    const size_t npt = (size_t)std::max<int64_t>(1, b->total_pts);
+    if ((pts_host && !b->d_pts) || (out_host && !b->d_out)) {
+        if (!b->d_pts) DD_CUDA_TRY(cudaMalloc(&b->d_pts, 2 * npt * sizeof(double)));
+        if (!b->d_out) DD_CUDA_TRY(cudaMalloc(&b->d_out, npt * sizeof(double)));
+    }
+    const double *pts = pts_xy_m;
+    double *dst = out;
+    if (pts_host) {
+        DD_CUDA_TRY(cudaMemcpyAsync(b->d_pts, pts_xy_m, 2 * (size_t)b->total_pts * sizeof(double),
+                                    cudaMemcpyHostToDevice, stream));
+        pts = b->d_pts;
+    }
+    if (out_host) dst = b->d_out;
+    if (!b->exec || b->g_pts != pts || b->g_out != dst || b->g_variant != b->variant) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        cudaGraph_t graph;
+        DD_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        dd_status st = enqueue(b, pts, dst, b->variant, b->cap);
+        cudaError_t err = cudaStreamEndCapture(b->cap, &graph);
+        if (st != DD_OK) return st;
+        if (err != cudaSuccess) return dd::fail_cuda(err, "cudaStreamEndCapture");
+        err = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (err != cudaSuccess) return dd::fail_cuda(err, "cudaGraphInstantiate");
+        b->g_pts = pts;
+        b->g_out = dst;
+        b->g_variant = b->variant;
+    }
+    {
+        dd::ProfScope ps(variant_name(b->prec, b->variant), stream);
+        DD_CUDA_TRY(cudaGraphLaunch(b->exec, stream));
+    }
+    if (out_host)
+        DD_CUDA_TRY(cudaMemcpyAsync(out, dst, (size_t)b->total_pts * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    if (out_host || pts_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    return DD_OK;
+}
+
+void dd_batch_destroy(dd_batch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->ws);
+    cudaFree(b->d_pts);
+    cudaFree(b->d_out);
+    cudaGetLastError();
+    delete b;
+}
+
+dd_status dd_batch_info(const dd_batch *b, int64_t *n_items, int64_t *pairs, int32_t *variant) {
+    dd::clear_error();
+    if (!b) return dd::fail(DD_EINVAL, "dd_batch_info: NULL plan");
+    if (n_items) *n_items = b->n_items;
+    if (variant) *variant = b->variant;
+    if (pairs) *pairs = b->pairs;
+    return DD_OK;
+}
+
+dd_status dd_field_batch(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
+                         const double *pts_xy_m, const double *times_s, dd_precision prec,
+                         double *out, void *cuda_stream) {
+    dd::clear_error();
+    if (!pts_xy_m || !out) return dd::fail(DD_EINVAL, "dd_field_batch: NULL buffer");
+    dd_batch *b = nullptr;
+    dd_status st = dd_batch_create(scans, n_scans, pt_offsets, times_s, prec, &b);
+    if (st != DD_OK) return st;
+    st = dd_batch_run(b, pts_xy_m, out, cuda_stream);
+    if (st == DD_OK) {
+        cudaError_t err = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        if (err != cudaSuccess) st = dd::fail_cuda(err, "dd_field_batch: stream");
+    }
+    dd_batch_destroy(b);
+    return st;
+}
+
+}  // extern "C"

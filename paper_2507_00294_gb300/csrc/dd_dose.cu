@@ -162,14 +162,17 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     auto *keep = new std::vector<int2>(its.size());
     for (size_t k = 0; k < its.size(); ++k) (*keep)[k] = its[k].second;
     if (n >= 2) {
-        ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
+        DD_PROFILED(Cfg::kLagCoefName, stream,
+                    (ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(n, scan->s, scan->kappa, d_rec)));
         DD_CUDA_TRY(cudaGetLastError());
         DD_CUDA_TRY(cudaMemcpyAsync(d_items, keep->data(), keep->size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
-        ddk::dose_kernel<Cfg><<<(unsigned)keep->size(), Cfg::kThreads, 0, stream>>>(
-            src, src + n, n, d_rec, d_items, lb, d_part);
+        DD_PROFILED(Cfg::kDoseName, stream,
+                    (ddk::dose_kernel<Cfg><<<(unsigned)keep->size(), Cfg::kThreads, 0, stream>>>(
+                        src, src + n, n, d_rec, d_items, lb, d_part)));
         DD_CUDA_TRY(cudaGetLastError());
     }
-    ddk::dose_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev);
+    DD_PROFILED("dose_reduce", stream,
+                (ddk::dose_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev)));
     DD_CUDA_TRY(cudaGetLastError());
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));

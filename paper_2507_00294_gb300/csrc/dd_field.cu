@@ -161,7 +161,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     Rec *d_rec = cv.take<Rec>((size_t)group * n_src);
     double *d_part = cv.take<double>((size_t)nblk_max * group * n_pts);
 
-    ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y);
+    DD_PROFILED("prep_points", stream,
+                (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y)));
     DD_CUDA_TRY(cudaGetLastError());
 
     const double *srcX = src, *srcY = src + n_src, *srcT = src + 2 * n_src, *srcTAU = src + 3 * n_src;
@@ -207,16 +208,19 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
             DD_CUDA_TRY(cudaMemcpyAsync(d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
         if (max_nact > 0) {
             dim3 cg((unsigned)((max_nact + 127) / 128), (unsigned)ng);
-            ddk::coef_kernel<Rec><<<cg, 128, 0, stream>>>(srcT, srcTAU, d_t, d_nact, scan->s, scan->kappa, d_rec, n_src);
+            DD_PROFILED(Cfg::kCoefName, stream,
+                        (ddk::coef_kernel<Rec><<<cg, 128, 0, stream>>>(srcT, srcTAU, d_t, d_nact, scan->s, scan->kappa, d_rec, n_src)));
             DD_CUDA_TRY(cudaGetLastError());
         }
         if (!it.empty()) {
-            ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
-                srcX, srcY, X, Y, n_pts, d_rec, n_src, d_nact, d_items, ng, sb, d_part);
+            DD_PROFILED(Cfg::kFieldName, stream,
+                        (ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
+                            srcX, srcY, X, Y, n_pts, d_rec, n_src, d_nact, d_items, ng, sb, d_part)));
             DD_CUDA_TRY(cudaGetLastError());
         }
         dim3 rg((unsigned)((n_pts + 255) / 256), (unsigned)ng);
-        ddk::reduce_kernel<<<rg, 256, 0, stream>>>(d_part, d_nblk, d_row, ng, n_pts, scan->pref, out_dev);
+        DD_PROFILED("field_reduce", stream,
+                    (ddk::reduce_kernel<<<rg, 256, 0, stream>>>(d_part, d_nblk, d_row, ng, n_pts, scan->pref, out_dev)));
         DD_CUDA_TRY(cudaGetLastError());
         keep->items.push_back(std::move(it));
         keep->ints.push_back(std::move(tabs));

@@ -68,42 +68,41 @@ struct CfgMixed {
     using Rec = RecF32;
     using Real = float;
     static constexpr int kThreads = 128, kPPT = 4, kTCH = 4, kSTILE = 64, kSB = 512, kFlush = 32;
+    static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
+                                *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
 struct CfgF64 {
     using Rec = RecF64;
     using Real = double;
     static constexpr int kThreads = 128, kPPT = 2, kTCH = 4, kSTILE = 32, kSB = 512, kFlush = 1 << 30;
+    static constexpr const char *kFieldName = "field_fp64", *kCoefName = "coef_fp64",
+                                *kDoseName = "dose_fp64", *kLagCoefName = "lag_coef_fp64";
 };
 
-// One work item per CTA: item = (point tile, snapshot chunk, visit block).
-// partial[(block * n_tg + j) * n_pts + p] receives sum_{i in block, i < nact[j]} pair_term.
-template <typename Cfg>
-__global__ void __launch_bounds__(Cfg::kThreads)
-field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
-             const double *__restrict__ X, const double *__restrict__ Y, int64_t n_pts,
-             const typename Cfg::Rec *__restrict__ rec, int64_t rec_stride,
-             const int *__restrict__ nact, const int4 *__restrict__ items, int n_tg, int sb,
-             double *__restrict__ partial) {
+// Shared memory of one tile pass: kSTILE staged visits (coordinates relative to the
+// tile origin) and their records for TCH snapshots.
+template <typename Cfg, int TCH>
+struct TileSmem {
+    typename Cfg::Real x[Cfg::kSTILE], y[Cfg::kSTILE];
+    __align__(16) typename Cfg::Rec rec[TCH][Cfg::kSTILE];
+};
+
+// Sum of pair terms over visits [s_begin, s_end) for the point tile starting at point
+// tile0 and TCH snapshots:  partial[jc * part_stride + p] = sum_{i < na[jc]} term(p, i, jc)
+// for jc < nj.  rec points at the record row of the first snapshot (row stride
+// rec_stride); records exist for visits below na[jc].  All threads of the CTA call it.
+template <typename Cfg, int TCH>
+__device__ __forceinline__ void field_tile(TileSmem<Cfg, TCH> &sm, const double *__restrict__ srcX,
+                                           const double *__restrict__ srcY, const double *__restrict__ X,
+                                           const double *__restrict__ Y, int64_t n_pts, int64_t tile0,
+                                           const typename Cfg::Rec *__restrict__ rec, int64_t rec_stride,
+                                           const int (&na)[TCH], int nj, int s_begin, int s_end,
+                                           double *__restrict__ partial, int64_t part_stride) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
-    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, TCH = Cfg::kTCH, STILE = Cfg::kSTILE;
+    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE;
     constexpr int RV = sizeof(Rec) / 16;   // 16-byte vectors per record
-    __shared__ Real s_x[STILE], s_y[STILE];
-    __shared__ __align__(16) Rec s_rec[TCH][STILE];
-
-    const int4 item = items[blockIdx.x];
     const int tid = threadIdx.x;
-    const int j0 = item.y * TCH;
-    int na[TCH];
-    int nmax = 0;
-#pragma unroll
-    for (int jc = 0; jc < TCH; ++jc) {
-        na[jc] = (j0 + jc < n_tg) ? nact[j0 + jc] : 0;
-        nmax = max(nmax, na[jc]);
-    }
-    const int s_begin = item.z * sb;
-    const int s_end = min(s_begin + sb, nmax);
-    const int64_t tile0 = (int64_t)item.x * (NT * PPT);
 
     // points relative to the tile's first point (keeps FP32 differences exact-ish)
     const double cx = X[tile0], cy = Y[tile0];
@@ -125,20 +124,20 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
         const int cnt = min(STILE, s_end - s0);
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
-            s_x[i] = (Real)(srcX[s0 + i] - cx);
-            s_y[i] = (Real)(srcY[s0 + i] - cy);
+            sm.x[i] = (Real)(srcX[s0 + i] - cx);
+            sm.y[i] = (Real)(srcY[s0 + i] - cy);
         }
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc) {
-            const float4 *row = reinterpret_cast<const float4 *>(rec + (int64_t)(j0 + jc) * rec_stride + s0);
+            const float4 *row = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0);
             const int lim = na[jc] - s0;           // records exist for visits below n_active
-            float4 *dst = reinterpret_cast<float4 *>(&s_rec[jc][0]);
+            float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
             for (int v = tid; v < cnt * RV; v += NT)
                 dst[v] = (v / RV < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
         for (int s = 0; s < cnt; ++s) {
-            const Real sx = s_x[s], sy = s_y[s];
+            const Real sx = sm.x[s], sy = sm.y[s];
             Real r2[PPT];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -149,7 +148,7 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
                 if (gs < na[jc]) {
-                    const Rec &R = s_rec[jc][s];
+                    const Rec &R = sm.rec[jc][s];
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) acc[jc][k] += pair_term(r2[k], R);
                 }
@@ -168,13 +167,40 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
     }
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc) {
-        if (j0 + jc >= n_tg) continue;
+        if (jc >= nj) continue;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int64_t p = tile0 + k * NT + tid;
-            if (p < n_pts) partial[((int64_t)item.z * n_tg + j0 + jc) * n_pts + p] = tot[jc][k];
+            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = tot[jc][k];
         }
     }
+}
+
+// One work item per CTA: item = (point tile, snapshot chunk, visit block).
+// partial[(block * n_tg + j) * n_pts + p] receives sum_{i in block, i < nact[j]} pair_term.
+template <typename Cfg>
+__global__ void __launch_bounds__(Cfg::kThreads)
+field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
+             const double *__restrict__ X, const double *__restrict__ Y, int64_t n_pts,
+             const typename Cfg::Rec *__restrict__ rec, int64_t rec_stride,
+             const int *__restrict__ nact, const int4 *__restrict__ items, int n_tg, int sb,
+             double *__restrict__ partial) {
+    constexpr int TCH = Cfg::kTCH;
+    __shared__ TileSmem<Cfg, TCH> sm;
+    const int4 item = items[blockIdx.x];
+    const int j0 = item.y * TCH;
+    int na[TCH];
+    int nmax = 0;
+#pragma unroll
+    for (int jc = 0; jc < TCH; ++jc) {
+        na[jc] = (j0 + jc < n_tg) ? nact[j0 + jc] : 0;
+        nmax = max(nmax, na[jc]);
+    }
+    const int s_begin = item.z * sb;
+    const int s_end = min(s_begin + sb, nmax);
+    field_tile<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, (int64_t)item.x * (Cfg::kThreads * Cfg::kPPT),
+                         rec + (int64_t)j0 * rec_stride, rec_stride, na, min(TCH, n_tg - j0), s_begin,
+                         s_end, partial + ((int64_t)item.z * n_tg + j0) * n_pts, n_pts);
 }
 
 }  // namespace ddk

@@ -49,7 +49,30 @@ const double *device_sources(const dd_scan *scan, dd_status *st);
 // True if `p` is device-accessible memory of the current device.
 bool is_device_pointer(const void *p);
 
+// Kernel timing scope (dd_profile.cpp): records an event pair around the launch
+// made inside the scope when profiling is enabled, nothing otherwise.
+class ProfScope {
+  public:
+    ProfScope(const char *name, cudaStream_t stream);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+  private:
+    const char *name_;
+    cudaStream_t stream_;
+    cudaEvent_t a_{}, b_{};
+    bool active_ = false;
+};
+
 }  // namespace dd
+
+// Launch `launch` (a kernel<<<...>>> expression) under a ProfScope named `name`.
+#define DD_PROFILED(name, stream, launch) \
+    do {                                   \
+        dd::ProfScope dd_ps_(name, stream); \
+        launch;                            \
+    } while (0)
 
 #define DD_CUDA_TRY(expr)                                              \
     do {                                                               \
