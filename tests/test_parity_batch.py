@@ -1,0 +1,97 @@
+"""GPU batched field (dd_batch_* / dd_field_batch: persistent, graph-replayed) against
+the CPU oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+from paper_2507_00294_gb300 import binding as b
+from paper_2507_00294_gb300 import workloads as w
+from parity_util import assert_fp64, assert_mixed, oracle_field, oracle_pairs
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch(seed=21, n_scans=24):
+    rng = np.random.default_rng(seed)
+    specs, pts, times = [], [], []
+    for k in range(n_scans):
+        n = int(rng.integers(3, 25))
+        s = w.ScanSpec(n, int(rng.integers(2, 25)), D_m2s=float(10 ** rng.uniform(-15, -12)),
+                       dwell_s=float(10 ** rng.uniform(-7, -5)), sigma_m=float(rng.uniform(0.05e-9, 0.2e-9)),
+                       order=[w.RASTER, w.SERPENTINE, w.RANDOM, w.INTERLEAVED][k % 4],
+                       interleave_stride=3, seed=k, keep_fraction=[1.0, 0.6, 0.3, 1.0][k % 4])
+        specs.append(s)
+        p = w.grid_points(max(s.nx, s.ny), s.pitch_m)
+        if k % 5 == 1:
+            p = p[: 1 + len(p) // 3]                 # ragged point count
+        pts.append(p)
+        nv = w.n_visits(s)
+        times.append([nv * s.dwell_s, 0.4 * nv * s.dwell_s, 0.0, 30 * nv * s.dwell_s][k % 4])
+    return specs, pts, np.array(times)
+
+
+def flat(pts):
+    offs = np.concatenate([[0], np.cumsum([len(p) for p in pts])]).astype(np.int64)
+    return offs, np.ascontiguousarray(np.concatenate(pts, axis=0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_small_uneven_batch_full(cuda, prec):
+    import torch
+    specs, pts, times = small_batch()
+    offs, allp = flat(pts)
+    scans = [b.Scan(s) for s in specs]
+    plan = b.Batch(scans, offs, times, prec)
+    dp = torch.from_numpy(allp).cuda()
+    out1 = plan.run(dp).cpu().numpy()
+    out2 = plan.run(dp).cpu().numpy()                # graph replay
+    np.testing.assert_array_equal(out1, out2)
+    host = plan.run(allp)                            # host buffers
+    np.testing.assert_array_equal(out1, host)
+    one = b.dd_field_batch(scans, offs, dp, times, prec).cpu().numpy()
+    np.testing.assert_array_equal(out1, one)
+    for k, s in enumerate(specs):
+        ref = oracle_field(s, pts[k], times[k:k + 1])[0]
+        got = out1[offs[k]:offs[k + 1]]
+        if times[k] == 0.0:
+            assert np.all(got == 0.0)
+            continue
+        if prec == "fp64":
+            assert_fp64(got, ref, "batch scan %d" % k)
+        else:
+            assert_mixed(got, ref, ref.max(), "batch scan %d" % k)
+
+
+def test_tuned_variants_agree(cuda):
+    import torch
+    specs, pts, times = small_batch(seed=5, n_scans=16)
+    offs, allp = flat(pts)
+    scans = [b.Scan(s) for s in specs]
+    plan = b.Batch(scans, offs, times, "mixed")
+    dp = torch.from_numpy(allp).cuda()
+    base = plan.run(dp).cpu().numpy()
+    v = plan.tune(dp)
+    assert v in (0, 1, 2) and plan.info()["variant"] == v
+    np.testing.assert_array_equal(plan.run(dp).cpu().numpy(), base)
+
+
+def test_batched_512_scans_sampled(cuda):
+    import torch
+    jobs = w.batched_scans()
+    offs, allp = flat([j.pts_xy for j in jobs])
+    times = np.array([j.times[0] for j in jobs])
+    scans = [b.Scan(j.scan) for j in jobs]
+    plan = b.Batch(scans, offs, times, "mixed")
+    info = plan.info()
+    assert info["pairs"] == sum(len(j.pts_xy) * w.n_visits(j.scan) for j in jobs)
+    out = plan.run(torch.from_numpy(allp).cuda()).cpu().numpy()
+    rng = np.random.default_rng(4)
+    for k in rng.choice(len(jobs), 48, replace=False):
+        j = jobs[k]
+        n = len(j.pts_xy)
+        ip = rng.choice(n, 3, replace=False)
+        # the last-visited probe gives a lower bound of the map's peak
+        _, ts, _ = scans[k].visits()
+        g_last = scans[k].visits()[0][-1]
+        ip = np.concatenate([ip, [g_last]])
+        ref = oracle_pairs(j.scan, j.pts_xy, j.times, ip, np.zeros(len(ip), int))
+        assert_mixed(out[offs[k] + ip], ref, ref[-1], "batch512 scan %d" % k)
