@@ -127,6 +127,24 @@ dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy_m, int64_t
 dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, double *out,
                             void *cuda_stream);
 
+/* Allocation-free variant of dd_per_probe_dose (the paper has no counterpart: this
+   entry point exists for callers that cannot allocate device memory while they run,
+   e.g. an acquisition loop that reserves its whole GPU memory budget before the scan
+   starts, or a host whose device allocator belongs to another framework).  Same
+   result as dd_per_probe_dose.  It calls no device allocator: its scratch lives in
+   one file-scope __device__ array of 8 MiB, which every GPU that loads the library
+   holds until the process exits, so scans of at most 16384 visits are accepted
+   (larger ones: DD_EINVAL with a message).  out must be device memory (else
+   DD_EINVAL).  The first call on each device looks up the array's device address
+   (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
+   share the array, which keeps the previous call's contents: every byte a kernel
+   reads is written earlier in the same call, and calls that overlap on the GPU (two
+   streams, or two host threads) race on it.  The call synchronises `cuda_stream`
+   before returning.  The scan must stay alive until the call returns.
+   Errors: DD_EINVAL, DD_ENOTSUP (non-uniform dwell or flyback), DD_ECUDA. */
+dd_status dd_per_probe_dose_noalloc(const dd_scan *scan, dd_precision prec, double *out,
+                                    void *cuda_stream);
+
 /* Many independent scans in one persistent launch (the paper's task partition
    over probe subsets, Sec. 3, applied across scans).  Scan k is evaluated at
    points pts_xy_m[2*pt_offsets[k] .. 2*pt_offsets[k+1]) and the single time

@@ -61,6 +61,8 @@ def load(build_if_missing=True):
     lib.dd_field_at_times.argtypes = [_VP, _VP, _I64, _VP, _I64, ctypes.c_int, _VP, _VP]
     lib.dd_per_probe_dose.argtypes = [_VP, ctypes.c_int, _VP, _VP]
     lib.dd_field_batch.argtypes = [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
+    lib.dd_per_probe_dose_noalloc.argtypes = [_VP, ctypes.c_int, _VP, _VP]
+    lib.dd_per_probe_dose_noalloc.restype = ctypes.c_int
     lib.dd_batch_create.argtypes = [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)]
     lib.dd_batch_run.argtypes = [_VP, _VP, _VP, _VP]
     lib.dd_batch_tune.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32)]
@@ -208,6 +210,15 @@ def dd_per_probe_dose(scan, prec="mixed", out=None, stream=None, device=None):
     o, ko = _ptr(out, np.float64)
     _check(load().dd_per_probe_dose(scan.handle, PRECISIONS[prec], o, _stream(stream, out)),
            "dd_per_probe_dose")
+    return out
+
+
+def dd_per_probe_dose_noalloc(scan, out, prec="mixed", stream=None):
+    """Dwell-start dose into a device tensor `out` without any device allocation
+    (scratch in the library's fixed 8 MiB area; at most 16384 visits)."""
+    o, ko = _ptr(out, np.float64)
+    _check(load().dd_per_probe_dose_noalloc(scan.handle, PRECISIONS[prec], o, _stream(stream, out)),
+           "dd_per_probe_dose_noalloc")
     return out
 
 

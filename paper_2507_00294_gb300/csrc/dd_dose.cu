@@ -11,6 +11,7 @@
 // per-block partial sums are reduced in block order (deterministic).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "dd_coef.cuh"
@@ -193,4 +194,129 @@ extern "C" dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, d
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     if (prec == DD_MIXED) return run_dose<ddk::CfgMixed>(scan, out, stream);
     return run_dose<ddk::CfgF64>(scan, out, stream);
+}
+
+// ---------------------------------------------------------------------------------
+// Allocation-free dose.  Some callers cannot allocate device memory during a run: a
+// microscope acquisition loop that reserves its whole memory budget before the scan
+// starts, a host that hands the device allocator to another framework, or code on a
+// path where cudaMalloc's implicit synchronisation is not allowed.  This entry point
+// keeps its scratch (visit coordinates, lag records, work list, partial sums) in one
+// file-scope device array and calls no device allocator.
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(8) << 20;       // 8 MiB: up to 16384 visits
+constexpr int64_t kNoAllocMaxVisits = 16384;
+constexpr int kNoAllocMaxItems = 4096;
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_dose_scratch[kNoAllocBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_dose_scratch on the current device; looked up once per device.
+dd_status noalloc_scratch(char **addr) {
+    int dev = 0;
+    DD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return dd::fail(DD_ENOTSUP, "dd_per_probe_dose_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t err = cudaGetSymbolAddress(&p, g_dose_scratch);
+        if (err != cudaSuccess) return dd::fail_cuda(err, "cudaGetSymbolAddress(g_dose_scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *addr = (char *)g_noalloc_addr[dev];
+    return DD_OK;
+}
+
+template <typename Cfg>
+dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream, char *scratch) {
+    using Rec = typename Cfg::Rec;
+    const int64_t n = scan->n;
+    constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
+    const int lb = Cfg::kSB;
+    const int64_t n_tiles = (n + TILE - 1) / TILE;
+    const int64_t nblk = n >= 2 ? (n - 2) / lb + 1 : 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = (off + 255) & ~size_t(255); size_t o = off; off += bytes; return o; };
+    const size_t o_x = take(2 * (size_t)n * sizeof(double));
+    const size_t o_rec = take((size_t)n * sizeof(Rec));
+    const size_t o_part = take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(double));
+    const size_t o_items = take((size_t)kNoAllocMaxItems * sizeof(int2));
+    if (off > kNoAllocBytes)
+        return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: scan needs more scratch than the 8 MiB built-in area");
+
+    // work list on the host (fixed storage, no heap), same cost order as dd_per_probe_dose
+    static thread_local std::pair<int64_t, int2> its[kNoAllocMaxItems];
+    static thread_local int2 flat[kNoAllocMaxItems];
+    int count = 0;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        const int64_t t0 = t * TILE, t1 = std::min(n, t0 + TILE);
+        if (t1 - 1 < 1) continue;
+        const int64_t nb = (t1 - 2) / lb + 1;
+        for (int64_t bk = 0; bk < nb; ++bk) {
+            const int64_t k0 = 1 + bk * lb, k1 = std::min(k0 + lb, t1);
+            int64_t cost = 0;
+            for (int64_t k = k0; k < k1; ++k) cost += std::max<int64_t>(0, t1 - std::max(t0, k));
+            if (count >= kNoAllocMaxItems)
+                return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: work list exceeds its fixed size");
+            its[count++] = {cost, make_int2((int)t, (int)bk)};
+        }
+    }
+    std::sort(its, its + count, [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) {
+        if (a.first != b.first) return a.first > b.first;
+        return a.second.x != b.second.x ? a.second.x < b.second.x : a.second.y < b.second.y;
+    });
+    for (int k = 0; k < count; ++k) flat[k] = its[k].second;
+
+    double *d_x = (double *)(scratch + o_x);
+    double *d_y = d_x + n;
+    Rec *d_rec = (Rec *)(scratch + o_rec);
+    double *d_part = (double *)(scratch + o_part);
+    int2 *d_items = (int2 *)(scratch + o_items);
+    // every scratch byte a kernel reads below is written earlier in this call, so
+    // nothing left by a previous call can leak into the result
+    DD_CUDA_TRY(cudaMemcpyAsync(d_x, scan->X.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
+    DD_CUDA_TRY(cudaMemcpyAsync(d_y, scan->Y.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
+    if (n >= 2) {
+        ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
+        DD_CUDA_TRY(cudaGetLastError());
+        DD_CUDA_TRY(cudaMemcpyAsync(d_items, flat, (size_t)count * sizeof(int2), cudaMemcpyHostToDevice, stream));
+        ddk::dose_kernel<Cfg><<<(unsigned)count, Cfg::kThreads, 0, stream>>>(d_x, d_y, n, d_rec, d_items, lb, d_part);
+        DD_CUDA_TRY(cudaGetLastError());
+    }
+    ddk::dose_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);
+    DD_CUDA_TRY(cudaGetLastError());
+    // the host staging above is reused by the next call on this thread
+    DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    return DD_OK;
+}
+
+}  // namespace
+
+extern "C" dd_status dd_per_probe_dose_noalloc(const dd_scan *scan, dd_precision prec, double *out,
+                                               void *cuda_stream) {
+    dd::clear_error();
+    if (!scan || !out) return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: NULL argument");
+    if (prec != DD_FP64 && prec != DD_MIXED)
+        return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: unknown precision");
+    if (!scan->uniform)
+        return dd::fail(DD_ENOTSUP, "dd_per_probe_dose_noalloc: needs a uniform dwell without flyback");
+    if (scan->n > kNoAllocMaxVisits)
+        return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: at most 16384 visits fit the 8 MiB built-in scratch");
+    if (!dd::is_device_pointer(out))
+        return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: out must be device memory");
+    char *scratch = nullptr;
+    dd_status st = noalloc_scratch(&scratch);
+    if (st != DD_OK) return st;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    if (prec == DD_MIXED) return run_dose_noalloc<ddk::CfgMixed>(scan, out, stream, scratch);
+    return run_dose_noalloc<ddk::CfgF64>(scan, out, stream, scratch);
 }
