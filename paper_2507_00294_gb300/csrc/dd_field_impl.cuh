@@ -1,6 +1,7 @@
 // dd_field_impl.cuh -- the field tile kernel shared by the field, dose and batch paths.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "dd_e1.cuh"
 
@@ -86,6 +87,177 @@ struct TileSmem {
     typename Cfg::Real x[Cfg::kSTILE], y[Cfg::kSTILE];
     __align__(16) typename Cfg::Rec rec[TCH][Cfg::kSTILE];
 };
+
+// ---- FP32-mixed tile with warp-uniform regime selection -------------------------
+//
+// For every staged visit and every warp, the staging threads bound the warp's a and h
+// from the bounding box of the warp's points: a_min = rho2_min q1 and h_max = rho2_max dq.
+// If a_min >= 87 for every snapshot the visit adds nothing to the warp's points (all
+// terms are below the FP32 normal range) and is skipped.  Otherwise the smallest
+// polynomial degree whose truncation bound e^{2h} h^{d+1}/(d+1)! stays below 4e-8 at
+// h_max is used for the whole warp: degree 2 (h_max <= 6.0e-3), 4 (<= 8.2e-2) or 8
+// (<= 0.5); beyond h_max = 0.5 every lane takes the per-lane regime test of pair_term.
+// Lanes whose own a is >= 87 inside a polynomial class get ex2 -> 0 (flush to zero), so
+// no per-lane test is needed on the polynomial paths.
+constexpr float kDeg2H = 6.0e-3f, kDeg4H = 8.2e-2f;
+enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeGeneral = 4 };
+
+template <int D>
+__device__ __forceinline__ float moment_poly(const float4 &r0, const float4 &r1, const float4 &r2, float h) {
+    // c_0 = r0.w, c_1..c_4 = r1, c_5..c_8 = r2
+    if (D == 2) return fmaf(fmaf(r1.y, h, r1.x), h, r0.w);
+    if (D == 4) return fmaf(fmaf(fmaf(fmaf(r1.w, h, r1.z), h, r1.y), h, r1.x), h, r0.w);
+    float p = fmaf(fmaf(fmaf(r2.w, h, r2.z), h, r2.y), h, r2.x);
+    p = fmaf(fmaf(fmaf(fmaf(p, h, r1.w), h, r1.z), h, r1.y), h, r1.x);
+    return fmaf(p, h, r0.w);
+}
+
+template <int D, int PPT>
+__device__ __forceinline__ void moment_pass(float (&acc)[PPT], const float (&r2)[PPT], const float4 &q0,
+                                            const float4 &q1, const float4 &q2) {
+    // q0 = (alpha, dq, q1, c0): e^-a = 2^(rho^2 alpha), h = rho^2 dq
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const float h = r2[k] * q0.y;
+        const float e = ex2_approx(r2[k] * q0.x);
+        acc[k] = fmaf(e, moment_poly<D>(q0, q1, q2, h), acc[k]);
+    }
+}
+
+template <typename Cfg, int TCH>
+struct TileSmemMixed {
+    float x[Cfg::kSTILE], y[Cfg::kSTILE];
+    uint32_t code[Cfg::kThreads / 32][Cfg::kSTILE];   // per warp: 8-bit class per snapshot
+    float4 box[Cfg::kThreads / 32];                     // per warp: (xmin, xmax, ymin, ymax)
+    __align__(16) RecF32 rec[TCH][Cfg::kSTILE];
+};
+
+template <typename Cfg, int TCH>
+__device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, const double *__restrict__ srcX,
+                                                 const double *__restrict__ srcY, const double *__restrict__ X,
+                                                 const double *__restrict__ Y, int64_t n_pts, int64_t tile0,
+                                                 const RecF32 *__restrict__ rec, int64_t rec_stride,
+                                                 const int (&na)[TCH], int nj, int s_begin, int s_end,
+                                                 double *__restrict__ partial, int64_t part_stride) {
+    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE, NW = NT / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const double cx = X[tile0], cy = Y[tile0];
+    float px[PPT], py[PPT];
+    float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int64_t p = tile0 + k * NT + tid;
+        px[k] = p < n_pts ? (float)(X[p] - cx) : 0.0f;
+        py[k] = p < n_pts ? (float)(Y[p] - cy) : 0.0f;
+        bx0 = fminf(bx0, px[k]); bx1 = fmaxf(bx1, px[k]);
+        by0 = fminf(by0, py[k]); by1 = fmaxf(by1, py[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+        bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+        by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+        by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+    }
+    __syncthreads();                       // previous item's readers of sm.box are done
+    if (lane == 0) sm.box[warp] = make_float4(bx0, bx1, by0, by1);
+
+    float acc[TCH][PPT];
+    double tot[TCH][PPT];
+#pragma unroll
+    for (int jc = 0; jc < TCH; ++jc)
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) { acc[jc][k] = 0.0f; tot[jc][k] = 0.0; }
+
+    for (int s0 = s_begin; s0 < s_end; s0 += STILE) {
+        const int cnt = min(STILE, s_end - s0);
+        __syncthreads();
+        for (int i = tid; i < cnt; i += NT) {
+            sm.x[i] = (float)(srcX[s0 + i] - cx);
+            sm.y[i] = (float)(srcY[s0 + i] - cy);
+        }
+#pragma unroll
+        for (int jc = 0; jc < TCH; ++jc) {
+            const float4 *row = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0);
+            const int lim = na[jc] - s0;
+            float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
+            for (int v = tid; v < cnt * 3; v += NT)
+                dst[v] = (v / 3 < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();                   // coordinates and box visible
+        for (int e = tid; e < cnt * NW; e += NT) {
+            const int i = e % cnt, w = e / cnt;
+            const float4 bb = sm.box[w];
+            const float sx = sm.x[i], sy = sm.y[i];
+            const float dx1 = fmaxf(fabsf(sx - bb.x), fabsf(sx - bb.y));
+            const float dy1 = fmaxf(fabsf(sy - bb.z), fabsf(sy - bb.w));
+            const float dx0 = fmaxf(0.0f, fmaxf(bb.x - sx, sx - bb.y));
+            const float dy0 = fmaxf(0.0f, fmaxf(bb.z - sy, sy - bb.w));
+            // rounding margin on the bounds of rho^2
+            const float r2max = (dx1 * dx1 + dy1 * dy1) * 1.0001f + 1e-6f;
+            const float r2min = (dx0 * dx0 + dy0 * dy0) * 0.9999f;
+            uint32_t word = 0;
+#pragma unroll
+            for (int jc = 0; jc < TCH; ++jc) {
+                uint32_t c = kCodeSkip;
+                if (s0 + i < na[jc]) {
+                    const float4 head = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0 + i)[0];
+                    const float hmax = r2max * head.y, amin = r2min * head.z;
+                    c = amin >= 87.0f ? kCodeSkip
+                      : hmax <= kDeg2H ? kCodeD2
+                      : hmax <= kDeg4H ? kCodeD4
+                      : hmax <= kHMaxF ? kCodeD8 : kCodeGeneral;
+                }
+                word |= c << (8 * jc);
+            }
+            sm.code[w][i] = word;
+        }
+        __syncthreads();
+        for (int s = 0; s < cnt; ++s) {
+            const uint32_t word = sm.code[warp][s];
+            if (word == 0) continue;                       // warp-uniform skip
+            const float sx = sm.x[s], sy = sm.y[s];
+            float r2[PPT];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const float dx = px[k] - sx, dy = py[k] - sy;
+                r2[k] = fmaf(dx, dx, dy * dy);
+            }
+#pragma unroll
+            for (int jc = 0; jc < TCH; ++jc) {
+                const uint32_t c = (word >> (8 * jc)) & 0xffu;
+                if (c == kCodeSkip) continue;
+                const float4 *rv = reinterpret_cast<const float4 *>(&sm.rec[jc][s]);
+                const float4 q0 = rv[0], q1 = rv[1], q2 = rv[2];
+                if (c == kCodeD2) {
+                    moment_pass<2, PPT>(acc[jc], r2, q0, q1, q2);
+                } else if (c == kCodeD4) {
+                    moment_pass<4, PPT>(acc[jc], r2, q0, q1, q2);
+                } else if (c == kCodeD8) {
+                    moment_pass<8, PPT>(acc[jc], r2, q0, q1, q2);
+                } else {
+                    const RecF32 &R = sm.rec[jc][s];
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) acc[jc][k] += pair_term(r2[k], R);
+                }
+            }
+        }
+#pragma unroll
+        for (int jc = 0; jc < TCH; ++jc)
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) { tot[jc][k] += (double)acc[jc][k]; acc[jc][k] = 0.0f; }
+    }
+#pragma unroll
+    for (int jc = 0; jc < TCH; ++jc) {
+        if (jc >= nj) continue;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const int64_t p = tile0 + k * NT + tid;
+            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = tot[jc][k];
+        }
+    }
+}
 
 // Sum of pair terms over visits [s_begin, s_end) for the point tile starting at point
 // tile0 and TCH snapshots:  partial[jc * part_stride + p] = sum_{i < na[jc]} term(p, i, jc)
@@ -186,7 +358,6 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
              const int *__restrict__ nact, const int4 *__restrict__ items, int n_tg, int sb,
              double *__restrict__ partial) {
     constexpr int TCH = Cfg::kTCH;
-    __shared__ TileSmem<Cfg, TCH> sm;
     const int4 item = items[blockIdx.x];
     const int j0 = item.y * TCH;
     int na[TCH];
@@ -198,9 +369,17 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
     }
     const int s_begin = item.z * sb;
     const int s_end = min(s_begin + sb, nmax);
-    field_tile<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, (int64_t)item.x * (Cfg::kThreads * Cfg::kPPT),
-                         rec + (int64_t)j0 * rec_stride, rec_stride, na, min(TCH, n_tg - j0), s_begin,
-                         s_end, partial + ((int64_t)item.z * n_tg + j0) * n_pts, n_pts);
+    const int64_t tile0 = (int64_t)item.x * (Cfg::kThreads * Cfg::kPPT);
+    double *part = partial + ((int64_t)item.z * n_tg + j0) * n_pts;
+    if constexpr (std::is_same<typename Cfg::Real, float>::value) {
+        __shared__ TileSmemMixed<Cfg, TCH> sm;
+        field_tile_mixed<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rec + (int64_t)j0 * rec_stride, rec_stride,
+                                   na, min(TCH, n_tg - j0), s_begin, s_end, part, n_pts);
+    } else {
+        __shared__ TileSmem<Cfg, TCH> sm;
+        field_tile<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rec + (int64_t)j0 * rec_stride, rec_stride, na,
+                             min(TCH, n_tg - j0), s_begin, s_end, part, n_pts);
+    }
 }
 
 }  // namespace ddk
