@@ -121,9 +121,11 @@ dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy_m, int64_t
 /* Dwell-start dose of every visit: the field at the probe's own position when
    its dwell starts, from the visits before it,
      out[j] = psi_{j-1}(r_j, t_j) = sum_{i<j} phi_i(r_j, t_j)   (Eq. 5 at r_j, t_j)
-   in visit order.  out: host or device, n_visits doubles.  The current build
-   needs a uniform dwell without flyback (t_k = k*tau); otherwise DD_ENOTSUP.
-   Errors: DD_EINVAL, DD_ENOTSUP, DD_ENOMEM, DD_ECUDA. */
+   in visit order.  out: host or device, n_visits doubles.  With a uniform dwell and no
+   flyback (t_k = k*tau) the pair coefficients depend on the lag j - i only and come
+   from a table of n_visits records; otherwise (per-visit dwells, flyback) they are
+   formed per pair in FP64, which costs more per pair.
+   Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
 dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, double *out,
                             void *cuda_stream);
 
@@ -180,11 +182,66 @@ dd_status dd_batch_info(const dd_batch *batch, int64_t *n_items, int64_t *pair_t
 void dd_batch_destroy(dd_batch *batch);
 
 /* Free a scan and its per-device caches (device caches are freed on their own
-   devices).  NULL is a no-op.  The scan must not be in use by an enqueued call. */
+   devices).  NULL, or a handle that was already destroyed, is a no-op.  The scan must
+   not be in use by an enqueued call.
+   Testing hook: with the environment variable DD_FAULT=alloc, the field workspace
+   allocation reports cudaErrorMemoryAllocation (the call returns DD_ENOMEM). */
 void dd_destroy(dd_scan *scan);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *dd_last_error(void);
+
+/* ---- Learned surrogate of the field map (no counterpart in the paper) ----------------
+   Building blocks of a small convolutional network that maps input planes of a scan
+   (visit-time map, visited mask, standardised log D and log dwell) to the final
+   log-damage map; it is trained on fields from the batched exact path, which also
+   serves as its fallback.  All tensors are device memory, NHWC, BF16 unless noted;
+   weights are [cout][3*3][cin] BF16 (tap = ky*3 + kx).  W must be a multiple of 64;
+   (cin, cout) in {(16,32), (32,32), (32,16), (16,16)}.  Calls enqueue on cuda_stream.
+
+   dd_sur_conv3x3: 3x3 convolution with dilation d in 1..32 (tap (ky, kx) reads the input
+   at (y + (ky-1) d, x + (kx-1) d)), zero "same" padding, implicit GEMM on the tensor
+   cores (BF16 x BF16 -> FP32).  epilogue 0: out = bf16(relu(z + bias)) [B,H,W,cout];
+   1: out = float(z + bias) of channel 0 only [B,H,W]; 2: out = bf16(z * (mask > 0))
+   with mask [B,H,W,cout] (the data gradient through a ReLU, using the flipped weights
+   that dd_sur_adam writes; bias unused).
+   dd_sur_wgrad: grad[cout*9*cin + cout] (FP32) = weight gradient [cout][9][cin] followed
+   by the bias gradient of the dilation-d convolution, from layer input x [B,H,W,cin] and output gradient dz
+   [B,H,W,cout]; part (FP32, part_floats >= 608 * (cout*9*cin + cout)) holds per-CTA
+   partial sums, reduced in a fixed order.
+   dd_sur_mse: loss_sum[0] (FP64, device) = sum (pred - target)^2 over n elements, and
+   dz [n][16] BF16 = (2 (pred - target) / n, 0, ..., 0); block_sums: ceil(n/256) doubles.
+   dd_sur_adam: Adam (bias-corrected, step >= 1) on FP32 param with grad, moments m, v;
+   when w_bf16 is given also writes the BF16 copy and the flipped copy [cin][8-tap][cout].
+   dd_sur_planes: x [B,H,W,16] BF16 from tmap [B,H,W] (visit time / total scan time,
+   < 0 where not visited) and scal [B][2] (standardised log D, log dwell).
+   dd_sur_targets: out [n_maps*hw] FP32 = (log10(max(f, peak * 10^floor_rel_log10)) - mu)
+   / sigma with f = psi*scale[map] and peak = max of f over the map (floor_rel_log10 < 0):
+   the network's normalised target from exact fields psi [n_maps*hw] (u/m^2, FP64) and
+   per-map scale[] = 4 pi D / Q0 (the dimensionless field).
+   dd_sur_fields: psi [n_maps*hw] (u/m^2, FP64) = 10^(pred*sigma + mu) / scale[map].
+   dd_sur_spot_error: err[m] = relative L2 error over k spot points of map m between the
+   field of pred [n_maps][hw] and exact [n_maps][k] (u/m^2) at canvas indices idx [n_maps][k]. */
+dd_status dd_sur_conv3x3(const void *in, const void *w, const float *bias, const void *mask, void *out,
+                         int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dilation,
+                         int32_t epilogue, void *cuda_stream);
+dd_status dd_sur_wgrad(const void *x, const void *dz, int32_t B, int32_t H, int32_t W, int32_t cin,
+                       int32_t cout, int32_t dilation, float *part, int64_t part_floats, float *grad,
+                       void *cuda_stream);
+dd_status dd_sur_mse(const float *pred, const float *target, int64_t n, void *dz, double *block_sums,
+                     double *loss_sum, void *cuda_stream);
+dd_status dd_sur_adam(float *param, const float *grad, float *m, float *v, int64_t n, float lr,
+                      float beta1, float beta2, float eps, int32_t step, void *w_bf16,
+                      void *w_flip_bf16, int32_t cin, int32_t cout, void *cuda_stream);
+dd_status dd_sur_planes(const float *tmap, const float *scal, int32_t B, int32_t H, int32_t W, void *x,
+                        void *cuda_stream);
+dd_status dd_sur_targets(const double *psi, const double *scale, int64_t n_maps, int64_t hw,
+                         double floor_rel_log10, float mu, float sigma, float *out, void *cuda_stream);
+dd_status dd_sur_fields(const float *pred, const double *scale, int64_t n_maps, int64_t hw, float mu,
+                        float sigma, double *psi, void *cuda_stream);
+dd_status dd_sur_spot_error(const float *pred, const int32_t *idx, const double *exact,
+                            const double *scale, int32_t n_maps, int32_t hw, int32_t k, float mu,
+                            float sigma, double *err, void *cuda_stream);
 
 /* Tracing (no counterpart in the paper): per-kernel device time of this library's
    own launches.  While enabled, each launch is bracketed by two CUDA events on its

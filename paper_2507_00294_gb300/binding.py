@@ -71,6 +71,19 @@ def load(build_if_missing=True):
         getattr(lib, name).restype = ctypes.c_int
     lib.dd_batch_destroy.argtypes = [_VP]
     lib.dd_batch_destroy.restype = None
+    i32 = ctypes.c_int32
+    lib.dd_sur_conv3x3.argtypes = [_VP, _VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, _VP]
+    lib.dd_sur_wgrad.argtypes = [_VP, _VP, i32, i32, i32, i32, i32, i32, _VP, _I64, _VP, _VP]
+    lib.dd_sur_mse.argtypes = [_VP, _VP, _I64, _VP, _VP, _VP, _VP]
+    lib.dd_sur_adam.argtypes = [_VP, _VP, _VP, _VP, _I64, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, i32, _VP, _VP, i32, i32, _VP]
+    lib.dd_sur_planes.argtypes = [_VP, _VP, i32, i32, i32, _VP, _VP]
+    lib.dd_sur_targets.argtypes = [_VP, _VP, _I64, _I64, ctypes.c_double, ctypes.c_float, ctypes.c_float, _VP, _VP]
+    lib.dd_sur_fields.argtypes = [_VP, _VP, _I64, _I64, ctypes.c_float, ctypes.c_float, _VP, _VP]
+    lib.dd_sur_spot_error.argtypes = [_VP, _VP, _VP, _VP, i32, i32, i32, ctypes.c_float, ctypes.c_float, _VP, _VP]
+    for name in ("dd_sur_conv3x3", "dd_sur_wgrad", "dd_sur_mse", "dd_sur_adam", "dd_sur_planes",
+                 "dd_sur_targets", "dd_sur_fields", "dd_sur_spot_error"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.dd_profile_enable.argtypes = [ctypes.c_int32]
     lib.dd_profile_reset.argtypes = []
     lib.dd_profile_read.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
@@ -173,6 +186,21 @@ class Scan:
 
     def __del__(self):
         self.close()
+
+
+def multi_frame_spec(spec, frames):
+    """Multi-frame acquisition (Sec. 1): the scan's own visit order repeated `frames` times
+    with the dwell divided by `frames`, as a custom-order scan description."""
+    from dataclasses import replace
+    if frames < 1:
+        raise ValueError("frames must be >= 1")
+    g, _, tau = Scan(spec).visits()
+    if spec.dwell_per_visit is not None:
+        per = np.tile(np.asarray(tau) / frames, frames)
+    else:
+        per = None
+    return replace(spec, order=DD_CUSTOM, custom_visit=np.tile(g, frames), keep_fraction=1.0, mask=None,
+                   dwell_s=spec.dwell_s / frames, dwell_per_visit=per, flyback_s=0.0)
 
 
 def dd_create_scan(spec):
@@ -290,6 +318,70 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def _dp(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _cs(stream, t):
+    import torch
+    if stream is not None:
+        return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def dd_sur_conv3x3(x, w, bias, mask, out, epilogue, dilation=1, stream=None):
+    """x [B,H,W,cin] bf16, w [cout,9,cin] bf16 -> out (see include/dd.h)."""
+    B, H, W, cin = x.shape
+    cout = w.shape[0]
+    _check(load().dd_sur_conv3x3(_dp(x), _dp(w), _dp(bias), _dp(mask), _dp(out), B, H, W, cin, cout,
+                                 int(dilation), int(epilogue), _cs(stream, x)), "dd_sur_conv3x3")
+    return out
+
+
+def dd_sur_wgrad(x, dz, part, grad, dilation=1, stream=None):
+    B, H, W, cin = x.shape
+    cout = dz.shape[3]
+    _check(load().dd_sur_wgrad(_dp(x), _dp(dz), B, H, W, cin, cout, int(dilation), _dp(part), part.numel(),
+                               _dp(grad), _cs(stream, x)), "dd_sur_wgrad")
+    return grad
+
+
+def dd_sur_mse(pred, target, dz, block_sums, loss_sum, stream=None):
+    _check(load().dd_sur_mse(_dp(pred), _dp(target), pred.numel(), _dp(dz), _dp(block_sums), _dp(loss_sum),
+                             _cs(stream, pred)), "dd_sur_mse")
+
+
+def dd_sur_adam(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, w_bf16=None, w_flip=None,
+                cin=0, cout=0, stream=None):
+    _check(load().dd_sur_adam(_dp(param), _dp(grad), _dp(m), _dp(v), param.numel(), lr, beta1, beta2, eps,
+                              int(step), _dp(w_bf16), _dp(w_flip), cin, cout, _cs(stream, param)), "dd_sur_adam")
+
+
+def dd_sur_planes(tmap, scal, x, stream=None):
+    B, H, W = tmap.shape
+    _check(load().dd_sur_planes(_dp(tmap), _dp(scal), B, H, W, _dp(x), _cs(stream, tmap)), "dd_sur_planes")
+    return x
+
+
+def dd_sur_targets(psi, scale, n_maps, hw, floor_rel_log10, mu, sigma, out, stream=None):
+    _check(load().dd_sur_targets(_dp(psi), _dp(scale), n_maps, hw, floor_rel_log10, mu, sigma, _dp(out),
+                                 _cs(stream, psi)), "dd_sur_targets")
+    return out
+
+
+def dd_sur_fields(pred, scale, n_maps, hw, mu, sigma, psi, stream=None):
+    _check(load().dd_sur_fields(_dp(pred), _dp(scale), n_maps, hw, mu, sigma, _dp(psi), _cs(stream, pred)),
+           "dd_sur_fields")
+    return psi
+
+
+def dd_sur_spot_error(pred, idx, exact, scale, n_maps, hw, k, mu, sigma, err, stream=None):
+    _check(load().dd_sur_spot_error(_dp(pred), _dp(idx), _dp(exact), _dp(scale), n_maps, hw, k, mu, sigma,
+                                    _dp(err), _cs(stream, pred)), "dd_sur_spot_error")
+    return err
 
 
 def dd_profile_enable(on=True):

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libdd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dd_scan.cpp", "dd_profile.cpp", "dd_field.cu", "dd_dose.cu", "dd_batch.cu"]
+SOURCES = ["dd_scan.cpp", "dd_profile.cpp", "dd_field.cu", "dd_dose.cu", "dd_batch.cu", "dd_surrogate.cu"]
 
 
 def nvcc():

@@ -12,6 +12,16 @@ namespace ddk {
 // J_m = 1/m - J_{m-1}/r (forward) is stable for r >= 1.  For r < 1 the same recurrence
 // is run downward from J_M, which comes from the positive series
 //   J_M = rho sum_k rho^k B(M+1, k+1),  rho = r/(1+r)  (expand 1/(1+rs) about s = 1).
+// 1/n for n = 0..95 (entry 0 unused), exact to FP64 rounding.
+struct RecipTable {
+    double v[96];
+    constexpr RecipTable() : v() {
+        for (int n = 1; n < 96; ++n) v[n] = 1.0 / n;
+    }
+};
+static __device__ __constant__ RecipTable kRecipTable = RecipTable();
+#define kRecip kRecipTable.v
+
 template <int M>
 __device__ void moment_coefficients(double r, double ell, double *c) {
     double J[M + 1];
@@ -19,25 +29,26 @@ __device__ void moment_coefficients(double r, double ell, double *c) {
         const double ir = 1.0 / r;
         J[0] = ell;
 #pragma unroll
-        for (int m = 1; m <= M; ++m) J[m] = 1.0 / m - J[m - 1] * ir;
+        for (int m = 1; m <= M; ++m) J[m] = kRecip[m] - J[m - 1] * ir;
     } else {
         const double rho = r / (1.0 + r);
-        double term = rho / (M + 1), sum = 0.0;
-        for (int k = 1; k < 2000; ++k) {
+        double term = rho * kRecip[M + 1], sum = 0.0;
+        // rho < 1/2 here, so the terms shrink at least geometrically: 64 suffice
+        for (int k = 1; k < 64; ++k) {
             sum += term;
-            term *= rho * k / (double)(M + 1 + k);
+            term *= rho * k * kRecip[M + 1 + k];
             if (term <= 1e-18 * sum) break;
         }
         J[M] = sum;
 #pragma unroll
-        for (int m = M; m >= 1; --m) J[m - 1] = r * (1.0 / m - J[m]);
+        for (int m = M; m >= 1; --m) J[m - 1] = r * (kRecip[m] - J[m]);
         J[0] = ell;
     }
     double inv_fact = 1.0;
 #pragma unroll
     for (int m = 0; m <= M; ++m) {
         c[m] = (m & 1) ? -J[m] * inv_fact : J[m] * inv_fact;
-        inv_fact /= (double)(m + 1);
+        inv_fact *= kRecip[m + 1];
     }
 }
 

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "dd_coef.cuh"
@@ -74,6 +75,40 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
         for (int c = 0; c < cnt; ++c) {
             const int k = kk + c;
             const Rec &R = s_rec[c];
+            if constexpr (std::is_same<Real, float>::value) {
+                // FP32: one polynomial degree for the whole warp, from the largest h and
+                // the smallest a over its lanes (the same classes as the field kernel)
+                float r2[PPT];
+                bool ok[PPT];
+                uint32_t cls = kCodeSkip;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    const int64_t i = jt[q] - k;
+                    ok[q] = i >= 0 && jt[q] < n;
+                    const float dx = ok[q] ? px[q] - s_x[i - w0] : 0.f;
+                    const float dy = ok[q] ? py[q] - s_y[i - w0] : 0.f;
+                    r2[q] = dx * dx + dy * dy;
+                    const float h = r2[q] * R.dq, a = r2[q] * R.q1;
+                    const uint32_t cq = !ok[q] || a >= 87.0f ? kCodeSkip
+                                      : h <= kDeg2H ? kCodeD2 : h <= kDeg4H ? kCodeD4
+                                      : h <= kHMaxF ? kCodeD8 : kCodeGeneral;
+                    cls = max(cls, cq);
+                }
+                cls = __reduce_max_sync(0xffffffffu, cls);
+                if (cls == kCodeSkip) continue;
+                const float4 *rv = reinterpret_cast<const float4 *>(&R);
+                const float4 q0 = rv[0], q1 = rv[1], q2 = rv[2];
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    float t;
+                    if (cls == kCodeD2) t = ex2_approx(r2[q] * q0.x) * moment_poly<2>(q0, q1, q2, r2[q] * q0.y);
+                    else if (cls == kCodeD4) t = ex2_approx(r2[q] * q0.x) * moment_poly<4>(q0, q1, q2, r2[q] * q0.y);
+                    else if (cls == kCodeD8) t = ex2_approx(r2[q] * q0.x) * moment_poly<8>(q0, q1, q2, r2[q] * q0.y);
+                    else t = pair_term(r2[q], R);
+                    acc[q] += ok[q] ? t : 0.f;
+                }
+                continue;
+            }
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
                 const int64_t i = jt[q] - k;
@@ -93,6 +128,52 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
 #pragma unroll
     for (int q = 0; q < PPT; ++q)
         if (jt[q] < n) partial[(int64_t)item.y * n + jt[q]] = tot[q];
+}
+
+// Dose for arbitrary visit timing (per-visit dwells, flyback): the pair (i, j) has its
+// own elapsed time t_j - t_i, so its coefficients are formed per pair in FP64 from the
+// same formulas as the (snapshot, visit) records (pair_geometry, moment_coefficients)
+// and evaluated with the precision's pair_term.  One thread per target j; the visits
+// before the CTA's last target are staged through shared memory in visit order.
+template <typename Cfg>
+__global__ void __launch_bounds__(128)
+dose_general_kernel(const double *__restrict__ src, int64_t n, double s, double kappa,
+                    double *__restrict__ out_partial) {
+    using Rec = typename Cfg::Rec;
+    using Real = typename Cfg::Real;
+    constexpr int TILE = 64;
+    __shared__ double s_x[TILE], s_y[TILE], s_t[TILE], s_tau[TILE];
+    const double *X = src, *Y = src + n, *T = src + 2 * n, *TAU = src + 3 * n;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j_last = min(n, (int64_t)(blockIdx.x + 1) * blockDim.x) - 1;
+    const bool live = j < n;
+    const double xj = live ? X[j] : 0.0, yj = live ? Y[j] : 0.0, tj = live ? T[j] : 0.0;
+    double tot = 0.0;
+    for (int64_t i0 = 0; i0 < j_last; i0 += TILE) {
+        const int cnt = (int)min((int64_t)TILE, j_last - i0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            s_x[q] = X[i0 + q]; s_y[q] = Y[i0 + q]; s_t[q] = T[i0 + q]; s_tau[q] = TAU[i0 + q];
+        }
+        __syncthreads();
+        Real acc = 0;
+        for (int q = 0; q < cnt; ++q) {
+            if (!live || i0 + q >= j) break;
+            double q1, dq, r, ell;
+            pair_geometry(tj - s_t[q], s_tau[q], s, kappa, q1, dq, r, ell);
+            Rec R;
+            RecTraits<Rec>::fill(R, q1, dq, r, ell);
+            const Real dx = (Real)(xj - s_x[q]), dy = (Real)(yj - s_y[q]);
+            acc += pair_term(dx * dx + dy * dy, R);
+        }
+        tot += (double)acc;
+    }
+    if (live) out_partial[j] = tot;
+}
+
+__global__ void scale_kernel(const double *__restrict__ v, int64_t n, double pref, double *__restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = pref * v[j];
 }
 
 __global__ void dose_reduce_kernel(const double *__restrict__ partial, int64_t n, int tile, int lb,
@@ -183,15 +264,49 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     return DD_OK;
 }
 
+template <typename Cfg>
+dd_status run_dose_general(const dd_scan *scan, double *out, cudaStream_t stream) {
+    const int64_t n = scan->n;
+    const bool out_host = !dd::is_device_pointer(out);
+    dd_status st = DD_OK;
+    const double *src = dd::device_sources(scan, &st);
+    if (!src) return st;
+    void *ws = nullptr;
+    const size_t bytes = (size_t)n * sizeof(double) * (out_host ? 2 : 1) + 512;
+    cudaError_t err = cudaMallocAsync(&ws, bytes, stream);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return dd::fail(err == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,
+                        std::string("cudaMallocAsync(dose workspace): ") + cudaGetErrorString(err));
+    }
+    double *sums = (double *)ws;
+    double *out_dev = out_host ? sums + n : out;
+    DD_PROFILED(Cfg::kDoseName, stream,
+                (ddk::dose_general_kernel<Cfg><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(
+                    src, n, scan->s, scan->kappa, sums)));
+    DD_CUDA_TRY(cudaGetLastError());
+    DD_PROFILED("dose_scale", stream,
+                (ddk::scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sums, n, scan->pref, out_dev)));
+    DD_CUDA_TRY(cudaGetLastError());
+    if (out_host)
+        DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    DD_CUDA_TRY(cudaFreeAsync(ws, stream));
+    if (out_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    return DD_OK;
+}
+
 }  // namespace
 
 extern "C" dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, double *out, void *cuda_stream) {
     dd::clear_error();
     if (!scan || !out) return dd::fail(DD_EINVAL, "dd_per_probe_dose: NULL argument");
     if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_per_probe_dose: unknown precision");
-    if (!scan->uniform)
-        return dd::fail(DD_ENOTSUP, "dd_per_probe_dose: needs a uniform dwell without flyback");
     cudaStream_t stream = (cudaStream_t)cuda_stream;
+    if (!scan->uniform) {
+        // per-visit dwells or flyback: no lag table, coefficients per pair
+        if (prec == DD_MIXED) return run_dose_general<ddk::CfgMixed>(scan, out, stream);
+        return run_dose_general<ddk::CfgF64>(scan, out, stream);
+    }
     if (prec == DD_MIXED) return run_dose<ddk::CfgMixed>(scan, out, stream);
     return run_dose<ddk::CfgF64>(scan, out, stream);
 }

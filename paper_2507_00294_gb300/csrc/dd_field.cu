@@ -128,7 +128,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     while (group > Cfg::kTCH &&
            (size_t)group * n_src * sizeof(Rec) + (size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget)
         group = std::max(Cfg::kTCH, group / 2);
-    while ((size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget && sb < (1 << 20)) sb *= 2;
+    // larger blocks only while the FP32 stage sums stay short (<= 32 stages of 64 visits)
+    while ((size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget && sb < 2048) sb *= 2;
     const int nblk_max = (int)((n_src + sb - 1) / sb);
     const int n_chunks_max = (group + Cfg::kTCH - 1) / Cfg::kTCH;
 
@@ -137,7 +138,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     const double *src = dd::device_sources(scan, &st);
     if (!src) return st;
     void *ws = nullptr;
-    cudaError_t err = cudaMallocAsync(&ws, ws_bytes, stream);
+    cudaError_t err = dd::fault_injected("alloc") ? cudaErrorMemoryAllocation
+                                                  : cudaMallocAsync(&ws, ws_bytes, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return dd::fail(err == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,

@@ -101,6 +101,8 @@ struct TileSmem {
 // no per-lane test is needed on the polynomial paths.
 constexpr float kDeg2H = 6.0e-3f, kDeg4H = 8.2e-2f;
 enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeGeneral = 4 };
+// per (warp, visit): all snapshots skipped / all on degree 2 / all on degree <= 4 / mixed
+enum : uint32_t { kModeSkip = 0, kModeAllD2 = 1, kModeAllD4 = 2, kModePerSnapshot = 3 };
 
 template <int D>
 __device__ __forceinline__ float moment_poly(const float4 &r0, const float4 &r1, const float4 &r2, float h) {
@@ -163,12 +165,15 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     __syncthreads();                       // previous item's readers of sm.box are done
     if (lane == 0) sm.box[warp] = make_float4(bx0, bx1, by0, by1);
 
-    float acc[TCH][PPT];
-    double tot[TCH][PPT];
+    // per (snapshot, point): FP32 sum of the current 64-visit stage, added after each
+    // stage to an FP32 running sum (8 stages per item at the default block of 512 visits,
+    // at most 32 with the largest block the dispatcher picks, so that sum adds at most
+    // 32 u = 2e-6 relative error), converted to FP64 at the end of the item.
+    float acc[TCH][PPT], ks[TCH][PPT];
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc)
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) { acc[jc][k] = 0.0f; tot[jc][k] = 0.0; }
+        for (int k = 0; k < PPT; ++k) { acc[jc][k] = 0.0f; ks[jc][k] = 0.0f; }
 
     for (int s0 = s_begin; s0 < s_end; s0 += STILE) {
         const int cnt = min(STILE, s_end - s0);
@@ -197,10 +202,13 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             // rounding margin on the bounds of rho^2
             const float r2max = (dx1 * dx1 + dy1 * dy1) * 1.0001f + 1e-6f;
             const float r2min = (dx0 * dx0 + dy0 * dy0) * 0.9999f;
-            uint32_t word = 0;
+            uint32_t word = 0, cmin = kCodeGeneral, cmax = kCodeSkip;
+            bool any = false;
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
-                uint32_t c = kCodeSkip;
+                // a snapshot for which this visit has not started has a zero record, which
+                // the degree-2 path turns into an exact 0
+                uint32_t c = kCodeD2;
                 if (s0 + i < na[jc]) {
                     const float4 head = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0 + i)[0];
                     const float hmax = r2max * head.y, amin = r2min * head.z;
@@ -208,15 +216,23 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                       : hmax <= kDeg2H ? kCodeD2
                       : hmax <= kDeg4H ? kCodeD4
                       : hmax <= kHMaxF ? kCodeD8 : kCodeGeneral;
+                    any = any || c != kCodeSkip;
                 }
+                cmin = min(cmin, c);
+                cmax = max(cmax, c);
                 word |= c << (8 * jc);
             }
-            sm.code[w][i] = word;
+            // bits 28..31: how the whole visit is handled for this warp
+            const uint32_t mode = !any ? kModeSkip
+                                : (cmin >= kCodeD2 && cmax == kCodeD2) ? kModeAllD2
+                                : (cmin >= kCodeD2 && cmax == kCodeD4) ? kModeAllD4 : kModePerSnapshot;
+            sm.code[w][i] = (word & 0x0fffffffu) | (mode << 28);
         }
         __syncthreads();
         for (int s = 0; s < cnt; ++s) {
             const uint32_t word = sm.code[warp][s];
-            if (word == 0) continue;                       // warp-uniform skip
+            const uint32_t mode = word >> 28;
+            if (mode == kModeSkip) continue;               // warp-uniform skip
             const float sx = sm.x[s], sy = sm.y[s];
             float r2[PPT];
 #pragma unroll
@@ -224,18 +240,38 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 const float dx = px[k] - sx, dy = py[k] - sy;
                 r2[k] = fmaf(dx, dx, dy * dy);
             }
+            if (mode == kModeAllD2 || mode == kModeAllD4) {
+                // every snapshot of the chunk on one low-degree polynomial: one straight
+                // block of TCH x PPT independent terms
+                if (mode == kModeAllD2) {
+#pragma unroll
+                    for (int jc = 0; jc < TCH; ++jc) {
+                        const float4 *rv = reinterpret_cast<const float4 *>(&sm.rec[jc][s]);
+                        const float4 a0 = rv[0], a1 = rv[1];
+                        moment_pass<2, PPT>(acc[jc], r2, a0, a1, a1);
+                    }
+                } else {
+#pragma unroll
+                    for (int jc = 0; jc < TCH; ++jc) {
+                        const float4 *rv = reinterpret_cast<const float4 *>(&sm.rec[jc][s]);
+                        const float4 a0 = rv[0], a1 = rv[1];
+                        moment_pass<4, PPT>(acc[jc], r2, a0, a1, a1);
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
-                const uint32_t c = (word >> (8 * jc)) & 0xffu;
+                const uint32_t c = (word >> (8 * jc)) & 0xfu;
                 if (c == kCodeSkip) continue;
                 const float4 *rv = reinterpret_cast<const float4 *>(&sm.rec[jc][s]);
-                const float4 q0 = rv[0], q1 = rv[1], q2 = rv[2];
+                const float4 q0 = rv[0], q1 = rv[1];
                 if (c == kCodeD2) {
-                    moment_pass<2, PPT>(acc[jc], r2, q0, q1, q2);
+                    moment_pass<2, PPT>(acc[jc], r2, q0, q1, q1);
                 } else if (c == kCodeD4) {
-                    moment_pass<4, PPT>(acc[jc], r2, q0, q1, q2);
+                    moment_pass<4, PPT>(acc[jc], r2, q0, q1, q1);
                 } else if (c == kCodeD8) {
-                    moment_pass<8, PPT>(acc[jc], r2, q0, q1, q2);
+                    moment_pass<8, PPT>(acc[jc], r2, q0, q1, rv[2]);
                 } else {
                     const RecF32 &R = sm.rec[jc][s];
 #pragma unroll
@@ -246,7 +282,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc)
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) { tot[jc][k] += (double)acc[jc][k]; acc[jc][k] = 0.0f; }
+            for (int k = 0; k < PPT; ++k) { ks[jc][k] += acc[jc][k]; acc[jc][k] = 0.0f; }
     }
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc) {
@@ -254,7 +290,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int64_t p = tile0 + k * NT + tid;
-            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = tot[jc][k];
+            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = (double)ks[jc][k];
         }
     }
 }

@@ -49,6 +49,15 @@ const double *device_sources(const dd_scan *scan, dd_status *st);
 // True if `p` is device-accessible memory of the current device.
 bool is_device_pointer(const void *p);
 
+// Host-side fault injection for tests: true when the environment variable DD_FAULT
+// names `site` (e.g. DD_FAULT=alloc makes the next workspace allocations fail as if
+// the device were out of memory).  No device fault is ever produced.
+bool fault_injected(const char *site);
+
+// Registry of live scan handles (guards dd_destroy against double frees).
+void register_scan(dd_scan *s);
+bool unregister_scan(dd_scan *s);
+
 // Kernel timing scope (dd_profile.cpp): records an event pair around the launch
 // made inside the scope when profiling is enabled, nothing otherwise.
 class ProfScope {

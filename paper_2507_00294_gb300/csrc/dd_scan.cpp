@@ -7,8 +7,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <unordered_set>
 
 #include "dd_internal.h"
 
@@ -27,6 +29,24 @@ dd_status fail_cuda(cudaError_t err, const char *what) {
 }
 
 void clear_error() { g_last_error.clear(); }
+
+bool fault_injected(const char *site) {
+    const char *v = std::getenv("DD_FAULT");
+    return v && std::strcmp(v, site) == 0;
+}
+
+static std::mutex g_scans_mu;
+static std::unordered_set<dd_scan *> g_scans;
+
+void register_scan(dd_scan *s) {
+    std::lock_guard<std::mutex> lock(g_scans_mu);
+    g_scans.insert(s);
+}
+
+bool unregister_scan(dd_scan *s) {
+    std::lock_guard<std::mutex> lock(g_scans_mu);
+    return g_scans.erase(s) == 1;
+}
 
 bool is_device_pointer(const void *p) {
     cudaPointerAttributes attr;
@@ -240,6 +260,7 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         delete s;
         return dd::fail(DD_ENOMEM, "dd_create_scan: out of host memory");
     }
+    dd::register_scan(s);
     *out = s;
     return DD_OK;
 }
@@ -262,7 +283,7 @@ dd_status dd_scan_visits(const dd_scan *scan, int32_t *grid_index, double *t_sta
 }
 
 void dd_destroy(dd_scan *scan) {
-    if (!scan) return;
+    if (!scan || !dd::unregister_scan(scan)) return;     // NULL or already destroyed
     int prev = -1;
     cudaGetDevice(&prev);
     for (auto &c : scan->dev) {

@@ -104,24 +104,41 @@ def precision_study(order, d_index, seed=3):
                     name="grid256_%s_D%.2e" % (ORDER_NAMES[order], s.D_m2s))
 
 
-def batched_scans(n_scans=512, seed=4, n_min=32, n_max=128):
-    """Uneven batch: n ~ U{n_min..n_max}; D log-uniform [1e-15, 1e-12]; dwell log-uniform
-    [1e-7, 1e-5] s; sigma ~ U[0.05, 0.2] nm; keep fraction f ~ U[0.1, 1] of the positions,
-    visited in seeded random order; field on the n x n probe grid at the end of the scan."""
+def batched_specs(n_scans=512, seed=4, n_min=32, n_max=128):
+    """Scan descriptions of the uneven batch: n ~ U{n_min..n_max}; D log-uniform
+    [1e-15, 1e-12] m^2/s; dwell log-uniform [1e-7, 1e-5] s; sigma ~ U[0.05, 0.2] nm; keep
+    fraction f ~ U[0.1, 1] of the positions, visited in seeded random order."""
     rng = np.random.default_rng(seed)
-    jobs = []
+    specs = []
     for k in range(n_scans):
         n = int(rng.integers(n_min, n_max + 1))
         D = float(10.0 ** rng.uniform(-15.0, -12.0))
         tau = float(10.0 ** rng.uniform(-7.0, -5.0))
         sigma = float(rng.uniform(0.05e-9, 0.2e-9))
         f = float(rng.uniform(0.1, 1.0))
-        s = ScanSpec(n, n, sigma_m=sigma, D_m2s=D, dwell_s=tau, order=RANDOM,
-                     seed=seed * 100003 + k, keep_fraction=f)
+        specs.append(ScanSpec(n, n, sigma_m=sigma, D_m2s=D, dwell_s=tau, order=RANDOM,
+                              seed=seed * 100003 + k, keep_fraction=f))
+    return specs
+
+
+def batched_scans(n_scans=512, seed=4, n_min=32, n_max=128):
+    """The uneven batch of batched_specs, each evaluated on its n x n probe grid at the
+    end of its scan."""
+    jobs = []
+    for k, s in enumerate(batched_specs(n_scans, seed, n_min, n_max)):
         nv = n_visits(s)
-        jobs.append(FieldJob(s, grid_points(n, s.pitch_m), np.array([nv * tau]),
-                             name="batch%03d_n%d" % (k, n)))
+        jobs.append(FieldJob(s, grid_points(s.nx, s.pitch_m), np.array([nv * s.dwell_s]),
+                             name="batch%03d_n%d" % (k, s.nx)))
     return jobs
+
+
+def live_mode(n, frame_s, dwell_s=DWELL):
+    """n x n raster, field on the probe grid at every frame time across the scan (the
+    runtime-vs-probe-count setting of Fig. 2: frame time delta_t, pixel = probe pitch)."""
+    s = ScanSpec(n, n, dwell_s=dwell_s)
+    end = n * n * dwell_s
+    times = np.arange(1, int(np.floor(end / frame_s + 1e-9)) + 1, dtype=np.float64) * frame_s
+    return FieldJob(s, grid_points(n, s.pitch_m), times, name="live%dx%d_frame%.0eus" % (n, n, frame_s * 1e6))
 
 
 def sample_pairs(n_pts, n_t, count, seed):

@@ -108,4 +108,14 @@ def test_null_and_size_arguments_rejected_without_gpu():
     assert lib.dd_field_at_times(s.handle, None, 0, None, 0, 1, None, None) == b.DD_OK
     assert lib.dd_per_probe_dose(s.handle, 5, out.ctypes.data, None) == b.DD_EINVAL
     fb = b.Scan(w.ScanSpec(3, 3, flyback_s=1e-7))
-    assert lib.dd_per_probe_dose(fb.handle, 1, out.ctypes.data, None) == b.DD_ENOTSUP
+    # the allocation-free dose keeps to uniform dwells (checked before any device work)
+    assert lib.dd_per_probe_dose_noalloc(fb.handle, 1, out.ctypes.data, None) == b.DD_ENOTSUP
+
+
+def test_double_destroy_is_harmless():
+    lib = b.load()
+    s = b.Scan(w.ScanSpec(3, 3))
+    h = s.handle
+    lib.dd_destroy(h)
+    lib.dd_destroy(h)             # second call finds no live handle: no-op
+    s.handle = None

@@ -14,29 +14,31 @@ def rand_params(rng, chans):
             for ci, co in zip(chans[:-1], chans[1:])]
 
 
-def test_conv_forward_matches_torch():
-    rng = np.random.default_rng(0)
+@pytest.mark.parametrize("dil", [1, 2, 3])
+def test_conv_forward_matches_torch(dil):
+    rng = np.random.default_rng(dil)
     x = rng.standard_normal((2, 7, 9, 5))
     w = rng.standard_normal((3, 3, 3, 5))
     b = rng.standard_normal(3)
-    got = conv_ref.conv3x3(x, w, b)
+    got = conv_ref.conv3x3(x, w, b, dil)
     ref = torch.nn.functional.conv2d(torch.from_numpy(x).permute(0, 3, 1, 2),
                                      torch.from_numpy(w).permute(0, 3, 1, 2), torch.from_numpy(b),
-                                     padding=1).permute(0, 2, 3, 1).numpy()
+                                     padding=dil, dilation=dil).permute(0, 2, 3, 1).numpy()
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
 def test_network_gradients_match_autograd():
     rng = np.random.default_rng(1)
     chans = [4, 6, 6, 6, 6, 6, 1]
+    dils = [1, 2, 3, 1, 2, 1]
     params = rand_params(rng, chans)
-    x = rng.standard_normal((2, 6, 5, 4))
-    y = rng.standard_normal((2, 6, 5, 1))
-    loss, grads = conv_ref.loss_and_grads(params, x, y)
+    x = rng.standard_normal((2, 9, 8, 4))
+    y = rng.standard_normal((2, 9, 8, 1))
+    loss, grads = conv_ref.loss_and_grads(params, x, y, dils)
     tp = [(torch.tensor(w, requires_grad=True), torch.tensor(b, requires_grad=True)) for w, b in params]
     a = torch.from_numpy(x).permute(0, 3, 1, 2)
     for k, (w, b) in enumerate(tp):
-        a = torch.nn.functional.conv2d(a, w.permute(0, 3, 1, 2), b, padding=1)
+        a = torch.nn.functional.conv2d(a, w.permute(0, 3, 1, 2), b, padding=dils[k], dilation=dils[k])
         if k < len(tp) - 1:
             a = torch.relu(a)
     tl = ((a.permute(0, 2, 3, 1) - torch.from_numpy(y)) ** 2).mean()

@@ -44,3 +44,19 @@ def test_dose_grid256_sampled(cuda):
     assert_fp64(g64[targets], ref, "dose256 fp64")
     gm = gpu_dose(spec, "mixed")
     assert_mixed(gm[targets], ref, ref.max(), "dose256 mixed")
+
+
+@pytest.mark.parametrize("spec", [
+    w.ScanSpec(12, 9, flyback_s=2.5e-6),
+    w.ScanSpec(10, 10, order=w.SERPENTINE, flyback_s=4e-7, D_m2s=1e-12),
+    w.ScanSpec(9, 9, order=w.RANDOM, seed=12,
+               dwell_per_visit=10 ** np.random.default_rng(1).uniform(-7, -5, 81)),
+])
+def test_dose_general_timing(cuda, spec):
+    src = oracle_sources(spec)
+    ref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0)
+    g64 = gpu_dose(spec, "fp64")
+    assert g64[0] == 0.0
+    assert_fp64(g64, ref, "general dose fp64")
+    gm = gpu_dose(spec, "mixed")
+    assert_mixed(gm[1:], ref[1:], ref.max(), "general dose mixed")

@@ -96,3 +96,32 @@ def test_deterministic_repeat(cuda):
     a = gpu_field(job.scan, job.pts_xy, job.times[-4:], "mixed")
     c = gpu_field(job.scan, job.pts_xy, job.times[-4:], "mixed")
     np.testing.assert_array_equal(a, c)
+
+
+@pytest.mark.parametrize("order,d_index", [(w.RASTER, 0), (w.INTERLEAVED, 7), (w.SERPENTINE, 3), (w.RANDOM, 5)])
+def test_grid256_precision_study_sampled(cuda, order, d_index):
+    """256x256 scans, the four orders, D from the seeded log-uniform draws, the end of the
+    scan and 16x later (t >> tau): oracle at 160 seeded points per snapshot."""
+    job = w.precision_study(order, d_index)
+    rng = np.random.default_rng(100 + d_index)
+    ip = rng.choice(len(job.pts_xy), 160, replace=False)
+    it = np.repeat([0, 1], 80)
+    ref = oracle_pairs(job.scan, job.pts_xy, job.times, ip, it)
+    peak = peak_lower_bound(job.scan, job.times)
+    gm = gpu_field(job.scan, job.pts_xy, job.times, "mixed")
+    assert_mixed(gm[it, ip], ref, peak[it], "grid256 mixed")
+    if order == w.RASTER:
+        g64 = gpu_field(job.scan, job.pts_xy, job.times, "fp64")
+        assert_fp64(g64[it, ip], ref, "grid256 fp64")
+
+
+def test_allocation_failure_is_reported_and_recoverable(cuda, monkeypatch):
+    job = w.small_raster_16()
+    scan = b.Scan(job.scan)
+    monkeypatch.setenv("DD_FAULT", "alloc")
+    with pytest.raises(b.DDError) as e:
+        gpu_field(job.scan, job.pts_xy, job.times[:3], "mixed")
+    assert e.value.status == b.DD_ENOMEM
+    monkeypatch.delenv("DD_FAULT")
+    out = gpu_field(job.scan, job.pts_xy, job.times[:3], "mixed")
+    assert np.all(np.isfinite(out)) and out.max() > 0
