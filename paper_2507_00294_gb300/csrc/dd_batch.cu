@@ -23,6 +23,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "dd_coef.cuh"
@@ -82,7 +83,9 @@ __global__ void __launch_bounds__(Cfg::kThreads)
 batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items, int n_items,
                    unsigned *__restrict__ counter, const double *__restrict__ X, const double *__restrict__ Y,
                    const typename Cfg::Rec *__restrict__ rec, int sb, double *__restrict__ partial) {
-    __shared__ TileSmem<Cfg, 1> sm;
+    constexpr bool kMixed = std::is_same<typename Cfg::Real, float>::value;
+    using Smem = typename std::conditional<kMixed, TileSmemMixed<Cfg, 1>, TileSmem<Cfg, 1>>::type;
+    __shared__ Smem sm;
     __shared__ int s_item;
     constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
     for (;;) {
@@ -96,9 +99,14 @@ batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items,
         const int na[1] = {S.nact};
         const int s_begin = item.z * sb;
         const int s_end = min(s_begin + sb, S.nact);
-        field_tile<Cfg, 1>(sm, S.src, S.src + S.n, X + S.pt_off, Y + S.pt_off, S.n_pts, (int64_t)item.y * TILE,
-                           rec + S.rec_off, 0, na, 1, s_begin, s_end,
-                           partial + S.part_off + (int64_t)item.z * S.n_pts, S.n_pts);
+        if constexpr (kMixed)
+            field_tile_mixed<Cfg, 1>(sm, S.src, S.src + S.n, X + S.pt_off, Y + S.pt_off, S.n_pts,
+                                     (int64_t)item.y * TILE, rec + S.rec_off, 0, na, 1, s_begin, s_end,
+                                     partial + S.part_off + (int64_t)item.z * S.n_pts, S.n_pts);
+        else
+            field_tile<Cfg, 1>(sm, S.src, S.src + S.n, X + S.pt_off, Y + S.pt_off, S.n_pts, (int64_t)item.y * TILE,
+                               rec + S.rec_off, 0, na, 1, s_begin, s_end,
+                               partial + S.part_off + (int64_t)item.z * S.n_pts, S.n_pts);
     }
 }
 

@@ -83,11 +83,11 @@ struct RecTraits<RecF32> {
     static __device__ void fill(RecF32 &o, double q1, double dq, double r, double ell) {
         double c[RecF32::kTerms];
         moment_coefficients<RecF32::kTerms - 1>(r, ell, c);
-        o.alpha = (float)(-q1 * 1.44269504088896340736);
-        o.dq = (float)dq;
-        o.q1 = (float)q1;
-#pragma unroll
-        for (int m = 0; m < RecF32::kTerms; ++m) o.c[m] = (float)c[m];
+        const double dq2 = dq * dq;
+        o.v0 = make_float4((float)(-q1 * 1.44269504088896340736), (float)c[0], (float)(c[1] * dq), (float)(c[2] * dq2));
+        o.v1 = make_float4((float)(c[3] * dq2 * dq), (float)(c[4] * dq2 * dq2), (float)dq, (float)c[1]);
+        o.v2 = make_float4((float)c[2], (float)c[3], (float)c[4], (float)c[5]);
+        o.v3 = make_float4((float)c[6], (float)c[7], (float)c[8], 0.0f);
     }
 };
 

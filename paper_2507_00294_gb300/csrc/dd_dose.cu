@@ -80,7 +80,7 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
                 // the smallest a over its lanes (the same classes as the field kernel)
                 float r2[PPT];
                 bool ok[PPT];
-                uint32_t cls = kCodeSkip;
+                bool lo = true;                 // every valid pair of this lane fits degree 2
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     const int64_t i = jt[q] - k;
@@ -88,22 +88,29 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
                     const float dx = ok[q] ? px[q] - s_x[i - w0] : 0.f;
                     const float dy = ok[q] ? py[q] - s_y[i - w0] : 0.f;
                     r2[q] = dx * dx + dy * dy;
-                    const float h = r2[q] * R.dq, a = r2[q] * R.q1;
-                    const uint32_t cq = !ok[q] || a >= 87.0f ? kCodeSkip
-                                      : h <= kDeg2H ? kCodeD2 : h <= kDeg4H ? kCodeD4
-                                      : h <= kHMaxF ? kCodeD8 : kCodeGeneral;
-                    cls = max(cls, cq);
+                    lo = lo && (r2[q] * R.dq() <= kDeg2H);
                 }
-                cls = __reduce_max_sync(0xffffffffu, cls);
+                uint32_t cls = kCodeD2;
+                // the common case is settled by one vote; otherwise classify every pair
+                if (!__all_sync(0xffffffffu, lo)) {
+                    cls = kCodeSkip;
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) {
+                        const float h = r2[q] * R.dq(), a = r2[q] * R.q1();
+                        const uint32_t cq = !ok[q] || a >= 87.0f ? kCodeSkip
+                                          : h <= kDeg2H ? kCodeD2 : h <= kDeg4H ? kCodeD4
+                                          : h <= kHMaxF ? kCodeD8 : kCodeGeneral;
+                        cls = max(cls, cq);
+                    }
+                    cls = __reduce_max_sync(0xffffffffu, cls);
+                }
                 if (cls == kCodeSkip) continue;
-                const float4 *rv = reinterpret_cast<const float4 *>(&R);
-                const float4 q0 = rv[0], q1 = rv[1], q2 = rv[2];
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     float t;
-                    if (cls == kCodeD2) t = ex2_approx(r2[q] * q0.x) * moment_poly<2>(q0, q1, q2, r2[q] * q0.y);
-                    else if (cls == kCodeD4) t = ex2_approx(r2[q] * q0.x) * moment_poly<4>(q0, q1, q2, r2[q] * q0.y);
-                    else if (cls == kCodeD8) t = ex2_approx(r2[q] * q0.x) * moment_poly<8>(q0, q1, q2, r2[q] * q0.y);
+                    if (cls == kCodeD2) t = moment_term<2>(r2[q], R.v0, R.v0, R.v0, R.v0);
+                    else if (cls == kCodeD4) t = moment_term<4>(r2[q], R.v0, R.v1, R.v1, R.v1);
+                    else if (cls == kCodeD8) t = moment_term<8>(r2[q], R.v0, R.v1, R.v2, R.v3);
                     else t = pair_term(r2[q], R);
                     acc[q] += ok[q] ? t : 0.f;
                 }

@@ -7,15 +7,27 @@
 
 namespace ddk {
 
-// Per (snapshot, visit) coefficients.  FP32-mixed: alpha = -log2(e)/w1 (so that
-// e^-a = 2^(rho^2 alpha)), dq = 1/w0 - 1/w1, q1 = 1/w1 and the moment coefficients
-// c_0..c_8 (c_0 = ln(w1/w0)); 48 bytes, read as three 16-byte vectors.
+// Per (snapshot, visit) coefficients, FP32-mixed, 64 bytes read as four 16-byte vectors:
+//   v0 = (alpha, c_0, e_1, e_2),  v1 = (e_3, e_4, dq, c_1),  v2 = (c_2, c_3, c_4, c_5),
+//   v3 = (c_6, c_7, c_8, 0)
+// with alpha = -log2(e)/w1 (so e^-a = 2^(rho^2 alpha)), dq = 1/w0 - 1/w1, the moment
+// coefficients c_m (c_0 = ln(w1/w0)) and e_m = c_m dq^m, which let the low-degree paths
+// run Horner in rho^2 directly:  sum_m c_m h^m = sum_m e_m (rho^2)^m with h = rho^2 dq.
 struct __align__(16) RecF32 {
     static constexpr int kTerms = 9;
-    float alpha, dq, q1;
-    float c[kTerms];
+    float4 v0, v1, v2, v3;
+    __device__ __forceinline__ float alpha() const { return v0.x; }
+    __device__ __forceinline__ float dq() const { return v1.z; }
+    __device__ __forceinline__ float q1() const { return -v0.x * 0.693147180559945309f; }
+    __device__ __forceinline__ float c(int m) const {
+        switch (m) {
+            case 0: return v0.y; case 1: return v1.w; case 2: return v2.x; case 3: return v2.y;
+            case 4: return v2.z; case 5: return v2.w; case 6: return v3.x; case 7: return v3.y;
+            default: return v3.z;
+        }
+    }
 };
-static_assert(sizeof(RecF32) == 48, "RecF32 layout");
+static_assert(sizeof(RecF32) == 64, "RecF32 layout");
 
 // FP64: q1, dq and c_0..c_15; 144 bytes.
 struct __align__(16) RecF64 {
@@ -35,16 +47,16 @@ constexpr double kHMaxD = 0.5;
 
 // One pair term E1(a) - E1(b), a = rho^2 q1, b = a + rho^2 dq, FP32 arithmetic.
 __device__ __forceinline__ float pair_term(float r2, const RecF32 &R) {
-    const float a = r2 * R.q1;
-    const float h = r2 * R.dq;
+    const float a = r2 * R.q1();
+    const float h = r2 * R.dq();
     if (a >= 87.0f) return 0.0f;                  // e^-a below the FP32 normal range
     if (h <= kHMaxF) {
-        float p = R.c[8];
+        float p = R.c(8);
 #pragma unroll
-        for (int m = 7; m >= 0; --m) p = fmaf(p, h, R.c[m]);
-        return ex2_approx(r2 * R.alpha) * p;
+        for (int m = 7; m >= 0; --m) p = fmaf(p, h, R.c(m));
+        return ex2_approx(r2 * R.alpha()) * p;
     }
-    return e1diff_general_f32(a, h, R.c[0]);
+    return e1diff_general_f32(a, h, R.c(0));
 }
 
 // The same in FP64.
@@ -69,6 +81,7 @@ struct CfgMixed {
     using Rec = RecF32;
     using Real = float;
     static constexpr int kThreads = 128, kPPT = 4, kTCH = 4, kSTILE = 64, kSB = 512, kFlush = 32;
+    static constexpr int kMinBlocks = 8;
     static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
                                 *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
@@ -76,6 +89,7 @@ struct CfgF64 {
     using Rec = RecF64;
     using Real = double;
     static constexpr int kThreads = 128, kPPT = 2, kTCH = 4, kSTILE = 32, kSB = 512, kFlush = 1 << 30;
+    static constexpr int kMinBlocks = 1;
     static constexpr const char *kFieldName = "field_fp64", *kCoefName = "coef_fp64",
                                 *kDoseName = "dose_fp64", *kLagCoefName = "lag_coef_fp64";
 };
@@ -104,30 +118,35 @@ enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeGen
 // per (warp, visit): all snapshots skipped / all on degree 2 / all on degree <= 4 / mixed
 enum : uint32_t { kModeSkip = 0, kModeAllD2 = 1, kModeAllD4 = 2, kModePerSnapshot = 3 };
 
+// Degree-D moment polynomial times e^-a for one pair, from the record vectors.
+// D = 2, 4: Horner in rho^2 with e_m (no h needed); D = 8: Horner in h with c_m.
 template <int D>
-__device__ __forceinline__ float moment_poly(const float4 &r0, const float4 &r1, const float4 &r2, float h) {
-    // c_0 = r0.w, c_1..c_4 = r1, c_5..c_8 = r2
-    if (D == 2) return fmaf(fmaf(r1.y, h, r1.x), h, r0.w);
-    if (D == 4) return fmaf(fmaf(fmaf(fmaf(r1.w, h, r1.z), h, r1.y), h, r1.x), h, r0.w);
-    float p = fmaf(fmaf(fmaf(r2.w, h, r2.z), h, r2.y), h, r2.x);
-    p = fmaf(fmaf(fmaf(fmaf(p, h, r1.w), h, r1.z), h, r1.y), h, r1.x);
-    return fmaf(p, h, r0.w);
+__device__ __forceinline__ float moment_term(float r2, const float4 &v0, const float4 &v1, const float4 &v2,
+                                             const float4 &v3) {
+    const float e = ex2_approx(r2 * v0.x);
+    float p;
+    if (D == 2) {
+        p = fmaf(fmaf(v0.w, r2, v0.z), r2, v0.y);
+    } else if (D == 4) {
+        p = fmaf(fmaf(fmaf(fmaf(v1.y, r2, v1.x), r2, v0.w), r2, v0.z), r2, v0.y);
+    } else {
+        const float h = r2 * v1.z;
+        p = fmaf(fmaf(fmaf(fmaf(v3.z, h, v3.y), h, v3.x), h, v2.w), h, v2.z);
+        p = fmaf(fmaf(fmaf(fmaf(p, h, v2.y), h, v2.x), h, v1.w), h, v0.y);
+    }
+    return e * p;
 }
 
 template <int D, int PPT>
-__device__ __forceinline__ void moment_pass(float (&acc)[PPT], const float (&r2)[PPT], const float4 &q0,
-                                            const float4 &q1, const float4 &q2) {
-    // q0 = (alpha, dq, q1, c0): e^-a = 2^(rho^2 alpha), h = rho^2 dq
+__device__ __forceinline__ void moment_pass(float (&acc)[PPT], const float (&r2)[PPT], const float4 &v0,
+                                            const float4 &v1, const float4 &v2, const float4 &v3) {
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const float h = r2[k] * q0.y;
-        const float e = ex2_approx(r2[k] * q0.x);
-        acc[k] = fmaf(e, moment_poly<D>(q0, q1, q2, h), acc[k]);
-    }
+    for (int k = 0; k < PPT; ++k) acc[k] += moment_term<D>(r2[k], v0, v1, v2, v3);
 }
 
 template <typename Cfg, int TCH>
 struct TileSmemMixed {
+    float run[TCH * Cfg::kPPT][Cfg::kThreads];         // per-thread running sums over stages
     float x[Cfg::kSTILE], y[Cfg::kSTILE];
     uint32_t code[Cfg::kThreads / 32][Cfg::kSTILE];   // per warp: 8-bit class per snapshot
     float4 box[Cfg::kThreads / 32];                     // per warp: (xmin, xmax, ymin, ymax)
@@ -165,15 +184,16 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     __syncthreads();                       // previous item's readers of sm.box are done
     if (lane == 0) sm.box[warp] = make_float4(bx0, bx1, by0, by1);
 
-    // per (snapshot, point): FP32 sum of the current 64-visit stage, added after each
-    // stage to an FP32 running sum (8 stages per item at the default block of 512 visits,
+    // per (snapshot, point): FP32 sum of the current 64-visit stage in registers, added
+    // after each stage to an FP32 running sum in shared memory (sm.run, one column per
+    // thread: conflict-free) (8 stages per item at the default block of 512 visits,
     // at most 32 with the largest block the dispatcher picks, so that sum adds at most
     // 32 u = 2e-6 relative error), converted to FP64 at the end of the item.
-    float acc[TCH][PPT], ks[TCH][PPT];
+    float acc[TCH][PPT];
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc)
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) { acc[jc][k] = 0.0f; ks[jc][k] = 0.0f; }
+        for (int k = 0; k < PPT; ++k) { acc[jc][k] = 0.0f; sm.run[jc * PPT + k][tid] = 0.0f; }
 
     for (int s0 = s_begin; s0 < s_end; s0 += STILE) {
         const int cnt = min(STILE, s_end - s0);
@@ -187,8 +207,8 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             const float4 *row = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0);
             const int lim = na[jc] - s0;
             float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
-            for (int v = tid; v < cnt * 3; v += NT)
-                dst[v] = (v / 3 < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int v = tid; v < cnt * 4; v += NT)
+                dst[v] = (v / 4 < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();                   // coordinates and box visible
         for (int e = tid; e < cnt * NW; e += NT) {
@@ -210,8 +230,8 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 // the degree-2 path turns into an exact 0
                 uint32_t c = kCodeD2;
                 if (s0 + i < na[jc]) {
-                    const float4 head = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0 + i)[0];
-                    const float hmax = r2max * head.y, amin = r2min * head.z;
+                    const RecF32 &R = rec[(int64_t)jc * rec_stride + s0 + i];
+                    const float hmax = r2max * R.dq(), amin = r2min * R.q1();
                     c = amin >= 87.0f ? kCodeSkip
                       : hmax <= kDeg2H ? kCodeD2
                       : hmax <= kDeg4H ? kCodeD4
@@ -246,16 +266,14 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 if (mode == kModeAllD2) {
 #pragma unroll
                     for (int jc = 0; jc < TCH; ++jc) {
-                        const float4 *rv = reinterpret_cast<const float4 *>(&sm.rec[jc][s]);
-                        const float4 a0 = rv[0], a1 = rv[1];
-                        moment_pass<2, PPT>(acc[jc], r2, a0, a1, a1);
+                        const float4 v0 = sm.rec[jc][s].v0;
+                        moment_pass<2, PPT>(acc[jc], r2, v0, v0, v0, v0);
                     }
                 } else {
 #pragma unroll
                     for (int jc = 0; jc < TCH; ++jc) {
-                        const float4 *rv = reinterpret_cast<const float4 *>(&sm.rec[jc][s]);
-                        const float4 a0 = rv[0], a1 = rv[1];
-                        moment_pass<4, PPT>(acc[jc], r2, a0, a1, a1);
+                        const float4 v0 = sm.rec[jc][s].v0, v1 = sm.rec[jc][s].v1;
+                        moment_pass<4, PPT>(acc[jc], r2, v0, v1, v1, v1);
                     }
                 }
                 continue;
@@ -264,14 +282,13 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             for (int jc = 0; jc < TCH; ++jc) {
                 const uint32_t c = (word >> (8 * jc)) & 0xfu;
                 if (c == kCodeSkip) continue;
-                const float4 *rv = reinterpret_cast<const float4 *>(&sm.rec[jc][s]);
-                const float4 q0 = rv[0], q1 = rv[1];
+                const RecF32 &Rs = sm.rec[jc][s];
                 if (c == kCodeD2) {
-                    moment_pass<2, PPT>(acc[jc], r2, q0, q1, q1);
+                    moment_pass<2, PPT>(acc[jc], r2, Rs.v0, Rs.v0, Rs.v0, Rs.v0);
                 } else if (c == kCodeD4) {
-                    moment_pass<4, PPT>(acc[jc], r2, q0, q1, q1);
+                    moment_pass<4, PPT>(acc[jc], r2, Rs.v0, Rs.v1, Rs.v1, Rs.v1);
                 } else if (c == kCodeD8) {
-                    moment_pass<8, PPT>(acc[jc], r2, q0, q1, rv[2]);
+                    moment_pass<8, PPT>(acc[jc], r2, Rs.v0, Rs.v1, Rs.v2, Rs.v3);
                 } else {
                     const RecF32 &R = sm.rec[jc][s];
 #pragma unroll
@@ -282,7 +299,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc)
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) { ks[jc][k] += acc[jc][k]; acc[jc][k] = 0.0f; }
+            for (int k = 0; k < PPT; ++k) { sm.run[jc * PPT + k][tid] += acc[jc][k]; acc[jc][k] = 0.0f; }
     }
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc) {
@@ -290,7 +307,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int64_t p = tile0 + k * NT + tid;
-            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = (double)ks[jc][k];
+            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = (double)sm.run[jc * PPT + k][tid];
         }
     }
 }
@@ -387,7 +404,7 @@ __device__ __forceinline__ void field_tile(TileSmem<Cfg, TCH> &sm, const double 
 // One work item per CTA: item = (point tile, snapshot chunk, visit block).
 // partial[(block * n_tg + j) * n_pts + p] receives sum_{i in block, i < nact[j]} pair_term.
 template <typename Cfg>
-__global__ void __launch_bounds__(Cfg::kThreads)
+__global__ void __launch_bounds__(Cfg::kThreads, Cfg::kMinBlocks)
 field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
              const double *__restrict__ X, const double *__restrict__ Y, int64_t n_pts,
              const typename Cfg::Rec *__restrict__ rec, int64_t rec_stride,
