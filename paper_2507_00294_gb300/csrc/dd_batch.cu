@@ -97,16 +97,17 @@ batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items,
         const int4 item = items[it];
         const BScan &S = sc[item.x];
         const int na[1] = {S.nact};
+        const typename Cfg::Rec *rows[1] = {rec + S.rec_off};
         const int s_begin = item.z * sb;
         const int s_end = min(s_begin + sb, S.nact);
         if constexpr (kMixed)
             field_tile_mixed<Cfg, 1>(sm, S.src, S.src + S.n, X + S.pt_off, Y + S.pt_off, S.n_pts,
-                                     (int64_t)item.y * TILE, rec + S.rec_off, 0, na, 1, s_begin, s_end,
+                                     (int64_t)item.y * TILE, rows, na, 1, s_begin, s_end,
                                      partial + S.part_off + (int64_t)item.z * S.n_pts, S.n_pts);
         else
             field_tile<Cfg, 1>(sm, S.src, S.src + S.n, X + S.pt_off, Y + S.pt_off, S.n_pts, (int64_t)item.y * TILE,
-                               rec + S.rec_off, 0, na, 1, s_begin, s_end,
-                               partial + S.part_off + (int64_t)item.z * S.n_pts, S.n_pts);
+                               rows, na, 1, s_begin, s_end, partial + S.part_off + (int64_t)item.z * S.n_pts,
+                               S.n_pts);
     }
 }
 

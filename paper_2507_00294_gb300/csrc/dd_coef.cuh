@@ -114,4 +114,21 @@ __global__ void lag_coef_kernel(int64_t n, double s, double kappa, Rec *__restri
     rec[k] = out;
 }
 
+// Reversed lag table for snapshots on the dwell lattice of a uniform scan:
+// rev[u] = record of lag L = M - u (dT = L dwells, tau = 1) for u < M, zero for u = M.
+// Snapshot t_j (an integer number of dwells) then reads visit i's record at
+// rev[M - t_j + i], contiguous in i.
+template <typename Rec>
+__global__ void rev_lag_coef_kernel(int64_t M, double s, double kappa, Rec *__restrict__ rev) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u > M) return;
+    const int64_t L = M - u;
+    if (L == 0) { rev[u] = Rec{}; return; }
+    double q1, dq, r, ell;
+    pair_geometry((double)L, 1.0, s, kappa, q1, dq, r, ell);
+    Rec out;
+    RecTraits<Rec>::fill(out, q1, dq, r, ell);
+    rev[u] = out;
+}
+
 }  // namespace ddk

@@ -199,13 +199,38 @@ __global__ void dose_reduce_kernel(const double *__restrict__ partial, int64_t n
 
 namespace {
 
+// Lag block of the dose work items: the largest of 512, 256, 128, 64 lags that still
+// gives at least 8 items per SM (the triangle of a few thousand visits is otherwise cut
+// into too few CTAs to fill the GPU).
+template <typename Cfg>
+int dose_lag_block(int64_t n) {
+    constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    int lb = Cfg::kSB;
+    while (lb > 64) {
+        int64_t items = 0;
+        for (int64_t t0 = 0; t0 < n; t0 += TILE) {
+            const int64_t t1 = std::min(n, t0 + TILE);
+            if (t1 >= 2) items += (t1 - 2) / lb + 1;
+        }
+        if (items >= 8 * (int64_t)sms) break;
+        lb /= 2;
+    }
+    return lb;
+}
+
 template <typename Cfg>
 dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     using Rec = typename Cfg::Rec;
     const int64_t n = scan->n;
     const bool out_host = !dd::is_device_pointer(out);
     constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
-    const int lb = Cfg::kSB;
+    const int lb = dose_lag_block<Cfg>(n);
     const int64_t n_tiles = (n + TILE - 1) / TILE;
     std::vector<std::pair<int64_t, int2>> its;
     for (int64_t t = 0; t < n_tiles; ++t) {

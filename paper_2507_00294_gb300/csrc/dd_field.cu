@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <numeric>
 #include <vector>
 
@@ -74,13 +75,14 @@ struct HostTables {
     std::vector<std::vector<int4>> items;
     std::vector<std::vector<int>> ints;
     std::vector<std::vector<double>> reals;
+    std::vector<std::vector<int64_t>> offs;
     static void CUDART_CB release(void *p) { delete static_cast<HostTables *>(p); }
 };
 
 // Sizes of the workspace a call needs (the same function drives the carve).
 template <typename Cfg>
 size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out_host, bool pts_host,
-                       int n_t) {
+                       int n_t, int64_t n_rec) {
     using Rec = typename Cfg::Rec;
     const int tile = Cfg::kThreads * Cfg::kPPT;
     const int64_t n_tiles = (n_pts + tile - 1) / tile;
@@ -93,8 +95,9 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
     add(2 * (size_t)n_pts * sizeof(double));                  // X, Y in pitch units
     add((size_t)group * sizeof(double));                      // snapshot times
     add((size_t)group * sizeof(int) * 3);                     // nact, row, nblk per snapshot
+    add((size_t)group * sizeof(int64_t));                     // record row offset per snapshot
     add((size_t)n_tiles * n_chunks * nblk_max * sizeof(int4));  // items
-    add((size_t)group * n_src * sizeof(Rec));                 // coefficient records
+    add((size_t)n_rec * sizeof(Rec));                         // coefficient records
     add((size_t)nblk_max * group * n_pts * sizeof(double));   // partial sums
     return b + 256;
 }
@@ -114,10 +117,23 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return times[a] < times[b]; });
     std::vector<double> tdim(n_t);
     std::vector<int> nact(n_t);
-    for (int k = 0; k < n_t; ++k) {
-        tdim[k] = times[order[k]] / scan->dwell;
-        nact[k] = (int)(std::lower_bound(scan->T.begin(), scan->T.end(), tdim[k]) - scan->T.begin());
+    for (int k = 0; k < n_t; ++k) tdim[k] = times[order[k]] / scan->dwell;
+    // Snapshots on the dwell lattice of a uniform scan (t = integer number of dwells, to
+    // within 2 ulp of the quotient -- the rounding t/dwell itself already carries): the
+    // record of (snapshot, visit) depends on the lag only, so one reversed lag table of
+    // M + 1 records (M = last snapshot) serves every snapshot.
+    bool lattice = scan->uniform;
+    int64_t M = 0;
+    for (int k = 0; k < n_t && lattice; ++k) {
+        const double r = std::nearbyint(tdim[k]);
+        if (std::fabs(tdim[k] - r) > 2.0 * std::numeric_limits<double>::epsilon() * std::fabs(r)) lattice = false;
+        else if (r > (double)M) M = (int64_t)r;
     }
+    if (M < 1 || M > 4 * n_src + 64) lattice = false;
+    if (lattice)
+        for (int k = 0; k < n_t; ++k) tdim[k] = std::nearbyint(tdim[k]);
+    for (int k = 0; k < n_t; ++k)
+        nact[k] = (int)(std::lower_bound(scan->T.begin(), scan->T.end(), tdim[k]) - scan->T.begin());
 
     // visit block size and snapshot groups bound the partial and record buffers
     const int tile = Cfg::kThreads * Cfg::kPPT;
@@ -126,14 +142,15 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     int group = n_t;
     const size_t budget = size_t(1) << 30;
     while (group > Cfg::kTCH &&
-           (size_t)group * n_src * sizeof(Rec) + (size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget)
+           (size_t)(lattice ? 0 : group * n_src) * sizeof(Rec) + (size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget)
         group = std::max(Cfg::kTCH, group / 2);
     // larger blocks only while the FP32 stage sums stay short (<= 32 stages of 64 visits)
     while ((size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget && sb < 2048) sb *= 2;
     const int nblk_max = (int)((n_src + sb - 1) / sb);
     const int n_chunks_max = (group + Cfg::kTCH - 1) / Cfg::kTCH;
 
-    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_host, pts_host, n_t);
+    const int64_t n_rec = lattice ? M + 1 : (int64_t)group * n_src;
+    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_host, pts_host, n_t, n_rec);
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, &st);
     if (!src) return st;
@@ -159,8 +176,9 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     int *d_nact = cv.take<int>(3 * (size_t)group);
     int *d_row = d_nact + group;
     int *d_nblk = d_row + group;
+    int64_t *d_roff = cv.take<int64_t>(group);
     int4 *d_items = cv.take<int4>((size_t)n_tiles * n_chunks_max * nblk_max);
-    Rec *d_rec = cv.take<Rec>((size_t)group * n_src);
+    Rec *d_rec = cv.take<Rec>((size_t)n_rec);
     double *d_part = cv.take<double>((size_t)nblk_max * group * n_pts);
 
     DD_PROFILED("prep_points", stream,
@@ -171,17 +189,27 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     // host staging for the per-group tables, released by a host callback once the
     // stream has consumed them (the copies below may read pageable memory late)
     HostTables *keep = new HostTables();
+    if (lattice) {
+        DD_PROFILED(Cfg::kCoefName, stream,
+                    (ddk::rev_lag_coef_kernel<Rec><<<(unsigned)((M + 1 + 127) / 128), 128, 0, stream>>>(
+                        M, scan->s, scan->kappa, d_rec)));
+        DD_CUDA_TRY(cudaGetLastError());
+    }
     for (int g0 = 0; g0 < n_t; g0 += group) {
         const int ng = std::min(group, n_t - g0);
         const int n_chunks = (ng + Cfg::kTCH - 1) / Cfg::kTCH;
         std::vector<int> tabs(3 * (size_t)ng);
         std::vector<double> tg(ng);
+        std::vector<int64_t> roff(ng);
         int max_nact = 0;
         for (int j = 0; j < ng; ++j) {
             tg[j] = tdim[g0 + j];
             tabs[j] = nact[g0 + j];
             tabs[ng + j] = order[g0 + j];
             max_nact = std::max(max_nact, nact[g0 + j]);
+            // lattice: snapshot t reads lag t - i at rev[M - t + i]; otherwise row j of the
+            // per-(snapshot, visit) records
+            roff[j] = lattice ? (tdim[g0 + j] > 0 ? M - (int64_t)tdim[g0 + j] : M) : (int64_t)j * n_src;
         }
         // work items: (tile, chunk, block) for every block below the chunk's largest n_active
         std::vector<std::pair<int64_t, int4>> items;
@@ -208,7 +236,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         DD_CUDA_TRY(cudaMemcpyAsync(d_nact, tabs.data(), 3 * (size_t)ng * sizeof(int), cudaMemcpyHostToDevice, stream));
         if (!it.empty())
             DD_CUDA_TRY(cudaMemcpyAsync(d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
-        if (max_nact > 0) {
+        DD_CUDA_TRY(cudaMemcpyAsync(d_roff, roff.data(), ng * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+        if (max_nact > 0 && !lattice) {
             dim3 cg((unsigned)((max_nact + 127) / 128), (unsigned)ng);
             DD_PROFILED(Cfg::kCoefName, stream,
                         (ddk::coef_kernel<Rec><<<cg, 128, 0, stream>>>(srcT, srcTAU, d_t, d_nact, scan->s, scan->kappa, d_rec, n_src)));
@@ -217,7 +246,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         if (!it.empty()) {
             DD_PROFILED(Cfg::kFieldName, stream,
                         (ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
-                            srcX, srcY, X, Y, n_pts, d_rec, n_src, d_nact, d_items, ng, sb, d_part)));
+                            srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_items, ng, sb, d_part)));
             DD_CUDA_TRY(cudaGetLastError());
         }
         dim3 rg((unsigned)((n_pts + 255) / 256), (unsigned)ng);
@@ -227,6 +256,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         keep->items.push_back(std::move(it));
         keep->ints.push_back(std::move(tabs));
         keep->reals.push_back(std::move(tg));
+        keep->offs.push_back(std::move(roff));
     }
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n_t * n_pts * sizeof(double), cudaMemcpyDeviceToHost, stream));

@@ -73,6 +73,18 @@ __device__ __forceinline__ double pair_term(double r2, const RecF64 &R) {
     return e1diff_general_f64(a, h, R.c[0]);
 }
 
+// FP64 moment term of degree D (truncation e^{2h} h^{D+1}/(D+1)! <= 1e-17 at the class
+// limits below): e^-a times Horner in h over c_0..c_D.
+constexpr double kDeg4HD = 1.0e-3, kDeg8HD = 5.2e-2, kDeg11HD = 0.19;
+template <int D>
+__device__ __forceinline__ double moment_term_f64(double r2, const RecF64 &R) {
+    const double h = r2 * R.dq;
+    double p = R.c[D];
+#pragma unroll
+    for (int m = D - 1; m >= 0; --m) p = fma(p, h, R.c[m]);
+    return exp(-r2 * R.q1) * p;
+}
+
 // Tile configurations.  kThreads threads x kPPT points per thread form a point tile;
 // kTCH snapshots share each staged visit; kSTILE visits are staged per round; kSB
 // visits form one work item's block; FP32 partial sums are folded into FP64 every
@@ -157,9 +169,9 @@ template <typename Cfg, int TCH>
 __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, const double *__restrict__ srcX,
                                                  const double *__restrict__ srcY, const double *__restrict__ X,
                                                  const double *__restrict__ Y, int64_t n_pts, int64_t tile0,
-                                                 const RecF32 *__restrict__ rec, int64_t rec_stride,
-                                                 const int (&na)[TCH], int nj, int s_begin, int s_end,
-                                                 double *__restrict__ partial, int64_t part_stride) {
+                                                 const RecF32 *const (&rows)[TCH], const int (&na)[TCH], int nj,
+                                                 int s_begin, int s_end, double *__restrict__ partial,
+                                                 int64_t part_stride) {
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE, NW = NT / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -204,7 +216,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
         }
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc) {
-            const float4 *row = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0);
+            const float4 *row = reinterpret_cast<const float4 *>(rows[jc] + s0);
             const int lim = na[jc] - s0;
             float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
             for (int v = tid; v < cnt * 4; v += NT)
@@ -230,7 +242,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 // the degree-2 path turns into an exact 0
                 uint32_t c = kCodeD2;
                 if (s0 + i < na[jc]) {
-                    const RecF32 &R = rec[(int64_t)jc * rec_stride + s0 + i];
+                    const RecF32 &R = rows[jc][s0 + i];
                     const float hmax = r2max * R.dq(), amin = r2min * R.q1();
                     c = amin >= 87.0f ? kCodeSkip
                       : hmax <= kDeg2H ? kCodeD2
@@ -320,9 +332,9 @@ template <typename Cfg, int TCH>
 __device__ __forceinline__ void field_tile(TileSmem<Cfg, TCH> &sm, const double *__restrict__ srcX,
                                            const double *__restrict__ srcY, const double *__restrict__ X,
                                            const double *__restrict__ Y, int64_t n_pts, int64_t tile0,
-                                           const typename Cfg::Rec *__restrict__ rec, int64_t rec_stride,
-                                           const int (&na)[TCH], int nj, int s_begin, int s_end,
-                                           double *__restrict__ partial, int64_t part_stride) {
+                                           const typename Cfg::Rec *const (&rows)[TCH], const int (&na)[TCH],
+                                           int nj, int s_begin, int s_end, double *__restrict__ partial,
+                                           int64_t part_stride) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE;
@@ -354,7 +366,7 @@ __device__ __forceinline__ void field_tile(TileSmem<Cfg, TCH> &sm, const double 
         }
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc) {
-            const float4 *row = reinterpret_cast<const float4 *>(rec + (int64_t)jc * rec_stride + s0);
+            const float4 *row = reinterpret_cast<const float4 *>(rows[jc] + s0);
             const int lim = na[jc] - s0;           // records exist for visits below n_active
             float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
             for (int v = tid; v < cnt * RV; v += NT)
@@ -374,8 +386,28 @@ __device__ __forceinline__ void field_tile(TileSmem<Cfg, TCH> &sm, const double 
             for (int jc = 0; jc < TCH; ++jc) {
                 if (gs < na[jc]) {
                     const Rec &R = sm.rec[jc][s];
+                    if constexpr (std::is_same<Rec, RecF64>::value) {
+                        // one polynomial degree for the warp, from every lane's own h and a
+                        uint32_t cls = 0;
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) acc[jc][k] += pair_term(r2[k], R);
+                        for (int k = 0; k < PPT; ++k) {
+                            const double h = r2[k] * R.dq, a = r2[k] * R.q1;
+                            const uint32_t c = a >= 745.0 ? 0u : h <= kDeg4HD ? 1u : h <= kDeg8HD ? 2u
+                                             : h <= kDeg11HD ? 3u : 4u;
+                            cls = max(cls, c);
+                        }
+                        cls = __reduce_max_sync(0xffffffffu, cls);
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            if (cls == 1u) acc[jc][k] += moment_term_f64<4>(r2[k], R);
+                            else if (cls == 2u) acc[jc][k] += moment_term_f64<8>(r2[k], R);
+                            else if (cls == 3u) acc[jc][k] += moment_term_f64<11>(r2[k], R);
+                            else if (cls == 4u) acc[jc][k] += pair_term(r2[k], R);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) acc[jc][k] += pair_term(r2[k], R);
+                    }
                 }
             }
             if (Cfg::kFlush < STILE && (s % Cfg::kFlush) == Cfg::kFlush - 1) {
@@ -407,17 +439,21 @@ template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kMinBlocks)
 field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
              const double *__restrict__ X, const double *__restrict__ Y, int64_t n_pts,
-             const typename Cfg::Rec *__restrict__ rec, int64_t rec_stride,
+             const typename Cfg::Rec *__restrict__ rec, const int64_t *__restrict__ row_off,
              const int *__restrict__ nact, const int4 *__restrict__ items, int n_tg, int sb,
              double *__restrict__ partial) {
+    using Rec = typename Cfg::Rec;
     constexpr int TCH = Cfg::kTCH;
     const int4 item = items[blockIdx.x];
     const int j0 = item.y * TCH;
     int na[TCH];
+    const Rec *rows[TCH];
     int nmax = 0;
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc) {
-        na[jc] = (j0 + jc < n_tg) ? nact[j0 + jc] : 0;
+        const bool live = j0 + jc < n_tg;
+        na[jc] = live ? nact[j0 + jc] : 0;
+        rows[jc] = live ? rec + row_off[j0 + jc] : rec;     // record of visit i: rows[jc][i]
         nmax = max(nmax, na[jc]);
     }
     const int s_begin = item.z * sb;
@@ -426,12 +462,12 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
     double *part = partial + ((int64_t)item.z * n_tg + j0) * n_pts;
     if constexpr (std::is_same<typename Cfg::Real, float>::value) {
         __shared__ TileSmemMixed<Cfg, TCH> sm;
-        field_tile_mixed<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rec + (int64_t)j0 * rec_stride, rec_stride,
-                                   na, min(TCH, n_tg - j0), s_begin, s_end, part, n_pts);
+        field_tile_mixed<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rows, na, min(TCH, n_tg - j0), s_begin,
+                                   s_end, part, n_pts);
     } else {
         __shared__ TileSmem<Cfg, TCH> sm;
-        field_tile<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rec + (int64_t)j0 * rec_stride, rec_stride, na,
-                             min(TCH, n_tg - j0), s_begin, s_end, part, n_pts);
+        field_tile<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rows, na, min(TCH, n_tg - j0), s_begin, s_end,
+                             part, n_pts);
     }
 }
 
