@@ -34,8 +34,9 @@ UNIT = "pair-terms/s"
 # FP32 FLOPs of one pair term on each path of the field kernel (FMA = 2): rho^2 costs 5
 # flops per (point, visit) and is shared by the 4 snapshots of a chunk (1.25 per pair);
 # the moment paths add h, the exponent argument, a Horner polynomial of degree d and the
-# fused scale-and-accumulate: 4 + 2d flops; the general path (two E1 values) about 55.
-FLOPS_MOMENT = {2: 9.25, 4: 13.25, 8: 21.25}
+# fused scale-and-accumulate: 4 + 2d flops (degree 2 up to h = 6e-3, 4 up to 8.2e-2, 8 up
+# to 0.5, 12 up to 1.2); the general path (two E1 values) about 55.
+FLOPS_MOMENT = {2: 9.25, 4: 13.25, 8: 21.25, 12: 29.25}
 FLOPS_GENERAL = 56.25
 FLOPS_ZERO = 1.25
 # FP32 peak from the unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz.
@@ -187,7 +188,8 @@ def flops_per_pair(job, samples=400_000, seed=5):
     f = np.where(a >= 87, FLOPS_ZERO,
                  np.where(h <= 6.0e-3, FLOPS_MOMENT[2],
                           np.where(h <= 8.2e-2, FLOPS_MOMENT[4],
-                                   np.where(h <= 0.5, FLOPS_MOMENT[8], FLOPS_GENERAL))))
+                                   np.where(h <= 0.5, FLOPS_MOMENT[8],
+                                            np.where(h <= 1.2, FLOPS_MOMENT[12], FLOPS_GENERAL)))))
     wgt = nact[np.arange(samples)]               # pairs are sampled per snapshot: weight by n_active
     return float(np.sum(f * wgt) / np.sum(wgt))
 

@@ -87,7 +87,8 @@ struct RecTraits<RecF32> {
         o.v0 = make_float4((float)(-q1 * 1.44269504088896340736), (float)c[0], (float)(c[1] * dq), (float)(c[2] * dq2));
         o.v1 = make_float4((float)(c[3] * dq2 * dq), (float)(c[4] * dq2 * dq2), (float)dq, (float)c[1]);
         o.v2 = make_float4((float)c[2], (float)c[3], (float)c[4], (float)c[5]);
-        o.v3 = make_float4((float)c[6], (float)c[7], (float)c[8], 0.0f);
+        o.v3 = make_float4((float)c[6], (float)c[7], (float)c[8], (float)c[9]);
+        o.v4 = make_float4((float)c[10], (float)c[11], (float)c[12], 0.0f);
     }
 };
 

@@ -99,7 +99,7 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
                         const float h = r2[q] * R.dq(), a = r2[q] * R.q1();
                         const uint32_t cq = !ok[q] || a >= 87.0f ? kCodeSkip
                                           : h <= kDeg2H ? kCodeD2 : h <= kDeg4H ? kCodeD4
-                                          : h <= kHMaxF ? kCodeD8 : kCodeGeneral;
+                                          : h <= kHMaxF ? kCodeD8 : h <= kHMax12F ? kCodeD12 : kCodeGeneral;
                         cls = max(cls, cq);
                     }
                     cls = __reduce_max_sync(0xffffffffu, cls);
@@ -108,9 +108,10 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     float t;
-                    if (cls == kCodeD2) t = moment_term<2>(r2[q], R.v0, R.v0, R.v0, R.v0);
-                    else if (cls == kCodeD4) t = moment_term<4>(r2[q], R.v0, R.v1, R.v1, R.v1);
-                    else if (cls == kCodeD8) t = moment_term<8>(r2[q], R.v0, R.v1, R.v2, R.v3);
+                    if (cls == kCodeD2) t = moment_term<2>(r2[q], R);
+                    else if (cls == kCodeD4) t = moment_term<4>(r2[q], R);
+                    else if (cls == kCodeD8) t = moment_term<8>(r2[q], R);
+                    else if (cls == kCodeD12) t = moment_term<12>(r2[q], R);
                     else t = pair_term(r2[q], R);
                     acc[q] += ok[q] ? t : 0.f;
                 }

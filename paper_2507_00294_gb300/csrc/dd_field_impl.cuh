@@ -7,15 +7,15 @@
 
 namespace ddk {
 
-// Per (snapshot, visit) coefficients, FP32-mixed, 64 bytes read as four 16-byte vectors:
+// Per (snapshot, visit) coefficients, FP32-mixed, 80 bytes read as five 16-byte vectors:
 //   v0 = (alpha, c_0, e_1, e_2),  v1 = (e_3, e_4, dq, c_1),  v2 = (c_2, c_3, c_4, c_5),
-//   v3 = (c_6, c_7, c_8, 0)
+//   v3 = (c_6, c_7, c_8, c_9),   v4 = (c_10, c_11, c_12, 0)
 // with alpha = -log2(e)/w1 (so e^-a = 2^(rho^2 alpha)), dq = 1/w0 - 1/w1, the moment
 // coefficients c_m (c_0 = ln(w1/w0)) and e_m = c_m dq^m, which let the low-degree paths
 // run Horner in rho^2 directly:  sum_m c_m h^m = sum_m e_m (rho^2)^m with h = rho^2 dq.
 struct __align__(16) RecF32 {
-    static constexpr int kTerms = 9;
-    float4 v0, v1, v2, v3;
+    static constexpr int kTerms = 13;
+    float4 v0, v1, v2, v3, v4;
     __device__ __forceinline__ float alpha() const { return v0.x; }
     __device__ __forceinline__ float dq() const { return v1.z; }
     __device__ __forceinline__ float q1() const { return -v0.x * 0.693147180559945309f; }
@@ -23,11 +23,12 @@ struct __align__(16) RecF32 {
         switch (m) {
             case 0: return v0.y; case 1: return v1.w; case 2: return v2.x; case 3: return v2.y;
             case 4: return v2.z; case 5: return v2.w; case 6: return v3.x; case 7: return v3.y;
-            default: return v3.z;
+            case 8: return v3.z; case 9: return v3.w; case 10: return v4.x; case 11: return v4.y;
+            default: return v4.z;
         }
     }
 };
-static_assert(sizeof(RecF32) == 64, "RecF32 layout");
+static_assert(sizeof(RecF32) == 80, "RecF32 layout");
 
 // FP64: q1, dq and c_0..c_15; 144 bytes.
 struct __align__(16) RecF64 {
@@ -40,9 +41,11 @@ static_assert(sizeof(RecF64) == 144, "RecF64 layout");
 template <typename Rec>
 struct RecTraits;
 
-// Largest h handled by the moment series: its truncation after c_8 (FP32) or c_15
-// (FP64) is below e^h h^(M+1)/(M+1)! = 9e-9 resp. 1.2e-18 relative at h = 1/2.
+// Largest h of the moment series.  FP32: degree 8 up to h = 1/2 and degree 12 up to
+// h = 1.2 (truncation e^{2h} h^{d+1}/(d+1)! below 4e-8 and 2e-8, cancellation at most
+// e^{2h} = 11); FP64: degree 15 up to h = 1/2 (1.2e-18).
 constexpr float kHMaxF = 0.5f;
+constexpr float kHMax12F = 1.2f;
 constexpr double kHMaxD = 0.5;
 
 // One pair term E1(a) - E1(b), a = rho^2 q1, b = a + rho^2 dq, FP32 arithmetic.
@@ -50,10 +53,10 @@ __device__ __forceinline__ float pair_term(float r2, const RecF32 &R) {
     const float a = r2 * R.q1();
     const float h = r2 * R.dq();
     if (a >= 87.0f) return 0.0f;                  // e^-a below the FP32 normal range
-    if (h <= kHMaxF) {
-        float p = R.c(8);
+    if (h <= kHMax12F) {
+        float p = R.c(12);
 #pragma unroll
-        for (int m = 7; m >= 0; --m) p = fmaf(p, h, R.c(m));
+        for (int m = 11; m >= 0; --m) p = fmaf(p, h, R.c(m));
         return ex2_approx(r2 * R.alpha()) * p;
     }
     return e1diff_general_f32(a, h, R.c(0));
@@ -93,7 +96,7 @@ struct CfgMixed {
     using Rec = RecF32;
     using Real = float;
     static constexpr int kThreads = 128, kPPT = 4, kTCH = 4, kSTILE = 64, kSB = 512, kFlush = 32;
-    static constexpr int kMinBlocks = 8;
+    static constexpr int kMinBlocks = 6;
     static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
                                 *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
@@ -126,34 +129,34 @@ struct TileSmem {
 // Lanes whose own a is >= 87 inside a polynomial class get ex2 -> 0 (flush to zero), so
 // no per-lane test is needed on the polynomial paths.
 constexpr float kDeg2H = 6.0e-3f, kDeg4H = 8.2e-2f;
-enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeGeneral = 4 };
+enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeD12 = 4, kCodeGeneral = 5 };
 // per (warp, visit): all snapshots skipped / all on degree 2 / all on degree <= 4 / mixed
 enum : uint32_t { kModeSkip = 0, kModeAllD2 = 1, kModeAllD4 = 2, kModePerSnapshot = 3 };
 
 // Degree-D moment polynomial times e^-a for one pair, from the record vectors.
-// D = 2, 4: Horner in rho^2 with e_m (no h needed); D = 8: Horner in h with c_m.
+// D = 2, 4: Horner in rho^2 with e_m (no h needed); D = 8, 12: Horner in h with c_m.
 template <int D>
-__device__ __forceinline__ float moment_term(float r2, const float4 &v0, const float4 &v1, const float4 &v2,
-                                             const float4 &v3) {
-    const float e = ex2_approx(r2 * v0.x);
+__device__ __forceinline__ float moment_term(float r2, const RecF32 &R) {
+    const float e = ex2_approx(r2 * R.v0.x);
     float p;
     if (D == 2) {
-        p = fmaf(fmaf(v0.w, r2, v0.z), r2, v0.y);
+        p = fmaf(fmaf(R.v0.w, r2, R.v0.z), r2, R.v0.y);
     } else if (D == 4) {
-        p = fmaf(fmaf(fmaf(fmaf(v1.y, r2, v1.x), r2, v0.w), r2, v0.z), r2, v0.y);
+        p = fmaf(fmaf(fmaf(fmaf(R.v1.y, r2, R.v1.x), r2, R.v0.w), r2, R.v0.z), r2, R.v0.y);
     } else {
-        const float h = r2 * v1.z;
-        p = fmaf(fmaf(fmaf(fmaf(v3.z, h, v3.y), h, v3.x), h, v2.w), h, v2.z);
-        p = fmaf(fmaf(fmaf(fmaf(p, h, v2.y), h, v2.x), h, v1.w), h, v0.y);
+        const float h = r2 * R.v1.z;
+        p = D == 12 ? fmaf(fmaf(fmaf(fmaf(R.v4.z, h, R.v4.y), h, R.v4.x), h, R.v3.w), h, R.v3.z)
+                    : R.v3.z;
+        p = fmaf(fmaf(fmaf(fmaf(p, h, R.v3.y), h, R.v3.x), h, R.v2.w), h, R.v2.z);
+        p = fmaf(fmaf(fmaf(fmaf(p, h, R.v2.y), h, R.v2.x), h, R.v1.w), h, R.v0.y);
     }
     return e * p;
 }
 
 template <int D, int PPT>
-__device__ __forceinline__ void moment_pass(float (&acc)[PPT], const float (&r2)[PPT], const float4 &v0,
-                                            const float4 &v1, const float4 &v2, const float4 &v3) {
+__device__ __forceinline__ void moment_pass(float (&acc)[PPT], const float (&r2)[PPT], const RecF32 &R) {
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) acc[k] += moment_term<D>(r2[k], v0, v1, v2, v3);
+    for (int k = 0; k < PPT; ++k) acc[k] += moment_term<D>(r2[k], R);
 }
 
 template <typename Cfg, int TCH>
@@ -219,8 +222,9 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             const float4 *row = reinterpret_cast<const float4 *>(rows[jc] + s0);
             const int lim = na[jc] - s0;
             float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
-            for (int v = tid; v < cnt * 4; v += NT)
-                dst[v] = (v / 4 < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+            constexpr int RV = sizeof(RecF32) / 16;
+            for (int v = tid; v < cnt * RV; v += NT)
+                dst[v] = (v / RV < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();                   // coordinates and box visible
         for (int e = tid; e < cnt * NW; e += NT) {
@@ -247,7 +251,8 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     c = amin >= 87.0f ? kCodeSkip
                       : hmax <= kDeg2H ? kCodeD2
                       : hmax <= kDeg4H ? kCodeD4
-                      : hmax <= kHMaxF ? kCodeD8 : kCodeGeneral;
+                      : hmax <= kHMaxF ? kCodeD8
+                      : hmax <= kHMax12F ? kCodeD12 : kCodeGeneral;
                     any = any || c != kCodeSkip;
                 }
                 cmin = min(cmin, c);
@@ -277,16 +282,10 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 // block of TCH x PPT independent terms
                 if (mode == kModeAllD2) {
 #pragma unroll
-                    for (int jc = 0; jc < TCH; ++jc) {
-                        const float4 v0 = sm.rec[jc][s].v0;
-                        moment_pass<2, PPT>(acc[jc], r2, v0, v0, v0, v0);
-                    }
+                    for (int jc = 0; jc < TCH; ++jc) moment_pass<2, PPT>(acc[jc], r2, sm.rec[jc][s]);
                 } else {
 #pragma unroll
-                    for (int jc = 0; jc < TCH; ++jc) {
-                        const float4 v0 = sm.rec[jc][s].v0, v1 = sm.rec[jc][s].v1;
-                        moment_pass<4, PPT>(acc[jc], r2, v0, v1, v1, v1);
-                    }
+                    for (int jc = 0; jc < TCH; ++jc) moment_pass<4, PPT>(acc[jc], r2, sm.rec[jc][s]);
                 }
                 continue;
             }
@@ -296,11 +295,13 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 if (c == kCodeSkip) continue;
                 const RecF32 &Rs = sm.rec[jc][s];
                 if (c == kCodeD2) {
-                    moment_pass<2, PPT>(acc[jc], r2, Rs.v0, Rs.v0, Rs.v0, Rs.v0);
+                    moment_pass<2, PPT>(acc[jc], r2, Rs);
                 } else if (c == kCodeD4) {
-                    moment_pass<4, PPT>(acc[jc], r2, Rs.v0, Rs.v1, Rs.v1, Rs.v1);
+                    moment_pass<4, PPT>(acc[jc], r2, Rs);
                 } else if (c == kCodeD8) {
-                    moment_pass<8, PPT>(acc[jc], r2, Rs.v0, Rs.v1, Rs.v2, Rs.v3);
+                    moment_pass<8, PPT>(acc[jc], r2, Rs);
+                } else if (c == kCodeD12) {
+                    moment_pass<12, PPT>(acc[jc], r2, Rs);
                 } else {
                     const RecF32 &R = sm.rec[jc][s];
 #pragma unroll

@@ -71,7 +71,11 @@ def test_tuned_variants_agree(cuda):
     base = plan.run(dp).cpu().numpy()
     v = plan.tune(dp)
     assert v in (0, 1, 2) and plan.info()["variant"] == v
-    np.testing.assert_array_equal(plan.run(dp).cpu().numpy(), base)
+    tuned = plan.run(dp).cpu().numpy()
+    # a fixed variant is bit-reproducible; another tile shape groups points into warps
+    # differently and may pick another (equally accurate) polynomial degree per warp
+    np.testing.assert_array_equal(plan.run(dp).cpu().numpy(), tuned)
+    np.testing.assert_allclose(tuned, base, rtol=1e-6, atol=0)
 
 
 def test_batched_512_scans_sampled(cuda):
