@@ -29,7 +29,7 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
             double *__restrict__ partial) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
-    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, TILE = NT * PPT, LBMAX = Cfg::kSB;
+    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
     constexpr int RV = sizeof(Rec) / 16;
     __shared__ Real s_x[TILE + LBMAX], s_y[TILE + LBMAX];
     __shared__ __align__(16) Rec s_rec[Cfg::kSTILE];
@@ -212,7 +212,7 @@ int dose_lag_block(int64_t n) {
         cudaGetLastError();
         sms = 1;
     }
-    int lb = Cfg::kSB;
+    int lb = Cfg::kDoseLB;
     while (lb > 64) {
         int64_t items = 0;
         for (int64_t t0 = 0; t0 < n; t0 += TILE) {
@@ -389,7 +389,7 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     using Rec = typename Cfg::Rec;
     const int64_t n = scan->n;
     constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
-    const int lb = Cfg::kSB;
+    const int lb = Cfg::kDoseLB;
     const int64_t n_tiles = (n + TILE - 1) / TILE;
     const int64_t nblk = n >= 2 ? (n - 2) / lb + 1 : 0;
     size_t off = 0;

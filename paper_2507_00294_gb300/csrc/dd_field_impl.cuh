@@ -91,12 +91,13 @@ __device__ __forceinline__ double moment_term_f64(double r2, const RecF64 &R) {
 // Tile configurations.  kThreads threads x kPPT points per thread form a point tile;
 // kTCH snapshots share each staged visit; kSTILE visits are staged per round; kSB
 // visits form one work item's block; FP32 partial sums are folded into FP64 every
-// kFlush visits.
+// kFlush visits; kDoseLB lags form the dose kernel's largest work-item block.
 struct CfgMixed {
     using Rec = RecF32;
     using Real = float;
     static constexpr int kThreads = 128, kPPT = 4, kTCH = 4, kSTILE = 64, kSB = 512, kFlush = 32;
     static constexpr int kMinBlocks = 6;
+    static constexpr int kDoseLB = 512;      // largest lag block of the dose kernel
     static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
                                 *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
@@ -105,6 +106,7 @@ struct CfgF64 {
     using Real = double;
     static constexpr int kThreads = 128, kPPT = 2, kTCH = 4, kSTILE = 32, kSB = 512, kFlush = 1 << 30;
     static constexpr int kMinBlocks = 1;
+    static constexpr int kDoseLB = 512;
     static constexpr const char *kFieldName = "field_fp64", *kCoefName = "coef_fp64",
                                 *kDoseName = "dose_fp64", *kLagCoefName = "lag_coef_fp64";
 };
@@ -130,6 +132,8 @@ struct TileSmem {
 // no per-lane test is needed on the polynomial paths.
 constexpr float kDeg2H = 6.0e-3f, kDeg4H = 8.2e-2f;
 enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeD12 = 4, kCodeGeneral = 5 };
+// classes are packed 3 bits per snapshot (up to 9 snapshots) below the 4 mode bits
+constexpr uint32_t kCodeBits = 3, kCodeMask = 7;
 // per (warp, visit): all snapshots skipped / all on degree 2 / all on degree <= 4 / mixed
 enum : uint32_t { kModeSkip = 0, kModeAllD2 = 1, kModeAllD4 = 2, kModePerSnapshot = 3 };
 
@@ -257,9 +261,10 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 }
                 cmin = min(cmin, c);
                 cmax = max(cmax, c);
-                word |= c << (8 * jc);
+                word |= c << (kCodeBits * jc);
             }
             // bits 28..31: how the whole visit is handled for this warp
+            static_assert(TCH * kCodeBits <= 28, "class codes overlap the mode bits");
             const uint32_t mode = !any ? kModeSkip
                                 : (cmin >= kCodeD2 && cmax == kCodeD2) ? kModeAllD2
                                 : (cmin >= kCodeD2 && cmax == kCodeD4) ? kModeAllD4 : kModePerSnapshot;
@@ -281,8 +286,16 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 // every snapshot of the chunk on one low-degree polynomial: one straight
                 // block of TCH x PPT independent terms
                 if (mode == kModeAllD2) {
+                    // all leading record vectors first, so their shared-memory latency overlaps
+                    float4 pv[TCH];
 #pragma unroll
-                    for (int jc = 0; jc < TCH; ++jc) moment_pass<2, PPT>(acc[jc], r2, sm.rec[jc][s]);
+                    for (int jc = 0; jc < TCH; ++jc) pv[jc] = sm.rec[jc][s].v0;
+#pragma unroll
+                    for (int jc = 0; jc < TCH; ++jc)
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k)
+                            acc[jc][k] = fmaf(ex2_approx(r2[k] * pv[jc].x),
+                                              fmaf(fmaf(pv[jc].w, r2[k], pv[jc].z), r2[k], pv[jc].y), acc[jc][k]);
                 } else {
 #pragma unroll
                     for (int jc = 0; jc < TCH; ++jc) moment_pass<4, PPT>(acc[jc], r2, sm.rec[jc][s]);
@@ -291,7 +304,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             }
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
-                const uint32_t c = (word >> (8 * jc)) & 0xfu;
+                const uint32_t c = (word >> (kCodeBits * jc)) & kCodeMask;
                 if (c == kCodeSkip) continue;
                 const RecF32 &Rs = sm.rec[jc][s];
                 if (c == kCodeD2) {
