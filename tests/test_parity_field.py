@@ -125,3 +125,27 @@ def test_allocation_failure_is_reported_and_recoverable(cuda, monkeypatch):
     monkeypatch.delenv("DD_FAULT")
     out = gpu_field(job.scan, job.pts_xy, job.times[:3], "mixed")
     assert np.all(np.isfinite(out)) and out.max() > 0
+
+
+def test_device_times_and_points_path(cuda):
+    """Times given as a device array are copied to the host first; the result is the same."""
+    import torch
+    job = w.small_raster_16()
+    scan = b.Scan(job.scan)
+    pts = torch.from_numpy(job.pts_xy).cuda()
+    t_dev = torch.from_numpy(job.times[::8].copy()).cuda()
+    a = b.dd_field_at_times(scan, pts, t_dev, "mixed").cpu().numpy()
+    c = b.dd_field_at_times(scan, pts, job.times[::8], "mixed").cpu().numpy()
+    np.testing.assert_array_equal(a, c)
+
+
+def test_single_visit_single_point_and_far_field(cuda):
+    """Degenerate sizes: one probe; points at the probe and 60 pitches away (exactly 0 during
+    the dwell, nonzero once diffusion reaches it); a snapshot long after the dwell."""
+    spec = w.ScanSpec(1, 1)
+    pts = np.array([[0.0, 0.0], [3e-8, 0.0]])
+    times = np.array([0.5e-6, 1e-6, 5e-3])
+    ref = oracle_field(spec, pts, times)
+    assert_fp64(gpu_field(spec, pts, times, "fp64"), ref, "single visit fp64")
+    got = gpu_field(spec, pts, times, "mixed")
+    assert_mixed(got, ref, ref.max(axis=1), "single visit mixed")
