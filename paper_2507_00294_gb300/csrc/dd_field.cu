@@ -15,6 +15,7 @@
 //   4. deterministic reduce of the per-block partial sums in block order, times
 //      Q0/(4 pi D), into out[snapshot][point] (reduce_kernel).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -100,6 +101,21 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
     add((size_t)n_rec * sizeof(Rec));                         // coefficient records
     add((size_t)nblk_max * group * n_pts * sizeof(double));   // partial sums
     return b + 256;
+}
+
+// The tile kernels want the whole L1/shared array as shared memory (6 CTAs of ~36 KB
+// per SM on the FP32-mixed path); set once per device.
+template <typename Cfg>
+cudaError_t prefer_shared() {
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess || dev >= 64) return err;
+    if (done.load() & (uint64_t(1) << dev)) return cudaSuccess;
+    err = cudaFuncSetAttribute(ddk::field_kernel<Cfg>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (err == cudaSuccess) done.fetch_or(uint64_t(1) << dev);
+    return err;
 }
 
 template <typename Cfg>
@@ -244,6 +260,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
             DD_CUDA_TRY(cudaGetLastError());
         }
         if (!it.empty()) {
+            DD_CUDA_TRY(prefer_shared<Cfg>());
             DD_PROFILED(Cfg::kFieldName, stream,
                         (ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
                             srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_items, ng, sb, d_part)));

@@ -157,20 +157,35 @@ __device__ __forceinline__ float moment_term(float r2, const RecF32 &R) {
     return e * p;
 }
 
-template <int D, int PPT>
-__device__ __forceinline__ void moment_pass(float (&acc)[PPT], const float (&r2)[PPT], const RecF32 &R) {
+// acc[k] (one half of each pair: H = 0 for .x, 1 for .y) += term of point k
+template <int D, int PPT, int H>
+__device__ __forceinline__ void moment_pass(float2 (&acc)[PPT], const float (&r2)[PPT], const RecF32 &R) {
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) acc[k] += moment_term<D>(r2[k], R);
+    for (int k = 0; k < PPT; ++k) {
+        const float t = moment_term<D>(r2[k], R);
+        if (H) acc[k].y += t; else acc[k].x += t;
+    }
 }
+
+// Leading record vectors of two snapshots (2P, 2P+1) of one visit, interleaved so that one
+// packed (f32x2) instruction evaluates the degree-2/4 polynomial of both snapshots:
+//   a = (alpha, alpha', c_0, c_0'),  b = (e_1, e_1', e_2, e_2'),  c = (e_3, e_3', e_4, e_4')
+struct __align__(16) PairRec {
+    float4 a, b, c;
+};
 
 template <typename Cfg, int TCH>
 struct TileSmemMixed {
+    static constexpr int kPairs = TCH / 2 > 0 ? TCH / 2 : 1;
     float run[TCH * Cfg::kPPT][Cfg::kThreads];         // per-thread running sums over stages
-    float x[Cfg::kSTILE], y[Cfg::kSTILE];
-    uint32_t code[Cfg::kThreads / 32][Cfg::kSTILE];   // per warp: 8-bit class per snapshot
+    float4 xy[Cfg::kSTILE];                             // (-x, -x, -y, -y) of each staged visit
+    uint32_t code[Cfg::kThreads / 32][Cfg::kSTILE];   // per warp: classes and mode of each visit
     float4 box[Cfg::kThreads / 32];                     // per warp: (xmin, xmax, ymin, ymax)
     __align__(16) RecF32 rec[TCH][Cfg::kSTILE];
+    PairRec pair[kPairs][Cfg::kSTILE];                  // snapshot pairs (even TCH only)
 };
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 template <typename Cfg, int TCH>
 __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, const double *__restrict__ srcX,
@@ -180,18 +195,23 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                                                  int s_begin, int s_end, double *__restrict__ partial,
                                                  int64_t part_stride) {
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE, NW = NT / 32;
+    constexpr bool kPacked = TCH % 2 == 0;       // snapshot pairs on f32x2 instructions
+    constexpr int NP = (TCH + 1) / 2;            // accumulator pairs
+    static_assert(PPT % 2 == 0, "points are processed in pairs");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const double cx = X[tile0], cy = Y[tile0];
-    float px[PPT], py[PPT];
+    // points k = 2m, 2m+1 in one pair
+    float2 px[PPT / 2], py[PPT / 2];
     float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int64_t p = tile0 + k * NT + tid;
-        px[k] = p < n_pts ? (float)(X[p] - cx) : 0.0f;
-        py[k] = p < n_pts ? (float)(Y[p] - cy) : 0.0f;
-        bx0 = fminf(bx0, px[k]); bx1 = fmaxf(bx1, px[k]);
-        by0 = fminf(by0, py[k]); by1 = fmaxf(by1, py[k]);
+        const float x = p < n_pts ? (float)(X[p] - cx) : 0.0f;
+        const float y = p < n_pts ? (float)(Y[p] - cy) : 0.0f;
+        if (k & 1) { px[k >> 1].y = x; py[k >> 1].y = y; } else { px[k >> 1].x = x; py[k >> 1].x = y; }
+        bx0 = fminf(bx0, x); bx1 = fmaxf(bx1, x);
+        by0 = fminf(by0, y); by1 = fmaxf(by1, y);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -203,23 +223,28 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     __syncthreads();                       // previous item's readers of sm.box are done
     if (lane == 0) sm.box[warp] = make_float4(bx0, bx1, by0, by1);
 
-    // per (snapshot, point): FP32 sum of the current 64-visit stage in registers, added
-    // after each stage to an FP32 running sum in shared memory (sm.run, one column per
-    // thread: conflict-free) (8 stages per item at the default block of 512 visits,
-    // at most 32 with the largest block the dispatcher picks, so that sum adds at most
-    // 32 u = 2e-6 relative error), converted to FP64 at the end of the item.
-    float acc[TCH][PPT];
+    // per (snapshot, point): FP32 sum of the current 64-visit stage in registers
+    // (acc[jc / 2][k], .x for even jc, .y for odd), added after each stage to an FP32
+    // running sum in shared memory (sm.run, one column per thread: conflict-free) (8
+    // stages per item at the default block of 512 visits, at most 32 with the largest
+    // block the dispatcher picks, so that sum adds at most 32 u = 2e-6 relative error),
+    // converted to FP64 at the end of the item.
+    float2 acc[NP][PPT];
+#pragma unroll
+    for (int m = 0; m < NP; ++m)
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) acc[m][k] = f2(0.0f, 0.0f);
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc)
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) { acc[jc][k] = 0.0f; sm.run[jc * PPT + k][tid] = 0.0f; }
+        for (int k = 0; k < PPT; ++k) sm.run[jc * PPT + k][tid] = 0.0f;
 
     for (int s0 = s_begin; s0 < s_end; s0 += STILE) {
         const int cnt = min(STILE, s_end - s0);
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
-            sm.x[i] = (float)(srcX[s0 + i] - cx);
-            sm.y[i] = (float)(srcY[s0 + i] - cy);
+            const float x = (float)(srcX[s0 + i] - cx), y = (float)(srcY[s0 + i] - cy);
+            sm.xy[i] = make_float4(-x, -x, -y, -y);
         }
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc) {
@@ -230,11 +255,26 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             for (int v = tid; v < cnt * RV; v += NT)
                 dst[v] = (v / RV < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        if constexpr (kPacked) {
+            // a snapshot for which this visit has not started gets a zero record: term 0
+            for (int i = tid; i < cnt; i += NT) {
+#pragma unroll
+                for (int P = 0; P < TCH / 2; ++P) {
+                    const bool l0 = s0 + i < na[2 * P], l1 = s0 + i < na[2 * P + 1];
+                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 a0 = l0 ? rows[2 * P][s0 + i].v0 : z, a1 = l1 ? rows[2 * P + 1][s0 + i].v0 : z;
+                    const float4 b0 = l0 ? rows[2 * P][s0 + i].v1 : z, b1 = l1 ? rows[2 * P + 1][s0 + i].v1 : z;
+                    sm.pair[P][i].a = make_float4(a0.x, a1.x, a0.y, a1.y);
+                    sm.pair[P][i].b = make_float4(a0.z, a1.z, a0.w, a1.w);
+                    sm.pair[P][i].c = make_float4(b0.x, b1.x, b0.y, b1.y);
+                }
+            }
+        }
         __syncthreads();                   // coordinates and box visible
         for (int e = tid; e < cnt * NW; e += NT) {
             const int i = e % cnt, w = e / cnt;
             const float4 bb = sm.box[w];
-            const float sx = sm.x[i], sy = sm.y[i];
+            const float sx = -sm.xy[i].x, sy = -sm.xy[i].z;
             const float dx1 = fmaxf(fabsf(sx - bb.x), fabsf(sx - bb.y));
             const float dy1 = fmaxf(fabsf(sy - bb.z), fabsf(sy - bb.w));
             const float dx0 = fmaxf(0.0f, fmaxf(bb.x - sx, sx - bb.y));
@@ -275,57 +315,88 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             const uint32_t word = sm.code[warp][s];
             const uint32_t mode = word >> 28;
             if (mode == kModeSkip) continue;               // warp-uniform skip
-            const float sx = sm.x[s], sy = sm.y[s];
+            // rho^2 of point pairs: (px - sx)^2 + (py - sy)^2 on f32x2
+            const float4 nxy = sm.xy[s];
             float r2[PPT];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float dx = px[k] - sx, dy = py[k] - sy;
-                r2[k] = fmaf(dx, dx, dy * dy);
+            for (int m = 0; m < PPT / 2; ++m) {
+                const float2 dx = __fadd2_rn(px[m], f2(nxy.x, nxy.y));
+                const float2 dy = __fadd2_rn(py[m], f2(nxy.z, nxy.w));
+                const float2 q = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                r2[2 * m] = q.x;
+                r2[2 * m + 1] = q.y;
             }
-            if (mode == kModeAllD2 || mode == kModeAllD4) {
-                // every snapshot of the chunk on one low-degree polynomial: one straight
-                // block of TCH x PPT independent terms
+            if (kPacked && (mode == kModeAllD2 || mode == kModeAllD4)) {
+                // every snapshot of the chunk on one low-degree polynomial: both snapshots
+                // of a pair in one f32x2 instruction; the leading vectors first, so their
+                // shared-memory latency overlaps
+                float4 va[NP], vb[NP];
+#pragma unroll
+                for (int P = 0; P < TCH / 2; ++P) { va[P] = sm.pair[P][s].a; vb[P] = sm.pair[P][s].b; }
                 if (mode == kModeAllD2) {
-                    // all leading record vectors first, so their shared-memory latency overlaps
-                    float4 pv[TCH];
 #pragma unroll
-                    for (int jc = 0; jc < TCH; ++jc) pv[jc] = sm.rec[jc][s].v0;
+                    for (int P = 0; P < TCH / 2; ++P)
 #pragma unroll
-                    for (int jc = 0; jc < TCH; ++jc)
-#pragma unroll
-                        for (int k = 0; k < PPT; ++k)
-                            acc[jc][k] = fmaf(ex2_approx(r2[k] * pv[jc].x),
-                                              fmaf(fmaf(pv[jc].w, r2[k], pv[jc].z), r2[k], pv[jc].y), acc[jc][k]);
+                        for (int k = 0; k < PPT; ++k) {
+                            const float2 r = f2(r2[k], r2[k]);
+                            const float2 t = __fmul2_rn(r, f2(va[P].x, va[P].y));
+                            const float2 e = f2(ex2_approx(t.x), ex2_approx(t.y));
+                            const float2 p = __ffma2_rn(__ffma2_rn(f2(vb[P].z, vb[P].w), r, f2(vb[P].x, vb[P].y)), r,
+                                                        f2(va[P].z, va[P].w));
+                            acc[P][k] = __ffma2_rn(e, p, acc[P][k]);
+                        }
                 } else {
 #pragma unroll
-                    for (int jc = 0; jc < TCH; ++jc) moment_pass<4, PPT>(acc[jc], r2, sm.rec[jc][s]);
+                    for (int P = 0; P < TCH / 2; ++P) {
+                        const float4 vc = sm.pair[P][s].c;
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            const float2 r = f2(r2[k], r2[k]);
+                            const float2 t = __fmul2_rn(r, f2(va[P].x, va[P].y));
+                            const float2 e = f2(ex2_approx(t.x), ex2_approx(t.y));
+                            float2 p = __ffma2_rn(f2(vc.z, vc.w), r, f2(vc.x, vc.y));
+                            p = __ffma2_rn(p, r, f2(vb[P].z, vb[P].w));
+                            p = __ffma2_rn(p, r, f2(vb[P].x, vb[P].y));
+                            p = __ffma2_rn(p, r, f2(va[P].z, va[P].w));
+                            acc[P][k] = __ffma2_rn(e, p, acc[P][k]);
+                        }
+                    }
                 }
                 continue;
             }
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
-                const uint32_t c = (word >> (kCodeBits * jc)) & kCodeMask;
+                const uint32_t c = mode == kModeAllD2 ? kCodeD2 : mode == kModeAllD4 ? kCodeD4
+                                 : (word >> (kCodeBits * jc)) & kCodeMask;
                 if (c == kCodeSkip) continue;
                 const RecF32 &Rs = sm.rec[jc][s];
+                float2 (&A)[PPT] = acc[jc >> 1];
                 if (c == kCodeD2) {
-                    moment_pass<2, PPT>(acc[jc], r2, Rs);
+                    if (jc & 1) moment_pass<2, PPT, 1>(A, r2, Rs); else moment_pass<2, PPT, 0>(A, r2, Rs);
                 } else if (c == kCodeD4) {
-                    moment_pass<4, PPT>(acc[jc], r2, Rs);
+                    if (jc & 1) moment_pass<4, PPT, 1>(A, r2, Rs); else moment_pass<4, PPT, 0>(A, r2, Rs);
                 } else if (c == kCodeD8) {
-                    moment_pass<8, PPT>(acc[jc], r2, Rs);
+                    if (jc & 1) moment_pass<8, PPT, 1>(A, r2, Rs); else moment_pass<8, PPT, 0>(A, r2, Rs);
                 } else if (c == kCodeD12) {
-                    moment_pass<12, PPT>(acc[jc], r2, Rs);
+                    if (jc & 1) moment_pass<12, PPT, 1>(A, r2, Rs); else moment_pass<12, PPT, 0>(A, r2, Rs);
                 } else {
-                    const RecF32 &R = sm.rec[jc][s];
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) acc[jc][k] += pair_term(r2[k], R);
+                    for (int k = 0; k < PPT; ++k) {
+                        const float t = pair_term(r2[k], Rs);
+                        if (jc & 1) A[k].y += t; else A[k].x += t;
+                    }
                 }
             }
         }
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc)
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) { sm.run[jc * PPT + k][tid] += acc[jc][k]; acc[jc][k] = 0.0f; }
+            for (int k = 0; k < PPT; ++k)
+                sm.run[jc * PPT + k][tid] += (jc & 1) ? acc[jc >> 1][k].y : acc[jc >> 1][k].x;
+#pragma unroll
+        for (int m = 0; m < NP; ++m)
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) acc[m][k] = f2(0.0f, 0.0f);
     }
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc) {
