@@ -467,11 +467,11 @@ def run_ours(args):
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": len(e64)}
         line["mixed_over_fp64"] = (value / world) / v64
 
-        # end to end through the public API with host buffers: scan build, H2D of the
-        # points and the visit list, both kernels chains, D2H of the field and the dose
-        pts_h = np.ascontiguousarray(job.pts_xy)
-        out_h = np.empty((len(times), len(job.pts_xy)))
-        dose_h = np.empty(n)
+        # end to end through the public API with pinned host buffers: scan build, H2D of
+        # the points and the visit list, both kernel chains, D2H of the field and the dose
+        pts_h = torch.from_numpy(np.ascontiguousarray(job.pts_xy)).pin_memory().numpy()
+        out_h = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True).numpy()
+        dose_h = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for k in range(args.steps):

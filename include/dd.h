@@ -25,8 +25,10 @@
  *     Host outputs are written before the call returns (the call synchronises
  *     the stream).  With device inputs and outputs the call only enqueues work on
  *     `cuda_stream` (NULL = the legacy default stream) and returns.
- *   - Device scratch is taken with cudaMallocAsync on the call's stream and
- *     returned with cudaFreeAsync; a scan caches its probe list per device.
+ *   - Device scratch is taken stream-ordered on the call's stream from a memory
+ *     pool the library owns per device (freed workspace up to 4 GiB stays mapped
+ *     for the next call) and returned with cudaFreeAsync; a scan caches its probe
+ *     list per device.
  */
 #ifndef DD_H
 #define DD_H

@@ -124,10 +124,10 @@ __global__ void batch_reduce_kernel(const BScan *__restrict__ sc, const int64_t 
 
 // Kernel variants with the same 512-point tile (so they share one work list).
 struct CfgMixed256 : CfgMixed {
-    static constexpr int kThreads = 256, kPPT = 2;
+    static constexpr int kThreads = 256, kPPT = 2, kSTILE = 64;
 };
 struct CfgMixed64 : CfgMixed {
-    static constexpr int kThreads = 64, kPPT = 8;
+    static constexpr int kThreads = 64, kPPT = 8, kSTILE = 64;
 };
 struct CfgF64x256 : CfgF64 {
     static constexpr int kThreads = 256, kPPT = 1;

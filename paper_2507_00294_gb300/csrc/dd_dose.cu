@@ -32,7 +32,7 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
     constexpr int RV = sizeof(Rec) / 16;
     __shared__ Real s_x[TILE + LBMAX], s_y[TILE + LBMAX];
-    __shared__ __align__(16) Rec s_rec[Cfg::kSTILE];
+    __shared__ __align__(16) Rec s_rec[Cfg::kDoseSTILE];
 
     const int2 item = items[blockIdx.x];
     const int tid = threadIdx.x;
@@ -63,8 +63,8 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
 #pragma unroll
     for (int q = 0; q < PPT; ++q) { acc[q] = 0; tot[q] = 0.0; }
 
-    for (int kk = k0; kk < k1; kk += Cfg::kSTILE) {
-        const int cnt = min(Cfg::kSTILE, k1 - kk);
+    for (int kk = k0; kk < k1; kk += Cfg::kDoseSTILE) {
+        const int cnt = min(Cfg::kDoseSTILE, k1 - kk);
         __syncthreads();
         {
             const float4 *row = reinterpret_cast<const float4 *>(lagrec + kk);
@@ -125,7 +125,7 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
                     acc[q] += pair_term(dx * dx + dy * dy, R);
                 }
             }
-            if (Cfg::kFlush < Cfg::kSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
+            if (Cfg::kFlush < Cfg::kDoseSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) { tot[q] += (double)acc[q]; acc[q] = 0; }
             }
@@ -260,11 +260,11 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     const double *src = dd::device_sources(scan, &st);
     if (!src) return st;
     void *ws = nullptr;
-    cudaError_t err = cudaMallocAsync(&ws, bytes, stream);
+    cudaError_t err = dd::workspace_alloc(&ws, bytes, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return dd::fail(err == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,
-                        std::string("cudaMallocAsync(dose workspace): ") + cudaGetErrorString(err));
+                        std::string("dose workspace allocation: ") + cudaGetErrorString(err));
     }
     char *base = (char *)ws;
     size_t off = 0;
@@ -306,11 +306,11 @@ dd_status run_dose_general(const dd_scan *scan, double *out, cudaStream_t stream
     if (!src) return st;
     void *ws = nullptr;
     const size_t bytes = (size_t)n * sizeof(double) * (out_host ? 2 : 1) + 512;
-    cudaError_t err = cudaMallocAsync(&ws, bytes, stream);
+    cudaError_t err = dd::workspace_alloc(&ws, bytes, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return dd::fail(err == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,
-                        std::string("cudaMallocAsync(dose workspace): ") + cudaGetErrorString(err));
+                        std::string("dose workspace allocation: ") + cudaGetErrorString(err));
     }
     double *sums = (double *)ws;
     double *out_dev = out_host ? sums + n : out;

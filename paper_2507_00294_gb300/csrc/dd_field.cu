@@ -118,6 +118,26 @@ cudaError_t prefer_shared() {
     return err;
 }
 
+// CTAs of field_kernel<Cfg> resident on the whole device at once (0 if unknown).
+template <typename Cfg>
+int64_t resident_ctas() {
+    static std::atomic<int64_t> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 0;
+    int64_t v = cached[dev].load();
+    if (v > 0) return v;
+    if (prefer_shared<Cfg>() != cudaSuccess) cudaGetLastError();   // occupancy at the carveout used
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ddk::field_kernel<Cfg>, Cfg::kThreads, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    v = (int64_t)per_sm * sms;
+    cached[dev].store(v);
+    return v;
+}
+
 template <typename Cfg>
 dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
                     const std::vector<double> &times, double *out, cudaStream_t stream) {
@@ -160,8 +180,26 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     while (group > Cfg::kTCH &&
            (size_t)(lattice ? 0 : group * n_src) * sizeof(Rec) + (size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget)
         group = std::max(Cfg::kTCH, group / 2);
-    // larger blocks only while the FP32 stage sums stay short (<= 32 stages of 64 visits)
-    while ((size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget && sb < 2048) sb *= 2;
+    // larger blocks only while the FP32 stage sums stay short (<= 32 stages)
+    while ((size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget && sb < 32 * Cfg::kSTILE) sb *= 2;
+    // smaller blocks (down to 128 visits) while one launch has fewer than 4 waves of
+    // resident CTAs, so that the last wave's stragglers cost little
+    {
+        const int64_t waves4 = 4 * resident_ctas<Cfg>();
+        const int n_groups = (n_t + group - 1) / group;
+        auto items_per_launch = [&](int b) {
+            int64_t blocks = 0;
+            for (int j0 = 0; j0 < n_t; j0 += Cfg::kTCH) {
+                int cmax = 0;
+                for (int j = j0; j < std::min(n_t, j0 + Cfg::kTCH); ++j) cmax = std::max(cmax, nact[j]);
+                blocks += (cmax + b - 1) / b;
+            }
+            return blocks * n_tiles / std::max(1, n_groups);
+        };
+        while (sb > 128 && waves4 > 0 && items_per_launch(sb) < waves4 &&
+               (size_t)((n_src + sb / 2 - 1) / (sb / 2)) * group * n_pts * 8 <= budget)
+            sb /= 2;
+    }
     const int nblk_max = (int)((n_src + sb - 1) / sb);
     const int n_chunks_max = (group + Cfg::kTCH - 1) / Cfg::kTCH;
 
@@ -172,11 +210,11 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     if (!src) return st;
     void *ws = nullptr;
     cudaError_t err = dd::fault_injected("alloc") ? cudaErrorMemoryAllocation
-                                                  : cudaMallocAsync(&ws, ws_bytes, stream);
+                                                  : dd::workspace_alloc(&ws, ws_bytes, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return dd::fail(err == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA,
-                        std::string("cudaMallocAsync(field workspace): ") + cudaGetErrorString(err));
+                        std::string("field workspace allocation: ") + cudaGetErrorString(err));
     }
     Carve cv(ws);
     const double *pts_dev = pts_xy_m;

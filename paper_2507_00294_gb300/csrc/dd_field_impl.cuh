@@ -95,9 +95,10 @@ __device__ __forceinline__ double moment_term_f64(double r2, const RecF64 &R) {
 struct CfgMixed {
     using Rec = RecF32;
     using Real = float;
-    static constexpr int kThreads = 128, kPPT = 4, kTCH = 4, kSTILE = 64, kSB = 512, kFlush = 32;
-    static constexpr int kMinBlocks = 6;
+    static constexpr int kThreads = 128, kPPT = 4, kTCH = 4, kSTILE = 32, kSB = 512, kFlush = 32;
+    static constexpr int kMinBlocks = 8;     // 32 warps per SM: at most 64 registers, 22 KB shared
     static constexpr int kDoseLB = 512;      // largest lag block of the dose kernel
+    static constexpr int kDoseSTILE = 64;    // lags staged per round by the dose kernel
     static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
                                 *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
@@ -107,6 +108,7 @@ struct CfgF64 {
     static constexpr int kThreads = 128, kPPT = 2, kTCH = 4, kSTILE = 32, kSB = 512, kFlush = 1 << 30;
     static constexpr int kMinBlocks = 1;
     static constexpr int kDoseLB = 512;
+    static constexpr int kDoseSTILE = 32;
     static constexpr const char *kFieldName = "field_fp64", *kCoefName = "coef_fp64",
                                 *kDoseName = "dose_fp64", *kLagCoefName = "lag_coef_fp64";
 };
@@ -223,12 +225,11 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     __syncthreads();                       // previous item's readers of sm.box are done
     if (lane == 0) sm.box[warp] = make_float4(bx0, bx1, by0, by1);
 
-    // per (snapshot, point): FP32 sum of the current 64-visit stage in registers
+    // per (snapshot, point): FP32 sum of the current stage of STILE visits in registers
     // (acc[jc / 2][k], .x for even jc, .y for odd), added after each stage to an FP32
-    // running sum in shared memory (sm.run, one column per thread: conflict-free) (8
-    // stages per item at the default block of 512 visits, at most 32 with the largest
-    // block the dispatcher picks, so that sum adds at most 32 u = 2e-6 relative error),
-    // converted to FP64 at the end of the item.
+    // running sum in shared memory (sm.run, one column per thread: conflict-free) (the
+    // dispatcher keeps blocks at or below 32 stages, so that sum adds at most 32 u = 2e-6
+    // relative error), converted to FP64 at the end of the item.
     float2 acc[NP][PPT];
 #pragma unroll
     for (int m = 0; m < NP; ++m)
@@ -290,7 +291,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 // the degree-2 path turns into an exact 0
                 uint32_t c = kCodeD2;
                 if (s0 + i < na[jc]) {
-                    const RecF32 &R = rows[jc][s0 + i];
+                    const RecF32 &R = sm.rec[jc][i];
                     const float hmax = r2max * R.dq(), amin = r2min * R.q1();
                     c = amin >= 87.0f ? kCodeSkip
                       : hmax <= kDeg2H ? kCodeD2

@@ -49,6 +49,12 @@ const double *device_sources(const dd_scan *scan, dd_status *st);
 // True if `p` is device-accessible memory of the current device.
 bool is_device_pointer(const void *p);
 
+// Stream-ordered workspace of a call, from the library's memory pool on the current
+// device.  The pool keeps up to 4 GiB of freed workspace mapped between calls (the
+// default pool returns it to the driver at every synchronisation, and mapping it again
+// costs more than a small call's kernels).  Returns the CUDA error.
+cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t stream);
+
 // Host-side fault injection for tests: true when the environment variable DD_FAULT
 // names `site` (e.g. DD_FAULT=alloc makes the next workspace allocations fail as if
 // the device were out of memory).  No device fault is ever produced.

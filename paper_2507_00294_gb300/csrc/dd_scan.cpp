@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <unordered_set>
 
@@ -55,6 +56,32 @@ bool is_device_pointer(const void *p) {
         return false;
     }
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t stream) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int device = 0;
+    cudaError_t err = cudaGetDevice(&device);
+    if (err != cudaSuccess) return err;
+    if (device < 0 || device >= 64) return cudaMallocAsync(p, bytes, stream);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!pools[device]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            err = cudaMemPoolCreate(&pools[device], &props);
+            if (err != cudaSuccess) { pools[device] = nullptr; return err; }
+            uint64_t keep = uint64_t(4) << 30;
+            err = cudaMemPoolSetAttribute(pools[device], cudaMemPoolAttrReleaseThreshold, &keep);
+            if (err != cudaSuccess) return err;
+        }
+        pool = pools[device];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, stream);
 }
 
 const double *device_sources(const dd_scan *scan, dd_status *st) {
