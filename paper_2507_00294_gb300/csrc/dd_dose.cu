@@ -26,7 +26,7 @@ template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads)
 dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, int64_t n,
             const typename Cfg::Rec *__restrict__ lagrec, const int2 *__restrict__ items, int lb,
-            double *__restrict__ partial) {
+            typename Cfg::Real *__restrict__ partial) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
@@ -58,10 +58,12 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
         px[q] = (Real)(srcX[jj] - cx);
         py[q] = (Real)(srcY[jj] - cy);
     }
+    // FP32 (or FP64) sums of up to kFlush lags, added into a compensated running sum
+    // (BlockSum: no FP64 arithmetic on the FP32 path)
     Real acc[PPT];
-    double tot[PPT];
+    BlockSum<Real> tot[PPT];
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) { acc[q] = 0; tot[q] = 0.0; }
+    for (int q = 0; q < PPT; ++q) acc[q] = 0;
 
     for (int kk = k0; kk < k1; kk += Cfg::kDoseSTILE) {
         const int cnt = min(Cfg::kDoseSTILE, k1 - kk);
@@ -127,15 +129,15 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
             }
             if (Cfg::kFlush < Cfg::kDoseSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) { tot[q] += (double)acc[q]; acc[q] = 0; }
+                for (int q = 0; q < PPT; ++q) { tot[q].add(acc[q]); acc[q] = 0; }
             }
         }
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) { tot[q] += (double)acc[q]; acc[q] = 0; }
+        for (int q = 0; q < PPT; ++q) { tot[q].add(acc[q]); acc[q] = 0; }
     }
 #pragma unroll
     for (int q = 0; q < PPT; ++q)
-        if (jt[q] < n) partial[(int64_t)item.y * n + jt[q]] = tot[q];
+        if (jt[q] < n) partial[(int64_t)item.y * n + jt[q]] = tot[q].result();
 }
 
 // Dose for arbitrary visit timing (per-visit dwells, flyback): the pair (i, j) has its
@@ -184,16 +186,19 @@ __global__ void scale_kernel(const double *__restrict__ v, int64_t n, double pre
     if (j < n) out[j] = pref * v[j];
 }
 
-__global__ void dose_reduce_kernel(const double *__restrict__ partial, int64_t n, int tile, int lb,
+template <typename Part>
+__global__ void dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int tile, int lb,
                                    double pref, double *__restrict__ out) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     // blocks written for target j: every lag block that starts below the tile's last target
     const int64_t tile_last = min(n, (j / tile + 1) * tile) - 1;
     const int64_t nb = tile_last >= 1 ? (tile_last - 1) / lb + 1 : 0;
-    double acc = 0.0;
-    for (int64_t b = 0; b < nb; ++b) acc += partial[b * n + j];
-    out[j] = pref * acc;
+    BlockSum<Part> acc;
+    // in block order (deterministic); unrolled so that several loads are in flight
+#pragma unroll 8
+    for (int64_t b = 0; b < nb; ++b) acc.add(partial[b * n + j]);
+    out[j] = pref * acc.value();
 }
 
 }  // namespace ddk
@@ -252,7 +257,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     auto add = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
     add((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
     add(its.size() * sizeof(int2) + 16);
-    add((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(double));
+    add((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(typename Cfg::Real));
     if (out_host) add((size_t)n * sizeof(double));
     bytes += 256;
 
@@ -271,14 +276,15 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     auto take = [&](size_t b) { off = (off + 255) & ~size_t(255); char *p = base + off; off += b; return p; };
     Rec *d_rec = (Rec *)take((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
     int2 *d_items = (int2 *)take(its.size() * sizeof(int2) + 16);
-    double *d_part = (double *)take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(double));
+    using Part = typename Cfg::Real;
+    Part *d_part = (Part *)take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(Part));
     double *out_dev = out_host ? (double *)take((size_t)n * sizeof(double)) : out;
 
     auto *keep = new std::vector<int2>(its.size());
     for (size_t k = 0; k < its.size(); ++k) (*keep)[k] = its[k].second;
     if (n >= 2) {
         DD_PROFILED(Cfg::kLagCoefName, stream,
-                    (ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(n, scan->s, scan->kappa, d_rec)));
+                    (ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 31) / 32), 32, 0, stream>>>(n, scan->s, scan->kappa, d_rec)));
         DD_CUDA_TRY(cudaGetLastError());
         DD_CUDA_TRY(cudaMemcpyAsync(d_items, keep->data(), keep->size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
         DD_PROFILED(Cfg::kDoseName, stream,
@@ -287,7 +293,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         DD_CUDA_TRY(cudaGetLastError());
     }
     DD_PROFILED("dose_reduce", stream,
-                (ddk::dose_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev)));
+                (ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 63) / 64), 64, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev)));
     DD_CUDA_TRY(cudaGetLastError());
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -396,7 +402,8 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     auto take = [&](size_t bytes) { off = (off + 255) & ~size_t(255); size_t o = off; off += bytes; return o; };
     const size_t o_x = take(2 * (size_t)n * sizeof(double));
     const size_t o_rec = take((size_t)n * sizeof(Rec));
-    const size_t o_part = take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(double));
+    using Part = typename Cfg::Real;
+    const size_t o_part = take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(Part));
     const size_t o_items = take((size_t)kNoAllocMaxItems * sizeof(int2));
     if (off > kNoAllocBytes)
         return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: scan needs more scratch than the 8 MiB built-in area");
@@ -427,20 +434,20 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     double *d_x = (double *)(scratch + o_x);
     double *d_y = d_x + n;
     Rec *d_rec = (Rec *)(scratch + o_rec);
-    double *d_part = (double *)(scratch + o_part);
+    Part *d_part = (Part *)(scratch + o_part);
     int2 *d_items = (int2 *)(scratch + o_items);
     // every scratch byte a kernel reads below is written earlier in this call, so
     // nothing left by a previous call can leak into the result
     DD_CUDA_TRY(cudaMemcpyAsync(d_x, scan->X.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
     DD_CUDA_TRY(cudaMemcpyAsync(d_y, scan->Y.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
     if (n >= 2) {
-        ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
+        ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 31) / 32), 32, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
         DD_CUDA_TRY(cudaGetLastError());
         DD_CUDA_TRY(cudaMemcpyAsync(d_items, flat, (size_t)count * sizeof(int2), cudaMemcpyHostToDevice, stream));
         ddk::dose_kernel<Cfg><<<(unsigned)count, Cfg::kThreads, 0, stream>>>(d_x, d_y, n, d_rec, d_items, lb, d_part);
         DD_CUDA_TRY(cudaGetLastError());
     }
-    ddk::dose_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);
+    ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 63) / 64), 64, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);
     DD_CUDA_TRY(cudaGetLastError());
     // the host staging above is reused by the next call on this thread
     DD_CUDA_TRY(cudaStreamSynchronize(stream));

@@ -38,16 +38,28 @@ __global__ void prep_points_kernel(const double *__restrict__ xy, int64_t n, dou
 }
 
 // out[row[j] * n_pts + p] = pref * sum_{k < nblk[chunk(j)]} partial[(k * n_tg + j) * n_pts + p]
-__global__ void reduce_kernel(const double *__restrict__ partial, const int *__restrict__ nblk_of_snap,
-                              const int *__restrict__ row, int n_tg, int64_t n_pts, double pref,
-                              double *__restrict__ out) {
+// out[row[j]][p] = pref * sum over the visit blocks of snapshot j, in block order
+// (deterministic); four points per thread, so that each load moves 16 bytes or more.
+template <typename Part>
+__global__ void reduce_kernel(const Part *__restrict__ partial, const int *__restrict__ nblk_of_snap,
+                              const int *__restrict__ row, int n_tg, int64_t n_pts, int64_t pstride,
+                              double pref, double *__restrict__ out) {
     const int j = blockIdx.y;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pts) return;
+    const int64_t p0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (p0 >= n_pts) return;
     const int nb = nblk_of_snap[j];
-    double acc = 0.0;
-    for (int k = 0; k < nb; ++k) acc += partial[((int64_t)k * n_tg + j) * n_pts + p];
-    out[(int64_t)row[j] * n_pts + p] = pref * acc;
+    BlockSum<Part> acc[4];
+#pragma unroll 4
+    for (int k = 0; k < nb; ++k) {
+        Part v[4];
+        load4_cg(partial + ((int64_t)k * n_tg + j) * pstride + p0, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q].add(v[q]);
+    }
+    double *o = out + (int64_t)row[j] * n_pts + p0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (p0 + q < n_pts) o[q] = pref * acc[q].value();
 }
 
 }  // namespace ddk
@@ -99,7 +111,7 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
     add((size_t)group * sizeof(int64_t));                     // record row offset per snapshot
     add((size_t)n_tiles * n_chunks * nblk_max * sizeof(int4));  // items
     add((size_t)n_rec * sizeof(Rec));                         // coefficient records
-    add((size_t)nblk_max * group * n_pts * sizeof(double));   // partial sums
+    add((size_t)nblk_max * group * ((n_pts + 3) / 4 * 4) * sizeof(typename Cfg::Real));   // partial sums
     return b + 256;
 }
 
@@ -178,14 +190,15 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     int group = n_t;
     const size_t budget = size_t(1) << 30;
     while (group > Cfg::kTCH &&
-           (size_t)(lattice ? 0 : group * n_src) * sizeof(Rec) + (size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget)
+           (size_t)(lattice ? 0 : group * n_src) * sizeof(Rec) + (size_t)((n_src + sb - 1) / sb) * group * ((n_pts + 3) / 4 * 4) * sizeof(typename Cfg::Real) > budget)
         group = std::max(Cfg::kTCH, group / 2);
     // larger blocks only while the FP32 stage sums stay short (<= 32 stages)
-    while ((size_t)((n_src + sb - 1) / sb) * group * n_pts * 8 > budget && sb < 32 * Cfg::kSTILE) sb *= 2;
+    while ((size_t)((n_src + sb - 1) / sb) * group * ((n_pts + 3) / 4 * 4) * sizeof(typename Cfg::Real) > budget && sb < 32 * Cfg::kSTILE) sb *= 2;
     // smaller blocks (down to 128 visits) while one launch has fewer than 4 waves of
     // resident CTAs, so that the last wave's stragglers cost little
     {
-        const int64_t waves4 = 4 * resident_ctas<Cfg>();
+        constexpr int kWaves = 4;
+        const int64_t waves4 = kWaves * resident_ctas<Cfg>();
         const int n_groups = (n_t + group - 1) / group;
         auto items_per_launch = [&](int b) {
             int64_t blocks = 0;
@@ -197,7 +210,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
             return blocks * n_tiles / std::max(1, n_groups);
         };
         while (sb > 128 && waves4 > 0 && items_per_launch(sb) < waves4 &&
-               (size_t)((n_src + sb / 2 - 1) / (sb / 2)) * group * n_pts * 8 <= budget)
+               (size_t)((n_src + sb / 2 - 1) / (sb / 2)) * group * ((n_pts + 3) / 4 * 4) * sizeof(typename Cfg::Real) <= budget)
             sb /= 2;
     }
     const int nblk_max = (int)((n_src + sb - 1) / sb);
@@ -233,7 +246,9 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     int64_t *d_roff = cv.take<int64_t>(group);
     int4 *d_items = cv.take<int4>((size_t)n_tiles * n_chunks_max * nblk_max);
     Rec *d_rec = cv.take<Rec>((size_t)n_rec);
-    double *d_part = cv.take<double>((size_t)nblk_max * group * n_pts);
+    using Part = typename Cfg::Real;
+    const int64_t pstride = (n_pts + 3) / 4 * 4;            // 16-byte aligned partial rows
+    Part *d_part = cv.take<Part>((size_t)nblk_max * group * pstride);
 
     DD_PROFILED("prep_points", stream,
                 (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y)));
@@ -245,7 +260,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     HostTables *keep = new HostTables();
     if (lattice) {
         DD_PROFILED(Cfg::kCoefName, stream,
-                    (ddk::rev_lag_coef_kernel<Rec><<<(unsigned)((M + 1 + 127) / 128), 128, 0, stream>>>(
+                    (ddk::rev_lag_coef_kernel<Rec><<<(unsigned)((M + 1 + 31) / 32), 32, 0, stream>>>(
                         M, scan->s, scan->kappa, d_rec)));
         DD_CUDA_TRY(cudaGetLastError());
     }
@@ -301,12 +316,12 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
             DD_CUDA_TRY(prefer_shared<Cfg>());
             DD_PROFILED(Cfg::kFieldName, stream,
                         (ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
-                            srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_items, ng, sb, d_part)));
+                            srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_items, ng, sb, d_part, pstride)));
             DD_CUDA_TRY(cudaGetLastError());
         }
-        dim3 rg((unsigned)((n_pts + 255) / 256), (unsigned)ng);
+        dim3 rg((unsigned)((n_pts + 1023) / 1024), (unsigned)ng);
         DD_PROFILED("field_reduce", stream,
-                    (ddk::reduce_kernel<<<rg, 256, 0, stream>>>(d_part, d_nblk, d_row, ng, n_pts, scan->pref, out_dev)));
+                    (ddk::reduce_kernel<Part><<<rg, 256, 0, stream>>>(d_part, d_nblk, d_row, ng, n_pts, pstride, scan->pref, out_dev)));
         DD_CUDA_TRY(cudaGetLastError());
         keep->items.push_back(std::move(it));
         keep->ints.push_back(std::move(tabs));

@@ -189,12 +189,12 @@ struct TileSmemMixed {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-template <typename Cfg, int TCH>
+template <typename Cfg, int TCH, typename Part>
 __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, const double *__restrict__ srcX,
                                                  const double *__restrict__ srcY, const double *__restrict__ X,
                                                  const double *__restrict__ Y, int64_t n_pts, int64_t tile0,
                                                  const RecF32 *const (&rows)[TCH], const int (&na)[TCH], int nj,
-                                                 int s_begin, int s_end, double *__restrict__ partial,
+                                                 int s_begin, int s_end, Part *__restrict__ partial,
                                                  int64_t part_stride) {
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE, NW = NT / 32;
     constexpr bool kPacked = TCH % 2 == 0;       // snapshot pairs on f32x2 instructions
@@ -405,7 +405,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int64_t p = tile0 + k * NT + tid;
-            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = (double)sm.run[jc * PPT + k][tid];
+            if (p < n_pts) partial[(int64_t)jc * part_stride + p] = (Part)sm.run[jc * PPT + k][tid];
         }
     }
 }
@@ -519,15 +519,55 @@ __device__ __forceinline__ void field_tile(TileSmem<Cfg, TCH> &sm, const double 
     }
 }
 
+// Running sum of FP32 (mixed path) or FP64 values.  FP32 values are added with Knuth's
+// two-sum, so s + c carries the sum to about one FP32 rounding without any FP64
+// arithmetic: FP64 runs at about 1/70 of the FP32 rate on this part, and a plain FP64
+// reduction of the FP32 partial sums ran at 0.8 TB/s instead of streaming them from HBM.
+// FP64 values are summed in FP64.
+template <typename Part>
+struct BlockSum;
+template <>
+struct BlockSum<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float b = t - s;
+        c += (s - (t - b)) + (x - b);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+    __device__ __forceinline__ float result() const { return s + c; }
+};
+template <>
+struct BlockSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ double result() const { return s; }
+};
+
+// Four consecutive per-item sums of one partial row, read at L2 (written by other SMs);
+// the row offset is a multiple of 4 elements.
+__device__ __forceinline__ void load4_cg(const float *p, float (&v)[4]) {
+    const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4_cg(const double *p, double (&v)[4]) {
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // One work item per CTA: item = (point tile, snapshot chunk, visit block).
-// partial[(block * n_tg + j) * n_pts + p] receives sum_{i in block, i < nact[j]} pair_term.
+// partial[(block * n_tg + j) * pstride + p] receives sum_{i in block, i < nact[j]} pair_term
+// (pstride = n_pts rounded up to a multiple of 4, so that rows are 16-byte aligned).
 template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kMinBlocks)
 field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
              const double *__restrict__ X, const double *__restrict__ Y, int64_t n_pts,
              const typename Cfg::Rec *__restrict__ rec, const int64_t *__restrict__ row_off,
              const int *__restrict__ nact, const int4 *__restrict__ items, int n_tg, int sb,
-             double *__restrict__ partial) {
+             typename Cfg::Real *__restrict__ partial, int64_t pstride) {
     using Rec = typename Cfg::Rec;
     constexpr int TCH = Cfg::kTCH;
     const int4 item = items[blockIdx.x];
@@ -545,16 +585,18 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
     const int s_begin = item.z * sb;
     const int s_end = min(s_begin + sb, nmax);
     const int64_t tile0 = (int64_t)item.x * (Cfg::kThreads * Cfg::kPPT);
-    double *part = partial + ((int64_t)item.z * n_tg + j0) * n_pts;
+    // per-item sums: FP32 on the mixed path (they are FP32 sums already), FP64 otherwise
+    typename Cfg::Real *part = partial + ((int64_t)item.z * n_tg + j0) * pstride;
     if constexpr (std::is_same<typename Cfg::Real, float>::value) {
         __shared__ TileSmemMixed<Cfg, TCH> sm;
         field_tile_mixed<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rows, na, min(TCH, n_tg - j0), s_begin,
-                                   s_end, part, n_pts);
+                                   s_end, part, pstride);
     } else {
         __shared__ TileSmem<Cfg, TCH> sm;
         field_tile<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rows, na, min(TCH, n_tg - j0), s_begin, s_end,
-                             part, n_pts);
+                             part, pstride);
     }
+
 }
 
 }  // namespace ddk
