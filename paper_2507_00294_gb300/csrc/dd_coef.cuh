@@ -80,15 +80,42 @@ __global__ void coef_kernel(const double *__restrict__ srcT, const double *__res
 
 template <>
 struct RecTraits<RecF32> {
+    // The exponent series of the FP32 record (see RecF32): l_m, the coefficients of
+    // ln(P(h)/c_0) with P(h) = sum_m c_m h^m, from the power-series logarithm
+    //   l_m = p_m - (1/m) sum_{k=1}^{m-1} k l_k p_{m-k},  p_m = c_m / c_0
+    // (P'/P = (ln P)'), all in FP64, rounded to FP32 once.
     static __device__ void fill(RecF32 &o, double q1, double dq, double r, double ell) {
-        double c[RecF32::kTerms];
-        moment_coefficients<RecF32::kTerms - 1>(r, ell, c);
+        constexpr int M = 12;
+        constexpr double kLog2e = 1.44269504088896340736;
+        double c[M + 1], p[M + 1], l[M + 1];
+        moment_coefficients<M>(r, ell, c);
+        const double ic0 = 1.0 / c[0];
+#pragma unroll
+        for (int m = 1; m <= M; ++m) p[m] = c[m] * ic0;
+#pragma unroll
+        for (int m = 1; m <= M; ++m) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 1; k < m; ++k) acc += k * l[k] * p[m - k];
+            l[m] = p[m] - acc * kRecip[m];
+        }
         const double dq2 = dq * dq;
-        o.v0 = make_float4((float)(-q1 * 1.44269504088896340736), (float)c[0], (float)(c[1] * dq), (float)(c[2] * dq2));
-        o.v1 = make_float4((float)(c[3] * dq2 * dq), (float)(c[4] * dq2 * dq2), (float)dq, (float)c[1]);
-        o.v2 = make_float4((float)c[2], (float)c[3], (float)c[4], (float)c[5]);
-        o.v3 = make_float4((float)c[6], (float)c[7], (float)c[8], (float)c[9]);
-        o.v4 = make_float4((float)c[10], (float)c[11], (float)c[12], 0.0f);
+        o.v0 = make_float4((float)(log(c[0]) * kLog2e), (float)(kLog2e * (l[1] * dq - q1)),
+                           (float)(kLog2e * l[2] * dq2), (float)(kLog2e * l[3] * dq2 * dq));
+        o.v1 = make_float4((float)(kLog2e * l[4] * dq2 * dq2), (float)dq, (float)q1, (float)c[0]);
+        o.v2 = make_float4((float)(kLog2e * (l[1] - 1.0 / r)), (float)(kLog2e * l[2]), (float)(kLog2e * l[3]),
+                           (float)(kLog2e * l[4]));
+        o.v3 = make_float4((float)(kLog2e * l[5]), (float)(kLog2e * l[6]), (float)(kLog2e * l[7]),
+                           (float)(kLog2e * l[8]));
+        o.v4 = make_float4((float)(kLog2e * l[9]), (float)(kLog2e * l[10]), (float)(kLog2e * l[11]),
+                           (float)(kLog2e * l[12]));
+    }
+    // a visit that has not started: every path yields 2^-inf = 0
+    static __device__ RecF32 zero() {
+        RecF32 z;
+        z.v0 = make_float4(-INFINITY, 0.f, 0.f, 0.f);
+        z.v1 = z.v2 = z.v3 = z.v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        return z;
     }
 };
 
@@ -99,6 +126,7 @@ struct RecTraits<RecF64> {
         o.q1 = q1;
         o.dq = dq;
     }
+    static __device__ RecF64 zero() { return RecF64{}; }
 };
 
 // Record for lag k = 1..n-1 of a scan with a uniform dwell (time unit = dwell):
@@ -107,7 +135,7 @@ template <typename Rec>
 __global__ void lag_coef_kernel(int64_t n, double s, double kappa, Rec *__restrict__ rec) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    if (k == 0) { rec[0] = Rec{}; return; }
+    if (k == 0) { rec[0] = RecTraits<Rec>::zero(); return; }
     double q1, dq, r, ell;
     pair_geometry((double)k, 1.0, s, kappa, q1, dq, r, ell);
     Rec out;
@@ -124,7 +152,7 @@ __global__ void rev_lag_coef_kernel(int64_t M, double s, double kappa, Rec *__re
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u > M) return;
     const int64_t L = M - u;
-    if (L == 0) { rev[u] = Rec{}; return; }
+    if (L == 0) { rev[u] = RecTraits<Rec>::zero(); return; }
     double q1, dq, r, ell;
     pair_geometry((double)L, 1.0, s, kappa, q1, dq, r, ell);
     Rec out;

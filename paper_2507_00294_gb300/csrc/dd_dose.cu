@@ -78,8 +78,8 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
             const int k = kk + c;
             const Rec &R = s_rec[c];
             if constexpr (std::is_same<Real, float>::value) {
-                // FP32: one polynomial degree for the whole warp, from the largest h and
-                // the smallest a over its lanes (the same classes as the field kernel)
+                // FP32: one exponent-series degree for the whole warp, from the largest h
+                // and the smallest a over its lanes (the same classes as the field kernel)
                 float r2[PPT];
                 bool ok[PPT];
                 bool lo = true;                 // every valid pair of this lane fits degree 2
@@ -90,18 +90,15 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
                     const float dx = ok[q] ? px[q] - s_x[i - w0] : 0.f;
                     const float dy = ok[q] ? py[q] - s_y[i - w0] : 0.f;
                     r2[q] = dx * dx + dy * dy;
-                    lo = lo && (r2[q] * R.dq() <= kDeg2H);
+                    lo = lo && (r2[q] * R.dq() <= kL2H);
                 }
                 uint32_t cls = kCodeD2;
                 // the common case is settled by one vote; otherwise classify every pair
-                if (!__all_sync(0xffffffffu, lo)) {
+                if (!__all_sync(0xffffffffu, lo && R.dq() >= kMinDqX)) {
                     cls = kCodeSkip;
 #pragma unroll
                     for (int q = 0; q < PPT; ++q) {
-                        const float h = r2[q] * R.dq(), a = r2[q] * R.q1();
-                        const uint32_t cq = !ok[q] || a >= 87.0f ? kCodeSkip
-                                          : h <= kDeg2H ? kCodeD2 : h <= kDeg4H ? kCodeD4
-                                          : h <= kHMaxF ? kCodeD8 : h <= kHMax12F ? kCodeD12 : kCodeGeneral;
+                        const uint32_t cq = !ok[q] ? kCodeSkip : series_class(r2[q] * R.dq(), r2[q] * R.q1(), R.dq());
                         cls = max(cls, cq);
                     }
                     cls = __reduce_max_sync(0xffffffffu, cls);
@@ -110,10 +107,10 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     float t;
-                    if (cls == kCodeD2) t = moment_term<2>(r2[q], R);
-                    else if (cls == kCodeD4) t = moment_term<4>(r2[q], R);
-                    else if (cls == kCodeD8) t = moment_term<8>(r2[q], R);
-                    else if (cls == kCodeD12) t = moment_term<12>(r2[q], R);
+                    if (cls == kCodeD2) t = log_term<2>(r2[q], R);
+                    else if (cls == kCodeD4) t = log_term<4>(r2[q], R);
+                    else if (cls == kCodeD8) t = log_term<8>(r2[q], R);
+                    else if (cls == kCodeD12) t = log_term<12>(r2[q], R);
                     else t = pair_term(r2[q], R);
                     acc[q] += ok[q] ? t : 0.f;
                 }

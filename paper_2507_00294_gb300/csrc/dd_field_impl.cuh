@@ -7,24 +7,38 @@
 
 namespace ddk {
 
-// Per (snapshot, visit) coefficients, FP32-mixed, 80 bytes read as five 16-byte vectors:
-//   v0 = (alpha, c_0, e_1, e_2),  v1 = (e_3, e_4, dq, c_1),  v2 = (c_2, c_3, c_4, c_5),
-//   v3 = (c_6, c_7, c_8, c_9),   v4 = (c_10, c_11, c_12, 0)
-// with alpha = -log2(e)/w1 (so e^-a = 2^(rho^2 alpha)), dq = 1/w0 - 1/w1, the moment
-// coefficients c_m (c_0 = ln(w1/w0)) and e_m = c_m dq^m, which let the low-degree paths
-// run Horner in rho^2 directly:  sum_m c_m h^m = sum_m e_m (rho^2)^m with h = rho^2 dq.
+// Per (snapshot, visit) coefficients, FP32-mixed, 80 bytes read as five 16-byte vectors.
+// The FP32 path evaluates the pair term as one power of two,
+//   E1(a) - E1(b) = e^-a P(h),  P(h) = sum_m c_m h^m,  h = rho^2 dq,  a = rho^2 q1,
+//   log2(e^-a P(h)) = g_0 - log2(e) a + log2(e) sum_{m>=1} l_m h^m,
+// where g_0 = log2(c_0), c_0 = ln(w1/w0), and l_m are the coefficients of the power series
+// of ln(P(h)/c_0) (the cumulants of the moment weight r/(1+rs) on [0,1], up to sign and
+// factorials; |l_m| <= 0.5, 0.042, 3.9e-3, 4.0e-4, 5.3e-5, 9.1e-6, 1.3e-6, 1.7e-7,
+// 3.1e-8 for m = 1..9 over r in [1e-6, 1e6], i.e. about (2 pi)^-m).  Layout:
+//   v0 = (g_0, g_1x, g_2x, g_3x),  v1 = (g_4x, dq, q1, c_0),  v2 = (k_1, k_2, k_3, k_4),
+//   v3 = (k_5, k_6, k_7, k_8),      v4 = (k_9, k_10, k_11, k_12)
+// with the exponent's coefficients in rho^2 for the low degrees,
+//   g_1x = log2(e) (l_1 dq - q1),  g_mx = log2(e) l_m dq^m  (m = 2..4),
+// and in h for the high degrees (the -a term folded in as -h/r, since a = h/r),
+//   k_1 = log2(e) (l_1 - 1/r),  k_m = log2(e) l_m  (m = 2..12).
+// A snapshot for which the visit has not started carries the zero record, g_0 = -inf and
+// everything else 0: every path then yields 2^-inf = 0.
 struct __align__(16) RecF32 {
-    static constexpr int kTerms = 13;
     float4 v0, v1, v2, v3, v4;
-    __device__ __forceinline__ float alpha() const { return v0.x; }
-    __device__ __forceinline__ float dq() const { return v1.z; }
-    __device__ __forceinline__ float q1() const { return -v0.x * 0.693147180559945309f; }
-    __device__ __forceinline__ float c(int m) const {
+    __device__ __forceinline__ float g0() const { return v0.x; }
+    __device__ __forceinline__ float dq() const { return v1.y; }
+    __device__ __forceinline__ float q1() const { return v1.z; }
+    __device__ __forceinline__ float c0() const { return v1.w; }
+    // exponent coefficient of (rho^2)^m, m = 1..4
+    __device__ __forceinline__ float gx(int m) const {
+        return m == 1 ? v0.y : m == 2 ? v0.z : m == 3 ? v0.w : v1.x;
+    }
+    // exponent coefficient of h^m, m = 1..12
+    __device__ __forceinline__ float k(int m) const {
         switch (m) {
-            case 0: return v0.y; case 1: return v1.w; case 2: return v2.x; case 3: return v2.y;
-            case 4: return v2.z; case 5: return v2.w; case 6: return v3.x; case 7: return v3.y;
-            case 8: return v3.z; case 9: return v3.w; case 10: return v4.x; case 11: return v4.y;
-            default: return v4.z;
+            case 1: return v2.x; case 2: return v2.y; case 3: return v2.z; case 4: return v2.w;
+            case 5: return v3.x; case 6: return v3.y; case 7: return v3.z; case 8: return v3.w;
+            case 9: return v4.x; case 10: return v4.y; case 11: return v4.z; default: return v4.w;
         }
     }
 };
@@ -41,25 +55,44 @@ static_assert(sizeof(RecF64) == 144, "RecF64 layout");
 template <typename Rec>
 struct RecTraits;
 
-// Largest h of the moment series.  FP32: degree 8 up to h = 1/2 and degree 12 up to
-// h = 1.2 (truncation e^{2h} h^{d+1}/(d+1)! below 4e-8 and 2e-8, cancellation at most
-// e^{2h} = 11); FP64: degree 15 up to h = 1/2 (1.2e-18).
-constexpr float kHMaxF = 0.5f;
-constexpr float kHMax12F = 1.2f;
+// Largest h of each FP32 class: the truncated exponent series of degree d stays within
+// 4e-8 of ln(P(h)/c_0) for every r in [1e-6, 1e6] (checked against 40-digit quadrature):
+// degree 2 up to h = 0.0215, 4 up to 0.235, 8 up to 1.0 and 12 up to 1.7.  FP64: the
+// moment polynomial of degree 15 up to h = 1/2 (1.2e-18).
+constexpr float kL2H = 0.0215f, kL4H = 0.235f, kL8H = 1.0f, kL12H = 1.7f;
 constexpr double kHMaxD = 0.5;
+// The rho^2 forms of degree 2 and 4 need dq^4 and dq^3 in the FP32 normal range; records
+// with a smaller dq (far beyond any scan's duration) take the h forms.
+constexpr float kMinDqX = 1.0e-8f;
 
-// One pair term E1(a) - E1(b), a = rho^2 q1, b = a + rho^2 dq, FP32 arithmetic.
-__device__ __forceinline__ float pair_term(float r2, const RecF32 &R) {
+// Degree-D exponent of one pair: rho^2 form for D = 2, 4, h form for D = 8, 12.
+template <int D, typename RV>
+__device__ __forceinline__ float log_exponent(float r2, const RV &R) {
+    if (D == 2) return fmaf(fmaf(R.gx(2), r2, R.gx(1)), r2, R.g0());
+    if (D == 4)
+        return fmaf(fmaf(fmaf(fmaf(R.gx(4), r2, R.gx(3)), r2, R.gx(2)), r2, R.gx(1)), r2, R.g0());
+    const float h = r2 * R.dq();
+    float p = R.k(D);
+#pragma unroll
+    for (int m = D - 1; m >= 1; --m) p = fmaf(p, h, R.k(m));
+    return fmaf(p, h, R.g0());
+}
+
+template <int D, typename RV>
+__device__ __forceinline__ float log_term(float r2, const RV &R) {
+    return ex2_approx(log_exponent<D>(r2, R));
+}
+
+// One pair term E1(a) - E1(b), a = rho^2 q1, b = a + rho^2 dq, FP32 arithmetic, with a
+// per-lane regime test: zero (a >= 87: below the FP32 normal range), the degree-12
+// exponent series (h <= 1.7), or the two E1 values (dd_e1.cuh).
+template <typename RV>
+__device__ __forceinline__ float pair_term(float r2, const RV &R) {
     const float a = r2 * R.q1();
     const float h = r2 * R.dq();
-    if (a >= 87.0f) return 0.0f;                  // e^-a below the FP32 normal range
-    if (h <= kHMax12F) {
-        float p = R.c(12);
-#pragma unroll
-        for (int m = 11; m >= 0; --m) p = fmaf(p, h, R.c(m));
-        return ex2_approx(r2 * R.alpha()) * p;
-    }
-    return e1diff_general_f32(a, h, R.c(0));
+    if (a >= 87.0f) return 0.0f;
+    if (h <= kL12H) return log_term<12>(r2, R);
+    return e1diff_general_f32(a, h, R.c0());
 }
 
 // The same in FP64.
@@ -125,38 +158,27 @@ struct TileSmem {
 //
 // For every staged visit and every warp, the staging threads bound the warp's a and h
 // from the bounding box of the warp's points: a_min = rho2_min q1 and h_max = rho2_max dq.
-// If a_min >= 87 for every snapshot the visit adds nothing to the warp's points (all
-// terms are below the FP32 normal range) and is skipped.  Otherwise the smallest
-// polynomial degree whose truncation bound e^{2h} h^{d+1}/(d+1)! stays below 4e-8 at
-// h_max is used for the whole warp: degree 2 (h_max <= 6.0e-3), 4 (<= 8.2e-2) or 8
-// (<= 0.5); beyond h_max = 0.5 every lane takes the per-lane regime test of pair_term.
-// Lanes whose own a is >= 87 inside a polynomial class get ex2 -> 0 (flush to zero), so
-// no per-lane test is needed on the polynomial paths.
-constexpr float kDeg2H = 6.0e-3f, kDeg4H = 8.2e-2f;
+// Per snapshot that gives a class: skip (a_min >= 87: every term is below the FP32 normal
+// range), the smallest exponent-series degree whose range holds h_max (2, 4, 8, 12), or
+// the per-lane regime test of pair_term.  When every snapshot of the chunk is on degree 2,
+// or on degree 2 or 4, the warp runs the whole visit on that degree, two snapshots per
+// f32x2 instruction; otherwise one snapshot at a time, each at its own class.  Lanes whose
+// own a is 87 or more inside a series class add terms below 2e-38, flushed to zero once
+// they leave the normal range, so the series paths need no per-lane test.
 enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeD12 = 4, kCodeGeneral = 5 };
 // classes are packed 3 bits per snapshot (up to 9 snapshots) below the 4 mode bits
 constexpr uint32_t kCodeBits = 3, kCodeMask = 7;
 // per (warp, visit): all snapshots skipped / all on degree 2 / all on degree <= 4 / mixed
 enum : uint32_t { kModeSkip = 0, kModeAllD2 = 1, kModeAllD4 = 2, kModePerSnapshot = 3 };
 
-// Degree-D moment polynomial times e^-a for one pair, from the record vectors.
-// D = 2, 4: Horner in rho^2 with e_m (no h needed); D = 8, 12: Horner in h with c_m.
-template <int D>
-__device__ __forceinline__ float moment_term(float r2, const RecF32 &R) {
-    const float e = ex2_approx(r2 * R.v0.x);
-    float p;
-    if (D == 2) {
-        p = fmaf(fmaf(R.v0.w, r2, R.v0.z), r2, R.v0.y);
-    } else if (D == 4) {
-        p = fmaf(fmaf(fmaf(fmaf(R.v1.y, r2, R.v1.x), r2, R.v0.w), r2, R.v0.z), r2, R.v0.y);
-    } else {
-        const float h = r2 * R.v1.z;
-        p = D == 12 ? fmaf(fmaf(fmaf(fmaf(R.v4.z, h, R.v4.y), h, R.v4.x), h, R.v3.w), h, R.v3.z)
-                    : R.v3.z;
-        p = fmaf(fmaf(fmaf(fmaf(p, h, R.v3.y), h, R.v3.x), h, R.v2.w), h, R.v2.z);
-        p = fmaf(fmaf(fmaf(fmaf(p, h, R.v2.y), h, R.v2.x), h, R.v1.w), h, R.v0.y);
-    }
-    return e * p;
+// Class of one (snapshot, visit) record for h_max and a_min over a set of pairs.
+__device__ __forceinline__ uint32_t series_class(float hmax, float amin, float dq) {
+    const bool x_ok = dq >= kMinDqX;
+    return amin >= 87.0f ? kCodeSkip
+         : (hmax <= kL2H && x_ok) ? kCodeD2
+         : (hmax <= kL4H && x_ok) ? kCodeD4
+         : hmax <= kL8H ? kCodeD8
+         : hmax <= kL12H ? kCodeD12 : kCodeGeneral;
 }
 
 // acc[k] (one half of each pair: H = 0 for .x, 1 for .y) += term of point k
@@ -164,17 +186,21 @@ template <int D, int PPT, int H>
 __device__ __forceinline__ void moment_pass(float2 (&acc)[PPT], const float (&r2)[PPT], const RecF32 &R) {
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const float t = moment_term<D>(r2[k], R);
+        const float t = log_term<D>(r2[k], R);
         if (H) acc[k].y += t; else acc[k].x += t;
     }
 }
 
-// Leading record vectors of two snapshots (2P, 2P+1) of one visit, interleaved so that one
-// packed (f32x2) instruction evaluates the degree-2/4 polynomial of both snapshots:
-//   a = (alpha, alpha', c_0, c_0'),  b = (e_1, e_1', e_2, e_2'),  c = (e_3, e_3', e_4, e_4')
+// Low-degree exponent coefficients of two snapshots (2P, 2P+1) of one visit, interleaved
+// so that one packed (f32x2) instruction evaluates the degree-2/4 exponent of both:
+//   a = (g_0, g_0', g_1x, g_1x'),  b = (g_2x, g_2x', g_3x, g_3x'),  c = (g_4x, g_4x', -, -)
 struct __align__(16) PairRec {
     float4 a, b, c;
 };
+
+// The zero record's leading vector (g_0 = -inf): a snapshot for which the visit has not
+// started, or a padding snapshot, adds 2^-inf = 0 on every path.
+__device__ __forceinline__ float4 zero_rec_v0() { return make_float4(-INFINITY, 0.f, 0.f, 0.f); }
 
 template <typename Cfg, int TCH>
 struct TileSmemMixed {
@@ -254,7 +280,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
             constexpr int RV = sizeof(RecF32) / 16;
             for (int v = tid; v < cnt * RV; v += NT)
-                dst[v] = (v / RV < lim) ? row[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+                dst[v] = (v / RV < lim) ? row[v] : (v % RV == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
         }
         if constexpr (kPacked) {
             // a snapshot for which this visit has not started gets a zero record: term 0
@@ -263,11 +289,12 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 for (int P = 0; P < TCH / 2; ++P) {
                     const bool l0 = s0 + i < na[2 * P], l1 = s0 + i < na[2 * P + 1];
                     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 a0 = l0 ? rows[2 * P][s0 + i].v0 : z, a1 = l1 ? rows[2 * P + 1][s0 + i].v0 : z;
+                    const float4 a0 = l0 ? rows[2 * P][s0 + i].v0 : zero_rec_v0();
+                    const float4 a1 = l1 ? rows[2 * P + 1][s0 + i].v0 : zero_rec_v0();
                     const float4 b0 = l0 ? rows[2 * P][s0 + i].v1 : z, b1 = l1 ? rows[2 * P + 1][s0 + i].v1 : z;
                     sm.pair[P][i].a = make_float4(a0.x, a1.x, a0.y, a1.y);
                     sm.pair[P][i].b = make_float4(a0.z, a1.z, a0.w, a1.w);
-                    sm.pair[P][i].c = make_float4(b0.x, b1.x, b0.y, b1.y);
+                    sm.pair[P][i].c = make_float4(b0.x, b1.x, 0.f, 0.f);
                 }
             }
         }
@@ -292,12 +319,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 uint32_t c = kCodeD2;
                 if (s0 + i < na[jc]) {
                     const RecF32 &R = sm.rec[jc][i];
-                    const float hmax = r2max * R.dq(), amin = r2min * R.q1();
-                    c = amin >= 87.0f ? kCodeSkip
-                      : hmax <= kDeg2H ? kCodeD2
-                      : hmax <= kDeg4H ? kCodeD4
-                      : hmax <= kHMaxF ? kCodeD8
-                      : hmax <= kHMax12F ? kCodeD12 : kCodeGeneral;
+                    c = series_class(r2max * R.dq(), r2min * R.q1(), R.dq());
                     any = any || c != kCodeSkip;
                 }
                 cmin = min(cmin, c);
@@ -328,9 +350,10 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 r2[2 * m + 1] = q.y;
             }
             if (kPacked && (mode == kModeAllD2 || mode == kModeAllD4)) {
-                // every snapshot of the chunk on one low-degree polynomial: both snapshots
-                // of a pair in one f32x2 instruction; the leading vectors first, so their
-                // shared-memory latency overlaps
+                // every snapshot of the chunk on one low-degree exponent series: both
+                // snapshots of a pair in one f32x2 instruction; the coefficient vectors
+                // first, so their shared-memory latency overlaps
+                //   term = 2^(g_0 + g_1x r + g_2x r^2 [+ g_3x r^3 + g_4x r^4]),  r = rho^2
                 float4 va[NP], vb[NP];
 #pragma unroll
                 for (int P = 0; P < TCH / 2; ++P) { va[P] = sm.pair[P][s].a; vb[P] = sm.pair[P][s].b; }
@@ -340,11 +363,9 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
                             const float2 r = f2(r2[k], r2[k]);
-                            const float2 t = __fmul2_rn(r, f2(va[P].x, va[P].y));
-                            const float2 e = f2(ex2_approx(t.x), ex2_approx(t.y));
-                            const float2 p = __ffma2_rn(__ffma2_rn(f2(vb[P].z, vb[P].w), r, f2(vb[P].x, vb[P].y)), r,
-                                                        f2(va[P].z, va[P].w));
-                            acc[P][k] = __ffma2_rn(e, p, acc[P][k]);
+                            const float2 g = __ffma2_rn(__ffma2_rn(f2(vb[P].x, vb[P].y), r, f2(va[P].z, va[P].w)), r,
+                                                        f2(va[P].x, va[P].y));
+                            acc[P][k] = __fadd2_rn(acc[P][k], f2(ex2_approx(g.x), ex2_approx(g.y)));
                         }
                 } else {
 #pragma unroll
@@ -353,13 +374,11 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
                             const float2 r = f2(r2[k], r2[k]);
-                            const float2 t = __fmul2_rn(r, f2(va[P].x, va[P].y));
-                            const float2 e = f2(ex2_approx(t.x), ex2_approx(t.y));
-                            float2 p = __ffma2_rn(f2(vc.z, vc.w), r, f2(vc.x, vc.y));
-                            p = __ffma2_rn(p, r, f2(vb[P].z, vb[P].w));
-                            p = __ffma2_rn(p, r, f2(vb[P].x, vb[P].y));
-                            p = __ffma2_rn(p, r, f2(va[P].z, va[P].w));
-                            acc[P][k] = __ffma2_rn(e, p, acc[P][k]);
+                            float2 g = __ffma2_rn(f2(vc.x, vc.y), r, f2(vb[P].z, vb[P].w));
+                            g = __ffma2_rn(g, r, f2(vb[P].x, vb[P].y));
+                            g = __ffma2_rn(g, r, f2(va[P].z, va[P].w));
+                            g = __ffma2_rn(g, r, f2(va[P].x, va[P].y));
+                            acc[P][k] = __fadd2_rn(acc[P][k], f2(ex2_approx(g.x), ex2_approx(g.y)));
                         }
                     }
                 }
