@@ -31,16 +31,22 @@ import numpy as np  # noqa: E402
 
 METRIC = "E1 pair-terms/s"
 UNIT = "pair-terms/s"
-# FP32 FLOPs of one pair term on each path of the field kernel (FMA = 2): rho^2 costs 5
-# flops per (point, visit) and is shared by the 4 snapshots of a chunk (1.25 per pair);
-# the moment paths add h, the exponent argument, a Horner polynomial of degree d and the
-# fused scale-and-accumulate: 4 + 2d flops (degree 2 up to h = 6e-3, 4 up to 8.2e-2, 8 up
-# to 0.5, 12 up to 1.2); the general path (two E1 values) about 55.
-FLOPS_MOMENT = {2: 9.25, 4: 13.25, 8: 21.25, 12: 29.25}
+# Algorithmic cost of one pair term on each path of the field kernel's FP32 exponent
+# series (FMA = 2 flops): rho^2 costs 5 flops per (point, visit), shared by the 4
+# snapshots of a chunk (1.25 per pair); a series path of degree d adds its exponent (2d
+# flops for d = 2, 4 in rho^2; 2d + 1 for d = 8, 12 in h) and the accumulating add, plus
+# one ex2 (degree 2 up to h = 0.0215, 4 up to 0.235, 8 up to 1.0, 12 up to 1.7); the
+# general path (two E1 values) about 55 flops and 4 MUFU operations (2 ex2, 2 rcp); a
+# pair with a >= 87 only its rho^2.
+FLOPS_SERIES = {2: 6.25, 4: 10.25, 8: 19.25, 12: 27.25}
 FLOPS_GENERAL = 56.25
 FLOPS_ZERO = 1.25
+MUFU_SERIES, MUFU_GENERAL = 1.0, 4.0
 # FP32 peak from the unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# MUFU ex2 peak: 32 per clock per SM (GB300 doubles the SFU exponential rate of B200; a
+# microbenchmark on this GPU measured 30.6 per clock per SM at 1.995 GHz) x 152 x 2.07 GHz.
+MUFU_PEAK_TOPS = 152 * 32 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -162,10 +168,11 @@ def recorded_traffic(kernel):
         return None
 
 
-def flops_per_pair(job, samples=400_000, seed=5):
-    """Algorithmic FP32 FLOPs per pair-term of the field kernel on this workload: the
-    cost of the cheapest path that meets the FP32 accuracy target for each pair (degree
-    from that pair's own h, zero when a >= 87), averaged over seeded pairs."""
+def ops_per_pair(job, samples=400_000, seed=5):
+    """Algorithmic FP32 FLOPs and MUFU operations per pair-term of the field kernel on this
+    workload: the cost of the cheapest path that meets the FP32 accuracy target for each
+    pair (series degree from that pair's own h, zero when a >= 87), averaged over seeded
+    pairs."""
     from paper_2507_00294_gb300 import workloads as w
     s = job.scan
     rng = np.random.default_rng(seed)
@@ -185,13 +192,15 @@ def flops_per_pair(job, samples=400_000, seed=5):
     w1 = 2 * Ds + 4 * D * dt
     w0 = np.where(dt <= tau, 2 * Ds, 2 * Ds + 4 * D * (dt - tau))
     a, h = rho2 / w1, rho2 / w0 - rho2 / w1
-    f = np.where(a >= 87, FLOPS_ZERO,
-                 np.where(h <= 6.0e-3, FLOPS_MOMENT[2],
-                          np.where(h <= 8.2e-2, FLOPS_MOMENT[4],
-                                   np.where(h <= 0.5, FLOPS_MOMENT[8],
-                                            np.where(h <= 1.2, FLOPS_MOMENT[12], FLOPS_GENERAL)))))
+    zero = a >= 87
+    f = np.where(zero, FLOPS_ZERO,
+                 np.where(h <= 0.0215, FLOPS_SERIES[2],
+                          np.where(h <= 0.235, FLOPS_SERIES[4],
+                                   np.where(h <= 1.0, FLOPS_SERIES[8],
+                                            np.where(h <= 1.7, FLOPS_SERIES[12], FLOPS_GENERAL)))))
+    m = np.where(zero, 0.0, np.where(h <= 1.7, MUFU_SERIES, MUFU_GENERAL))
     wgt = nact[np.arange(samples)]               # pairs are sampled per snapshot: weight by n_active
-    return float(np.sum(f * wgt) / np.sum(wgt))
+    return float(np.sum(f * wgt) / np.sum(wgt)), float(np.sum(m * wgt) / np.sum(wgt))
 
 
 def workload():
@@ -421,16 +430,25 @@ def run_ours(args):
     # roofline of the dominant kernel (field_mixed), from its own events in the timed region
     fl, fms = prof.get("field_mixed", (0, 0.0))
     avg_ms = fms / max(1, fl)
-    fpp = flops_per_pair(job)
-    achieved = fpp * field_pairs / (avg_ms / 1e3) / 1e12 if fl else None
+    fpp, mpp = ops_per_pair(job)
+    rate = field_pairs / (avg_ms / 1e3) if fl else None
     traffic = recorded_traffic("field_mixed")
-    roofline = {"bound": "alu", "kernel": "field_mixed", "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
-                "traffic": traffic, "avg_launch_ms": avg_ms,
-                "flops_per_pair": round(fpp, 3), "pairs_per_launch": field_pairs,
-                "kernel_pairs_per_s": field_pairs / (avg_ms / 1e3) if fl else None,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"}
+    # the pair term needs FP32 issue and one MUFU ex2: report the pipe this algorithm's mix
+    # binds (the larger fraction), with the other beside it
+    fp32 = {"achieved": fpp * rate / 1e12 if rate else None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "per_pair": round(fpp, 3),
+            "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"}
+    mufu = {"achieved": mpp * rate / 1e12 if rate else None, "peak": MUFU_PEAK_TOPS, "unit": "TOP/s",
+            "per_pair": round(mpp, 4),
+            "peak_note": "MUFU ex2: 152 SMs x 32 per clock x 2070 MHz"}
+    for x in (fp32, mufu):
+        x["frac"] = x["achieved"] / x["peak"] if x["achieved"] else None
+    bind, other = (mufu, fp32) if (mufu["frac"] or 0) >= (fp32["frac"] or 0) else (fp32, mufu)
+    roofline = {"bound": "alu", "kernel": "field_mixed", "pipe": "mufu" if bind is mufu else "fp32",
+                "achieved": bind["achieved"], "peak": bind["peak"], "unit": bind["unit"], "frac": bind["frac"],
+                "traffic": traffic, "avg_launch_ms": avg_ms, "pairs_per_launch": field_pairs,
+                "kernel_pairs_per_s": rate, "ops_per_pair": bind["per_pair"], "peak_note": bind["peak_note"],
+                "other_pipe": {"pipe": "fp32" if bind is mufu else "mufu", **other}}
     launches = int(sum(v[0] for v in prof.values()))
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
 
