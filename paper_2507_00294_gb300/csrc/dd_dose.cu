@@ -277,15 +277,21 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     Part *d_part = (Part *)take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(Part));
     double *out_dev = out_host ? (double *)take((size_t)n * sizeof(double)) : out;
 
-    auto *keep = new std::vector<int2>(its.size());
-    for (size_t k = 0; k < its.size(); ++k) (*keep)[k] = its[k].second;
+    // work list, kept until the stream has consumed its upload (pinned staging when available)
+    struct Keep {
+        std::vector<int2> items;
+        dd::CallStaging staging;
+    };
+    auto *keep = new Keep();
+    keep->items.resize(its.size());
+    for (size_t k = 0; k < its.size(); ++k) keep->items[k] = its[k].second;
     if (n >= 2) {
         DD_PROFILED(Cfg::kLagCoefName, stream,
                     (ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 31) / 32), 32, 0, stream>>>(n, scan->s, scan->kappa, d_rec)));
         DD_CUDA_TRY(cudaGetLastError());
-        DD_CUDA_TRY(cudaMemcpyAsync(d_items, keep->data(), keep->size() * sizeof(int2), cudaMemcpyHostToDevice, stream));
+        DD_CUDA_TRY(keep->staging.upload(d_items, keep->items.data(), keep->items.size() * sizeof(int2), stream));
         DD_PROFILED(Cfg::kDoseName, stream,
-                    (ddk::dose_kernel<Cfg><<<(unsigned)keep->size(), Cfg::kThreads, 0, stream>>>(
+                    (ddk::dose_kernel<Cfg><<<(unsigned)keep->items.size(), Cfg::kThreads, 0, stream>>>(
                         src, src + n, n, d_rec, d_items, lb, d_part)));
         DD_CUDA_TRY(cudaGetLastError());
     }
@@ -295,7 +301,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
-    DD_CUDA_TRY(cudaLaunchHostFunc(stream, [](void *p) { delete static_cast<std::vector<int2> *>(p); }, keep));
+    DD_CUDA_TRY(dd::defer_release(stream, keep, [](void *p) { delete static_cast<Keep *>(p); }));
     if (out_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
 }

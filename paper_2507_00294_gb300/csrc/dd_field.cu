@@ -83,13 +83,16 @@ struct Carve {
     }
 };
 
-// Host-side tables uploaded with cudaMemcpyAsync; freed from a stream callback.
+// Host-side tables, uploaded through pinned staging blocks; freed (and the blocks given
+// back) once an event recorded after the uploads has completed.
 struct HostTables {
     std::vector<std::vector<int4>> items;
     std::vector<std::vector<int>> ints;
     std::vector<std::vector<double>> reals;
     std::vector<std::vector<int64_t>> offs;
-    static void CUDART_CB release(void *p) { delete static_cast<HostTables *>(p); }
+    std::vector<std::vector<char>> images; // per group: the tables as laid out on the device
+    dd::CallStaging staging;               // pinned copies the uploads were made from
+    static void release(void *p) { delete static_cast<HostTables *>(p); }
 };
 
 // Sizes of the workspace a call needs (the same function drives the carve).
@@ -301,11 +304,18 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         std::vector<int4> it(items.size());
         for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
 
-        DD_CUDA_TRY(cudaMemcpyAsync(d_t, tg.data(), ng * sizeof(double), cudaMemcpyHostToDevice, stream));
-        DD_CUDA_TRY(cudaMemcpyAsync(d_nact, tabs.data(), 3 * (size_t)ng * sizeof(int), cudaMemcpyHostToDevice, stream));
-        if (!it.empty())
-            DD_CUDA_TRY(cudaMemcpyAsync(d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, stream));
-        DD_CUDA_TRY(cudaMemcpyAsync(d_roff, roff.data(), ng * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+        // the group's tables in one copy: a host image of the device span d_t .. items end
+        {
+            char *const d0 = reinterpret_cast<char *>(d_t);
+            const size_t span = reinterpret_cast<char *>(d_items + it.size()) - d0;
+            std::vector<char> img(span);
+            std::memcpy(img.data(), tg.data(), ng * sizeof(double));
+            std::memcpy(img.data() + (reinterpret_cast<char *>(d_nact) - d0), tabs.data(), 3 * (size_t)ng * sizeof(int));
+            std::memcpy(img.data() + (reinterpret_cast<char *>(d_roff) - d0), roff.data(), ng * sizeof(int64_t));
+            std::memcpy(img.data() + (reinterpret_cast<char *>(d_items) - d0), it.data(), it.size() * sizeof(int4));
+            DD_CUDA_TRY(keep->staging.upload(d0, img.data(), span, stream));
+            keep->images.push_back(std::move(img));
+        }
         if (max_nact > 0 && !lattice) {
             dim3 cg((unsigned)((max_nact + 127) / 128), (unsigned)ng);
             DD_PROFILED(Cfg::kCoefName, stream,
@@ -331,7 +341,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n_t * n_pts * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
-    DD_CUDA_TRY(cudaLaunchHostFunc(stream, HostTables::release, keep));
+    DD_CUDA_TRY(dd::defer_release(stream, keep, HostTables::release));
     if (out_host || pts_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
 }

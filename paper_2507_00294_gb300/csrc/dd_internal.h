@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units (not installed).
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -54,6 +55,53 @@ bool is_device_pointer(const void *p);
 // default pool returns it to the driver at every synchronisation, and mapping it again
 // costs more than a small call's kernels).  Returns the CUDA error.
 cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t stream);
+
+// Pinned host staging for the small tables a call uploads (work lists, snapshot
+// tables).  A copy from pageable memory is staged by the driver and can hold the host
+// until the stream drains, which serialises the host's preparation of the next call
+// with the GPU; from pinned memory it is a plain asynchronous DMA.  Blocks are recycled:
+// a call takes blocks, and the host function it enqueues after its copies gives them
+// back once the copies have completed.  pinned_take returns
+// {nullptr, 0} if pinned memory cannot be had; the caller then copies from pageable
+// memory.
+struct PinnedBlock {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+PinnedBlock pinned_take(size_t bytes);
+void pinned_give(PinnedBlock b);
+
+// The pinned blocks one call staged its uploads through; given back when this is deleted
+// (after the stream has consumed the copies: see defer_release).
+struct CallStaging {
+    std::vector<PinnedBlock> blocks;
+    CallStaging() = default;
+    CallStaging(const CallStaging &) = delete;
+    CallStaging &operator=(const CallStaging &) = delete;
+    ~CallStaging() {
+        for (auto &b : blocks) pinned_give(b);
+    }
+    // n bytes at host src to device dst on `stream`, through a pinned block when one can be
+    // had (src must then stay valid only for this call), else straight from src (which
+    // must stay valid until the stream has consumed the copy).
+    cudaError_t upload(void *dst, const void *src, size_t n, cudaStream_t stream) {
+        if (n == 0) return cudaSuccess;
+        PinnedBlock b = pinned_take(n);
+        if (!b.p) return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, stream);
+        std::memcpy(b.p, src, n);
+        blocks.push_back(b);
+        return cudaMemcpyAsync(dst, b.p, n, cudaMemcpyHostToDevice, stream);
+    }
+};
+
+// Keeps a call's host tables (and the pinned blocks their uploads came from) alive until
+// the work enqueued so far on `stream` has completed, without putting a host function in
+// the stream (a host function stalls the stream until the driver's callback thread has
+// run it).  An event recorded now marks the point; later calls release every entry whose
+// event has completed, and wait for the oldest once more than 256 are pending.  `obj` is
+// deleted by `del`.  Returns the CUDA error of the event record (then `obj` is deleted
+// only after a device synchronisation).
+cudaError_t defer_release(cudaStream_t stream, void *obj, void (*del)(void *));
 
 // Host-side fault injection for tests: true when the environment variable DD_FAULT
 // names `site` (e.g. DD_FAULT=alloc makes the next workspace allocations fail as if

@@ -9,9 +9,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <new>
 #include <unordered_set>
+#include <vector>
 
 #include "dd_internal.h"
 
@@ -82,6 +84,93 @@ cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t stream) {
         pool = pools[device];
     }
     return cudaMallocFromPoolAsync(p, bytes, pool, stream);
+}
+
+static std::mutex g_pinned_mu;
+static std::vector<void *> g_pinned_free[48];    // by size class: 2^k bytes
+
+PinnedBlock pinned_take(size_t bytes) {
+    int k = 12;                                    // at least 4 KiB
+    while (k < 47 && (size_t(1) << k) < bytes) ++k;
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        if (!g_pinned_free[k].empty()) {
+            void *p = g_pinned_free[k].back();
+            g_pinned_free[k].pop_back();
+            return {p, size_t(1) << k};
+        }
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, size_t(1) << k, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return {};
+    }
+    return {p, size_t(1) << k};
+}
+
+void pinned_give(PinnedBlock b) {
+    if (!b.p) return;
+    int k = 12;
+    while (k < 47 && (size_t(1) << k) < b.cap) ++k;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free[k].push_back(b.p);
+}
+
+struct Deferred {
+    cudaEvent_t ev;
+    int device;
+    void *obj;
+    void (*del)(void *);
+};
+static std::mutex g_deferred_mu;
+static std::deque<Deferred> g_deferred;
+static std::vector<cudaEvent_t> g_free_events[64];   // events are per device
+
+cudaError_t defer_release(cudaStream_t stream, void *obj, void (*del)(void *)) {
+    std::vector<Deferred> done;
+    int device = 0;
+    cudaError_t err = cudaGetDevice(&device);
+    if (err == cudaSuccess && (device < 0 || device >= 64)) err = cudaErrorInvalidDevice;
+    if (err == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_deferred_mu);
+        // release what has completed (in order: the list is in enqueue order per stream)
+        for (auto it = g_deferred.begin(); it != g_deferred.end();) {
+            if (cudaEventQuery(it->ev) == cudaSuccess) {
+                done.push_back(*it);
+                it = g_deferred.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        cudaGetLastError();                         // a query of unfinished work is not an error
+        if (g_deferred.size() > 256) {
+            Deferred d = g_deferred.front();
+            g_deferred.pop_front();
+            cudaEventSynchronize(d.ev);
+            done.push_back(d);
+        }
+        cudaEvent_t ev = nullptr;
+        if (!g_free_events[device].empty()) {
+            ev = g_free_events[device].back();
+            g_free_events[device].pop_back();
+        } else {
+            err = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(ev, stream);
+        if (err == cudaSuccess) {
+            g_deferred.push_back({ev, device, obj, del});
+        } else {
+            cudaGetLastError();
+            if (ev) g_free_events[device].push_back(ev);
+        }
+        for (auto &d : done) g_free_events[d.device].push_back(d.ev);
+    }
+    for (auto &d : done) d.del(d.obj);
+    if (err != cudaSuccess) {
+        cudaDeviceSynchronize();
+        del(obj);
+    }
+    return err;
 }
 
 const double *device_sources(const dd_scan *scan, dd_status *st) {
