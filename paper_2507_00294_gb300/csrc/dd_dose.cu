@@ -29,7 +29,7 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
             typename Cfg::Real *__restrict__ partial) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
-    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
+    constexpr int NT = Cfg::kThreads, PPT = Cfg::kDosePPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
     constexpr int RV = sizeof(Rec) / 16;
     __shared__ Real s_x[TILE + LBMAX], s_y[TILE + LBMAX];
     __shared__ __align__(16) Rec s_rec[Cfg::kDoseSTILE];
@@ -207,7 +207,7 @@ namespace {
 // into too few CTAs to fill the GPU).
 template <typename Cfg>
 int dose_lag_block(int64_t n) {
-    constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
+    constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
@@ -232,7 +232,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     using Rec = typename Cfg::Rec;
     const int64_t n = scan->n;
     const bool out_host = !dd::is_device_pointer(out);
-    constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
+    constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     const int lb = dose_lag_block<Cfg>(n);
     const int64_t n_tiles = (n + TILE - 1) / TILE;
     std::vector<std::pair<int64_t, int2>> its;
@@ -397,7 +397,7 @@ template <typename Cfg>
 dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream, char *scratch) {
     using Rec = typename Cfg::Rec;
     const int64_t n = scan->n;
-    constexpr int TILE = Cfg::kThreads * Cfg::kPPT;
+    constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     const int lb = Cfg::kDoseLB;
     const int64_t n_tiles = (n + TILE - 1) / TILE;
     const int64_t nblk = n >= 2 ? (n - 2) / lb + 1 : 0;

@@ -132,6 +132,7 @@ struct CfgMixed {
     static constexpr int kMinBlocks = 8;     // 32 warps per SM: at most 64 registers, 22 KB shared
     static constexpr int kDoseLB = 512;      // largest lag block of the dose kernel
     static constexpr int kDoseSTILE = 64;    // lags staged per round by the dose kernel
+    static constexpr int kDosePPT = 1;       // targets per thread in the dose kernel (128-target tiles)
     static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
                                 *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
@@ -142,6 +143,7 @@ struct CfgF64 {
     static constexpr int kMinBlocks = 1;
     static constexpr int kDoseLB = 512;
     static constexpr int kDoseSTILE = 32;
+    static constexpr int kDosePPT = 2;
     static constexpr const char *kFieldName = "field_fp64", *kCoefName = "coef_fp64",
                                 *kDoseName = "dose_fp64", *kLagCoefName = "lag_coef_fp64";
 };
