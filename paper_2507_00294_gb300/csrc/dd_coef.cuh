@@ -52,6 +52,39 @@ __device__ void moment_coefficients(double r, double ell, double *c) {
     }
 }
 
+// The same in FP32 (for the FP32 record's exponent series, whose coefficients beyond
+// c_0 only enter as corrections l_m h^m next to the FP64-computed exponent terms; the
+// recurrences are the stable ones above, so FP32 keeps them to a few ulp, and the
+// dependent chain is a few hundred cycles instead of the FP64 unit's tens of thousands).
+template <int M>
+__device__ void moment_coefficients_f32(float r, float ell, float *c) {
+    float J[M + 1];
+    if (r >= 1.0f) {
+        const float ir = 1.0f / r;
+        J[0] = ell;
+#pragma unroll
+        for (int m = 1; m <= M; ++m) J[m] = (float)kRecip[m] - J[m - 1] * ir;
+    } else {
+        const float rho = r / (1.0f + r);
+        float term = rho * (float)kRecip[M + 1], sum = 0.0f;
+        for (int k = 1; k < 64; ++k) {
+            sum += term;
+            term *= rho * (float)k * (float)kRecip[M + 1 + k];
+            if (term <= 1e-9f * sum) break;
+        }
+        J[M] = sum;
+#pragma unroll
+        for (int m = M; m >= 1; --m) J[m - 1] = r * ((float)kRecip[m] - J[m]);
+        J[0] = ell;
+    }
+    float inv_fact = 1.0f;
+#pragma unroll
+    for (int m = 0; m <= M; ++m) {
+        c[m] = (m & 1) ? -J[m] * inv_fact : J[m] * inv_fact;
+        inv_fact *= (float)kRecip[m + 1];
+    }
+}
+
 __device__ __forceinline__ void pair_geometry(double dT, double tau, double s, double kappa,
                                               double &q1, double &dq, double &r, double &ell) {
     const bool on = dT <= tau;                         // Eq. 1 while t_i <= t <= t_i + tau_i
@@ -83,32 +116,32 @@ struct RecTraits<RecF32> {
     // The exponent series of the FP32 record (see RecF32): l_m, the coefficients of
     // ln(P(h)/c_0) with P(h) = sum_m c_m h^m, from the power-series logarithm
     //   l_m = p_m - (1/m) sum_{k=1}^{m-1} k l_k p_{m-k},  p_m = c_m / c_0
-    // (P'/P = (ln P)'), all in FP64, rounded to FP32 once.
+    // (P'/P = (ln P)').
     static __device__ void fill(RecF32 &o, double q1, double dq, double r, double ell) {
         constexpr int M = 12;
         constexpr double kLog2e = 1.44269504088896340736;
-        double c[M + 1], p[M + 1], l[M + 1];
-        moment_coefficients<M>(r, ell, c);
-        const double ic0 = 1.0 / c[0];
+        // the exponent's leading terms (q1, dq, 1/r, log2 c_0) in FP64; the corrections
+        // l_m (|l_m h^m| <= 0.85, rounded to FP32 in the record anyway) in FP32
+        float cf[M + 1], p[M + 1], l[M + 1];
+        moment_coefficients_f32<M>((float)r, (float)ell, cf);
+        const float ic0 = 1.0f / cf[0];
 #pragma unroll
-        for (int m = 1; m <= M; ++m) p[m] = c[m] * ic0;
+        for (int m = 1; m <= M; ++m) p[m] = cf[m] * ic0;
 #pragma unroll
         for (int m = 1; m <= M; ++m) {
-            double acc = 0.0;
+            float acc = 0.0f;
 #pragma unroll
-            for (int k = 1; k < m; ++k) acc += k * l[k] * p[m - k];
-            l[m] = p[m] - acc * kRecip[m];
+            for (int k = 1; k < m; ++k) acc = fmaf((float)k * l[k], p[m - k], acc);
+            l[m] = p[m] - acc * (float)kRecip[m];
         }
+        const float kLog2eF = (float)kLog2e;
         const double dq2 = dq * dq;
-        o.v0 = make_float4((float)(log(c[0]) * kLog2e), (float)(kLog2e * (l[1] * dq - q1)),
-                           (float)(kLog2e * l[2] * dq2), (float)(kLog2e * l[3] * dq2 * dq));
-        o.v1 = make_float4((float)(kLog2e * l[4] * dq2 * dq2), (float)dq, (float)q1, (float)c[0]);
-        o.v2 = make_float4((float)(kLog2e * (l[1] - 1.0 / r)), (float)(kLog2e * l[2]), (float)(kLog2e * l[3]),
-                           (float)(kLog2e * l[4]));
-        o.v3 = make_float4((float)(kLog2e * l[5]), (float)(kLog2e * l[6]), (float)(kLog2e * l[7]),
-                           (float)(kLog2e * l[8]));
-        o.v4 = make_float4((float)(kLog2e * l[9]), (float)(kLog2e * l[10]), (float)(kLog2e * l[11]),
-                           (float)(kLog2e * l[12]));
+        o.v0 = make_float4((float)(log(ell) * kLog2e), (float)(kLog2e * ((double)l[1] * dq - q1)),
+                           (float)(kLog2e * dq2) * l[2], (float)(kLog2e * dq2 * dq) * l[3]);
+        o.v1 = make_float4((float)(kLog2e * dq2 * dq2) * l[4], (float)dq, (float)q1, (float)ell);
+        o.v2 = make_float4((float)(kLog2e * ((double)l[1] - 1.0 / r)), kLog2eF * l[2], kLog2eF * l[3], kLog2eF * l[4]);
+        o.v3 = make_float4(kLog2eF * l[5], kLog2eF * l[6], kLog2eF * l[7], kLog2eF * l[8]);
+        o.v4 = make_float4(kLog2eF * l[9], kLog2eF * l[10], kLog2eF * l[11], kLog2eF * l[12]);
     }
     // a visit that has not started: every path yields 2^-inf = 0
     static __device__ RecF32 zero() {

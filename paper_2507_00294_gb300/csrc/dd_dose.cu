@@ -183,19 +183,36 @@ __global__ void scale_kernel(const double *__restrict__ v, int64_t n, double pre
     if (j < n) out[j] = pref * v[j];
 }
 
+// out[j] = pref * sum over the lag blocks of target j.  A block of 256 threads serves 32
+// targets: lane t of warp q sums the blocks b = q, q + 8, q + 16, ... of target t (in
+// order), and warp 0 adds the eight results in q order -- a fixed association, so the
+// result is deterministic, with eight times the loads in flight of one thread per target.
+constexpr int kDoseReduceSplit = 8;
 template <typename Part>
-__global__ void dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int tile, int lb,
-                                   double pref, double *__restrict__ out) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    // blocks written for target j: every lag block that starts below the tile's last target
-    const int64_t tile_last = min(n, (j / tile + 1) * tile) - 1;
-    const int64_t nb = tile_last >= 1 ? (tile_last - 1) / lb + 1 : 0;
-    BlockSum<Part> acc;
-    // in block order (deterministic); unrolled so that several loads are in flight
-#pragma unroll 8
-    for (int64_t b = 0; b < nb; ++b) acc.add(partial[b * n + j]);
-    out[j] = pref * acc.value();
+__global__ void __launch_bounds__(32 * kDoseReduceSplit)
+dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int tile, int lb, double pref,
+                   double *__restrict__ out) {
+    __shared__ double s_sum[kDoseReduceSplit][32];
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    double v = 0.0;
+    if (j < n) {
+        // blocks written for target j: every lag block that starts below the tile's last target
+        const int64_t tile_last = min(n, (j / tile + 1) * tile) - 1;
+        const int64_t nb = tile_last >= 1 ? (tile_last - 1) / lb + 1 : 0;
+        BlockSum<Part> acc;
+#pragma unroll 4
+        for (int64_t b = q; b < nb; b += kDoseReduceSplit) acc.add(partial[b * n + j]);
+        v = acc.value();
+    }
+    s_sum[q][lane] = v;
+    __syncthreads();
+    if (q == 0 && j < n) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < kDoseReduceSplit; ++k) t += s_sum[k][lane];
+        out[j] = pref * t;
+    }
 }
 
 }  // namespace ddk
@@ -296,7 +313,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         DD_CUDA_TRY(cudaGetLastError());
     }
     DD_PROFILED("dose_reduce", stream,
-                (ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 63) / 64), 64, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev)));
+                (ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev)));
     DD_CUDA_TRY(cudaGetLastError());
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -450,7 +467,7 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
         ddk::dose_kernel<Cfg><<<(unsigned)count, Cfg::kThreads, 0, stream>>>(d_x, d_y, n, d_rec, d_items, lb, d_part);
         DD_CUDA_TRY(cudaGetLastError());
     }
-    ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 63) / 64), 64, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);
+    ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);
     DD_CUDA_TRY(cudaGetLastError());
     // the host staging above is reused by the next call on this thread
     DD_CUDA_TRY(cudaStreamSynchronize(stream));

@@ -59,7 +59,7 @@ __global__ void reduce_kernel(const Part *__restrict__ partial, const int *__res
     double *o = out + (int64_t)row[j] * n_pts + p0;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        if (p0 + q < n_pts) o[q] = pref * acc[q].value();
+        if (p0 + q < n_pts) o[q] = pref * acc[q].result();
 }
 
 }  // namespace ddk

@@ -557,6 +557,7 @@ struct BlockSum<float> {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+    // s + c rounded to FP32 (one rounding; no FP64 arithmetic)
     __device__ __forceinline__ float result() const { return s + c; }
 };
 template <>
