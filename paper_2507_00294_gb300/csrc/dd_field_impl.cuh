@@ -158,8 +158,8 @@ struct TileSmem {
 
 // ---- FP32-mixed tile with warp-uniform regime selection -------------------------
 //
-// For every staged visit and every warp, the staging threads bound the warp's a and h
-// from the bounding box of the warp's points: a_min = rho2_min q1 and h_max = rho2_max dq.
+// For every staged visit, each warp bounds its own a and h from the bounding box of its
+// points (one visit per lane): a_min = rho2_min q1 and h_max = rho2_max dq.
 // Per snapshot that gives a class: skip (a_min >= 87: every term is below the FP32 normal
 // range), the smallest exponent-series degree whose range holds h_max (2, 4, 8, 12), or
 // the per-lane regime test of pair_term.  When every snapshot of the chunk is on degree 2,
@@ -209,8 +209,6 @@ struct TileSmemMixed {
     static constexpr int kPairs = TCH / 2 > 0 ? TCH / 2 : 1;
     float run[TCH * Cfg::kPPT][Cfg::kThreads];         // per-thread running sums over stages
     float4 xy[Cfg::kSTILE];                             // (-x, -x, -y, -y) of each staged visit
-    uint32_t code[Cfg::kThreads / 32][Cfg::kSTILE];   // per warp: classes and mode of each visit
-    float4 box[Cfg::kThreads / 32];                     // per warp: (xmin, xmax, ymin, ymax)
     __align__(16) RecF32 rec[TCH][Cfg::kSTILE];
     PairRec pair[kPairs][Cfg::kSTILE];                  // snapshot pairs (even TCH only)
 };
@@ -228,7 +226,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     constexpr bool kPacked = TCH % 2 == 0;       // snapshot pairs on f32x2 instructions
     constexpr int NP = (TCH + 1) / 2;            // accumulator pairs
     static_assert(PPT % 2 == 0, "points are processed in pairs");
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
 
     const double cx = X[tile0], cy = Y[tile0];
     // points k = 2m, 2m+1 in one pair
@@ -250,8 +248,6 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
         by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
         by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
     }
-    __syncthreads();                       // previous item's readers of sm.box are done
-    if (lane == 0) sm.box[warp] = make_float4(bx0, bx1, by0, by1);
 
     // per (snapshot, point): FP32 sum of the current stage of STILE visits in registers
     // (acc[jc / 2][k], .x for even jc, .y for odd), added after each stage to an FP32
@@ -300,44 +296,49 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 }
             }
         }
-        __syncthreads();                   // coordinates and box visible
-        for (int e = tid; e < cnt * NW; e += NT) {
-            const int i = e % cnt, w = e / cnt;
-            const float4 bb = sm.box[w];
-            const float sx = -sm.xy[i].x, sy = -sm.xy[i].z;
-            const float dx1 = fmaxf(fabsf(sx - bb.x), fabsf(sx - bb.y));
-            const float dy1 = fmaxf(fabsf(sy - bb.z), fabsf(sy - bb.w));
-            const float dx0 = fmaxf(0.0f, fmaxf(bb.x - sx, sx - bb.y));
-            const float dy0 = fmaxf(0.0f, fmaxf(bb.z - sy, sy - bb.w));
-            // rounding margin on the bounds of rho^2
-            const float r2max = (dx1 * dx1 + dy1 * dy1) * 1.0001f + 1e-6f;
-            const float r2min = (dx0 * dx0 + dy0 * dy0) * 0.9999f;
-            uint32_t word = 0, cmin = kCodeGeneral, cmax = kCodeSkip;
-            bool any = false;
+        __syncthreads();                   // staged coordinates and records visible
+        // classification: lane i of each warp classifies staged visits i, i + 32, .. for
+        // its own warp (box in registers); the words stay in registers and the loop below
+        // broadcasts them
+        constexpr int NCW = (STILE + 31) / 32;
+        uint32_t my_word[NCW];
 #pragma unroll
-            for (int jc = 0; jc < TCH; ++jc) {
-                // a snapshot for which this visit has not started has a zero record, which
-                // the degree-2 path turns into an exact 0
-                uint32_t c = kCodeD2;
-                if (s0 + i < na[jc]) {
-                    const RecF32 &R = sm.rec[jc][i];
-                    c = series_class(r2max * R.dq(), r2min * R.q1(), R.dq());
-                    any = any || c != kCodeSkip;
+        for (int cw = 0; cw < NCW; ++cw) {
+            const int i = cw * 32 + lane;
+            my_word[cw] = kModeSkip << 28;
+            if (i < cnt) {
+                const float sx = -sm.xy[i].x, sy = -sm.xy[i].z;
+                const float dx1 = fmaxf(fabsf(sx - bx0), fabsf(sx - bx1));
+                const float dy1 = fmaxf(fabsf(sy - by0), fabsf(sy - by1));
+                const float dx0 = fmaxf(0.0f, fmaxf(bx0 - sx, sx - bx1));
+                const float dy0 = fmaxf(0.0f, fmaxf(by0 - sy, sy - by1));
+                const float r2max = (dx1 * dx1 + dy1 * dy1) * 1.0001f + 1e-6f;
+                const float r2min = (dx0 * dx0 + dy0 * dy0) * 0.9999f;
+                uint32_t word = 0, cmin = kCodeGeneral, cmax = kCodeSkip;
+                bool any = false;
+#pragma unroll
+                for (int jc = 0; jc < TCH; ++jc) {
+                    uint32_t c = kCodeD2;
+                    if (s0 + i < na[jc]) {
+                        const RecF32 &R = sm.rec[jc][i];
+                        c = series_class(r2max * R.dq(), r2min * R.q1(), R.dq());
+                        any = any || c != kCodeSkip;
+                    }
+                    cmin = min(cmin, c);
+                    cmax = max(cmax, c);
+                    word |= c << (kCodeBits * jc);
                 }
-                cmin = min(cmin, c);
-                cmax = max(cmax, c);
-                word |= c << (kCodeBits * jc);
+                const uint32_t mode = !any ? kModeSkip
+                                    : (cmin >= kCodeD2 && cmax == kCodeD2) ? kModeAllD2
+                                    : (cmin >= kCodeD2 && cmax == kCodeD4) ? kModeAllD4 : kModePerSnapshot;
+                my_word[cw] = (word & 0x0fffffffu) | (mode << 28);
             }
-            // bits 28..31: how the whole visit is handled for this warp
-            static_assert(TCH * kCodeBits <= 28, "class codes overlap the mode bits");
-            const uint32_t mode = !any ? kModeSkip
-                                : (cmin >= kCodeD2 && cmax == kCodeD2) ? kModeAllD2
-                                : (cmin >= kCodeD2 && cmax == kCodeD4) ? kModeAllD4 : kModePerSnapshot;
-            sm.code[w][i] = (word & 0x0fffffffu) | (mode << 28);
         }
-        __syncthreads();
         for (int s = 0; s < cnt; ++s) {
-            const uint32_t word = sm.code[warp][s];
+            uint32_t w0 = my_word[0];
+#pragma unroll
+            for (int cw = 1; cw < NCW; ++cw) if ((s >> 5) == cw) w0 = my_word[cw];
+            const uint32_t word = __shfl_sync(0xffffffffu, w0, s & 31);
             const uint32_t mode = word >> 28;
             if (mode == kModeSkip) continue;               // warp-uniform skip
             // rho^2 of point pairs: (px - sx)^2 + (py - sy)^2 on f32x2
