@@ -271,28 +271,23 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             const float x = (float)(srcX[s0 + i] - cx), y = (float)(srcY[s0 + i] - cy);
             sm.xy[i] = make_float4(-x, -x, -y, -y);
         }
+        // records; a snapshot for which the visit has not started gets the zero record,
+        // whose terms are 0.  The low-degree coefficients also go, interleaved by snapshot
+        // pair, into sm.pair for the f32x2 paths (half jc & 1 of pair jc / 2).
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc) {
             const float4 *row = reinterpret_cast<const float4 *>(rows[jc] + s0);
             const int lim = na[jc] - s0;
             float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
             constexpr int RV = sizeof(RecF32) / 16;
-            for (int v = tid; v < cnt * RV; v += NT)
-                dst[v] = (v / RV < lim) ? row[v] : (v % RV == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
-        }
-        if constexpr (kPacked) {
-            // a snapshot for which this visit has not started gets a zero record: term 0
-            for (int i = tid; i < cnt; i += NT) {
-#pragma unroll
-                for (int P = 0; P < TCH / 2; ++P) {
-                    const bool l0 = s0 + i < na[2 * P], l1 = s0 + i < na[2 * P + 1];
-                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 a0 = l0 ? rows[2 * P][s0 + i].v0 : zero_rec_v0();
-                    const float4 a1 = l1 ? rows[2 * P + 1][s0 + i].v0 : zero_rec_v0();
-                    const float4 b0 = l0 ? rows[2 * P][s0 + i].v1 : z, b1 = l1 ? rows[2 * P + 1][s0 + i].v1 : z;
-                    sm.pair[P][i].a = make_float4(a0.x, a1.x, a0.y, a1.y);
-                    sm.pair[P][i].b = make_float4(a0.z, a1.z, a0.w, a1.w);
-                    sm.pair[P][i].c = make_float4(b0.x, b1.x, 0.f, 0.f);
+            for (int v = tid; v < cnt * RV; v += NT) {
+                const int i = v / RV, q = v - i * RV;
+                const float4 r = i < lim ? row[v] : (q == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
+                dst[v] = r;
+                if (kPacked && q <= 1) {
+                    float *pa = reinterpret_cast<float *>(&sm.pair[jc >> 1][i]) + (jc & 1);
+                    if (q == 0) { pa[0] = r.x; pa[2] = r.y; pa[4] = r.z; pa[6] = r.w; }
+                    else pa[8] = r.x;
                 }
             }
         }
