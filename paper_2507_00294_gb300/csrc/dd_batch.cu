@@ -35,6 +35,7 @@ namespace ddk {
 
 struct BScan {
     const double *src;          // X | Y | T | TAU of the scan, n each (dimensionless)
+    const float4 *srcF;         // X, Y of the scan's visits as float-float pairs
     int64_t n;                  // visits
     int64_t pt_off, n_pts;      // points of the scan in the global arrays
     int64_t rec_off;            // first record of the scan
@@ -52,14 +53,18 @@ __device__ __forceinline__ int find_segment(const int64_t *__restrict__ offs, in
     return lo;
 }
 
+// Points in pitch units: FP64 X, Y and float-float F (x_hi, x_lo, y_hi, y_lo).
 __global__ void batch_prep_kernel(const BScan *__restrict__ sc, const int64_t *__restrict__ pt_offs, int n_scans,
                                   const double *__restrict__ xy, int64_t total, double *__restrict__ X,
-                                  double *__restrict__ Y) {
+                                  double *__restrict__ Y, float4 *__restrict__ F) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
     const double ip = sc[find_segment(pt_offs, n_scans, g)].inv_pitch;
-    X[g] = xy[2 * g] * ip;
-    Y[g] = xy[2 * g + 1] * ip;
+    const double x = xy[2 * g] * ip, y = xy[2 * g + 1] * ip;
+    X[g] = x;
+    Y[g] = y;
+    const float xh = (float)x, yh = (float)y;
+    F[g] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
 }
 
 template <typename Rec>
@@ -82,7 +87,8 @@ template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads)
 batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items, int n_items,
                    unsigned *__restrict__ counter, const double *__restrict__ X, const double *__restrict__ Y,
-                   const typename Cfg::Rec *__restrict__ rec, int sb, double *__restrict__ partial) {
+                   const float4 *__restrict__ F, const typename Cfg::Rec *__restrict__ rec, int sb,
+                   double *__restrict__ partial) {
     constexpr bool kMixed = std::is_same<typename Cfg::Real, float>::value;
     using Smem = typename std::conditional<kMixed, TileSmemMixed<Cfg, 1>, TileSmem<Cfg, 1>>::type;
     __shared__ Smem sm;
@@ -101,7 +107,7 @@ batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items,
         const int s_begin = item.z * sb;
         const int s_end = min(s_begin + sb, S.nact);
         if constexpr (kMixed)
-            field_tile_mixed<Cfg, 1>(sm, S.src, S.src + S.n, X + S.pt_off, Y + S.pt_off, S.n_pts,
+            field_tile_mixed<Cfg, 1>(sm, S.srcF, F + S.pt_off, S.n_pts,
                                      (int64_t)item.y * TILE, rows, na, 1, s_begin, s_end,
                                      partial + S.part_off + (int64_t)item.z * S.n_pts, S.n_pts);
         else
@@ -150,6 +156,7 @@ struct dd_batch {
     int4 *d_items = nullptr;
     unsigned *d_counter = nullptr;
     double *d_X = nullptr, *d_Y = nullptr, *d_part = nullptr;
+    float4 *d_F = nullptr;
     void *d_rec = nullptr;
     double *d_pts = nullptr, *d_out = nullptr;   // staging for host buffers
     cudaStream_t cap = nullptr;
@@ -183,7 +190,7 @@ int persistent_grid() {
 template <typename Cfg>
 void launch_field(dd_batch *b, int grid, cudaStream_t st) {
     ddk::batch_field_kernel<Cfg><<<grid, Cfg::kThreads, 0, st>>>(
-        b->d_sc, b->d_items, b->n_items, b->d_counter, b->d_X, b->d_Y,
+        b->d_sc, b->d_items, b->n_items, b->d_counter, b->d_X, b->d_Y, b->d_F,
         (const typename Cfg::Rec *)b->d_rec, b->sb, b->d_part);
 }
 
@@ -191,7 +198,7 @@ void launch_field(dd_batch *b, int grid, cudaStream_t st) {
 dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cudaStream_t st) {
     const unsigned nb_pts = (unsigned)((b->total_pts + 255) / 256);
     DD_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st));
-    ddk::batch_prep_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, pts, b->total_pts, b->d_X, b->d_Y);
+    ddk::batch_prep_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, pts, b->total_pts, b->d_X, b->d_Y, b->d_F);
     if (b->total_rec > 0) {
         const unsigned nb = (unsigned)((b->total_rec + 127) / 128);
         if (b->prec == DD_MIXED)
@@ -278,6 +285,7 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
         if (!src) return st;
         ddk::BScan &S = sc[(size_t)k];
         S.src = src;
+        S.srcF = dd::device_sources_ff(s, &st);
         S.n = s->n;
         S.pt_off = pt_offsets[k];
         S.n_pts = pt_offsets[k + 1] - pt_offsets[k];
@@ -316,6 +324,7 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
     const size_t o_it = add(std::max<size_t>(1, items.size()) * sizeof(int4));
     const size_t o_ct = add(sizeof(unsigned));
     const size_t o_x = add(2 * (size_t)std::max<int64_t>(1, b->total_pts) * sizeof(double));
+    const size_t o_f = add((size_t)std::max<int64_t>(1, b->total_pts) * sizeof(float4));
     const size_t o_rec = add((size_t)std::max<int64_t>(1, rec) * rec_size);
     const size_t o_part = add((size_t)std::max<int64_t>(1, part) * sizeof(double));
     cudaError_t err = cudaMalloc(&b->ws, bytes);
@@ -331,6 +340,7 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
     b->d_counter = (unsigned *)(base + o_ct);
     b->d_X = (double *)(base + o_x);
     b->d_Y = b->d_X + std::max<int64_t>(1, b->total_pts);
+    b->d_F = (float4 *)(base + o_f);
     b->d_rec = base + o_rec;
     b->d_part = (double *)(base + o_part);
     std::vector<int4> it(items.size());

@@ -26,7 +26,7 @@ template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads)
 dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, int64_t n,
             const typename Cfg::Rec *__restrict__ lagrec, const int2 *__restrict__ items, int lb,
-            typename Cfg::Real *__restrict__ partial) {
+            typename Cfg::Real *__restrict__ partial, const float4 *__restrict__ srcF) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kDosePPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
@@ -43,11 +43,21 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     // sources needed: i = j - k for j in [t0, t1), k in [k0, k1): i in [t0 - k1 + 1, t1 - k0)
     const int64_t w0 = t0 - k1 + 1;
     const int64_t w1 = t1 - k0;
+    // coordinates relative to the tile's first target: FP32 from the float-float copy on
+    // the FP32 path (no FP64 arithmetic), FP64 otherwise
+    constexpr bool kF32 = std::is_same<Real, float>::value;
     const double cx = srcX[t0], cy = srcY[t0];
+    const float4 org = kF32 ? srcF[t0] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = w0 + tid; i < w1; i += NT) {
         const int64_t ic = i < 0 ? 0 : i;                  // i < 0 never used
-        s_x[i - w0] = (Real)(srcX[ic] - cx);
-        s_y[i - w0] = (Real)(srcY[ic] - cy);
+        if constexpr (kF32) {
+            const float2 d = ff_diff(srcF[ic], org);
+            s_x[i - w0] = d.x;
+            s_y[i - w0] = d.y;
+        } else {
+            s_x[i - w0] = (Real)(srcX[ic] - cx);
+            s_y[i - w0] = (Real)(srcY[ic] - cy);
+        }
     }
     Real px[PPT], py[PPT];
     int64_t jt[PPT];
@@ -55,8 +65,14 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     for (int q = 0; q < PPT; ++q) {
         jt[q] = t0 + q * NT + tid;
         const int64_t jj = jt[q] < n ? jt[q] : t0;
-        px[q] = (Real)(srcX[jj] - cx);
-        py[q] = (Real)(srcY[jj] - cy);
+        if constexpr (kF32) {
+            const float2 d = ff_diff(srcF[jj], org);
+            px[q] = d.x;
+            py[q] = d.y;
+        } else {
+            px[q] = (Real)(srcX[jj] - cx);
+            py[q] = (Real)(srcY[jj] - cy);
+        }
     }
     // FP32 (or FP64) sums of up to kFlush lags, added into a compensated running sum
     // (BlockSum: no FP64 arithmetic on the FP32 path)
@@ -278,6 +294,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, &st);
     if (!src) return st;
+    const float4 *srcF = dd::device_sources_ff(scan, &st);
     void *ws = nullptr;
     cudaError_t err = dd::workspace_alloc(&ws, bytes, stream);
     if (err != cudaSuccess) {
@@ -309,7 +326,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         DD_CUDA_TRY(keep->staging.upload(d_items, keep->items.data(), keep->items.size() * sizeof(int2), stream));
         DD_PROFILED(Cfg::kDoseName, stream,
                     (ddk::dose_kernel<Cfg><<<(unsigned)keep->items.size(), Cfg::kThreads, 0, stream>>>(
-                        src, src + n, n, d_rec, d_items, lb, d_part)));
+                        src, src + n, n, d_rec, d_items, lb, d_part, srcF)));
         DD_CUDA_TRY(cudaGetLastError());
     }
     DD_PROFILED("dose_reduce", stream,
@@ -421,6 +438,7 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + 255) & ~size_t(255); size_t o = off; off += bytes; return o; };
     const size_t o_x = take(2 * (size_t)n * sizeof(double));
+    const size_t o_f = take((size_t)n * sizeof(float4));
     const size_t o_rec = take((size_t)n * sizeof(Rec));
     using Part = typename Cfg::Real;
     const size_t o_part = take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(Part));
@@ -453,6 +471,15 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
 
     double *d_x = (double *)(scratch + o_x);
     double *d_y = d_x + n;
+    float4 *d_f = (float4 *)(scratch + o_f);
+    // float-float copy of the coordinates (host staging reused by the next call)
+    static thread_local std::vector<float4> ffh;
+    ffh.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const float xh = (float)scan->X[(size_t)i], yh = (float)scan->Y[(size_t)i];
+        ffh[(size_t)i] = make_float4(xh, (float)(scan->X[(size_t)i] - (double)xh), yh,
+                                     (float)(scan->Y[(size_t)i] - (double)yh));
+    }
     Rec *d_rec = (Rec *)(scratch + o_rec);
     Part *d_part = (Part *)(scratch + o_part);
     int2 *d_items = (int2 *)(scratch + o_items);
@@ -460,11 +487,12 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     // nothing left by a previous call can leak into the result
     DD_CUDA_TRY(cudaMemcpyAsync(d_x, scan->X.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
     DD_CUDA_TRY(cudaMemcpyAsync(d_y, scan->Y.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
+    DD_CUDA_TRY(cudaMemcpyAsync(d_f, ffh.data(), (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, stream));
     if (n >= 2) {
         ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 31) / 32), 32, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
         DD_CUDA_TRY(cudaGetLastError());
         DD_CUDA_TRY(cudaMemcpyAsync(d_items, flat, (size_t)count * sizeof(int2), cudaMemcpyHostToDevice, stream));
-        ddk::dose_kernel<Cfg><<<(unsigned)count, Cfg::kThreads, 0, stream>>>(d_x, d_y, n, d_rec, d_items, lb, d_part);
+        ddk::dose_kernel<Cfg><<<(unsigned)count, Cfg::kThreads, 0, stream>>>(d_x, d_y, n, d_rec, d_items, lb, d_part, d_f);
         DD_CUDA_TRY(cudaGetLastError());
     }
     ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);

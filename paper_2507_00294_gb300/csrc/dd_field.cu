@@ -29,12 +29,17 @@
 
 namespace ddk {
 
+// Points in pitch units: FP64 X, Y, and float-float (x_hi, x_lo, y_hi, y_lo) for the FP32
+// tile, so that the FP32 kernels form coordinate differences without FP64 arithmetic.
 __global__ void prep_points_kernel(const double *__restrict__ xy, int64_t n, double inv_p,
-                                   double *__restrict__ X, double *__restrict__ Y) {
+                                   double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    X[k] = xy[2 * k] * inv_p;
-    Y[k] = xy[2 * k + 1] * inv_p;
+    const double x = xy[2 * k] * inv_p, y = xy[2 * k + 1] * inv_p;
+    X[k] = x;
+    Y[k] = y;
+    const float xh = (float)x, yh = (float)y;
+    F[k] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
 }
 
 // out[row[j] * n_pts + p] = pref * sum_{k < nblk[chunk(j)]} partial[(k * n_tg + j) * n_pts + p]
@@ -109,6 +114,7 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
     if (pts_host) add(2 * (size_t)n_pts * sizeof(double));
     if (out_host) add((size_t)n_t * n_pts * sizeof(double));
     add(2 * (size_t)n_pts * sizeof(double));                  // X, Y in pitch units
+    add((size_t)n_pts * sizeof(float4));                      // the same as float-float
     add((size_t)group * sizeof(double));                      // snapshot times
     add((size_t)group * sizeof(int) * 3);                     // nact, row, nblk per snapshot
     add((size_t)group * sizeof(int64_t));                     // record row offset per snapshot
@@ -224,6 +230,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, &st);
     if (!src) return st;
+    const float4 *srcF = dd::device_sources_ff(scan, &st);
     void *ws = nullptr;
     cudaError_t err = dd::fault_injected("alloc") ? cudaErrorMemoryAllocation
                                                   : dd::workspace_alloc(&ws, ws_bytes, stream);
@@ -242,6 +249,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     double *out_dev = out_host ? cv.take<double>((size_t)n_t * n_pts) : out;
     double *X = cv.take<double>(2 * (size_t)n_pts);
     double *Y = X + n_pts;
+    float4 *PF = cv.take<float4>((size_t)n_pts);
     double *d_t = cv.take<double>(group);
     int *d_nact = cv.take<int>(3 * (size_t)group);
     int *d_row = d_nact + group;
@@ -254,7 +262,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     Part *d_part = cv.take<Part>((size_t)nblk_max * group * pstride);
 
     DD_PROFILED("prep_points", stream,
-                (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y)));
+                (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y, PF)));
     DD_CUDA_TRY(cudaGetLastError());
 
     const double *srcX = src, *srcY = src + n_src, *srcT = src + 2 * n_src, *srcTAU = src + 3 * n_src;
@@ -326,7 +334,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
             DD_CUDA_TRY(prefer_shared<Cfg>());
             DD_PROFILED(Cfg::kFieldName, stream,
                         (ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
-                            srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_items, ng, sb, d_part, pstride)));
+                            srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_items, ng, sb, d_part, pstride, srcF, PF)));
             DD_CUDA_TRY(cudaGetLastError());
         }
         dim3 rg((unsigned)((n_pts + 1023) / 1024), (unsigned)ng);

@@ -215,10 +215,16 @@ struct TileSmemMixed {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Coordinate difference a - b of two float-float values (x_hi, x_lo, y_hi, y_lo): FP32
+// arithmetic only, within about one FP32 rounding of the exact difference.
+__device__ __forceinline__ float2 ff_diff(const float4 &a, const float4 &b) {
+    return make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
+}
+
+// srcF: visit coordinates, ptsF: point coordinates, both float-float in pitch units.
 template <typename Cfg, int TCH, typename Part>
-__device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, const double *__restrict__ srcX,
-                                                 const double *__restrict__ srcY, const double *__restrict__ X,
-                                                 const double *__restrict__ Y, int64_t n_pts, int64_t tile0,
+__device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, const float4 *__restrict__ srcF,
+                                                 const float4 *__restrict__ ptsF, int64_t n_pts, int64_t tile0,
                                                  const RecF32 *const (&rows)[TCH], const int (&na)[TCH], int nj,
                                                  int s_begin, int s_end, Part *__restrict__ partial,
                                                  int64_t part_stride) {
@@ -228,15 +234,16 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     static_assert(PPT % 2 == 0, "points are processed in pairs");
     const int tid = threadIdx.x, lane = tid & 31;
 
-    const double cx = X[tile0], cy = Y[tile0];
-    // points k = 2m, 2m+1 in one pair
+    // coordinates relative to the tile's first point (keeps FP32 differences precise far
+    // from the origin); points k = 2m, 2m+1 in one pair
+    const float4 org = ptsF[tile0];
     float2 px[PPT / 2], py[PPT / 2];
     float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int64_t p = tile0 + k * NT + tid;
-        const float x = p < n_pts ? (float)(X[p] - cx) : 0.0f;
-        const float y = p < n_pts ? (float)(Y[p] - cy) : 0.0f;
+        const float2 d = p < n_pts ? ff_diff(ptsF[p], org) : make_float2(0.0f, 0.0f);
+        const float x = d.x, y = d.y;
         if (k & 1) { px[k >> 1].y = x; py[k >> 1].y = y; } else { px[k >> 1].x = x; py[k >> 1].x = y; }
         bx0 = fminf(bx0, x); bx1 = fmaxf(bx1, x);
         by0 = fminf(by0, y); by1 = fmaxf(by1, y);
@@ -268,8 +275,8 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
         const int cnt = min(STILE, s_end - s0);
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
-            const float x = (float)(srcX[s0 + i] - cx), y = (float)(srcY[s0 + i] - cy);
-            sm.xy[i] = make_float4(-x, -x, -y, -y);
+            const float2 d = ff_diff(srcF[s0 + i], org);
+            sm.xy[i] = make_float4(-d.x, -d.x, -d.y, -d.y);
         }
         // records; a snapshot for which the visit has not started gets the zero record,
         // whose terms are 0.  The low-degree coefficients also go, interleaved by snapshot
@@ -585,7 +592,8 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
              const double *__restrict__ X, const double *__restrict__ Y, int64_t n_pts,
              const typename Cfg::Rec *__restrict__ rec, const int64_t *__restrict__ row_off,
              const int *__restrict__ nact, const int4 *__restrict__ items, int n_tg, int sb,
-             typename Cfg::Real *__restrict__ partial, int64_t pstride) {
+             typename Cfg::Real *__restrict__ partial, int64_t pstride, const float4 *__restrict__ srcF,
+             const float4 *__restrict__ ptsF) {
     using Rec = typename Cfg::Rec;
     constexpr int TCH = Cfg::kTCH;
     const int4 item = items[blockIdx.x];
@@ -607,7 +615,7 @@ field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
     typename Cfg::Real *part = partial + ((int64_t)item.z * n_tg + j0) * pstride;
     if constexpr (std::is_same<typename Cfg::Real, float>::value) {
         __shared__ TileSmemMixed<Cfg, TCH> sm;
-        field_tile_mixed<Cfg, TCH>(sm, srcX, srcY, X, Y, n_pts, tile0, rows, na, min(TCH, n_tg - j0), s_begin,
+        field_tile_mixed<Cfg, TCH>(sm, srcF, ptsF, n_pts, tile0, rows, na, min(TCH, n_tg - j0), s_begin,
                                    s_end, part, pstride);
     } else {
         __shared__ TileSmem<Cfg, TCH> sm;

@@ -30,7 +30,8 @@ struct dd_scan {
     double s = 0, kappa = 0, pref = 0;   // dimensionless Ds, D, and Q0/(4 pi D) [u/m^2]
     std::vector<double> X, Y, T, TAU;    // dimensionless, visit order
 
-    struct DevCache { int device; double *src; };   // 4n doubles: X | Y | T | TAU
+    // per device: 4n doubles X | Y | T | TAU, then n float4 (x_hi, x_lo, y_hi, y_lo)
+    struct DevCache { int device; double *src; };
     mutable std::mutex mu;
     mutable std::vector<DevCache> dev;
 };
@@ -46,6 +47,10 @@ void clear_error();
 // (created on first use with cudaMalloc, synchronously).  Returns NULL on failure
 // after recording the error in *st.
 const double *device_sources(const dd_scan *scan, dd_status *st);
+// The same visits' X, Y as float-float pairs (hi = fl32(v), lo = fl32(v - hi)), so FP32
+// kernels form coordinate differences without FP64 arithmetic: n float4 stored after the
+// FP64 arrays of the same cache.
+const float4 *device_sources_ff(const dd_scan *scan, dd_status *st);
 
 // True if `p` is device-accessible memory of the current device.
 bool is_device_pointer(const void *p);

@@ -181,18 +181,32 @@ const double *device_sources(const dd_scan *scan, dd_status *st) {
     for (auto &c : scan->dev)
         if (c.device == device) return c.src;
     const size_t n = (size_t)scan->n;
-    std::vector<double> host(4 * n);
+    // 4n doubles, then n float4 of float-float coordinates (16-byte aligned: 32n bytes in)
+    std::vector<double> host(4 * n + 2 * n);
     std::memcpy(host.data(), scan->X.data(), n * sizeof(double));
     std::memcpy(host.data() + n, scan->Y.data(), n * sizeof(double));
     std::memcpy(host.data() + 2 * n, scan->T.data(), n * sizeof(double));
     std::memcpy(host.data() + 3 * n, scan->TAU.data(), n * sizeof(double));
+    float *ff = reinterpret_cast<float *>(host.data() + 4 * n);
+    for (size_t i = 0; i < n; ++i) {
+        const float xh = (float)scan->X[i], yh = (float)scan->Y[i];
+        ff[4 * i] = xh;
+        ff[4 * i + 1] = (float)(scan->X[i] - (double)xh);
+        ff[4 * i + 2] = yh;
+        ff[4 * i + 3] = (float)(scan->Y[i] - (double)yh);
+    }
     double *d = nullptr;
-    err = cudaMalloc(&d, 4 * n * sizeof(double));
+    err = cudaMalloc(&d, host.size() * sizeof(double));
     if (err != cudaSuccess) { *st = fail_cuda(err, "cudaMalloc(scan visit cache)"); cudaGetLastError(); return nullptr; }
-    err = cudaMemcpy(d, host.data(), 4 * n * sizeof(double), cudaMemcpyHostToDevice);
+    err = cudaMemcpy(d, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) { cudaFree(d); *st = fail_cuda(err, "cudaMemcpy(scan visit cache)"); return nullptr; }
     scan->dev.push_back({device, d});
     return d;
+}
+
+const float4 *device_sources_ff(const dd_scan *scan, dd_status *st) {
+    const double *d = device_sources(scan, st);
+    return d ? reinterpret_cast<const float4 *>(d + 4 * scan->n) : nullptr;
 }
 
 }  // namespace dd
