@@ -193,6 +193,17 @@ __device__ __forceinline__ void moment_pass(float2 (&acc)[PPT], const float (&r2
     }
 }
 
+// One snapshot at PPT points into point-pair accumulators: acc[k / 2].x (k even) or .y
+// (k odd) += term of point k.
+template <int D, int PPT>
+__device__ __forceinline__ void point_pass(float2 (&acc)[PPT], const float (&r2)[PPT], const RecF32 &R) {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const float t = log_term<D>(r2[k], R);
+        if (k & 1) acc[k >> 1].y += t; else acc[k >> 1].x += t;
+    }
+}
+
 // Low-degree exponent coefficients of two snapshots (2P, 2P+1) of one visit, interleaved
 // so that one packed (f32x2) instruction evaluates the degree-2/4 exponent of both:
 //   a = (g_0, g_0', g_1x, g_1x'),  b = (g_2x, g_2x', g_3x, g_3x'),  c = (g_4x, g_4x', -, -)
@@ -230,7 +241,10 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                                                  int64_t part_stride) {
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE, NW = NT / 32;
     constexpr bool kPacked = TCH % 2 == 0;       // snapshot pairs on f32x2 instructions
-    constexpr int NP = (TCH + 1) / 2;            // accumulator pairs
+    constexpr bool kSingle = TCH == 1;           // one snapshot: point pairs on f32x2 instead
+    static_assert(kPacked || kSingle, "snapshot chunks of one or an even number");
+    constexpr int NP = (TCH + 1) / 2;            // accumulator pairs (acc[0][k / 2] holds
+                                                 // points (k, k + 1) when kSingle)
     static_assert(PPT % 2 == 0, "points are processed in pairs");
     const int tid = threadIdx.x, lane = tid & 31;
 
@@ -389,6 +403,43 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 }
                 continue;
             }
+            if (kSingle && (mode == kModeAllD2 || mode == kModeAllD4)) {
+                // one snapshot: points (2m, 2m+1) in one f32x2 instruction instead
+                const float4 v0 = sm.rec[0][s].v0;                 // (g_0, g_1x, g_2x, g_3x)
+                const float g4 = mode == kModeAllD4 ? sm.rec[0][s].v1.x : 0.0f;
+#pragma unroll
+                for (int m = 0; m < PPT / 2; ++m) {
+                    const float2 r = f2(r2[2 * m], r2[2 * m + 1]);
+                    float2 g;
+                    if (mode == kModeAllD2) {
+                        g = __ffma2_rn(f2(v0.z, v0.z), r, f2(v0.y, v0.y));
+                    } else {
+                        g = __ffma2_rn(f2(g4, g4), r, f2(v0.w, v0.w));
+                        g = __ffma2_rn(g, r, f2(v0.z, v0.z));
+                        g = __ffma2_rn(g, r, f2(v0.y, v0.y));
+                    }
+                    g = __ffma2_rn(g, r, f2(v0.x, v0.x));
+                    acc[0][m] = __fadd2_rn(acc[0][m], f2(ex2_approx(g.x), ex2_approx(g.y)));
+                }
+                continue;
+            }
+            if constexpr (kSingle) {
+                // one snapshot, another class: per point, into the point-pair accumulators
+                const uint32_t c = word & kCodeMask;
+                const RecF32 &Rs = sm.rec[0][s];
+                if (c == kCodeD8) {
+                    point_pass<8, PPT>(acc[0], r2, Rs);
+                } else if (c == kCodeD12) {
+                    point_pass<12, PPT>(acc[0], r2, Rs);
+                } else if (c == kCodeGeneral) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        const float t = pair_term(r2[k], Rs);
+                        if (k & 1) acc[0][k >> 1].y += t; else acc[0][k >> 1].x += t;
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
                 const uint32_t c = mode == kModeAllD2 ? kCodeD2 : mode == kModeAllD4 ? kCodeD4
@@ -417,7 +468,8 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
         for (int jc = 0; jc < TCH; ++jc)
 #pragma unroll
             for (int k = 0; k < PPT; ++k)
-                sm.run[jc * PPT + k][tid] += (jc & 1) ? acc[jc >> 1][k].y : acc[jc >> 1][k].x;
+                sm.run[jc * PPT + k][tid] += kSingle ? ((k & 1) ? acc[0][k >> 1].y : acc[0][k >> 1].x)
+                                                     : ((jc & 1) ? acc[jc >> 1][k].y : acc[jc >> 1][k].x);
 #pragma unroll
         for (int m = 0; m < NP; ++m)
 #pragma unroll
