@@ -220,8 +220,12 @@ struct TileSmemMixed {
     static constexpr int kPairs = TCH / 2 > 0 ? TCH / 2 : 1;
     float run[TCH * Cfg::kPPT][Cfg::kThreads];         // per-thread running sums over stages
     float4 xy[Cfg::kSTILE];                             // (-x, -x, -y, -y) of each staged visit
-    __align__(16) RecF32 rec[TCH][Cfg::kSTILE];
+    float4 lo[TCH][Cfg::kSTILE];                        // record vector v0: (g_0, g_1x, g_2x, g_3x)
+    float4 hi[TCH][Cfg::kSTILE];                        // record vector v1: (g_4x, dq, q1, c_0)
     PairRec pair[kPairs][Cfg::kSTILE];                  // snapshot pairs (even TCH only)
+    // whole records for the one-snapshot tile (its minority classes read them here; the
+    // multi-snapshot tile reads them from global memory)
+    __align__(16) RecF32 rec[TCH == 1 ? Cfg::kSTILE : 1];
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -299,12 +303,14 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
         for (int jc = 0; jc < TCH; ++jc) {
             const float4 *row = reinterpret_cast<const float4 *>(rows[jc] + s0);
             const int lim = na[jc] - s0;
-            float4 *dst = reinterpret_cast<float4 *>(&sm.rec[jc][0]);
             constexpr int RV = sizeof(RecF32) / 16;
-            for (int v = tid; v < cnt * RV; v += NT) {
-                const int i = v / RV, q = v - i * RV;
-                const float4 r = i < lim ? row[v] : (q == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
-                dst[v] = r;
+            constexpr int NV = kSingle ? RV : 2;          // record vectors staged per visit
+            for (int v = tid; v < cnt * NV; v += NT) {
+                const int i = v / NV, q = v - i * NV;
+                const float4 r = i < lim ? row[i * RV + q] : (q == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
+                if (q == 0) sm.lo[jc][i] = r;
+                else if (q == 1) sm.hi[jc][i] = r;
+                if (kSingle) reinterpret_cast<float4 *>(&sm.rec[i])[q] = r;
                 if (kPacked && q <= 1) {
                     float *pa = reinterpret_cast<float *>(&sm.pair[jc >> 1][i]) + (jc & 1);
                     if (q == 0) { pa[0] = r.x; pa[2] = r.y; pa[4] = r.z; pa[6] = r.w; }
@@ -334,15 +340,18 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                 bool any = false;
 #pragma unroll
                 for (int jc = 0; jc < TCH; ++jc) {
-                    uint32_t c = kCodeD2;
+                    // a snapshot for which the visit has not started counts as degree 2 for the
+                    // warp's mode (its zero record yields 0 there) and as skip for the
+                    // one-snapshot-at-a-time path (which reads records from global memory)
+                    uint32_t c = kCodeD2, cw = kCodeSkip;
                     if (s0 + i < na[jc]) {
-                        const RecF32 &R = sm.rec[jc][i];
-                        c = series_class(r2max * R.dq(), r2min * R.q1(), R.dq());
+                        const float4 h = sm.hi[jc][i];
+                        c = cw = series_class(r2max * h.y, r2min * h.z, h.y);
                         any = any || c != kCodeSkip;
                     }
                     cmin = min(cmin, c);
                     cmax = max(cmax, c);
-                    word |= c << (kCodeBits * jc);
+                    word |= cw << (kCodeBits * jc);
                 }
                 const uint32_t mode = !any ? kModeSkip
                                     : (cmin >= kCodeD2 && cmax == kCodeD2) ? kModeAllD2
@@ -405,8 +414,8 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             }
             if (kSingle && (mode == kModeAllD2 || mode == kModeAllD4)) {
                 // one snapshot: points (2m, 2m+1) in one f32x2 instruction instead
-                const float4 v0 = sm.rec[0][s].v0;                 // (g_0, g_1x, g_2x, g_3x)
-                const float g4 = mode == kModeAllD4 ? sm.rec[0][s].v1.x : 0.0f;
+                const float4 v0 = sm.lo[0][s];                     // (g_0, g_1x, g_2x, g_3x)
+                const float g4 = mode == kModeAllD4 ? sm.hi[0][s].x : 0.0f;
 #pragma unroll
                 for (int m = 0; m < PPT / 2; ++m) {
                     const float2 r = f2(r2[2 * m], r2[2 * m + 1]);
@@ -426,7 +435,8 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             if constexpr (kSingle) {
                 // one snapshot, another class: per point, into the point-pair accumulators
                 const uint32_t c = word & kCodeMask;
-                const RecF32 &Rs = sm.rec[0][s];
+                if (c == kCodeSkip) continue;
+                const RecF32 &Rs = sm.rec[s];
                 if (c == kCodeD8) {
                     point_pass<8, PPT>(acc[0], r2, Rs);
                 } else if (c == kCodeD12) {
@@ -442,10 +452,9 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             }
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
-                const uint32_t c = mode == kModeAllD2 ? kCodeD2 : mode == kModeAllD4 ? kCodeD4
-                                 : (word >> (kCodeBits * jc)) & kCodeMask;
+                const uint32_t c = (word >> (kCodeBits * jc)) & kCodeMask;
                 if (c == kCodeSkip) continue;
-                const RecF32 &Rs = sm.rec[jc][s];
+                const RecF32 &Rs = rows[jc][s0 + s];            // active: the record exists
                 float2 (&A)[PPT] = acc[jc >> 1];
                 if (c == kCodeD2) {
                     if (jc & 1) moment_pass<2, PPT, 1>(A, r2, Rs); else moment_pass<2, PPT, 0>(A, r2, Rs);
