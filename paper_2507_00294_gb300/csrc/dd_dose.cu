@@ -235,9 +235,9 @@ dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int tile, int lb
 
 namespace {
 
-// Lag block of the dose work items: the largest of 512, 256, 128, 64 lags that still
-// gives at least 8 items per SM (the triangle of a few thousand visits is otherwise cut
-// into too few CTAs to fill the GPU).
+// Lag block of the dose work items: the largest power-of-two fraction of kDoseLB, down to
+// kDoseLBMin lags, that still gives at least 8 items per SM (the triangle of a few
+// thousand visits is otherwise cut into too few CTAs to fill the GPU).
 template <typename Cfg>
 int dose_lag_block(int64_t n) {
     constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
@@ -248,7 +248,7 @@ int dose_lag_block(int64_t n) {
         sms = 1;
     }
     int lb = Cfg::kDoseLB;
-    while (lb > 64) {
+    while (lb > Cfg::kDoseLBMin) {
         int64_t items = 0;
         for (int64_t t0 = 0; t0 < n; t0 += TILE) {
             const int64_t t1 = std::min(n, t0 + TILE);

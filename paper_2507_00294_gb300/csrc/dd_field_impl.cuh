@@ -133,6 +133,7 @@ struct CfgMixed {
     static constexpr int kDoseLB = 512;      // largest lag block of the dose kernel
     static constexpr int kDoseSTILE = 64;    // lags staged per round by the dose kernel
     static constexpr int kDosePPT = 1;       // targets per thread in the dose kernel (128-target tiles)
+    static constexpr int kDoseLBMin = 64;    // smallest lag block of the dose kernel
     static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
                                 *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
@@ -144,6 +145,7 @@ struct CfgF64 {
     static constexpr int kDoseLB = 512;
     static constexpr int kDoseSTILE = 32;
     static constexpr int kDosePPT = 2;
+    static constexpr int kDoseLBMin = 64;
     static constexpr const char *kFieldName = "field_fp64", *kCoefName = "coef_fp64",
                                 *kDoseName = "dose_fp64", *kLagCoefName = "lag_coef_fp64";
 };
