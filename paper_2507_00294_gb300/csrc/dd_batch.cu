@@ -76,7 +76,7 @@ __global__ void batch_coef_kernel(const BScan *__restrict__ sc, const int64_t *_
     const int64_t i = g - S.rec_off;
     if (i >= S.nact) return;
     double q1, dq, r, ell;
-    pair_geometry(S.tdim - S.src[2 * S.n + i], S.src[3 * S.n + i], S.s, S.kappa, q1, dq, r, ell);
+    pair_geometry<RecTraits<Rec>::kFP64Ell>(S.tdim - S.src[2 * S.n + i], S.src[3 * S.n + i], S.s, S.kappa, q1, dq, r, ell);
     Rec out;
     RecTraits<Rec>::fill(out, q1, dq, r, ell);
     rec[g] = out;

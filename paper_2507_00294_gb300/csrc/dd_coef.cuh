@@ -85,6 +85,9 @@ __device__ void moment_coefficients_f32(float r, float ell, float *c) {
     }
 }
 
+// kEll: also ell = ln(w1/w0) in FP64 (the FP64 record needs it; the FP32 record forms
+// its own in FP32, which is all its rounding to FP32 keeps).
+template <bool kEll = true>
 __device__ __forceinline__ void pair_geometry(double dT, double tau, double s, double kappa,
                                               double &q1, double &dq, double &r, double &ell) {
     const bool on = dT <= tau;                         // Eq. 1 while t_i <= t <= t_i + tau_i
@@ -94,7 +97,7 @@ __device__ __forceinline__ void pair_geometry(double dT, double tau, double s, d
     q1 = 1.0 / w1;
     r = dw / w0;
     dq = r * q1;                                       // 1/w0 - 1/w1
-    ell = log1p(r);                                    // ln(w1/w0) = ln(b/a)
+    ell = kEll ? log1p(r) : 0.0;                       // ln(w1/w0) = ln(b/a)
 }
 
 template <typename Rec>
@@ -105,7 +108,7 @@ __global__ void coef_kernel(const double *__restrict__ srcT, const double *__res
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nact[j]) return;
     double q1, dq, r, ell;
-    pair_geometry(tsnap[j] - srcT[i], srcTAU[i], s, kappa, q1, dq, r, ell);
+    pair_geometry<RecTraits<Rec>::kFP64Ell>(tsnap[j] - srcT[i], srcTAU[i], s, kappa, q1, dq, r, ell);
     Rec out;
     RecTraits<Rec>::fill(out, q1, dq, r, ell);
     rec[(int64_t)j * stride + i] = out;
@@ -117,13 +120,18 @@ struct RecTraits<RecF32> {
     // ln(P(h)/c_0) with P(h) = sum_m c_m h^m, from the power-series logarithm
     //   l_m = p_m - (1/m) sum_{k=1}^{m-1} k l_k p_{m-k},  p_m = c_m / c_0
     // (P'/P = (ln P)').
-    static __device__ void fill(RecF32 &o, double q1, double dq, double r, double ell) {
+    static constexpr bool kFP64Ell = false;
+    // ell: unused (c_0 = ln(1 + r) is formed here in FP32)
+    static __device__ void fill(RecF32 &o, double q1, double dq, double r, double) {
         constexpr int M = 12;
         constexpr double kLog2e = 1.44269504088896340736;
-        // the exponent's leading terms (q1, dq, 1/r, log2 c_0) in FP64; the corrections
-        // l_m (|l_m h^m| <= 0.85, rounded to FP32 in the record anyway) in FP32
+        const float kLog2eF = (float)kLog2e;
+        // the exponent's leading terms: q1 and dq from FP64 (rounded once), the logs and
+        // 1/r in FP32 (they enter as g_0 = log2 c_0 and k_1, both kept to FP32 rounding);
+        // the corrections l_m (|l_m h^m| <= 0.85) in FP32
+        const float rf = (float)r, ellf = log1pf(rf);
         float cf[M + 1], p[M + 1], l[M + 1];
-        moment_coefficients_f32<M>((float)r, (float)ell, cf);
+        moment_coefficients_f32<M>(rf, ellf, cf);
         const float ic0 = 1.0f / cf[0];
 #pragma unroll
         for (int m = 1; m <= M; ++m) p[m] = cf[m] * ic0;
@@ -134,12 +142,11 @@ struct RecTraits<RecF32> {
             for (int k = 1; k < m; ++k) acc = fmaf((float)k * l[k], p[m - k], acc);
             l[m] = p[m] - acc * (float)kRecip[m];
         }
-        const float kLog2eF = (float)kLog2e;
-        const double dq2 = dq * dq;
-        o.v0 = make_float4((float)(log(ell) * kLog2e), (float)(kLog2e * ((double)l[1] * dq - q1)),
-                           (float)(kLog2e * dq2) * l[2], (float)(kLog2e * dq2 * dq) * l[3]);
-        o.v1 = make_float4((float)(kLog2e * dq2 * dq2) * l[4], (float)dq, (float)q1, (float)ell);
-        o.v2 = make_float4((float)(kLog2e * ((double)l[1] - 1.0 / r)), kLog2eF * l[2], kLog2eF * l[3], kLog2eF * l[4]);
+        const float dqf = (float)dq, dq2 = dqf * dqf;
+        o.v0 = make_float4(log2f(ellf), (float)(kLog2e * ((double)l[1] * dq - q1)),
+                           kLog2eF * dq2 * l[2], kLog2eF * dq2 * dqf * l[3]);
+        o.v1 = make_float4(kLog2eF * dq2 * dq2 * l[4], dqf, (float)q1, ellf);
+        o.v2 = make_float4(kLog2eF * (l[1] - 1.0f / rf), kLog2eF * l[2], kLog2eF * l[3], kLog2eF * l[4]);
         o.v3 = make_float4(kLog2eF * l[5], kLog2eF * l[6], kLog2eF * l[7], kLog2eF * l[8]);
         o.v4 = make_float4(kLog2eF * l[9], kLog2eF * l[10], kLog2eF * l[11], kLog2eF * l[12]);
     }
@@ -160,6 +167,7 @@ struct RecTraits<RecF64> {
         o.dq = dq;
     }
     static __device__ RecF64 zero() { return RecF64{}; }
+    static constexpr bool kFP64Ell = true;
 };
 
 // Record for lag k = 1..n-1 of a scan with a uniform dwell (time unit = dwell):
@@ -170,7 +178,7 @@ __global__ void lag_coef_kernel(int64_t n, double s, double kappa, Rec *__restri
     if (k >= n) return;
     if (k == 0) { rec[0] = RecTraits<Rec>::zero(); return; }
     double q1, dq, r, ell;
-    pair_geometry((double)k, 1.0, s, kappa, q1, dq, r, ell);
+    pair_geometry<RecTraits<Rec>::kFP64Ell>((double)k, 1.0, s, kappa, q1, dq, r, ell);
     Rec out;
     RecTraits<Rec>::fill(out, q1, dq, r, ell);
     rec[k] = out;
@@ -187,7 +195,7 @@ __global__ void rev_lag_coef_kernel(int64_t M, double s, double kappa, Rec *__re
     const int64_t L = M - u;
     if (L == 0) { rev[u] = RecTraits<Rec>::zero(); return; }
     double q1, dq, r, ell;
-    pair_geometry((double)L, 1.0, s, kappa, q1, dq, r, ell);
+    pair_geometry<RecTraits<Rec>::kFP64Ell>((double)L, 1.0, s, kappa, q1, dq, r, ell);
     Rec out;
     RecTraits<Rec>::fill(out, q1, dq, r, ell);
     rev[u] = out;

@@ -183,7 +183,7 @@ dose_general_kernel(const double *__restrict__ src, int64_t n, double s, double 
         for (int q = 0; q < cnt; ++q) {
             if (!live || i0 + q >= j) break;
             double q1, dq, r, ell;
-            pair_geometry(tj - s_t[q], s_tau[q], s, kappa, q1, dq, r, ell);
+            pair_geometry<RecTraits<Rec>::kFP64Ell>(tj - s_t[q], s_tau[q], s, kappa, q1, dq, r, ell);
             Rec R;
             RecTraits<Rec>::fill(R, q1, dq, r, ell);
             const Real dx = (Real)(xj - s_x[q]), dy = (Real)(yj - s_y[q]);
