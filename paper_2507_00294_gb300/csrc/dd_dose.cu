@@ -31,7 +31,10 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     using Real = typename Cfg::Real;
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kDosePPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
     constexpr int RV = sizeof(Rec) / 16;
-    __shared__ Real s_x[TILE + LBMAX], s_y[TILE + LBMAX];
+    constexpr bool kF32 = std::is_same<Real, float>::value;
+    static_assert(!kF32 || PPT % 2 == 0, "the FP32 path takes targets in pairs");
+    __shared__ Real s_x[kF32 ? 1 : TILE + LBMAX], s_y[kF32 ? 1 : TILE + LBMAX];   // FP64 path
+    __shared__ float2 s_xy[kF32 ? TILE + LBMAX : 1];                               // FP32 path
     __shared__ __align__(16) Rec s_rec[Cfg::kDoseSTILE];
 
     const int2 item = items[blockIdx.x];
@@ -45,15 +48,12 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     const int64_t w1 = t1 - k0;
     // coordinates relative to the tile's first target: FP32 from the float-float copy on
     // the FP32 path (no FP64 arithmetic), FP64 otherwise
-    constexpr bool kF32 = std::is_same<Real, float>::value;
     const double cx = srcX[t0], cy = srcY[t0];
     const float4 org = kF32 ? srcF[t0] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = w0 + tid; i < w1; i += NT) {
         const int64_t ic = i < 0 ? 0 : i;                  // i < 0 never used
         if constexpr (kF32) {
-            const float2 d = ff_diff(srcF[ic], org);
-            s_x[i - w0] = d.x;
-            s_y[i - w0] = d.y;
+            s_xy[i - w0] = ff_diff(srcF[ic], org);
         } else {
             s_x[i - w0] = (Real)(srcX[ic] - cx);
             s_y[i - w0] = (Real)(srcY[ic] - cy);
@@ -77,9 +77,15 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     // FP32 (or FP64) sums of up to kFlush lags, added into a compensated running sum
     // (BlockSum: no FP64 arithmetic on the FP32 path)
     Real acc[PPT];
+    float2 acc2[PPT / 2 > 0 ? PPT / 2 : 1];               // FP32 path: targets (2m, 2m+1)
     BlockSum<Real> tot[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) acc[q] = 0;
+#pragma unroll
+    for (int m = 0; m < (PPT / 2 > 0 ? PPT / 2 : 1); ++m) acc2[m] = make_float2(0.f, 0.f);
+    // every (target, lag) pair of this item exists: the whole tile lies in [0, n) and its
+    // first target is beyond the block's largest lag
+    const bool full = t0 + TILE <= n && (int64_t)k1 - 1 <= t0;
 
     for (int kk = k0; kk < k1; kk += Cfg::kDoseSTILE) {
         const int cnt = min(Cfg::kDoseSTILE, k1 - kk);
@@ -99,36 +105,57 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
                 float r2[PPT];
                 bool ok[PPT];
                 bool lo = true;                 // every valid pair of this lane fits degree 2
+                const float dqR = R.dq();
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    const int64_t i = jt[q] - k;
-                    ok[q] = i >= 0 && jt[q] < n;
-                    const float dx = ok[q] ? px[q] - s_x[i - w0] : 0.f;
-                    const float dy = ok[q] ? py[q] - s_y[i - w0] : 0.f;
-                    r2[q] = dx * dx + dy * dy;
-                    lo = lo && (r2[q] * R.dq() <= kL2H);
+                for (int m = 0; m < PPT / 2; ++m) {
+                    // targets (2m, 2m+1) of this thread on f32x2: their sources are the visits
+                    // k before them
+                    const int64_t i0 = jt[2 * m] - k, i1 = jt[2 * m + 1] - k;
+                    ok[2 * m] = full || (i0 >= 0 && jt[2 * m] < n);
+                    ok[2 * m + 1] = full || (i1 >= 0 && jt[2 * m + 1] < n);
+                    const float2 sa = ok[2 * m] ? s_xy[i0 - w0] : make_float2(px[2 * m], py[2 * m]);
+                    const float2 sb = ok[2 * m + 1] ? s_xy[i1 - w0] : make_float2(px[2 * m + 1], py[2 * m + 1]);
+                    const float2 dx = __fadd2_rn(make_float2(px[2 * m], px[2 * m + 1]), make_float2(-sa.x, -sb.x));
+                    const float2 dy = __fadd2_rn(make_float2(py[2 * m], py[2 * m + 1]), make_float2(-sa.y, -sb.y));
+                    const float2 q2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                    r2[2 * m] = q2.x;
+                    r2[2 * m + 1] = q2.y;
+                    lo = lo && (fmaxf(q2.x, q2.y) * dqR <= kL2H);
                 }
                 uint32_t cls = kCodeD2;
                 // the common case is settled by one vote; otherwise classify every pair
-                if (!__all_sync(0xffffffffu, lo && R.dq() >= kMinDqX)) {
+                if (!__all_sync(0xffffffffu, lo && dqR >= kMinDqX)) {
                     cls = kCodeSkip;
 #pragma unroll
                     for (int q = 0; q < PPT; ++q) {
-                        const uint32_t cq = !ok[q] ? kCodeSkip : series_class(r2[q] * R.dq(), r2[q] * R.q1(), R.dq());
+                        const uint32_t cq = !ok[q] ? kCodeSkip : series_class(r2[q] * dqR, r2[q] * R.q1(), dqR);
                         cls = max(cls, cq);
                     }
                     cls = __reduce_max_sync(0xffffffffu, cls);
                 }
                 if (cls == kCodeSkip) continue;
+                if (cls == kCodeD2) {
+                    // degree 2 on f32x2 over target pairs; a pair that does not exist gets the
+                    // exponent -inf (term 0)
+                    const float4 v0 = R.v0;                // (g_0, g_1x, g_2x, g_3x)
+                    const float2 g2 = make_float2(v0.z, v0.z), g1 = make_float2(v0.y, v0.y);
+#pragma unroll
+                    for (int m = 0; m < PPT / 2; ++m) {
+                        const float2 r = make_float2(r2[2 * m], r2[2 * m + 1]);
+                        const float2 g0 = make_float2(ok[2 * m] ? v0.x : -INFINITY, ok[2 * m + 1] ? v0.x : -INFINITY);
+                        const float2 g = __ffma2_rn(__ffma2_rn(g2, r, g1), r, g0);
+                        acc2[m] = __fadd2_rn(acc2[m], make_float2(ex2_approx(g.x), ex2_approx(g.y)));
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     float t;
-                    if (cls == kCodeD2) t = log_term<2>(r2[q], R);
-                    else if (cls == kCodeD4) t = log_term<4>(r2[q], R);
+                    if (cls == kCodeD4) t = log_term<4>(r2[q], R);
                     else if (cls == kCodeD8) t = log_term<8>(r2[q], R);
                     else if (cls == kCodeD12) t = log_term<12>(r2[q], R);
                     else t = pair_term(r2[q], R);
-                    acc[q] += ok[q] ? t : 0.f;
+                    if (ok[q]) { if (q & 1) acc2[q >> 1].y += t; else acc2[q >> 1].x += t; }
                 }
                 continue;
             }
@@ -146,7 +173,16 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
             }
         }
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) { tot[q].add(acc[q]); acc[q] = 0; }
+        for (int q = 0; q < PPT; ++q) {
+            if constexpr (std::is_same<Real, float>::value) {
+                tot[q].add((q & 1) ? acc2[q >> 1].y : acc2[q >> 1].x);
+            } else {
+                tot[q].add(acc[q]);
+            }
+            acc[q] = 0;
+        }
+#pragma unroll
+        for (int m = 0; m < (PPT / 2 > 0 ? PPT / 2 : 1); ++m) acc2[m] = make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int q = 0; q < PPT; ++q)

@@ -132,8 +132,8 @@ struct CfgMixed {
     static constexpr int kMinBlocks = 8;     // 32 warps per SM: at most 64 registers, 22 KB shared
     static constexpr int kDoseLB = 512;      // largest lag block of the dose kernel
     static constexpr int kDoseSTILE = 64;    // lags staged per round by the dose kernel
-    static constexpr int kDosePPT = 1;       // targets per thread in the dose kernel (128-target tiles)
-    static constexpr int kDoseLBMin = 64;    // smallest lag block of the dose kernel
+    static constexpr int kDosePPT = 2;       // targets per thread in the dose kernel (256-target tiles)
+    static constexpr int kDoseLBMin = 32;    // smallest lag block of the dose kernel
     static constexpr const char *kFieldName = "field_mixed", *kCoefName = "coef_mixed",
                                 *kDoseName = "dose_mixed", *kLagCoefName = "lag_coef_mixed";
 };
