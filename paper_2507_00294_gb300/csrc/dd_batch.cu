@@ -281,11 +281,11 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
     for (int k = 0; k < n_scans; ++k) {
         const dd_scan *s = scans[k];
         dd_status st = DD_OK;
-        const double *src = dd::device_sources(s, &st);
+        const double *src = dd::device_sources(s, nullptr, &st);
         if (!src) return st;
         ddk::BScan &S = sc[(size_t)k];
         S.src = src;
-        S.srcF = dd::device_sources_ff(s, &st);
+        S.srcF = dd::device_sources_ff(s, nullptr, &st);
         S.n = s->n;
         S.pt_off = pt_offsets[k];
         S.n_pts = pt_offsets[k + 1] - pt_offsets[k];

@@ -301,6 +301,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     using Rec = typename Cfg::Rec;
     const int64_t n = scan->n;
     const bool out_host = !dd::is_device_pointer(out);
+    const bool out_copy = out_host;
     constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     const int lb = dose_lag_block<Cfg>(n);
     const int64_t n_tiles = (n + TILE - 1) / TILE;
@@ -324,13 +325,13 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     add((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
     add(its.size() * sizeof(int2) + 16);
     add((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(typename Cfg::Real));
-    if (out_host) add((size_t)n * sizeof(double));
+    if (out_copy) add((size_t)n * sizeof(double));
     bytes += 256;
 
     dd_status st = DD_OK;
-    const double *src = dd::device_sources(scan, &st);
+    const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
-    const float4 *srcF = dd::device_sources_ff(scan, &st);
+    const float4 *srcF = dd::device_sources_ff(scan, stream, &st);
     void *ws = nullptr;
     cudaError_t err = dd::workspace_alloc(&ws, bytes, stream);
     if (err != cudaSuccess) {
@@ -345,7 +346,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     int2 *d_items = (int2 *)take(its.size() * sizeof(int2) + 16);
     using Part = typename Cfg::Real;
     Part *d_part = (Part *)take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(Part));
-    double *out_dev = out_host ? (double *)take((size_t)n * sizeof(double)) : out;
+    double *out_dev = out_copy ? (double *)take((size_t)n * sizeof(double)) : out;
 
     // work list, kept until the stream has consumed its upload (pinned staging when available)
     struct Keep {
@@ -368,7 +369,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     DD_PROFILED("dose_reduce", stream,
                 (ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev)));
     DD_CUDA_TRY(cudaGetLastError());
-    if (out_host)
+    if (out_copy)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
     DD_CUDA_TRY(dd::defer_release(stream, keep, [](void *p) { delete static_cast<Keep *>(p); }));
@@ -381,7 +382,7 @@ dd_status run_dose_general(const dd_scan *scan, double *out, cudaStream_t stream
     const int64_t n = scan->n;
     const bool out_host = !dd::is_device_pointer(out);
     dd_status st = DD_OK;
-    const double *src = dd::device_sources(scan, &st);
+    const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
     void *ws = nullptr;
     const size_t bytes = (size_t)n * sizeof(double) * (out_host ? 2 : 1) + 512;

@@ -62,9 +62,15 @@ __global__ void reduce_kernel(const Part *__restrict__ partial, const int *__res
         for (int q = 0; q < 4; ++q) acc[q].add(v[q]);
     }
     double *o = out + (int64_t)row[j] * n_pts + p0;
+    if (p0 + 3 < n_pts && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+        // 32 contiguous bytes per thread: whole lines per warp
+        reinterpret_cast<double2 *>(o)[0] = make_double2(pref * acc[0].result(), pref * acc[1].result());
+        reinterpret_cast<double2 *>(o)[1] = make_double2(pref * acc[2].result(), pref * acc[3].result());
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (p0 + q < n_pts) o[q] = pref * acc[q].result();
+        for (int q = 0; q < 4; ++q)
+            if (p0 + q < n_pts) o[q] = pref * acc[q].result();
+    }
 }
 
 }  // namespace ddk
@@ -167,6 +173,9 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     const int n_t = (int)times.size();
     const bool pts_host = !dd::is_device_pointer(pts_xy_m);
     const bool out_host = !dd::is_device_pointer(out);
+    // host buffers go through a workspace copy (a pinned output written in place by the
+    // reduce measured slower than the copy engine's transfer)
+    const bool pts_copy = pts_host, out_copy = out_host;
 
     // sort snapshots by time; n_active(t) = #{i : T_i < t} over the increasing T_i
     std::vector<int> order(n_t);
@@ -226,11 +235,11 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     const int n_chunks_max = (group + Cfg::kTCH - 1) / Cfg::kTCH;
 
     const int64_t n_rec = lattice ? M + 1 : (int64_t)group * n_src;
-    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_host, pts_host, n_t, n_rec);
+    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_copy, pts_copy, n_t, n_rec);
     dd_status st = DD_OK;
-    const double *src = dd::device_sources(scan, &st);
+    const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
-    const float4 *srcF = dd::device_sources_ff(scan, &st);
+    const float4 *srcF = dd::device_sources_ff(scan, stream, &st);
     void *ws = nullptr;
     cudaError_t err = dd::fault_injected("alloc") ? cudaErrorMemoryAllocation
                                                   : dd::workspace_alloc(&ws, ws_bytes, stream);
@@ -241,12 +250,12 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     }
     Carve cv(ws);
     const double *pts_dev = pts_xy_m;
-    if (pts_host) {
+    if (pts_copy) {
         double *p = cv.take<double>(2 * (size_t)n_pts);
         DD_CUDA_TRY(cudaMemcpyAsync(p, pts_xy_m, 2 * (size_t)n_pts * sizeof(double), cudaMemcpyHostToDevice, stream));
         pts_dev = p;
     }
-    double *out_dev = out_host ? cv.take<double>((size_t)n_t * n_pts) : out;
+    double *out_dev = out_copy ? cv.take<double>((size_t)n_t * n_pts) : out;
     double *X = cv.take<double>(2 * (size_t)n_pts);
     double *Y = X + n_pts;
     float4 *PF = cv.take<float4>((size_t)n_pts);
@@ -346,7 +355,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         keep->reals.push_back(std::move(tg));
         keep->offs.push_back(std::move(roff));
     }
-    if (out_host)
+    if (out_copy)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n_t * n_pts * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
     DD_CUDA_TRY(dd::defer_release(stream, keep, HostTables::release));

@@ -30,8 +30,15 @@ struct dd_scan {
     double s = 0, kappa = 0, pref = 0;   // dimensionless Ds, D, and Q0/(4 pi D) [u/m^2]
     std::vector<double> X, Y, T, TAU;    // dimensionless, visit order
 
-    // per device: 4n doubles X | Y | T | TAU, then n float4 (x_hi, x_lo, y_hi, y_lo)
-    struct DevCache { int device; double *src; };
+    // per device: 4n doubles X | Y | T | TAU, then n float4 (x_hi, x_lo, y_hi, y_lo),
+    // uploaded stream-ordered on `home`; `ready` marks the end of the upload for calls on
+    // other streams
+    struct DevCache {
+        int device;
+        double *src;
+        cudaStream_t home;
+        cudaEvent_t ready;
+    };
     mutable std::mutex mu;
     mutable std::vector<DevCache> dev;
 };
@@ -43,14 +50,16 @@ dd_status fail(dd_status st, const std::string &msg);
 dd_status fail_cuda(cudaError_t err, const char *what);
 void clear_error();
 
-// Device copy of the scan's dimensionless visit arrays on the current device
-// (created on first use with cudaMalloc, synchronously).  Returns NULL on failure
-// after recording the error in *st.
-const double *device_sources(const dd_scan *scan, dd_status *st);
+// Device copy of the scan's dimensionless visit arrays on the current device, usable by
+// work enqueued on `stream` after this call: created on first use from the library's
+// memory pool and uploaded on `stream` (no host synchronisation); a call on another
+// stream waits for the upload's event.  Returns NULL on failure after recording the
+// error in *st.
+const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status *st);
 // The same visits' X, Y as float-float pairs (hi = fl32(v), lo = fl32(v - hi)), so FP32
 // kernels form coordinate differences without FP64 arithmetic: n float4 stored after the
-// FP64 arrays of the same cache.
-const float4 *device_sources_ff(const dd_scan *scan, dd_status *st);
+// FP64 arrays of the same cache (call after device_sources on the same stream).
+const float4 *device_sources_ff(const dd_scan *scan, cudaStream_t stream, dd_status *st);
 
 // True if `p` is device-accessible memory of the current device.
 bool is_device_pointer(const void *p);

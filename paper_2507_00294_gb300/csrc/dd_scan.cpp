@@ -173,13 +173,19 @@ cudaError_t defer_release(cudaStream_t stream, void *obj, void (*del)(void *)) {
     return err;
 }
 
-const double *device_sources(const dd_scan *scan, dd_status *st) {
+const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status *st) {
     int device = 0;
     cudaError_t err = cudaGetDevice(&device);
     if (err != cudaSuccess) { *st = fail_cuda(err, "cudaGetDevice"); return nullptr; }
     std::lock_guard<std::mutex> lock(scan->mu);
     for (auto &c : scan->dev)
-        if (c.device == device) return c.src;
+        if (c.device == device) {
+            if (stream != c.home) {
+                err = cudaStreamWaitEvent(stream, c.ready, 0);
+                if (err != cudaSuccess) { *st = fail_cuda(err, "cudaStreamWaitEvent(scan visit cache)"); return nullptr; }
+            }
+            return c.src;
+        }
     const size_t n = (size_t)scan->n;
     // 4n doubles, then n float4 of float-float coordinates (16-byte aligned: 32n bytes in)
     std::vector<double> host(4 * n + 2 * n);
@@ -195,17 +201,33 @@ const double *device_sources(const dd_scan *scan, dd_status *st) {
         ff[4 * i + 2] = yh;
         ff[4 * i + 3] = (float)(scan->Y[i] - (double)yh);
     }
-    double *d = nullptr;
-    err = cudaMalloc(&d, host.size() * sizeof(double));
-    if (err != cudaSuccess) { *st = fail_cuda(err, "cudaMalloc(scan visit cache)"); cudaGetLastError(); return nullptr; }
-    err = cudaMemcpy(d, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (err != cudaSuccess) { cudaFree(d); *st = fail_cuda(err, "cudaMemcpy(scan visit cache)"); return nullptr; }
-    scan->dev.push_back({device, d});
-    return d;
+    const size_t bytes = host.size() * sizeof(double);
+    void *d = nullptr;
+    err = workspace_alloc(&d, bytes, stream);
+    if (err != cudaSuccess) { *st = fail_cuda(err, "scan visit cache allocation"); cudaGetLastError(); return nullptr; }
+    cudaEvent_t ready = nullptr;
+    err = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (err != cudaSuccess) { cudaFreeAsync(d, stream); *st = fail_cuda(err, "cudaEventCreate"); return nullptr; }
+    // upload through pinned staging, released once the copy has completed
+    auto *stage = new CallStaging();
+    err = stage->upload(d, host.data(), bytes, stream);
+    if (err == cudaSuccess && stage->blocks.empty()) err = cudaStreamSynchronize(stream);  // pageable source
+    if (err == cudaSuccess) err = cudaEventRecord(ready, stream);
+    if (err != cudaSuccess) {
+        cudaStreamSynchronize(stream);
+        delete stage;
+        cudaFreeAsync(d, stream);
+        cudaEventDestroy(ready);
+        *st = fail_cuda(err, "scan visit cache upload");
+        return nullptr;
+    }
+    defer_release(stream, stage, [](void *p) { delete static_cast<CallStaging *>(p); });
+    scan->dev.push_back({device, static_cast<double *>(d), stream, ready});
+    return static_cast<double *>(d);
 }
 
-const float4 *device_sources_ff(const dd_scan *scan, dd_status *st) {
-    const double *d = device_sources(scan, st);
+const float4 *device_sources_ff(const dd_scan *scan, cudaStream_t stream, dd_status *st) {
+    const double *d = device_sources(scan, stream, st);
     return d ? reinterpret_cast<const float4 *>(d + 4 * scan->n) : nullptr;
 }
 
@@ -417,7 +439,13 @@ void dd_destroy(dd_scan *scan) {
     int prev = -1;
     cudaGetDevice(&prev);
     for (auto &c : scan->dev) {
-        if (cudaSetDevice(c.device) == cudaSuccess) cudaFree(c.src);
+        if (cudaSetDevice(c.device) == cudaSuccess) {
+            // no enqueued call may still use the scan (the caller's contract); the device
+            // synchronisation makes that hold regardless, and returns at once when idle
+            cudaDeviceSynchronize();
+            cudaFreeAsync(c.src, 0);
+            cudaEventDestroy(c.ready);
+        }
     }
     if (!scan->dev.empty() && prev >= 0) cudaSetDevice(prev);
     cudaGetLastError();
