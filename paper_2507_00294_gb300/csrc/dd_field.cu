@@ -300,8 +300,11 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
             // per-(snapshot, visit) records
             roff[j] = lattice ? (tdim[g0 + j] > 0 ? M - (int64_t)tdim[g0 + j] : M) : (int64_t)j * n_src;
         }
-        // work items: (tile, chunk, block) for every block below the chunk's largest n_active
-        std::vector<std::pair<int64_t, int4>> items;
+        // work items: (tile, chunk, block) for every block below the chunk's largest
+        // n_active, longest first.  Every tile of a (chunk, block) costs the same, so the
+        // (chunk, block) pairs are sorted (stable: ties keep chunk, block order) and each
+        // expands into its tiles in tile order.
+        std::vector<std::pair<int64_t, int2>> blocks;
         for (int c = 0; c < n_chunks; ++c) {
             const int j0 = c * Cfg::kTCH, j1 = std::min(ng, j0 + Cfg::kTCH);
             int cmax = 0;
@@ -312,14 +315,17 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
                 int64_t cost = 0;
                 for (int j = j0; j < j1; ++j)
                     cost += std::max(0, std::min(nact[g0 + j], (k + 1) * sb) - k * sb);
-                for (int64_t t = 0; t < n_tiles; ++t)
-                    items.push_back({cost, make_int4((int)t, c, k, 0)});
+                blocks.push_back({cost, make_int2(c, k)});
             }
         }
-        std::stable_sort(items.begin(), items.end(),
-                         [](const std::pair<int64_t, int4> &a, const std::pair<int64_t, int4> &b) { return a.first > b.first; });
-        std::vector<int4> it(items.size());
-        for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
+        std::stable_sort(blocks.begin(), blocks.end(),
+                         [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
+        std::vector<int4> it(blocks.size() * (size_t)n_tiles);
+        {
+            size_t q = 0;
+            for (const auto &bk : blocks)
+                for (int64_t t = 0; t < n_tiles; ++t) it[q++] = make_int4((int)t, bk.second.x, bk.second.y, 0);
+        }
 
         // the group's tables in one copy: a host image of the device span d_t .. items end
         {
