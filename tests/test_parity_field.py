@@ -170,3 +170,39 @@ def test_single_visit_single_point_and_far_field(cuda):
     assert_fp64(gpu_field(spec, pts, times, "fp64"), ref, "single visit fp64")
     got = gpu_field(spec, pts, times, "mixed")
     assert_mixed(got, ref, ref.max(axis=1), "single visit mixed")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_snapshot_groups_off_lattice(cuda, prec):
+    """256 snapshots off the dwell lattice of a 256x256 scan: the per-(snapshot, visit)
+    records exceed the call's 1 GiB budget, so the snapshots run in groups (two for FP32,
+    four for FP64); sampled pairs against the oracle."""
+    spec = w.ScanSpec(256, 256)
+    n = w.n_visits(spec)
+    rng = np.random.default_rng(11)
+    pts = np.column_stack([rng.uniform(-2e-9, 130e-9, 200), rng.uniform(-2e-9, 130e-9, 200)])
+    times = (np.sort(rng.uniform(1, n, 256)).astype(np.int64) + 0.37) * spec.dwell_s
+    rng.shuffle(times)
+    ip = rng.integers(0, len(pts), 256)
+    it = rng.integers(0, len(times), 256)
+    ref = oracle_pairs(spec, pts, times, ip, it)
+    got = gpu_field(spec, pts, times, prec)[it, ip]
+    if prec == "fp64":
+        assert_fp64(got, ref, "groups fp64")
+    else:
+        peak = peak_lower_bound(spec, times)
+        assert_mixed(got, ref, peak[it], "groups mixed")
+
+
+def test_million_points_ragged(cuda):
+    """1,000,003 points (a ragged last tile, 1954 point tiles) of a small scan: sampled
+    pairs against the oracle, including the last points."""
+    spec = w.ScanSpec(8, 8, order=w.SERPENTINE)
+    rng = np.random.default_rng(12)
+    pts = np.column_stack([rng.uniform(-1e-9, 5e-9, 1_000_003), rng.uniform(-1e-9, 5e-9, 1_000_003)])
+    times = np.array([10.5e-6, 64e-6, 300e-6])
+    ip = np.concatenate([rng.integers(0, len(pts), 250), np.arange(len(pts) - 6, len(pts))])
+    it = rng.integers(0, len(times), len(ip))
+    ref = oracle_pairs(spec, pts, times, ip, it)
+    got = gpu_field(spec, pts, times, "mixed")[it, ip]
+    assert_mixed(got, ref, peak_lower_bound(spec, times)[it], "1M points mixed")
