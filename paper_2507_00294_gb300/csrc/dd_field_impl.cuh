@@ -170,7 +170,7 @@ struct TileSmem {
 // own a is 87 or more inside a series class add terms below 2e-38, flushed to zero once
 // they leave the normal range, so the series paths need no per-lane test.
 enum : uint32_t { kCodeSkip = 0, kCodeD2 = 1, kCodeD4 = 2, kCodeD8 = 3, kCodeD12 = 4, kCodeGeneral = 5 };
-// classes are packed 3 bits per snapshot (up to 9 snapshots) below the 4 mode bits
+// classes are packed 3 bits per snapshot in one word (up to 10 snapshots)
 constexpr uint32_t kCodeBits = 3, kCodeMask = 7;
 // per (warp, visit): all snapshots skipped / all on degree 2 / all on degree <= 4 / mixed
 enum : uint32_t { kModeSkip = 0, kModeAllD2 = 1, kModeAllD4 = 2, kModePerSnapshot = 3 };
@@ -206,28 +206,40 @@ __device__ __forceinline__ void point_pass(float2 (&acc)[PPT], const float (&r2)
     }
 }
 
-// Low-degree exponent coefficients of two snapshots (2P, 2P+1) of one visit, interleaved
-// so that one packed (f32x2) instruction evaluates the degree-2/4 exponent of both:
-//   a = (g_0, g_0', g_1x, g_1x'),  b = (g_2x, g_2x', g_3x, g_3x'),  c = (g_4x, g_4x', -, -)
-struct __align__(16) PairRec {
-    float4 a, b, c;
-};
-
 // The zero record's leading vector (g_0 = -inf): a snapshot for which the visit has not
 // started, or a padding snapshot, adds 2^-inf = 0 on every path.
 __device__ __forceinline__ float4 zero_rec_v0() { return make_float4(-INFINITY, 0.f, 0.f, 0.f); }
 
+// Shared memory of the FP32-mixed tile: the staged visits' coordinates, the running sums,
+// and
+//  * snapshot-pair tiles (even TCH): the low-degree exponent coefficients of a visit,
+//    laid out so that one f32x2 instruction evaluates the two snapshots of a pair
+//    (2P, 2P+1) and a degree-2 visit needs few 16-byte loads:
+//      pa[P] = (g_0, g_0', g_1x, g_1x') of pair P,  gm[m - 2] = g_mx of the TCH snapshots
+//    (m = 2, 3, 4), and (dq, q1) of every snapshot for the classification (the minority
+//    classes read whole records from global memory);
+//  * one-snapshot tiles: the leading record vectors and whole records.
+template <typename Cfg, int TCH, bool kPacked = TCH % 2 == 0>
+struct TileSmemMixed;
+
 template <typename Cfg, int TCH>
-struct TileSmemMixed {
-    static constexpr int kPairs = TCH / 2 > 0 ? TCH / 2 : 1;
-    float run[TCH * Cfg::kPPT][Cfg::kThreads];         // per-thread running sums over stages
-    float4 xy[Cfg::kSTILE];                             // (-x, -x, -y, -y) of each staged visit
+struct TileSmemMixed<Cfg, TCH, true> {
+    static constexpr int NP = TCH / 2, ST = Cfg::kSTILE;
+    static_assert(TCH == 4, "gm holds the coefficients of four snapshots as one vector");
+    float run[TCH * Cfg::kPPT][Cfg::kThreads];          // per-thread running sums over stages
+    float4 xy[ST];                                      // (-x, -x, -y, -y) of each staged visit
+    float4 pa[NP][ST];
+    float4 gm[3][ST];
+    float2 cls[TCH][ST];                                // (dq, q1)
+};
+
+template <typename Cfg, int TCH>
+struct TileSmemMixed<Cfg, TCH, false> {
+    float run[TCH * Cfg::kPPT][Cfg::kThreads];
+    float4 xy[Cfg::kSTILE];
     float4 lo[TCH][Cfg::kSTILE];                        // record vector v0: (g_0, g_1x, g_2x, g_3x)
     float4 hi[TCH][Cfg::kSTILE];                        // record vector v1: (g_4x, dq, q1, c_0)
-    PairRec pair[kPairs][Cfg::kSTILE];                  // snapshot pairs (even TCH only)
-    // whole records for the one-snapshot tile (its minority classes read them here; the
-    // multi-snapshot tile reads them from global memory)
-    __align__(16) RecF32 rec[TCH == 1 ? Cfg::kSTILE : 1];
+    __align__(16) RecF32 rec[Cfg::kSTILE];              // whole records (minority classes)
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -238,6 +250,34 @@ __device__ __forceinline__ float2 ff_diff(const float4 &a, const float4 &b) {
     return make_float2((a.x - b.x) + (a.y - b.y), (a.z - b.z) + (a.w - b.w));
 }
 
+// Bounds of rho^2 between a visit at (sx, sy) and any point of the box [bx0, bx1] x
+// [by0, by1], widened (relative 1e-4, absolute 1e-6) to cover the FP32 rounding of each
+// pair's own rho^2.
+__device__ __forceinline__ void box_rho2(float sx, float sy, float bx0, float bx1, float by0, float by1,
+                                         float &r2min, float &r2max) {
+    const float dx1 = fmaxf(fabsf(sx - bx0), fabsf(sx - bx1));
+    const float dy1 = fmaxf(fabsf(sy - by0), fabsf(sy - by1));
+    const float dx0 = fmaxf(0.0f, fmaxf(bx0 - sx, sx - bx1));
+    const float dy0 = fmaxf(0.0f, fmaxf(by0 - sy, sy - by1));
+    r2max = (dx1 * dx1 + dy1 * dy1) * 1.0001f + 1e-6f;
+    r2min = (dx0 * dx0 + dy0 * dy0) * 0.9999f;
+}
+
+// rho^2 of PPT points (in pairs: px[m] = (x_2m, x_2m+1)) to the visit nxy = (-x, -x, -y, -y)
+// on f32x2 instructions.
+template <int PPT>
+__device__ __forceinline__ void rho2_points(const float2 (&px)[PPT / 2], const float2 (&py)[PPT / 2],
+                                            const float4 &nxy, float (&r2)[PPT]) {
+#pragma unroll
+    for (int m = 0; m < PPT / 2; ++m) {
+        const float2 dx = __fadd2_rn(px[m], f2(nxy.x, nxy.y));
+        const float2 dy = __fadd2_rn(py[m], f2(nxy.z, nxy.w));
+        const float2 q = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        r2[2 * m] = q.x;
+        r2[2 * m + 1] = q.y;
+    }
+}
+
 // srcF: visit coordinates, ptsF: point coordinates, both float-float in pitch units.
 template <typename Cfg, int TCH, typename Part>
 __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, const float4 *__restrict__ srcF,
@@ -245,7 +285,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                                                  const RecF32 *const (&rows)[TCH], const int (&na)[TCH], int nj,
                                                  int s_begin, int s_end, Part *__restrict__ partial,
                                                  int64_t part_stride) {
-    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE, NW = NT / 32;
+    constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE;
     constexpr bool kPacked = TCH % 2 == 0;       // snapshot pairs on f32x2 instructions
     constexpr bool kSingle = TCH == 1;           // one snapshot: point pairs on f32x2 instead
     static_assert(kPacked || kSingle, "snapshot chunks of one or an even number");
@@ -291,6 +331,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
 #pragma unroll
         for (int k = 0; k < PPT; ++k) sm.run[jc * PPT + k][tid] = 0.0f;
 
+    constexpr int NCW = (STILE + 31) / 32;
     for (int s0 = s_begin; s0 < s_end; s0 += STILE) {
         const int cnt = min(STILE, s_end - s0);
         __syncthreads();
@@ -299,178 +340,198 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
             sm.xy[i] = make_float4(-d.x, -d.x, -d.y, -d.y);
         }
         // records; a snapshot for which the visit has not started gets the zero record,
-        // whose terms are 0.  The low-degree coefficients also go, interleaved by snapshot
-        // pair, into sm.pair for the f32x2 paths (half jc & 1 of pair jc / 2).
+        // whose terms are 0
+        constexpr int RV = sizeof(RecF32) / 16;
+        constexpr int NV = kSingle ? RV : 2;          // record vectors staged per visit
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc) {
             const float4 *row = reinterpret_cast<const float4 *>(rows[jc] + s0);
             const int lim = na[jc] - s0;
-            constexpr int RV = sizeof(RecF32) / 16;
-            constexpr int NV = kSingle ? RV : 2;          // record vectors staged per visit
             for (int v = tid; v < cnt * NV; v += NT) {
                 const int i = v / NV, q = v - i * NV;
                 const float4 r = i < lim ? row[i * RV + q] : (q == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
-                if (q == 0) sm.lo[jc][i] = r;
-                else if (q == 1) sm.hi[jc][i] = r;
-                if (kSingle) reinterpret_cast<float4 *>(&sm.rec[i])[q] = r;
-                if (kPacked && q <= 1) {
-                    float *pa = reinterpret_cast<float *>(&sm.pair[jc >> 1][i]) + (jc & 1);
-                    if (q == 0) { pa[0] = r.x; pa[2] = r.y; pa[4] = r.z; pa[6] = r.w; }
-                    else pa[8] = r.x;
+                if constexpr (kPacked) {
+                    // half jc & 1 of snapshot pair jc / 2, element jc of the g_mx vectors
+                    if (q == 0) {
+                        float *a = reinterpret_cast<float *>(&sm.pa[jc >> 1][i]) + (jc & 1);
+                        a[0] = r.x; a[2] = r.y;
+                        reinterpret_cast<float *>(&sm.gm[0][i])[jc] = r.z;
+                        reinterpret_cast<float *>(&sm.gm[1][i])[jc] = r.w;
+                    } else {
+                        reinterpret_cast<float *>(&sm.gm[2][i])[jc] = r.x;
+                        sm.cls[jc][i] = make_float2(r.y, r.z);
+                    }
+                } else {
+                    if (q == 0) sm.lo[jc][i] = r;
+                    else if (q == 1) sm.hi[jc][i] = r;
+                    reinterpret_cast<float4 *>(&sm.rec[i])[q] = r;
                 }
             }
         }
         __syncthreads();                   // staged coordinates and records visible
-        // classification: lane i of each warp classifies staged visits i, i + 32, .. for
-        // its own warp (box in registers); the words stay in registers and the loop below
-        // broadcasts them
-        constexpr int NCW = (STILE + 31) / 32;
-        uint32_t my_word[NCW];
+        // Class words: lane i of each warp classifies staged visits i, i + 32, .. against
+        // its own warp's box.  Per snapshot: skip (a_min >= 87: every term is below the
+        // FP32 normal range), the smallest exponent-series degree whose range holds h_max,
+        // or the per-lane regime test.  A snapshot for which the visit has not started
+        // counts as degree 2 for the warp's mode (its zero record yields 0 there) and as
+        // skip for the one-snapshot-at-a-time path (which reads records from global memory).
+        uint32_t my_word[NCW], my_mode[NCW];
 #pragma unroll
         for (int cw = 0; cw < NCW; ++cw) {
             const int i = cw * 32 + lane;
-            my_word[cw] = kModeSkip << 28;
+            my_word[cw] = 0;
+            my_mode[cw] = kModeSkip;
             if (i < cnt) {
-                const float sx = -sm.xy[i].x, sy = -sm.xy[i].z;
-                const float dx1 = fmaxf(fabsf(sx - bx0), fabsf(sx - bx1));
-                const float dy1 = fmaxf(fabsf(sy - by0), fabsf(sy - by1));
-                const float dx0 = fmaxf(0.0f, fmaxf(bx0 - sx, sx - bx1));
-                const float dy0 = fmaxf(0.0f, fmaxf(by0 - sy, sy - by1));
-                const float r2max = (dx1 * dx1 + dy1 * dy1) * 1.0001f + 1e-6f;
-                const float r2min = (dx0 * dx0 + dy0 * dy0) * 0.9999f;
-                uint32_t word = 0, cmin = kCodeGeneral, cmax = kCodeSkip;
+                float r2min, r2max;
+                box_rho2(-sm.xy[i].x, -sm.xy[i].z, bx0, bx1, by0, by1, r2min, r2max);
+                uint32_t codes = 0, cmin = kCodeGeneral, cmax = kCodeSkip;
                 bool any = false;
 #pragma unroll
                 for (int jc = 0; jc < TCH; ++jc) {
-                    // a snapshot for which the visit has not started counts as degree 2 for the
-                    // warp's mode (its zero record yields 0 there) and as skip for the
-                    // one-snapshot-at-a-time path (which reads records from global memory)
-                    uint32_t c = kCodeD2, cw = kCodeSkip;
+                    uint32_t c = kCodeD2, code = kCodeSkip;
                     if (s0 + i < na[jc]) {
-                        const float4 h = sm.hi[jc][i];
-                        c = cw = series_class(r2max * h.y, r2min * h.z, h.y);
+                        float dq, q1;
+                        if constexpr (kPacked) { const float2 h = sm.cls[jc][i]; dq = h.x; q1 = h.y; }
+                        else { const float4 h = sm.hi[jc][i]; dq = h.y; q1 = h.z; }
+                        c = code = series_class(r2max * dq, r2min * q1, dq);
                         any = any || c != kCodeSkip;
                     }
                     cmin = min(cmin, c);
                     cmax = max(cmax, c);
-                    word |= cw << (kCodeBits * jc);
+                    codes |= code << (kCodeBits * jc);
                 }
-                const uint32_t mode = !any ? kModeSkip
-                                    : (cmin >= kCodeD2 && cmax == kCodeD2) ? kModeAllD2
-                                    : (cmin >= kCodeD2 && cmax == kCodeD4) ? kModeAllD4 : kModePerSnapshot;
-                my_word[cw] = (word & 0x0fffffffu) | (mode << 28);
+                my_word[cw] = codes;
+                my_mode[cw] = !any ? kModeSkip
+                            : (cmin >= kCodeD2 && cmax == kCodeD2) ? kModeAllD2
+                            : (cmin >= kCodeD2 && cmax == kCodeD4) ? kModeAllD4 : kModePerSnapshot;
             }
         }
-        for (int s = 0; s < cnt; ++s) {
-            uint32_t w0 = my_word[0];
+        // The warp's visits by mode, as bit masks (bit b of word cw: staged visit 32 cw + b);
+        // each mode runs its visits in a loop of its own, without per-visit dispatch.
 #pragma unroll
-            for (int cw = 1; cw < NCW; ++cw) if ((s >> 5) == cw) w0 = my_word[cw];
-            const uint32_t word = __shfl_sync(0xffffffffu, w0, s & 31);
-            const uint32_t mode = word >> 28;
-            if (mode == kModeSkip) continue;               // warp-uniform skip
-            // rho^2 of point pairs: (px - sx)^2 + (py - sy)^2 on f32x2
-            const float4 nxy = sm.xy[s];
-            float r2[PPT];
+        for (int cw = 0; cw < NCW; ++cw) {
+            const uint32_t m2 = __ballot_sync(0xffffffffu, my_mode[cw] == kModeAllD2);
+            const uint32_t m4 = __ballot_sync(0xffffffffu, my_mode[cw] == kModeAllD4);
+            const uint32_t mp = __ballot_sync(0xffffffffu, my_mode[cw] == kModePerSnapshot);
+            if constexpr (kPacked) {
+                // every snapshot of the chunk on degree 2 (then on degree 4): both
+                // snapshots of a pair in one f32x2 instruction,
+                //   term = 2^(g_0 + g_1x r + g_2x r^2 [+ g_3x r^3 + g_4x r^4]),  r = rho^2;
+                // the coefficient vectors first, so their shared-memory latency overlaps
+                for (uint32_t m = m2; m; m &= m - 1) {
+                    const int s = cw * 32 + __ffs(m) - 1;
+                    float4 va[NP];
 #pragma unroll
-            for (int m = 0; m < PPT / 2; ++m) {
-                const float2 dx = __fadd2_rn(px[m], f2(nxy.x, nxy.y));
-                const float2 dy = __fadd2_rn(py[m], f2(nxy.z, nxy.w));
-                const float2 q = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-                r2[2 * m] = q.x;
-                r2[2 * m + 1] = q.y;
-            }
-            if (kPacked && (mode == kModeAllD2 || mode == kModeAllD4)) {
-                // every snapshot of the chunk on one low-degree exponent series: both
-                // snapshots of a pair in one f32x2 instruction; the coefficient vectors
-                // first, so their shared-memory latency overlaps
-                //   term = 2^(g_0 + g_1x r + g_2x r^2 [+ g_3x r^3 + g_4x r^4]),  r = rho^2
-                float4 va[NP], vb[NP];
+                    for (int P = 0; P < NP; ++P) va[P] = sm.pa[P][s];
+                    const float4 g2 = sm.gm[0][s];
+                    const float2 g2p[2] = {f2(g2.x, g2.y), f2(g2.z, g2.w)};
+                    float r2[PPT];
+                    rho2_points<PPT>(px, py, sm.xy[s], r2);
 #pragma unroll
-                for (int P = 0; P < TCH / 2; ++P) { va[P] = sm.pair[P][s].a; vb[P] = sm.pair[P][s].b; }
-                if (mode == kModeAllD2) {
-#pragma unroll
-                    for (int P = 0; P < TCH / 2; ++P)
+                    for (int P = 0; P < NP; ++P)
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
                             const float2 r = f2(r2[k], r2[k]);
-                            const float2 g = __ffma2_rn(__ffma2_rn(f2(vb[P].x, vb[P].y), r, f2(va[P].z, va[P].w)), r,
+                            const float2 g = __ffma2_rn(__ffma2_rn(g2p[P], r, f2(va[P].z, va[P].w)), r,
                                                         f2(va[P].x, va[P].y));
                             acc[P][k] = __fadd2_rn(acc[P][k], f2(ex2_approx(g.x), ex2_approx(g.y)));
                         }
-                } else {
+                }
+                for (uint32_t m = m4; m; m &= m - 1) {
+                    const int s = cw * 32 + __ffs(m) - 1;
+                    float4 va[NP];
 #pragma unroll
-                    for (int P = 0; P < TCH / 2; ++P) {
-                        const float4 vc = sm.pair[P][s].c;
+                    for (int P = 0; P < NP; ++P) va[P] = sm.pa[P][s];
+                    const float4 g2 = sm.gm[0][s], g3 = sm.gm[1][s], g4 = sm.gm[2][s];
+                    const float2 g2p[2] = {f2(g2.x, g2.y), f2(g2.z, g2.w)};
+                    const float2 g3p[2] = {f2(g3.x, g3.y), f2(g3.z, g3.w)};
+                    const float2 g4p[2] = {f2(g4.x, g4.y), f2(g4.z, g4.w)};
+                    float r2[PPT];
+                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+#pragma unroll
+                    for (int P = 0; P < NP; ++P)
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
                             const float2 r = f2(r2[k], r2[k]);
-                            float2 g = __ffma2_rn(f2(vc.x, vc.y), r, f2(vb[P].z, vb[P].w));
-                            g = __ffma2_rn(g, r, f2(vb[P].x, vb[P].y));
+                            float2 g = __ffma2_rn(g4p[P], r, g3p[P]);
+                            g = __ffma2_rn(g, r, g2p[P]);
                             g = __ffma2_rn(g, r, f2(va[P].z, va[P].w));
                             g = __ffma2_rn(g, r, f2(va[P].x, va[P].y));
                             acc[P][k] = __fadd2_rn(acc[P][k], f2(ex2_approx(g.x), ex2_approx(g.y)));
                         }
+                }
+                // the rest: one snapshot at a time, each at its own class, whole records
+                // from global memory
+                for (uint32_t m = mp; m; m &= m - 1) {
+                    const int b = __ffs(m) - 1, s = cw * 32 + b;
+                    const uint32_t word = __shfl_sync(0xffffffffu, my_word[cw], b);
+                    float r2[PPT];
+                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+#pragma unroll
+                    for (int jc = 0; jc < TCH; ++jc) {
+                        const uint32_t c = (word >> (kCodeBits * jc)) & kCodeMask;
+                        if (c == kCodeSkip) continue;
+                        const RecF32 &Rs = rows[jc][s0 + s];            // active: the record exists
+                        float2 (&A)[PPT] = acc[jc >> 1];
+                        if (c == kCodeD2) {
+                            if (jc & 1) moment_pass<2, PPT, 1>(A, r2, Rs); else moment_pass<2, PPT, 0>(A, r2, Rs);
+                        } else if (c == kCodeD4) {
+                            if (jc & 1) moment_pass<4, PPT, 1>(A, r2, Rs); else moment_pass<4, PPT, 0>(A, r2, Rs);
+                        } else if (c == kCodeD8) {
+                            if (jc & 1) moment_pass<8, PPT, 1>(A, r2, Rs); else moment_pass<8, PPT, 0>(A, r2, Rs);
+                        } else if (c == kCodeD12) {
+                            if (jc & 1) moment_pass<12, PPT, 1>(A, r2, Rs); else moment_pass<12, PPT, 0>(A, r2, Rs);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < PPT; ++k) {
+                                const float t = pair_term(r2[k], Rs);
+                                if (jc & 1) A[k].y += t; else A[k].x += t;
+                            }
+                        }
                     }
                 }
-                continue;
-            }
-            if (kSingle && (mode == kModeAllD2 || mode == kModeAllD4)) {
+            } else {
                 // one snapshot: points (2m, 2m+1) in one f32x2 instruction instead
-                const float4 v0 = sm.lo[0][s];                     // (g_0, g_1x, g_2x, g_3x)
-                const float g4 = mode == kModeAllD4 ? sm.hi[0][s].x : 0.0f;
+                for (uint32_t m = m2 | m4; m; m &= m - 1) {
+                    const int b = __ffs(m) - 1, s = cw * 32 + b;
+                    const bool d4 = (m4 >> b) & 1u;
+                    const float4 v0 = sm.lo[0][s];                     // (g_0, g_1x, g_2x, g_3x)
+                    const float g4 = d4 ? sm.hi[0][s].x : 0.0f;
+                    float r2[PPT];
+                    rho2_points<PPT>(px, py, sm.xy[s], r2);
 #pragma unroll
-                for (int m = 0; m < PPT / 2; ++m) {
-                    const float2 r = f2(r2[2 * m], r2[2 * m + 1]);
-                    float2 g;
-                    if (mode == kModeAllD2) {
-                        g = __ffma2_rn(f2(v0.z, v0.z), r, f2(v0.y, v0.y));
-                    } else {
-                        g = __ffma2_rn(f2(g4, g4), r, f2(v0.w, v0.w));
-                        g = __ffma2_rn(g, r, f2(v0.z, v0.z));
-                        g = __ffma2_rn(g, r, f2(v0.y, v0.y));
-                    }
-                    g = __ffma2_rn(g, r, f2(v0.x, v0.x));
-                    acc[0][m] = __fadd2_rn(acc[0][m], f2(ex2_approx(g.x), ex2_approx(g.y)));
-                }
-                continue;
-            }
-            if constexpr (kSingle) {
-                // one snapshot, another class: per point, into the point-pair accumulators
-                const uint32_t c = word & kCodeMask;
-                if (c == kCodeSkip) continue;
-                const RecF32 &Rs = sm.rec[s];
-                if (c == kCodeD8) {
-                    point_pass<8, PPT>(acc[0], r2, Rs);
-                } else if (c == kCodeD12) {
-                    point_pass<12, PPT>(acc[0], r2, Rs);
-                } else if (c == kCodeGeneral) {
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        const float t = pair_term(r2[k], Rs);
-                        if (k & 1) acc[0][k >> 1].y += t; else acc[0][k >> 1].x += t;
+                    for (int mm = 0; mm < PPT / 2; ++mm) {
+                        const float2 r = f2(r2[2 * mm], r2[2 * mm + 1]);
+                        float2 g;
+                        if (!d4) {
+                            g = __ffma2_rn(f2(v0.z, v0.z), r, f2(v0.y, v0.y));
+                        } else {
+                            g = __ffma2_rn(f2(g4, g4), r, f2(v0.w, v0.w));
+                            g = __ffma2_rn(g, r, f2(v0.z, v0.z));
+                            g = __ffma2_rn(g, r, f2(v0.y, v0.y));
+                        }
+                        g = __ffma2_rn(g, r, f2(v0.x, v0.x));
+                        acc[0][mm] = __fadd2_rn(acc[0][mm], f2(ex2_approx(g.x), ex2_approx(g.y)));
                     }
                 }
-                continue;
-            }
+                // another class: per point, into the point-pair accumulators
+                for (uint32_t m = mp; m; m &= m - 1) {
+                    const int b = __ffs(m) - 1, s = cw * 32 + b;
+                    const uint32_t c = __shfl_sync(0xffffffffu, my_word[cw], b) & kCodeMask;
+                    if (c == kCodeSkip) continue;
+                    float r2[PPT];
+                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+                    const RecF32 &Rs = sm.rec[s];
+                    if (c == kCodeD8) {
+                        point_pass<8, PPT>(acc[0], r2, Rs);
+                    } else if (c == kCodeD12) {
+                        point_pass<12, PPT>(acc[0], r2, Rs);
+                    } else if (c == kCodeGeneral) {
 #pragma unroll
-            for (int jc = 0; jc < TCH; ++jc) {
-                const uint32_t c = (word >> (kCodeBits * jc)) & kCodeMask;
-                if (c == kCodeSkip) continue;
-                const RecF32 &Rs = rows[jc][s0 + s];            // active: the record exists
-                float2 (&A)[PPT] = acc[jc >> 1];
-                if (c == kCodeD2) {
-                    if (jc & 1) moment_pass<2, PPT, 1>(A, r2, Rs); else moment_pass<2, PPT, 0>(A, r2, Rs);
-                } else if (c == kCodeD4) {
-                    if (jc & 1) moment_pass<4, PPT, 1>(A, r2, Rs); else moment_pass<4, PPT, 0>(A, r2, Rs);
-                } else if (c == kCodeD8) {
-                    if (jc & 1) moment_pass<8, PPT, 1>(A, r2, Rs); else moment_pass<8, PPT, 0>(A, r2, Rs);
-                } else if (c == kCodeD12) {
-                    if (jc & 1) moment_pass<12, PPT, 1>(A, r2, Rs); else moment_pass<12, PPT, 0>(A, r2, Rs);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        const float t = pair_term(r2[k], Rs);
-                        if (jc & 1) A[k].y += t; else A[k].x += t;
+                        for (int k = 0; k < PPT; ++k) {
+                            const float t = pair_term(r2[k], Rs);
+                            if (k & 1) acc[0][k >> 1].y += t; else acc[0][k >> 1].x += t;
+                        }
                     }
                 }
             }
