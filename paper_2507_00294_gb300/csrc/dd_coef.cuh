@@ -21,6 +21,17 @@ struct RecipTable {
 };
 static __device__ __constant__ RecipTable kRecipTable = RecipTable();
 #define kRecip kRecipTable.v
+// The same rounded to FP32 (bit for bit (float)kRecip[n]), for the FP32 recurrences: an
+// FP64 -> FP32 conversion per use would run on the FP64 unit, a small fraction of the
+// FP32 rate on this part, inside each thread's serial chain.
+struct RecipTableF {
+    float v[96];
+    constexpr RecipTableF() : v() {
+        for (int n = 1; n < 96; ++n) v[n] = (float)(1.0 / n);
+    }
+};
+static __device__ __constant__ RecipTableF kRecipFTable = RecipTableF();
+#define kRecipF kRecipFTable.v
 
 template <int M>
 __device__ void moment_coefficients(double r, double ell, double *c) {
@@ -63,25 +74,25 @@ __device__ void moment_coefficients_f32(float r, float ell, float *c) {
         const float ir = 1.0f / r;
         J[0] = ell;
 #pragma unroll
-        for (int m = 1; m <= M; ++m) J[m] = (float)kRecip[m] - J[m - 1] * ir;
+        for (int m = 1; m <= M; ++m) J[m] = kRecipF[m] - J[m - 1] * ir;
     } else {
         const float rho = r / (1.0f + r);
-        float term = rho * (float)kRecip[M + 1], sum = 0.0f;
+        float term = rho * kRecipF[M + 1], sum = 0.0f;
         for (int k = 1; k < 64; ++k) {
             sum += term;
-            term *= rho * (float)k * (float)kRecip[M + 1 + k];
+            term *= rho * (float)k * kRecipF[M + 1 + k];
             if (term <= 1e-9f * sum) break;
         }
         J[M] = sum;
 #pragma unroll
-        for (int m = M; m >= 1; --m) J[m - 1] = r * ((float)kRecip[m] - J[m]);
+        for (int m = M; m >= 1; --m) J[m - 1] = r * (kRecipF[m] - J[m]);
         J[0] = ell;
     }
     float inv_fact = 1.0f;
 #pragma unroll
     for (int m = 0; m <= M; ++m) {
         c[m] = (m & 1) ? -J[m] * inv_fact : J[m] * inv_fact;
-        inv_fact *= (float)kRecip[m + 1];
+        inv_fact *= kRecipF[m + 1];
     }
 }
 
@@ -140,7 +151,7 @@ struct RecTraits<RecF32> {
             float acc = 0.0f;
 #pragma unroll
             for (int k = 1; k < m; ++k) acc = fmaf((float)k * l[k], p[m - k], acc);
-            l[m] = p[m] - acc * (float)kRecip[m];
+            l[m] = p[m] - acc * kRecipF[m];
         }
         const float dqf = (float)dq, dq2 = dqf * dqf;
         o.v0 = make_float4(log2f(ellf), (float)(kLog2e * ((double)l[1] * dq - q1)),
