@@ -296,6 +296,15 @@ int dose_lag_block(int64_t n) {
     return lb;
 }
 
+// Valid (target j, lag k) pairs of a dose work item: targets [t0, t1), lags [k0, k1) with
+// k1 <= t1, pair valid when k <= j, i.e. sum_k (t1 - max(t0, k)): t1 - t0 for every lag up
+// to t0, then t1 - k (an arithmetic series) for the lags beyond.
+inline int64_t dose_item_pairs(int64_t t0, int64_t t1, int64_t k0, int64_t k1) {
+    const int64_t full = std::max<int64_t>(0, std::min(k1, t0 + 1) - k0) * (t1 - t0);
+    const int64_t a = std::max(k0, t0 + 1), b = k1 - 1;
+    return full + (a <= b ? (b - a + 1) * t1 - (a + b) * (b - a + 1) / 2 : 0);
+}
+
 template <typename Cfg>
 dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     using Rec = typename Cfg::Rec;
@@ -312,9 +321,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         const int64_t nb = (t1 - 1 - 1) / lb + 1;                    // lags 1 .. t1-1
         for (int64_t b = 0; b < nb; ++b) {
             const int64_t k0 = 1 + b * lb, k1 = std::min(k0 + lb, t1);
-            int64_t cost = 0;                                        // valid (j, k) pairs
-            for (int64_t k = k0; k < k1; ++k) cost += std::max<int64_t>(0, t1 - std::max(t0, k));
-            its.push_back({cost, make_int2((int)t, (int)b)});
+            its.push_back({dose_item_pairs(t0, t1, k0, k1), make_int2((int)t, (int)b)});
         }
     }
     std::stable_sort(its.begin(), its.end(),
@@ -493,8 +500,7 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
         const int64_t nb = (t1 - 2) / lb + 1;
         for (int64_t bk = 0; bk < nb; ++bk) {
             const int64_t k0 = 1 + bk * lb, k1 = std::min(k0 + lb, t1);
-            int64_t cost = 0;
-            for (int64_t k = k0; k < k1; ++k) cost += std::max<int64_t>(0, t1 - std::max(t0, k));
+            const int64_t cost = dose_item_pairs(t0, t1, k0, k1);
             if (count >= kNoAllocMaxItems)
                 return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: work list exceeds its fixed size");
             its[count++] = {cost, make_int2((int)t, (int)bk)};

@@ -97,7 +97,7 @@ struct Carve {
 // Host-side tables, uploaded through pinned staging blocks; freed (and the blocks given
 // back) once an event recorded after the uploads has completed.
 struct HostTables {
-    std::vector<std::vector<int4>> items;
+    std::vector<std::vector<int2>> items;
     std::vector<std::vector<int>> ints;
     std::vector<std::vector<double>> reals;
     std::vector<std::vector<int64_t>> offs;
@@ -124,7 +124,7 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
     add((size_t)group * sizeof(double));                      // snapshot times
     add((size_t)group * sizeof(int) * 3);                     // nact, row, nblk per snapshot
     add((size_t)group * sizeof(int64_t));                     // record row offset per snapshot
-    add((size_t)n_tiles * n_chunks * nblk_max * sizeof(int4));  // items
+    add((size_t)n_chunks * nblk_max * sizeof(int2));          // (chunk, block) descriptors
     add((size_t)n_rec * sizeof(Rec));                         // coefficient records
     add((size_t)nblk_max * group * ((n_pts + 3) / 4 * 4) * sizeof(typename Cfg::Real));   // partial sums
     return b + 256;
@@ -264,7 +264,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     int *d_row = d_nact + group;
     int *d_nblk = d_row + group;
     int64_t *d_roff = cv.take<int64_t>(group);
-    int4 *d_items = cv.take<int4>((size_t)n_tiles * n_chunks_max * nblk_max);
+    int2 *d_desc = cv.take<int2>((size_t)n_chunks_max * nblk_max);
     Rec *d_rec = cv.take<Rec>((size_t)n_rec);
     using Part = typename Cfg::Real;
     const int64_t pstride = (n_pts + 3) / 4 * 4;            // 16-byte aligned partial rows
@@ -302,8 +302,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         }
         // work items: (tile, chunk, block) for every block below the chunk's largest
         // n_active, longest first.  Every tile of a (chunk, block) costs the same, so the
-        // (chunk, block) pairs are sorted (stable: ties keep chunk, block order) and each
-        // expands into its tiles in tile order.
+        // (chunk, block) descriptors are sorted (stable: ties keep chunk, block order) and
+        // the kernel expands each into its tiles in tile order.
         std::vector<std::pair<int64_t, int2>> blocks;
         for (int c = 0; c < n_chunks; ++c) {
             const int j0 = c * Cfg::kTCH, j1 = std::min(ng, j0 + Cfg::kTCH);
@@ -320,22 +320,18 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         }
         std::stable_sort(blocks.begin(), blocks.end(),
                          [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
-        std::vector<int4> it(blocks.size() * (size_t)n_tiles);
-        {
-            size_t q = 0;
-            for (const auto &bk : blocks)
-                for (int64_t t = 0; t < n_tiles; ++t) it[q++] = make_int4((int)t, bk.second.x, bk.second.y, 0);
-        }
+        std::vector<int2> it(blocks.size());
+        for (size_t q = 0; q < blocks.size(); ++q) it[q] = blocks[q].second;
 
-        // the group's tables in one copy: a host image of the device span d_t .. items end
+        // the group's tables in one copy: a host image of the device span d_t .. descriptors end
         {
             char *const d0 = reinterpret_cast<char *>(d_t);
-            const size_t span = reinterpret_cast<char *>(d_items + it.size()) - d0;
+            const size_t span = reinterpret_cast<char *>(d_desc + it.size()) - d0;
             std::vector<char> img(span);
             std::memcpy(img.data(), tg.data(), ng * sizeof(double));
             std::memcpy(img.data() + (reinterpret_cast<char *>(d_nact) - d0), tabs.data(), 3 * (size_t)ng * sizeof(int));
             std::memcpy(img.data() + (reinterpret_cast<char *>(d_roff) - d0), roff.data(), ng * sizeof(int64_t));
-            std::memcpy(img.data() + (reinterpret_cast<char *>(d_items) - d0), it.data(), it.size() * sizeof(int4));
+            std::memcpy(img.data() + (reinterpret_cast<char *>(d_desc) - d0), it.data(), it.size() * sizeof(int2));
             DD_CUDA_TRY(keep->staging.upload(d0, img.data(), span, stream));
             keep->images.push_back(std::move(img));
         }
@@ -347,10 +343,16 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         }
         if (!it.empty()) {
             DD_CUDA_TRY(prefer_shared<Cfg>());
-            DD_PROFILED(Cfg::kFieldName, stream,
-                        (ddk::field_kernel<Cfg><<<(unsigned)it.size(), Cfg::kThreads, 0, stream>>>(
-                            srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_items, ng, sb, d_part, pstride, srcF, PF)));
-            DD_CUDA_TRY(cudaGetLastError());
+            // one CTA per item, in launches of at most 2^31 - 1 CTAs (the grid's x limit)
+            const int64_t n_items = (int64_t)it.size() * n_tiles, kMaxGrid = (int64_t(1) << 31) - 1;
+            for (int64_t item0 = 0; item0 < n_items; item0 += kMaxGrid) {
+                const unsigned grid = (unsigned)std::min(kMaxGrid, n_items - item0);
+                DD_PROFILED(Cfg::kFieldName, stream,
+                            (ddk::field_kernel<Cfg><<<grid, Cfg::kThreads, 0, stream>>>(
+                                srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_desc, n_tiles, item0, ng, sb, d_part,
+                                pstride, srcF, PF)));
+                DD_CUDA_TRY(cudaGetLastError());
+            }
         }
         dim3 rg((unsigned)((n_pts + 1023) / 1024), (unsigned)ng);
         DD_PROFILED("field_reduce", stream,

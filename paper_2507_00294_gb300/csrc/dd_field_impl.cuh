@@ -707,7 +707,10 @@ __device__ __forceinline__ void load4_cg(const double *p, double (&v)[4]) {
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
-// One work item per CTA: item = (point tile, snapshot chunk, visit block).
+// One work item per CTA: item = (point tile, snapshot chunk, visit block).  The items are
+// the (chunk, block) descriptors desc[] (in cost order) times the point tiles in tile
+// order: CTA item0 + blockIdx.x takes descriptor (item0 + blockIdx.x) / n_tiles and tile
+// (item0 + blockIdx.x) % n_tiles.
 // partial[(block * n_tg + j) * pstride + p] receives sum_{i in block, i < nact[j]} pair_term
 // (pstride = n_pts rounded up to a multiple of 4, so that rows are 16-byte aligned).
 template <typename Cfg>
@@ -715,12 +718,14 @@ __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kMinBlocks)
 field_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY,
              const double *__restrict__ X, const double *__restrict__ Y, int64_t n_pts,
              const typename Cfg::Rec *__restrict__ rec, const int64_t *__restrict__ row_off,
-             const int *__restrict__ nact, const int4 *__restrict__ items, int n_tg, int sb,
-             typename Cfg::Real *__restrict__ partial, int64_t pstride, const float4 *__restrict__ srcF,
-             const float4 *__restrict__ ptsF) {
+             const int *__restrict__ nact, const int2 *__restrict__ desc, int64_t n_tiles, int64_t item0,
+             int n_tg, int sb, typename Cfg::Real *__restrict__ partial, int64_t pstride,
+             const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF) {
     using Rec = typename Cfg::Rec;
     constexpr int TCH = Cfg::kTCH;
-    const int4 item = items[blockIdx.x];
+    const int64_t q = item0 + blockIdx.x;
+    const int2 dc = desc[q / n_tiles];                     // (chunk, block)
+    const int4 item = make_int4((int)(q % n_tiles), dc.x, dc.y, 0);
     const int j0 = item.y * TCH;
     int na[TCH];
     const Rec *rows[TCH];
