@@ -314,23 +314,16 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     const int lb = dose_lag_block<Cfg>(n);
     const int64_t n_tiles = (n + TILE - 1) / TILE;
-    std::vector<std::pair<int64_t, int2>> its;
+    int64_t n_items = 0;
     for (int64_t t = 0; t < n_tiles; ++t) {
-        const int64_t t0 = t * TILE, t1 = std::min(n, t0 + TILE);
-        if (t1 - 1 < 1) continue;                                    // target 0 has no source
-        const int64_t nb = (t1 - 1 - 1) / lb + 1;                    // lags 1 .. t1-1
-        for (int64_t b = 0; b < nb; ++b) {
-            const int64_t k0 = 1 + b * lb, k1 = std::min(k0 + lb, t1);
-            its.push_back({dose_item_pairs(t0, t1, k0, k1), make_int2((int)t, (int)b)});
-        }
+        const int64_t t1 = std::min(n, t * TILE + TILE);
+        if (t1 >= 2) n_items += (t1 - 2) / lb + 1;                   // lags 1 .. t1-1
     }
-    std::stable_sort(its.begin(), its.end(),
-                     [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
     const int64_t nblk = n >= 2 ? (n - 2) / lb + 1 : 0;
     size_t bytes = 0;
     auto add = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
     add((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
-    add(its.size() * sizeof(int2) + 16);
+    add((size_t)n_items * sizeof(int2) + 16);
     add((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(typename Cfg::Real));
     if (out_copy) add((size_t)n * sizeof(double));
     bytes += 256;
@@ -350,7 +343,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     size_t off = 0;
     auto take = [&](size_t b) { off = (off + 255) & ~size_t(255); char *p = base + off; off += b; return p; };
     Rec *d_rec = (Rec *)take((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
-    int2 *d_items = (int2 *)take(its.size() * sizeof(int2) + 16);
+    int2 *d_items = (int2 *)take((size_t)n_items * sizeof(int2) + 16);
     using Part = typename Cfg::Real;
     Part *d_part = (Part *)take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(Part));
     double *out_dev = out_copy ? (double *)take((size_t)n * sizeof(double)) : out;
@@ -361,12 +354,26 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         dd::CallStaging staging;
     };
     auto *keep = new Keep();
-    keep->items.resize(its.size());
-    for (size_t k = 0; k < its.size(); ++k) keep->items[k] = its[k].second;
     if (n >= 2) {
+        // the lag table first: the GPU builds it while the host sorts the work list
         DD_PROFILED(Cfg::kLagCoefName, stream,
                     (ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 31) / 32), 32, 0, stream>>>(n, scan->s, scan->kappa, d_rec)));
         DD_CUDA_TRY(cudaGetLastError());
+        std::vector<std::pair<int64_t, int2>> its;
+        its.reserve((size_t)n_items);
+        for (int64_t t = 0; t < n_tiles; ++t) {
+            const int64_t t0 = t * TILE, t1 = std::min(n, t0 + TILE);
+            if (t1 - 1 < 1) continue;                                // target 0 has no source
+            const int64_t nb = (t1 - 1 - 1) / lb + 1;                // lags 1 .. t1-1
+            for (int64_t b = 0; b < nb; ++b) {
+                const int64_t k0 = 1 + b * lb, k1 = std::min(k0 + lb, t1);
+                its.push_back({dose_item_pairs(t0, t1, k0, k1), make_int2((int)t, (int)b)});
+            }
+        }
+        std::stable_sort(its.begin(), its.end(),
+                         [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
+        keep->items.resize(its.size());
+        for (size_t k = 0; k < its.size(); ++k) keep->items[k] = its[k].second;
         DD_CUDA_TRY(keep->staging.upload(d_items, keep->items.data(), keep->items.size() * sizeof(int2), stream));
         DD_PROFILED(Cfg::kDoseName, stream,
                     (ddk::dose_kernel<Cfg><<<(unsigned)keep->items.size(), Cfg::kThreads, 0, stream>>>(
