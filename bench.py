@@ -35,7 +35,7 @@ UNIT = "pair-terms/s"
 # series (FMA = 2 flops): rho^2 costs 5 flops per (point, visit), shared by the 4
 # snapshots of a chunk (1.25 per pair); a series path of degree d adds its exponent (2d
 # flops for d = 2, 4 in rho^2; 2d + 1 for d = 8, 12 in h) and the accumulating add, plus
-# one ex2 (degree 2 up to h = 0.0215, 4 up to 0.235, 8 up to 1.0, 12 up to 1.7); the
+# one ex2 (degree 2 up to h = 0.04, 4 up to 0.33, 8 up to 1.25, 12 up to 2.0); the
 # general path (two E1 values) about 55 flops and 4 MUFU operations (2 ex2, 2 rcp); a
 # pair with a >= 87 only its rho^2.
 FLOPS_SERIES = {2: 6.25, 4: 10.25, 8: 19.25, 12: 27.25}
@@ -194,11 +194,11 @@ def ops_per_pair(job, samples=400_000, seed=5):
     a, h = rho2 / w1, rho2 / w0 - rho2 / w1
     zero = a >= 87
     f = np.where(zero, FLOPS_ZERO,
-                 np.where(h <= 0.0215, FLOPS_SERIES[2],
-                          np.where(h <= 0.235, FLOPS_SERIES[4],
-                                   np.where(h <= 1.0, FLOPS_SERIES[8],
-                                            np.where(h <= 1.7, FLOPS_SERIES[12], FLOPS_GENERAL)))))
-    m = np.where(zero, 0.0, np.where(h <= 1.7, MUFU_SERIES, MUFU_GENERAL))
+                 np.where(h <= 0.04, FLOPS_SERIES[2],
+                          np.where(h <= 0.33, FLOPS_SERIES[4],
+                                   np.where(h <= 1.25, FLOPS_SERIES[8],
+                                            np.where(h <= 2.0, FLOPS_SERIES[12], FLOPS_GENERAL)))))
+    m = np.where(zero, 0.0, np.where(h <= 2.0, MUFU_SERIES, MUFU_GENERAL))
     wgt = nact[np.arange(samples)]               # pairs are sampled per snapshot: weight by n_active
     return float(np.sum(f * wgt) / np.sum(wgt)), float(np.sum(m * wgt) / np.sum(wgt))
 

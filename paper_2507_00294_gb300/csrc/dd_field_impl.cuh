@@ -56,10 +56,11 @@ template <typename Rec>
 struct RecTraits;
 
 // Largest h of each FP32 class: the truncated exponent series of degree d stays within
-// 4e-8 of ln(P(h)/c_0) for every r in [1e-6, 1e6] (checked against 40-digit quadrature):
-// degree 2 up to h = 0.0215, 4 up to 0.235, 8 up to 1.0 and 12 up to 1.7.  FP64: the
-// moment polynomial of degree 15 up to h = 1/2 (1.2e-18).
-constexpr float kL2H = 0.0215f, kL4H = 0.235f, kL8H = 1.0f, kL12H = 1.7f;
+// 2.5e-7 of ln(P(h)/c_0) for every r in [1e-6, 1e6] (checked against 30-digit quadrature;
+// about four FP32 roundings of the term, below the exponent's own rounding for all but the
+// largest terms): degree 2 up to h = 0.04, 4 up to 0.33, 8 up to 1.25 and 12 up to 2.0.
+// FP64: the moment polynomial of degree 15 up to h = 1/2 (1.2e-18).
+constexpr float kL2H = 0.04f, kL4H = 0.33f, kL8H = 1.25f, kL12H = 2.0f;
 constexpr double kHMaxD = 0.5;
 // The rho^2 forms of degree 2 and 4 need dq^4 and dq^3 in the FP32 normal range; records
 // with a smaller dq (far beyond any scan's duration) take the h forms.
@@ -85,7 +86,7 @@ __device__ __forceinline__ float log_term(float r2, const RV &R) {
 
 // One pair term E1(a) - E1(b), a = rho^2 q1, b = a + rho^2 dq, FP32 arithmetic, with a
 // per-lane regime test: zero (a >= 87: below the FP32 normal range), the degree-12
-// exponent series (h <= 1.7), or the two E1 values (dd_e1.cuh).
+// exponent series (h <= 2.0), or the two E1 values (dd_e1.cuh).
 template <typename RV>
 __device__ __forceinline__ float pair_term(float r2, const RV &R) {
     const float a = r2 * R.q1();
