@@ -22,6 +22,26 @@
 
 namespace ddk {
 
+// Lag blocks of the dose work items.  The smallest lags are the costliest pairs (at dwell
+// start the source k visits back lies about k pitches away, so h = rho^2 dq stays near 1:
+// the high series degrees and the two-E1 path), so the first lb lags come in kDoseSplit
+// blocks of lb / kDoseSplit, and every later block holds lb lags: block b covers lags
+// [k0, k1) below.  lb is a multiple of kDoseSplit.
+constexpr int kDoseSplit = 8;
+__host__ __device__ inline void dose_block_lags(int64_t b, int lb, int64_t &k0, int64_t &k1) {
+    const int q = lb / kDoseSplit;
+    if (b < kDoseSplit) { k0 = 1 + b * q; k1 = k0 + q; }
+    else { k0 = 1 + (b - kDoseSplit + 1) * (int64_t)lb; k1 = k0 + lb; }
+}
+// Blocks needed for the lags 1 .. t1 - 1 of a tile whose last target is t1 - 1.
+__host__ __device__ inline int64_t dose_blocks(int64_t t1, int lb) {
+    const int64_t kmax = t1 - 1;                     // largest lag
+    if (kmax < 1) return 0;
+    const int q = lb / kDoseSplit;
+    if (kmax <= lb) return (kmax - 1) / q + 1;
+    return kDoseSplit + (kmax - lb - 1) / lb + 1;
+}
+
 template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads)
 dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, int64_t n,
@@ -41,8 +61,10 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     const int tid = threadIdx.x;
     const int64_t t0 = (int64_t)item.x * TILE;             // first target of the tile
     const int64_t t1 = min((int64_t)n, t0 + TILE);
-    const int k0 = 1 + item.y * lb;                        // lags [k0, k1)
-    const int k1 = (int)min((int64_t)k0 + lb, t1);         // lag < target index <= t1 - 1
+    int64_t kb0, kb1;
+    dose_block_lags(item.y, lb, kb0, kb1);
+    const int k0 = (int)kb0;                               // lags [k0, k1)
+    const int k1 = (int)min(kb1, t1);                      // lag < target index <= t1 - 1
     // sources needed: i = j - k for j in [t0, t1), k in [k0, k1): i in [t0 - k1 + 1, t1 - k0)
     const int64_t w0 = t0 - k1 + 1;
     const int64_t w1 = t1 - k0;
@@ -251,7 +273,7 @@ dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int tile, int lb
     if (j < n) {
         // blocks written for target j: every lag block that starts below the tile's last target
         const int64_t tile_last = min(n, (j / tile + 1) * tile) - 1;
-        const int64_t nb = tile_last >= 1 ? (tile_last - 1) / lb + 1 : 0;
+        const int64_t nb = dose_blocks(tile_last + 1, lb);
         BlockSum<Part> acc;
 #pragma unroll 4
         for (int64_t b = q; b < nb; b += kDoseReduceSplit) acc.add(partial[b * n + j]);
@@ -288,7 +310,7 @@ int dose_lag_block(int64_t n) {
         int64_t items = 0;
         for (int64_t t0 = 0; t0 < n; t0 += TILE) {
             const int64_t t1 = std::min(n, t0 + TILE);
-            if (t1 >= 2) items += (t1 - 2) / lb + 1;
+            items += ddk::dose_blocks(t1, lb);
         }
         if (items >= 8 * (int64_t)sms) break;
         lb /= 2;
@@ -317,9 +339,9 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     int64_t n_items = 0;
     for (int64_t t = 0; t < n_tiles; ++t) {
         const int64_t t1 = std::min(n, t * TILE + TILE);
-        if (t1 >= 2) n_items += (t1 - 2) / lb + 1;                   // lags 1 .. t1-1
+        n_items += ddk::dose_blocks(t1, lb);                          // lags 1 .. t1-1
     }
-    const int64_t nblk = n >= 2 ? (n - 2) / lb + 1 : 0;
+    const int64_t nblk = ddk::dose_blocks(n, lb);
     size_t bytes = 0;
     auto add = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
     add((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
@@ -364,9 +386,11 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         for (int64_t t = 0; t < n_tiles; ++t) {
             const int64_t t0 = t * TILE, t1 = std::min(n, t0 + TILE);
             if (t1 - 1 < 1) continue;                                // target 0 has no source
-            const int64_t nb = (t1 - 1 - 1) / lb + 1;                // lags 1 .. t1-1
+            const int64_t nb = ddk::dose_blocks(t1, lb);             // lags 1 .. t1-1
             for (int64_t b = 0; b < nb; ++b) {
-                const int64_t k0 = 1 + b * lb, k1 = std::min(k0 + lb, t1);
+                int64_t k0, k1;
+                ddk::dose_block_lags(b, lb, k0, k1);
+                k1 = std::min(k1, t1);
                 its.push_back({dose_item_pairs(t0, t1, k0, k1), make_int2((int)t, (int)b)});
             }
         }
@@ -485,7 +509,7 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     const int lb = Cfg::kDoseLB;
     const int64_t n_tiles = (n + TILE - 1) / TILE;
-    const int64_t nblk = n >= 2 ? (n - 2) / lb + 1 : 0;
+    const int64_t nblk = ddk::dose_blocks(n, lb);
     size_t off = 0;
     auto take = [&](size_t bytes) { off = (off + 255) & ~size_t(255); size_t o = off; off += bytes; return o; };
     const size_t o_x = take(2 * (size_t)n * sizeof(double));
@@ -504,9 +528,11 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     for (int64_t t = 0; t < n_tiles; ++t) {
         const int64_t t0 = t * TILE, t1 = std::min(n, t0 + TILE);
         if (t1 - 1 < 1) continue;
-        const int64_t nb = (t1 - 2) / lb + 1;
+        const int64_t nb = ddk::dose_blocks(t1, lb);
         for (int64_t bk = 0; bk < nb; ++bk) {
-            const int64_t k0 = 1 + bk * lb, k1 = std::min(k0 + lb, t1);
+            int64_t k0, k1;
+            ddk::dose_block_lags(bk, lb, k0, k1);
+            k1 = std::min(k1, t1);
             const int64_t cost = dose_item_pairs(t0, t1, k0, k1);
             if (count >= kNoAllocMaxItems)
                 return dd::fail(DD_EINVAL, "dd_per_probe_dose_noalloc: work list exceeds its fixed size");
