@@ -207,6 +207,31 @@ __device__ __forceinline__ void point_pass(float2 (&acc)[PPT], const float (&r2)
     }
 }
 
+// One snapshot at PPT points, the h form of degree D (8, 12) on f32x2 instructions over
+// point pairs: acc[m] += (2^G(r_2m), 2^G(r_2m+1)), each half rounded as log_exponent<D>
+// rounds it.
+template <int D, int PPT>
+__device__ __forceinline__ void point_pass_h2(float2 (&acc)[PPT], const float (&r2)[PPT], const RecF32 &R) {
+    const float2 dq = make_float2(R.dq(), R.dq()), g0 = make_float2(R.g0(), R.g0());
+    float2 h[PPT / 2], p[PPT / 2];
+#pragma unroll
+    for (int m = 0; m < PPT / 2; ++m) {
+        h[m] = __fmul2_rn(make_float2(r2[2 * m], r2[2 * m + 1]), dq);
+        p[m] = make_float2(R.k(D), R.k(D));
+    }
+#pragma unroll
+    for (int j = D - 1; j >= 1; --j) {
+        const float2 c = make_float2(R.k(j), R.k(j));
+#pragma unroll
+        for (int m = 0; m < PPT / 2; ++m) p[m] = __ffma2_rn(p[m], h[m], c);
+    }
+#pragma unroll
+    for (int m = 0; m < PPT / 2; ++m) {
+        const float2 g = __ffma2_rn(p[m], h[m], g0);
+        acc[m] = __fadd2_rn(acc[m], make_float2(ex2_approx(g.x), ex2_approx(g.y)));
+    }
+}
+
 // The zero record's leading vector (g_0 = -inf): a snapshot for which the visit has not
 // started, or a padding snapshot, adds 2^-inf = 0 on every path.
 __device__ __forceinline__ float4 zero_rec_v0() { return make_float4(-INFINITY, 0.f, 0.f, 0.f); }
@@ -524,9 +549,9 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     rho2_points<PPT>(px, py, sm.xy[s], r2);
                     const RecF32 &Rs = sm.rec[s];
                     if (c == kCodeD8) {
-                        point_pass<8, PPT>(acc[0], r2, Rs);
+                        point_pass_h2<8, PPT>(acc[0], r2, Rs);
                     } else if (c == kCodeD12) {
-                        point_pass<12, PPT>(acc[0], r2, Rs);
+                        point_pass_h2<12, PPT>(acc[0], r2, Rs);
                     } else if (c == kCodeGeneral) {
 #pragma unroll
                         for (int k = 0; k < PPT; ++k) {
