@@ -130,7 +130,8 @@ struct CfgMixed {
     using Rec = RecF32;
     using Real = float;
     static constexpr int kThreads = 128, kPPT = 4, kTCH = 4, kSTILE = 32, kSB = 512, kFlush = 32;
-    static constexpr int kMinBlocks = 8;     // 32 warps per SM: at most 64 registers, 22 KB shared
+    static constexpr int kMinBlocks = 8;     // 32 warps per SM: at most 64 registers, 12 KB shared
+    static constexpr int kCarveout = 58;     // percent of the L1/shared array as shared memory (132 KB)
     static constexpr int kDoseLB = 512;      // largest lag block of the dose kernel
     static constexpr int kDoseSTILE = 64;    // lags staged per round by the dose kernel
     static constexpr int kDosePPT = 2;       // targets per thread in the dose kernel (256-target tiles)
@@ -143,6 +144,7 @@ struct CfgF64 {
     using Real = double;
     static constexpr int kThreads = 128, kPPT = 2, kTCH = 4, kSTILE = 32, kSB = 512, kFlush = 1 << 30;
     static constexpr int kMinBlocks = 1;
+    static constexpr int kCarveout = (int)cudaSharedmemCarveoutMaxShared;
     static constexpr int kDoseLB = 512;
     static constexpr int kDoseSTILE = 32;
     static constexpr int kDosePPT = 2;
