@@ -22,9 +22,13 @@
  *     used from several threads; calls that write the same output race.
  *   - Pointers marked "host or device" may point to host memory or to CUDA device
  *     memory of the current device (detected with cudaPointerGetAttributes).
- *     Host outputs are written before the call returns (the call synchronises
- *     the stream).  With device inputs and outputs the call only enqueues work on
- *     `cuda_stream` (NULL = the legacy default stream) and returns.
+ *     With device inputs and outputs the call only enqueues work on `cuda_stream`
+ *     (NULL = the legacy default stream) and returns.  With a host input or output
+ *     the call synchronises the stream before it returns (host outputs are then
+ *     written), except when a stream other than NULL is given and every host buffer
+ *     of the call is page-locked (cudaHostAlloc / cudaHostRegister): then its copies
+ *     stay enqueued on `cuda_stream` like its kernels, and the caller synchronises
+ *     the stream before reading the outputs or reusing the inputs.
  *   - Device scratch is taken stream-ordered on the call's stream from a memory
  *     pool the library owns per device (freed workspace up to 4 GiB stays mapped
  *     for the next call) and returned with cudaFreeAsync; a scan caches its probe

@@ -208,7 +208,10 @@ def dd_create_scan(spec):
 
 
 def dd_field_at_times(scan, pts_xy_m, times_s, prec="mixed", out=None, stream=None):
-    """psi at every (time, point); returns `out` ([n_t, n_pts] float64, numpy or torch)."""
+    """psi at every (time, point); returns `out` ([n_t, n_pts] float64, numpy or torch).
+
+    With a `stream` and only page-locked host buffers the host copies stay enqueued on
+    that stream: synchronise it before reading `out`."""
     n_pts = (pts_xy_m.shape[0] if hasattr(pts_xy_m, "shape") else len(pts_xy_m))
     n_t = len(times_s)
     if out is None:

@@ -331,7 +331,8 @@ template <typename Cfg>
 dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     using Rec = typename Cfg::Rec;
     const int64_t n = scan->n;
-    const bool out_host = !dd::is_device_pointer(out);
+    const dd::MemKind out_kind = dd::memory_kind(out);
+    const bool out_host = out_kind != dd::MemKind::Device;
     const bool out_copy = out_host;
     constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     const int lb = dose_lag_block<Cfg>(n);
@@ -411,14 +412,15 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
     DD_CUDA_TRY(dd::defer_release(stream, keep, [](void *p) { delete static_cast<Keep *>(p); }));
-    if (out_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (dd::host_sync_needed(stream, {out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
 }
 
 template <typename Cfg>
 dd_status run_dose_general(const dd_scan *scan, double *out, cudaStream_t stream) {
     const int64_t n = scan->n;
-    const bool out_host = !dd::is_device_pointer(out);
+    const dd::MemKind out_kind = dd::memory_kind(out);
+    const bool out_host = out_kind != dd::MemKind::Device;
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
@@ -442,7 +444,7 @@ dd_status run_dose_general(const dd_scan *scan, double *out, cudaStream_t stream
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
-    if (out_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (dd::host_sync_needed(stream, {out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
 }
 

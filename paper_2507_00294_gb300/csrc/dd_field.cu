@@ -173,8 +173,9 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     using Rec = typename Cfg::Rec;
     const int64_t n_src = scan->n;
     const int n_t = (int)times.size();
-    const bool pts_host = !dd::is_device_pointer(pts_xy_m);
-    const bool out_host = !dd::is_device_pointer(out);
+    const dd::MemKind pts_kind = dd::memory_kind(pts_xy_m), out_kind = dd::memory_kind(out);
+    const bool pts_host = pts_kind != dd::MemKind::Device;
+    const bool out_host = out_kind != dd::MemKind::Device;
     // host buffers go through a workspace copy (a pinned output written in place by the
     // reduce measured slower than the copy engine's transfer)
     const bool pts_copy = pts_host, out_copy = out_host;
@@ -369,7 +370,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n_t * n_pts * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
     DD_CUDA_TRY(dd::defer_release(stream, keep, HostTables::release));
-    if (out_host || pts_host) DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (dd::host_sync_needed(stream, {pts_kind, out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
 }
 

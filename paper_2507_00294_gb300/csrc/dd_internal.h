@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units (not installed).
 #pragma once
+#include <initializer_list>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -63,6 +64,15 @@ const float4 *device_sources_ff(const dd_scan *scan, cudaStream_t stream, dd_sta
 
 // True if `p` is device-accessible memory of the current device.
 bool is_device_pointer(const void *p);
+// Where a user buffer lives: device (or managed) memory, page-locked host memory, or
+// pageable host memory.
+enum class MemKind { Device, Pinned, Pageable };
+MemKind memory_kind(const void *p);
+// Whether a call with these buffers must synchronise its stream before returning: it has
+// a host buffer, and either runs on the legacy default stream (NULL) or one of its host
+// buffers is pageable.  With a stream given and only page-locked host buffers the call
+// leaves its copies enqueued (the caller synchronises before reading).
+bool host_sync_needed(cudaStream_t stream, std::initializer_list<MemKind> kinds);
 
 // Stream-ordered workspace of a call, from the library's memory pool on the current
 // device.  The pool keeps up to 4 GiB of freed workspace mapped between calls (the

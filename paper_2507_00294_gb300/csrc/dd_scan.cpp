@@ -52,12 +52,27 @@ bool unregister_scan(dd_scan *s) {
 }
 
 bool is_device_pointer(const void *p) {
+    return memory_kind(p) == MemKind::Device;
+}
+
+MemKind memory_kind(const void *p) {
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
         cudaGetLastError();   // unregistered host memory on old runtimes
-        return false;
+        return MemKind::Pageable;
     }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) return MemKind::Device;
+    return attr.type == cudaMemoryTypeHost ? MemKind::Pinned : MemKind::Pageable;
+}
+
+bool host_sync_needed(cudaStream_t stream, std::initializer_list<MemKind> kinds) {
+    bool any_host = false, all_pinned = true;
+    for (MemKind k : kinds) {
+        if (k == MemKind::Device) continue;
+        any_host = true;
+        all_pinned = all_pinned && k == MemKind::Pinned;
+    }
+    return any_host && (stream == nullptr || !all_pinned);
 }
 
 cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t stream) {

@@ -112,6 +112,32 @@ def test_pinned_host_buffers_in_place(cuda):
     np.testing.assert_array_equal(pin_dose.numpy(), d_dev.cpu().numpy())
 
 
+def test_pinned_host_buffers_on_a_stream(cuda):
+    """With a stream and page-locked host buffers the field's and the dose's copies stay
+    enqueued: after one synchronisation of that stream both outputs equal the
+    device-buffer results bit for bit (also for a second scan whose visit list is uploaded
+    on the same stream)."""
+    import torch
+    job = w.raster_64_supersampled()
+    pts = job.pts_xy[:9001]
+    times = job.times[::7]
+    st = torch.cuda.Stream()
+    for spec in (job.scan, w.ScanSpec(20, 20, order=w.SERPENTINE)):
+        scan = b.Scan(spec)
+        pin_pts = torch.from_numpy(np.ascontiguousarray(pts)).pin_memory()
+        pin_out = torch.full((len(times), len(pts)), -1.0, dtype=torch.float64).pin_memory()
+        pin_dose = torch.full((w.n_visits(spec),), -1.0, dtype=torch.float64).pin_memory()
+        b.dd_field_at_times(scan, pin_pts.numpy(), times, "mixed", out=pin_out.numpy(), stream=st)
+        b.dd_per_probe_dose(scan, "mixed", out=pin_dose.numpy(), stream=st)
+        st.synchronize()
+        dev = b.dd_field_at_times(scan, torch.from_numpy(np.ascontiguousarray(pts)).cuda(), times, "mixed")
+        d_dev = b.dd_per_probe_dose(scan, "mixed", device=torch.device("cuda", 0))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(pin_out.numpy(), dev.cpu().numpy())
+        np.testing.assert_array_equal(pin_dose.numpy(), d_dev.cpu().numpy())
+        scan.close()
+
+
 def test_deterministic_repeat(cuda):
     job = w.raster_64_supersampled()
     a = gpu_field(job.scan, job.pts_xy, job.times[-4:], "mixed")
