@@ -116,6 +116,14 @@ struct CallStaging {
         blocks.push_back(b);
         return cudaMemcpyAsync(dst, b.p, n, cudaMemcpyHostToDevice, stream);
     }
+    // A pinned block of n bytes, kept with the others, for the caller to fill in place and
+    // copy from (one pass over the data instead of two); nullptr when none can be had.
+    void *stage(size_t n) {
+        PinnedBlock b = pinned_take(n);
+        if (!b.p) return nullptr;
+        blocks.push_back(b);
+        return b.p;
+    }
 };
 
 // Keeps a call's host tables (and the pinned blocks their uploads came from) alive until

@@ -202,13 +202,27 @@ const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status
             return c.src;
         }
     const size_t n = (size_t)scan->n;
-    // 4n doubles, then n float4 of float-float coordinates (16-byte aligned: 32n bytes in)
-    std::vector<double> host(4 * n + 2 * n);
-    std::memcpy(host.data(), scan->X.data(), n * sizeof(double));
-    std::memcpy(host.data() + n, scan->Y.data(), n * sizeof(double));
-    std::memcpy(host.data() + 2 * n, scan->T.data(), n * sizeof(double));
-    std::memcpy(host.data() + 3 * n, scan->TAU.data(), n * sizeof(double));
-    float *ff = reinterpret_cast<float *>(host.data() + 4 * n);
+    // 4n doubles, then n float4 of float-float coordinates (16-byte aligned: 32n bytes in),
+    // written straight into a pinned staging block (a pageable vector when none is free)
+    const size_t bytes = 6 * n * sizeof(double);
+    void *d = nullptr;
+    err = workspace_alloc(&d, bytes, stream);
+    if (err != cudaSuccess) { *st = fail_cuda(err, "scan visit cache allocation"); cudaGetLastError(); return nullptr; }
+    cudaEvent_t ready = nullptr;
+    err = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (err != cudaSuccess) { cudaFreeAsync(d, stream); *st = fail_cuda(err, "cudaEventCreate"); return nullptr; }
+    auto *stage = new CallStaging();
+    std::vector<double> pageable;
+    double *host = static_cast<double *>(stage->stage(bytes));
+    if (!host) {
+        pageable.resize(6 * n);
+        host = pageable.data();
+    }
+    std::memcpy(host, scan->X.data(), n * sizeof(double));
+    std::memcpy(host + n, scan->Y.data(), n * sizeof(double));
+    std::memcpy(host + 2 * n, scan->T.data(), n * sizeof(double));
+    std::memcpy(host + 3 * n, scan->TAU.data(), n * sizeof(double));
+    float *ff = reinterpret_cast<float *>(host + 4 * n);
     for (size_t i = 0; i < n; ++i) {
         const float xh = (float)scan->X[i], yh = (float)scan->Y[i];
         ff[4 * i] = xh;
@@ -216,17 +230,8 @@ const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status
         ff[4 * i + 2] = yh;
         ff[4 * i + 3] = (float)(scan->Y[i] - (double)yh);
     }
-    const size_t bytes = host.size() * sizeof(double);
-    void *d = nullptr;
-    err = workspace_alloc(&d, bytes, stream);
-    if (err != cudaSuccess) { *st = fail_cuda(err, "scan visit cache allocation"); cudaGetLastError(); return nullptr; }
-    cudaEvent_t ready = nullptr;
-    err = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    if (err != cudaSuccess) { cudaFreeAsync(d, stream); *st = fail_cuda(err, "cudaEventCreate"); return nullptr; }
-    // upload through pinned staging, released once the copy has completed
-    auto *stage = new CallStaging();
-    err = stage->upload(d, host.data(), bytes, stream);
-    if (err == cudaSuccess && stage->blocks.empty()) err = cudaStreamSynchronize(stream);  // pageable source
+    err = cudaMemcpyAsync(d, host, bytes, cudaMemcpyHostToDevice, stream);
+    if (err == cudaSuccess && !pageable.empty()) err = cudaStreamSynchronize(stream);  // pageable source
     if (err == cudaSuccess) err = cudaEventRecord(ready, stream);
     if (err != cudaSuccess) {
         cudaStreamSynchronize(stream);
