@@ -200,8 +200,7 @@ __global__ void lag_coef_kernel(int64_t n, double s, double kappa, Rec *__restri
 // Snapshot t_j (an integer number of dwells) then reads visit i's record at
 // rev[M - t_j + i], contiguous in i.
 template <typename Rec>
-__global__ void rev_lag_coef_kernel(int64_t M, double s, double kappa, Rec *__restrict__ rev) {
-    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void rev_lag_record(int64_t u, int64_t M, double s, double kappa, Rec *__restrict__ rev) {
     if (u > M) return;
     const int64_t L = M - u;
     if (L == 0) { rev[u] = RecTraits<Rec>::zero(); return; }

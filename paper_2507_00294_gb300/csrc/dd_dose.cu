@@ -179,19 +179,19 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
                     else t = pair_term(r2[q], R);
                     if (ok[q]) { if (q & 1) acc2[q >> 1].y += t; else acc2[q >> 1].x += t; }
                 }
-                continue;
-            }
+            } else {
 #pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                const int64_t i = jt[q] - k;
-                if (i >= 0 && jt[q] < n) {
-                    const Real dx = px[q] - s_x[i - w0], dy = py[q] - s_y[i - w0];
-                    acc[q] += pair_term(dx * dx + dy * dy, R);
+                for (int q = 0; q < PPT; ++q) {
+                    const int64_t i = jt[q] - k;
+                    if (i >= 0 && jt[q] < n) {
+                        const Real dx = px[q] - s_x[i - w0], dy = py[q] - s_y[i - w0];
+                        acc[q] += pair_term(dx * dx + dy * dy, R);
+                    }
                 }
-            }
-            if (Cfg::kFlush < Cfg::kDoseSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
+                if (Cfg::kFlush < Cfg::kDoseSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) { tot[q].add(acc[q]); acc[q] = 0; }
+                    for (int q = 0; q < PPT; ++q) { tot[q].add(acc[q]); acc[q] = 0; }
+                }
             }
         }
 #pragma unroll

@@ -5,7 +5,8 @@
 //   (beam off, Eq. 2), in units of the pitch and the reference dwell (dd_internal.h).
 //
 // Pipeline of one dd_field_at_times call (all on the caller's stream):
-//   1. points SI -> pitch units (prep_points_kernel);
+//   1. points SI -> pitch units (prep_points_kernel; with the lag table of step 2 in one
+//      launch, prep_points_lag_kernel, when the snapshots lie on the dwell lattice);
 //   2. per (snapshot, visit) FP64 coefficients: q1 = 1/w1, dq = 1/w0 - 1/w1 and the
 //      moment coefficients c_0..c_M of dd_e1.cuh (coef_kernel);
 //   3. work items (point tile, snapshot chunk, visit block), sorted by cost, one CTA
@@ -31,15 +32,31 @@ namespace ddk {
 
 // Points in pitch units: FP64 X, Y, and float-float (x_hi, x_lo, y_hi, y_lo) for the FP32
 // tile, so that the FP32 kernels form coordinate differences without FP64 arithmetic.
-__global__ void prep_points_kernel(const double *__restrict__ xy, int64_t n, double inv_p,
-                                   double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void prep_point(int64_t k, const double *__restrict__ xy, int64_t n, double inv_p,
+                                           double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
     if (k >= n) return;
     const double x = xy[2 * k] * inv_p, y = xy[2 * k + 1] * inv_p;
     X[k] = x;
     Y[k] = y;
     const float xh = (float)x, yh = (float)y;
     F[k] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
+}
+__global__ void prep_points_kernel(const double *__restrict__ xy, int64_t n, double inv_p,
+                                   double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
+    prep_point((int64_t)blockIdx.x * blockDim.x + threadIdx.x, xy, n, inv_p, X, Y, F);
+}
+
+// The reversed lag table (blocks [0, nb_lag), one record per thread: a long serial chain,
+// so these blocks go first) and the points in pitch units (the blocks after) in one
+// launch: the field's two preparation steps cost one launch instead of two.
+template <typename Rec>
+__global__ void prep_points_lag_kernel(int nb_lag, int64_t M, double s, double kappa, Rec *__restrict__ rev,
+                                       const double *__restrict__ xy, int64_t n, double inv_p,
+                                       double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
+    if ((int)blockIdx.x < nb_lag)
+        rev_lag_record<Rec>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, M, s, kappa, rev);
+    else
+        prep_point((int64_t)(blockIdx.x - nb_lag) * blockDim.x + threadIdx.x, xy, n, inv_p, X, Y, F);
 }
 
 // out[row[j] * n_pts + p] = pref * sum_{k < nblk[chunk(j)]} partial[(k * n_tg + j) * n_pts + p]
@@ -111,8 +128,6 @@ template <typename Cfg>
 size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out_host, bool pts_host,
                        int n_t, int64_t n_rec) {
     using Rec = typename Cfg::Rec;
-    const int tile = Cfg::kThreads * Cfg::kPPT;
-    const int64_t n_tiles = (n_pts + tile - 1) / tile;
     const int nblk_max = (int)((n_src + sb - 1) / sb);
     const int n_chunks = (group + Cfg::kTCH - 1) / Cfg::kTCH;
     size_t b = 0;
@@ -273,18 +288,23 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     const int64_t pstride = (n_pts + 3) / 4 * 4;            // 16-byte aligned partial rows
     Part *d_part = cv.take<Part>((size_t)nblk_max * group * pstride);
 
-    DD_PROFILED("prep_points", stream,
-                (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y, PF)));
-    DD_CUDA_TRY(cudaGetLastError());
+    if (!lattice) {
+        DD_PROFILED("prep_points", stream,
+                    (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y, PF)));
+        DD_CUDA_TRY(cudaGetLastError());
+    }
 
     const double *srcX = src, *srcY = src + n_src, *srcT = src + 2 * n_src, *srcTAU = src + 3 * n_src;
     // host staging for the per-group tables, released by a host callback once the
     // stream has consumed them (the copies below may read pageable memory late)
     HostTables *keep = new HostTables();
     if (lattice) {
+        // the lag table and the points in one launch of 32-thread blocks
+        const int nb_lag = (int)((M + 1 + 31) / 32);
+        const int64_t nb_pts = (n_pts + 31) / 32;
         DD_PROFILED(Cfg::kCoefName, stream,
-                    (ddk::rev_lag_coef_kernel<Rec><<<(unsigned)((M + 1 + 31) / 32), 32, 0, stream>>>(
-                        M, scan->s, scan->kappa, d_rec)));
+                    (ddk::prep_points_lag_kernel<Rec><<<(unsigned)(nb_lag + nb_pts), 32, 0, stream>>>(
+                        nb_lag, M, scan->s, scan->kappa, d_rec, pts_dev, n_pts, 1.0 / scan->pitch, X, Y, PF)));
         DD_CUDA_TRY(cudaGetLastError());
     }
     for (int g0 = 0; g0 < n_t; g0 += group) {
