@@ -198,17 +198,6 @@ __device__ __forceinline__ void moment_pass(float2 (&acc)[PPT], const float (&r2
     }
 }
 
-// One snapshot at PPT points into point-pair accumulators: acc[k / 2].x (k even) or .y
-// (k odd) += term of point k.
-template <int D, int PPT>
-__device__ __forceinline__ void point_pass(float2 (&acc)[PPT], const float (&r2)[PPT], const RecF32 &R) {
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const float t = log_term<D>(r2[k], R);
-        if (k & 1) acc[k >> 1].y += t; else acc[k >> 1].x += t;
-    }
-}
-
 // One snapshot at PPT points, the h form of degree D (8, 12) on f32x2 instructions over
 // point pairs: acc[m] += (2^G(r_2m), 2^G(r_2m+1)), each half rounded as log_exponent<D>
 // rounds it.
