@@ -232,3 +232,25 @@ def test_million_points_ragged(cuda):
     ref = oracle_pairs(spec, pts, times, ip, it)
     got = gpu_field(spec, pts, times, "mixed")[it, ip]
     assert_mixed(got, ref, peak_lower_bound(spec, times)[it], "1M points mixed")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_series_class_limits_swept(cuda, prec):
+    """One visit seen at the end of its dwell (h = r a with r = 12 at the default physics)
+    and half a dwell later: 6,001 points along a line whose h = rho^2 dq sweeps 0 .. 3.5
+    in steps of 5.8e-4, so that each warp's 32 neighbouring points put its largest h just
+    below (or above) every series-class limit; every point against the oracle."""
+    spec = w.ScanSpec(1, 1)
+    tau, p = spec.dwell_s, spec.pitch_m
+    s, kappa = spec.sigma_m ** 2 / p ** 2, spec.D_m2s * tau / p ** 2
+    dq = 1.0 / (2 * s) - 1.0 / (2 * s + 4 * kappa)          # at t = tau (Eq. 1, R3)
+    h = np.linspace(0.0, 3.5, 6001)
+    x = p * np.sqrt(h / dq)
+    pts = np.column_stack([x, np.zeros_like(x)])
+    times = np.array([tau, 1.5 * tau])
+    ref = oracle_field(spec, pts, times)
+    got = gpu_field(spec, pts, times, prec)
+    if prec == "fp64":
+        assert_fp64(got, ref, "class limits fp64")
+    else:
+        assert_mixed(got, ref, ref.max(axis=1), "class limits mixed")
