@@ -207,7 +207,8 @@ const char *dd_last_error(void);
 
    dd_sur_conv3x3: 3x3 convolution with dilation d in 1..32 (tap (ky, kx) reads the input
    at (y + (ky-1) d, x + (kx-1) d)), zero "same" padding, implicit GEMM on the tensor
-   cores (BF16 x BF16 -> FP32).  epilogue 0: out = bf16(relu(z + bias)) [B,H,W,cout];
+   cores (BF16 x BF16 -> FP32; tcgen05.mma with the accumulator in tensor memory when W
+   is a multiple of 128, mma.sync otherwise).  epilogue 0: out = bf16(relu(z + bias)) [B,H,W,cout];
    1: out = float(z + bias) of channel 0 only [B,H,W]; 2: out = bf16(z * (mask > 0))
    with mask [B,H,W,cout] (the data gradient through a ReLU, using the flipped weights
    that dd_sur_adam writes; bias unused).
@@ -227,7 +228,10 @@ const char *dd_last_error(void);
    per-map scale[] = 4 pi D / Q0 (the dimensionless field).
    dd_sur_fields: psi [n_maps*hw] (u/m^2, FP64) = 10^(pred*sigma + mu) / scale[map].
    dd_sur_spot_error: err[m] = relative L2 error over k spot points of map m between the
-   field of pred [n_maps][hw] and exact [n_maps][k] (u/m^2) at canvas indices idx [n_maps][k]. */
+   field of pred [n_maps][hw] and exact [n_maps][k] (u/m^2) at canvas indices idx [n_maps][k].
+   dd_sur_check: synchronises the device and returns DD_ETIMEOUT (clearing the flag) if a
+   tensor-memory convolution since the last check gave up waiting for its MMAs (an
+   iteration-limited wait; its output is then not written), DD_OK otherwise. */
 dd_status dd_sur_conv3x3(const void *in, const void *w, const float *bias, const void *mask, void *out,
                          int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout, int32_t dilation,
                          int32_t epilogue, void *cuda_stream);
@@ -248,6 +252,7 @@ dd_status dd_sur_fields(const float *pred, const double *scale, int64_t n_maps, 
 dd_status dd_sur_spot_error(const float *pred, const int32_t *idx, const double *exact,
                             const double *scale, int32_t n_maps, int32_t hw, int32_t k, float mu,
                             float sigma, double *err, void *cuda_stream);
+dd_status dd_sur_check(void);
 
 /* Tracing (no counterpart in the paper): per-kernel device time of this library's
    own launches.  While enabled, each launch is bracketed by two CUDA events on its

@@ -136,6 +136,182 @@ conv3x3_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const fl
     }
 }
 
+// ---- the forward / data-gradient convolution on the 5th-generation tensor cores ------
+//
+// One CTA computes M = 128 pixels (one image row segment) x N = Cout with tcgen05.mma
+// (kind::f16, BF16 operands, FP32 accumulator in tensor memory): 9 taps x Cin/16 MMAs of
+// K = 16, issued by one thread; the accumulator is read back with tcgen05.ld (warp w reads
+// TMEM lanes 32w..32w+31, i.e. its 32 pixels) for the epilogue.  Operands are staged in
+// the canonical K-major layout without swizzle: "core matrices" of 8 rows x 16 bytes.
+//   input  [ky][c8][px][8]: pixel rows 16 bytes apart, so the 128 pixels of any tap
+//          (shifted by kx*dil columns) form 16 core matrices 128 bytes apart (SBO), and
+//          the next 8 channels sit one channel-group plane further (LBO = cols*16 bytes);
+//   weight [tap][c8][co][8]: SBO 128 bytes (next 8 outputs), LBO Cout*16 bytes.
+constexpr int kTW5 = 128;
+static __device__ int g_tc_timeout;       // set when an MMA completion wait gives up
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);           // start address, 16-byte units
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;              // leading (K) byte offset
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;              // stride (M/N) byte offset
+    d |= (uint64_t)1 << 46;                                     // descriptor version of sm_100
+    return d;                                                   // base offset 0, no swizzle
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+// 32 lanes x N consecutive 32-bit columns: register j of lane i = column j of TMEM lane
+// (warp quarter base + i)
+template <int N>
+__device__ __forceinline__ void tmem_ld_32x32b(uint32_t taddr, uint32_t (&v)[N]);
+template <>
+__device__ __forceinline__ void tmem_ld_32x32b<16>(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                 "%12, %13, %14, %15}, [%16];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr));
+}
+template <>
+__device__ __forceinline__ void tmem_ld_32x32b<32>(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                 "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+                 "%30, %31}, [%32];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+}
+
+template <int CI, int CO, int EPI>
+__global__ void __launch_bounds__(128)
+conv3x3_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const float *__restrict__ bias,
+                  const bf16 *__restrict__ mask, void *__restrict__ out, int H, int W, int dil) {
+    constexpr int C8 = CI / 8;
+    static_assert(CI % 16 == 0 && (CO == 16 || CO == 32), "K steps of 16; 16 or 32 accumulator columns");
+    // dynamic shared memory: weights [9][C8][CO][8], input [3][C8][cols][8], mbarrier, TMEM address
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bf16 *s_w = reinterpret_cast<bf16 *>(smem_raw);
+    bf16 *s_in = s_w + 9 * C8 * CO * 8;
+    const int cols = kTW5 + 2 * dil;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(s_in + 3 * C8 * cols * 8);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(s_bar + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_per_row = W / kTW5;
+    const int x0 = (blockIdx.x % tiles_per_row) * kTW5;
+    const int row = blockIdx.x / tiles_per_row;          // b * H + y
+    const int y = row % H;
+    const int64_t img0 = (int64_t)(row - y) * W;         // first pixel of image b
+
+    for (int v = tid; v < CO * 9 * C8; v += 128) {
+        const int co = v / (9 * C8), r = v - co * (9 * C8);      // r = tap * C8 + c8
+        *reinterpret_cast<uint4 *>(s_w + ((size_t)r * CO + co) * 8) =
+            *reinterpret_cast<const uint4 *>(w + (int64_t)co * 9 * CI + r * 8);
+    }
+    // staged column px holds input column x0 - dil + px (zero outside the image)
+    for (int v = tid; v < 3 * cols * C8; v += 128) {
+        const int ky = v / (cols * C8);
+        const int rem = v - ky * cols * C8;
+        const int c8 = rem / cols, px = rem - c8 * cols;
+        const int yy = y + (ky - 1) * dil, xx = x0 + px - dil;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            val = *reinterpret_cast<const uint4 *>(in + (img0 + (int64_t)yy * W + xx) * CI + c8 * 8);
+        *reinterpret_cast<uint4 *>(s_in + ((size_t)(ky * C8 + c8) * cols + px) * 8) = val;
+    }
+    // the staged operands are read by the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" :: "r"(smem_u32(s_tmem)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(s_bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+
+    if (tid == 0) {
+        constexpr uint32_t idesc = umma_idesc_bf16(kTW5, CO);
+        int accumulate = 0;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+            for (int c0 = 0; c0 < CI; c0 += 16) {
+                const uint32_t a = smem_u32(s_in + ((size_t)(ky * C8 + c0 / 8) * cols + kx * dil) * 8);
+                const uint32_t bb = smem_u32(s_w + ((size_t)(tap * C8 + c0 / 8) * CO) * 8);
+                umma_bf16(tmem, umma_smem_desc(a, (uint32_t)cols * 16u, 128u), umma_smem_desc(bb, CO * 16u, 128u), idesc,
+                          accumulate);
+                accumulate = 1;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(s_bar)) : "memory");
+    }
+    // wait for the MMAs (phase 0 of the barrier), with an iteration limit
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 18) && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(smem_u32(s_bar)) : "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done) {
+        uint32_t v[CO];
+        tmem_ld_32x32b<CO>(tmem + ((uint32_t)(32 * warp) << 16), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int64_t pix = img0 + (int64_t)y * W + x0 + 32 * warp + lane;
+        if (EPI == kEpiLinearF32) {
+            static_cast<float *>(out)[pix] = __uint_as_float(v[0]) + bias[0];
+        } else {
+            uint4 o[CO / 8];
+            uint4 mk[CO / 8];
+            if (EPI == kEpiMaskBf16) {
+#pragma unroll
+                for (int q = 0; q < CO / 8; ++q) mk[q] = reinterpret_cast<const uint4 *>(mask + pix * CO)[q];
+            }
+#pragma unroll
+            for (int q = 0; q < CO / 8; ++q) {
+                uint32_t packed[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int ch = 8 * q + 2 * e;
+                    float v0 = __uint_as_float(v[ch]), v1 = __uint_as_float(v[ch + 1]);
+                    if (EPI == kEpiReluBf16) {
+                        v0 = fmaxf(v0 + bias[ch], 0.f);
+                        v1 = fmaxf(v1 + bias[ch + 1], 0.f);
+                    } else {
+                        const uint32_t mw = e == 0 ? mk[q].x : e == 1 ? mk[q].y : e == 2 ? mk[q].z : mk[q].w;
+                        const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw);
+                        v0 = __bfloat162float(m2.x) > 0.f ? v0 : 0.f;
+                        v1 = __bfloat162float(m2.y) > 0.f ? v1 : 0.f;
+                    }
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                    packed[e] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                o[q] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            }
+#pragma unroll
+            for (int q = 0; q < CO / 8; ++q) reinterpret_cast<uint4 *>(static_cast<bf16 *>(out) + pix * CO)[q] = o[q];
+        }
+    } else if (lane == 0) {
+        atomicExch(&g_tc_timeout, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" :: "r"(tmem) : "memory");
+}
+
 // Weight gradient partials: CTA c sums rows [c*rows, (c+1)*rows) of the B*H image rows.
 //   part[c][co*9*CI + tap*CI + ci] = sum_p dz[p][co] * x[p + offset(tap)][ci]
 //   part[c][CO*9*CI + co]          = sum_p dz[p][co]
@@ -385,6 +561,26 @@ cudaError_t launch_conv(const void *in, const void *w, const float *bias, const 
     return cudaGetLastError();
 }
 
+// The tensor-memory variant: one CTA per 128-pixel row segment (W a multiple of 128).
+template <int CI, int CO, int EPI>
+cudaError_t launch_conv_tc(const void *in, const void *w, const float *bias, const void *mask, void *out, int B,
+                           int H, int W, int dil, cudaStream_t st) {
+    auto bytes = [](int d) {
+        return sizeof(ddk::bf16) * ((size_t)9 * CI * CO + (size_t)3 * CI * (ddk::kTW5 + 2 * d)) + 16;
+    };
+    static bool configured = false;     // allow the largest dilation's staging area once
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(ddk::conv3x3_tc_kernel<CI, CO, EPI>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(ddk::kMaxDil));
+        if (err != cudaSuccess) return err;
+        configured = true;
+    }
+    const unsigned grid = (unsigned)(B * H * (W / ddk::kTW5));
+    ddk::conv3x3_tc_kernel<CI, CO, EPI><<<grid, 128, bytes(dil), st>>>((const ddk::bf16 *)in, (const ddk::bf16 *)w, bias,
+                                                                        (const ddk::bf16 *)mask, out, H, W, dil);
+    return cudaGetLastError();
+}
+
 bool conv_shape_ok(int cin, int cout) {
     return (cin == 16 && cout == 32) || (cin == 32 && cout == 32) || (cin == 32 && cout == 16) ||
            (cin == 16 && cout == 16);
@@ -408,11 +604,19 @@ dd_status dd_sur_conv3x3(const void *in, const void *w, const float *bias, const
     const char *name = epilogue == 2 ? "conv3x3_dgrad" : "conv3x3_fwd";
     dd::ProfScope ps(name, st);
     cudaError_t err = cudaSuccess;
+    // rows of 128 pixels: one tcgen05 MMA tile per CTA; otherwise 64-pixel tiles on mma.sync
+    const bool tc = W % ddk::kTW5 == 0;
 #define DD_CONV(CI, CO)                                                                                   \
     if (cin == CI && cout == CO) {                                                                        \
-        if (epilogue == 0) err = launch_conv<CI, CO, ddk::kEpiReluBf16>(in, w, bias, mask, out, B, H, W, dilation, st);  \
-        else if (epilogue == 1) err = launch_conv<CI, CO, ddk::kEpiLinearF32>(in, w, bias, mask, out, B, H, W, dilation, st); \
-        else err = launch_conv<CI, CO, ddk::kEpiMaskBf16>(in, w, bias, mask, out, B, H, W, dilation, st);  \
+        if (tc) {                                                                                         \
+            if (epilogue == 0) err = launch_conv_tc<CI, CO, ddk::kEpiReluBf16>(in, w, bias, mask, out, B, H, W, dilation, st);  \
+            else if (epilogue == 1) err = launch_conv_tc<CI, CO, ddk::kEpiLinearF32>(in, w, bias, mask, out, B, H, W, dilation, st); \
+            else err = launch_conv_tc<CI, CO, ddk::kEpiMaskBf16>(in, w, bias, mask, out, B, H, W, dilation, st);  \
+        } else {                                                                                          \
+            if (epilogue == 0) err = launch_conv<CI, CO, ddk::kEpiReluBf16>(in, w, bias, mask, out, B, H, W, dilation, st);  \
+            else if (epilogue == 1) err = launch_conv<CI, CO, ddk::kEpiLinearF32>(in, w, bias, mask, out, B, H, W, dilation, st); \
+            else err = launch_conv<CI, CO, ddk::kEpiMaskBf16>(in, w, bias, mask, out, B, H, W, dilation, st);  \
+        }                                                                                                 \
     }
     DD_CONV(16, 32)
     DD_CONV(32, 32)
@@ -421,6 +625,17 @@ dd_status dd_sur_conv3x3(const void *in, const void *w, const float *bias, const
 #undef DD_CONV
     if (err != cudaSuccess) return dd::fail_cuda(err, "dd_sur_conv3x3 launch");
     return DD_OK;
+}
+
+dd_status dd_sur_check(void) {
+    dd::clear_error();
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    int flag = 0;
+    DD_CUDA_TRY(cudaMemcpyFromSymbol(&flag, ddk::g_tc_timeout, sizeof(int)));
+    if (!flag) return DD_OK;
+    const int zero = 0;
+    DD_CUDA_TRY(cudaMemcpyToSymbol(ddk::g_tc_timeout, &zero, sizeof(int)));
+    return dd::fail(DD_ETIMEOUT, "dd_sur_check: a tensor-core convolution gave up waiting for its MMAs");
 }
 
 dd_status dd_sur_wgrad(const void *x, const void *dz, int32_t B, int32_t H, int32_t W, int32_t cin, int32_t cout,

@@ -40,6 +40,7 @@ def test_conv_forward(cuda, ci, co, dil):
     np.testing.assert_allclose(r64(out), relu, rtol=8e-3, atol=1e-3 * np.abs(ref).max())
     lin = torch.empty((2, 40, 128), dtype=torch.float32, device=cuda)
     b.dd_sur_conv3x3(x, wt, bias, None, lin, 1, dil)
+    b.dd_sur_check()                 # no tensor-memory convolution gave up waiting
     np.testing.assert_allclose(r64(lin), ref[..., 0], rtol=1e-4, atol=1e-5 * np.abs(ref).max())
 
 
@@ -52,8 +53,23 @@ def test_conv_data_gradient(cuda, ci, co, dil):
     wfl = bf(flip(r64(bf(wt)))).to(cuda)
     out = torch.empty((2, 36, 128, ci), dtype=torch.bfloat16, device=cuda)
     b.dd_sur_conv3x3(dz, wfl, None, a, out, 2, dil)
+    b.dd_sur_check()
     ref = conv_ref.conv3x3_dgrad(r64(dz), r64(bf(wt)).reshape(co, 3, 3, ci), dil) * (r64(a) > 0)
     np.testing.assert_allclose(r64(out), ref, rtol=8e-3, atol=1e-3 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("ci,co,dil", [(32, 32, 2), (16, 16, 32)])
+def test_conv_forward_64_pixel_tiles(cuda, ci, co, dil):
+    """Rows that are not a multiple of 128 pixels (W = 192) take the 64-pixel mma.sync
+    tiles instead of the 128-pixel tensor-memory tile: same results."""
+    rng = np.random.default_rng(31 + ci + co + dil)
+    x = bf(rng.standard_normal((1, 24, 192, ci))).to(cuda)
+    wt = bf(rng.standard_normal((co, 9, ci)) * 0.2).to(cuda)
+    bias = torch.from_numpy(rng.standard_normal(co).astype(np.float32)).to(cuda)
+    ref = conv_ref.conv3x3(r64(x), r64(wt).reshape(co, 3, 3, ci), bias.double().cpu().numpy(), dil)
+    out = torch.empty((1, 24, 192, co), dtype=torch.bfloat16, device=cuda)
+    b.dd_sur_conv3x3(x, wt, bias, None, out, 0, dil)
+    np.testing.assert_allclose(r64(out), np.maximum(ref, 0), rtol=8e-3, atol=1e-3 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("ci,co,dil", [(16, 32, 1), (32, 32, 1), (32, 16, 1), (32, 32, 16), (16, 32, 32)])
