@@ -340,7 +340,7 @@ def bench_surrogate(dev, maps, epochs):
             "fallback_fraction": float(np.mean(fell)), "max_rel_err_after_fallback": float(err_after.max()),
             "train_maps": n_train, "test_maps": n_test, "epochs": epochs, "final_train_loss": losses[-1],
             "seconds": {"dataset": t_data, "train": t_train},
-            "net": "6 x conv3x3 (4->32->32->32->32->32->1, padded 16/32/16), BF16 mma.sync, FP32 accum, Adam",
+            "net": "6 x conv3x3 (4->32->32->32->32->32->1, padded 16/32/16), BF16 tcgen05.mma (forward, data gradient) and mma.sync (weight gradient), FP32 accum, Adam",
             "error": "relative L2 of the linear field over the 128x128 canvas; fallback above 1e-2 "
                      "(estimated from 64 exact spot points per map)"}
 

@@ -1,6 +1,7 @@
 // dd_surrogate.cu -- kernels of the learned surrogate of the field map (no counterpart
 // in the paper): six 3x3 convolutions, NHWC BF16 activations, FP32 accumulation on the
-// tensor cores (mma.sync m16n8k16 BF16), FP32 master weights with Adam.
+// tensor cores (tcgen05.mma with TMEM accumulators for rows of 128 pixels, mma.sync
+// m16n8k16 for other rows and the weight gradient), FP32 master weights with Adam.
 //
 // Layers: 16 -> 32 -> 32 -> 32 -> 32 -> 32 -> 16 channels (the first layer's input has 4
 // real planes padded to 16, the last layer's output 1 real channel padded to 16), ReLU
@@ -11,6 +12,7 @@
 // (split over CTAs by image rows, partials reduced in a fixed order).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "dd_internal.h"
@@ -138,12 +140,12 @@ conv3x3_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const fl
 
 // ---- the forward / data-gradient convolution on the 5th-generation tensor cores ------
 //
-// One CTA computes M = 128 pixels (one image row segment) x N = Cout with tcgen05.mma
-// (kind::f16, BF16 operands, FP32 accumulator in tensor memory): 9 taps x Cin/16 MMAs of
-// K = 16, issued by one thread; the accumulator is read back with tcgen05.ld (warp w reads
-// TMEM lanes 32w..32w+31, i.e. its 32 pixels) for the epilogue.  Operands are staged in
-// the canonical K-major layout without swizzle: "core matrices" of 8 rows x 16 bytes.
-//   input  [ky][c8][px][8]: pixel rows 16 bytes apart, so the 128 pixels of any tap
+// An output row tile is M = 128 pixels x N = Cout, computed with tcgen05.mma (kind::f16,
+// BF16 operands, FP32 accumulator in tensor memory): 9 taps x Cin/16 MMAs of K = 16,
+// issued by one thread; the accumulator is read back with tcgen05.ld (warp w reads TMEM
+// lanes 32w..32w+31, i.e. its 32 pixels) for the epilogue.  Operands are staged in the
+// canonical K-major layout without swizzle: "core matrices" of 8 rows x 16 bytes.
+//   input row [c8][px][8]: pixel rows 16 bytes apart, so the 128 pixels of any tap
 //          (shifted by kx*dil columns) form 16 core matrices 128 bytes apart (SBO), and
 //          the next 8 channels sit one channel-group plane further (LBO = cols*16 bytes);
 //   weight [tap][c8][co][8]: SBO 128 bytes (next 8 outputs), LBO Cout*16 bytes.
@@ -191,50 +193,101 @@ __device__ __forceinline__ void tmem_ld_32x32b<32>(uint32_t taddr, uint32_t (&v)
                  : "r"(taddr));
 }
 
+// 16-byte global -> shared copy that completes asynchronously; src_bytes 0 writes zeros.
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+
+// Persistent CTAs: each stages the weights once and allocates two TMEM accumulators once,
+// then walks work items.  An item is a segment of kSeg output rows of one 128-pixel column
+// strip, taken with stride dil (rows y0, y0 + dil, ...), so that consecutive rows share two
+// of their three input rows: input rows live in a ring of four slots [C8][cols][8], and
+// each output row copies in (cp.async) only the row its successor needs while its own
+// MMAs run; the MMAs of the next row are issued once this row's epilogue has read the
+// other accumulator.
+constexpr int kSeg = 8;
 template <int CI, int CO, int EPI>
 __global__ void __launch_bounds__(128)
 conv3x3_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const float *__restrict__ bias,
-                  const bf16 *__restrict__ mask, void *__restrict__ out, int H, int W, int dil) {
+                  const bf16 *__restrict__ mask, void *__restrict__ out, int H, int W, int dil, int items_per_strip,
+                  int n_items) {
     constexpr int C8 = CI / 8;
     static_assert(CI % 16 == 0 && (CO == 16 || CO == 32), "K steps of 16; 16 or 32 accumulator columns");
-    // dynamic shared memory: weights [9][C8][CO][8], input [3][C8][cols][8], mbarrier, TMEM address
+    // dynamic shared memory: weights [9][C8][CO][8], the ring of 4 input rows
+    // [slot][C8][cols][8], two mbarriers, the TMEM address
     extern __shared__ __align__(16) unsigned char smem_raw[];
     bf16 *s_w = reinterpret_cast<bf16 *>(smem_raw);
-    bf16 *s_in = s_w + 9 * C8 * CO * 8;
     const int cols = kTW5 + 2 * dil;
-    uint64_t *s_bar = reinterpret_cast<uint64_t *>(s_in + 3 * C8 * cols * 8);
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(s_bar + 1);
+    const int slot_elems = C8 * cols * 8;
+    bf16 *s_ring = s_w + 9 * C8 * CO * 8;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(s_ring + 4 * slot_elems);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(s_bar + 2);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tiles_per_row = W / kTW5;
-    const int x0 = (blockIdx.x % tiles_per_row) * kTW5;
-    const int row = blockIdx.x / tiles_per_row;          // b * H + y
-    const int y = row % H;
-    const int64_t img0 = (int64_t)(row - y) * W;         // first pixel of image b
+
+    // input row yy (zeros outside the image) of image img0, columns x0 - dil .., into slot
+    auto stage_row = [&](int64_t img0, int x0, int yy, int slot) {
+        bf16 *dst = s_ring + slot * slot_elems;
+        const bool row_in = yy >= 0 && yy < H;
+        for (int v = tid; v < cols * C8; v += 128) {
+            const int c8 = v / cols, px = v - c8 * cols;
+            const int xx = x0 + px - dil;
+            const bool inside = row_in && xx >= 0 && xx < W;
+            const bf16 *src = inside ? in + (img0 + (int64_t)yy * W + xx) * CI + c8 * 8 : in;
+            cp_async16_zfill(dst + ((size_t)c8 * cols + px) * 8, src, inside ? 16 : 0);
+        }
+    };
+    // the 9 x Cin/16 MMAs of chain row j (input rows j - 1, j, j + 1 in slots (j + 3) % 4,
+    // j % 4, (j + 1) % 4) into accumulator b, committed to barrier b
+    auto issue = [&](int j, int b, uint32_t tmem) {
+        constexpr uint32_t idesc = umma_idesc_bf16(kTW5, CO);
+        int accumulate = 0;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+            const bf16 *row = s_ring + ((j + 3 + ky) & 3) * slot_elems;
+#pragma unroll
+            for (int c0 = 0; c0 < CI; c0 += 16) {
+                const uint32_t a = smem_u32(row + ((size_t)(c0 / 8) * cols + kx * dil) * 8);
+                const uint32_t bb = smem_u32(s_w + ((size_t)(tap * C8 + c0 / 8) * CO) * 8);
+                umma_bf16(tmem + 32u * b, umma_smem_desc(a, (uint32_t)cols * 16u, 128u),
+                          umma_smem_desc(bb, CO * 16u, 128u), idesc, accumulate);
+                accumulate = 1;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(s_bar + b)) : "memory");
+    };
+    // item q: strip (image, column tile), then the segment within the strip: rows
+    // rho + dil * (seg * kSeg + i), i < kSeg, for the residue rho of its chain
+    auto decode = [&](int q, int64_t &img0, int &x0, int &rho, int &j0, int &j1) {
+        const int strip = q / items_per_strip;
+        int r = q - strip * items_per_strip;
+        const int bimg = strip / tiles_per_row;
+        x0 = (strip - bimg * tiles_per_row) * kTW5;
+        img0 = (int64_t)bimg * H * W;
+        for (rho = 0; rho < dil; ++rho) {
+            const int J = (H - rho + dil - 1) / dil;             // chain rows rho, rho + dil, .. < H
+            const int ns = (J + kSeg - 1) / kSeg;
+            if (r < ns) { j0 = r * kSeg; j1 = min(J, j0 + kSeg); return; }
+            r -= ns;
+        }
+        j0 = j1 = 0;                                             // not reached for q < n_items
+    };
 
     for (int v = tid; v < CO * 9 * C8; v += 128) {
         const int co = v / (9 * C8), r = v - co * (9 * C8);      // r = tap * C8 + c8
-        *reinterpret_cast<uint4 *>(s_w + ((size_t)r * CO + co) * 8) =
-            *reinterpret_cast<const uint4 *>(w + (int64_t)co * 9 * CI + r * 8);
+        cp_async16_zfill(s_w + ((size_t)r * CO + co) * 8, w + (int64_t)co * 9 * CI + r * 8, 16);
     }
-    // staged column px holds input column x0 - dil + px (zero outside the image)
-    for (int v = tid; v < 3 * cols * C8; v += 128) {
-        const int ky = v / (cols * C8);
-        const int rem = v - ky * cols * C8;
-        const int c8 = rem / cols, px = rem - c8 * cols;
-        const int yy = y + (ky - 1) * dil, xx = x0 + px - dil;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-            val = *reinterpret_cast<const uint4 *>(in + (img0 + (int64_t)yy * W + xx) * CI + c8 * 8);
-        *reinterpret_cast<uint4 *>(s_in + ((size_t)(ky * C8 + c8) * cols + px) * 8) = val;
-    }
-    // the staged operands are read by the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" :: "r"(smem_u32(s_tmem)) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" :: "r"(smem_u32(s_tmem)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(s_bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(s_bar + 1)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -242,74 +295,91 @@ conv3x3_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
 
-    if (tid == 0) {
-        constexpr uint32_t idesc = umma_idesc_bf16(kTW5, CO);
-        int accumulate = 0;
+    int k = 0;                      // rows done by this CTA: accumulator k & 1, barrier use k >> 1
+    bool ok = true;
+    for (int q = blockIdx.x; q < n_items && ok; q += gridDim.x) {
+        int64_t img0;
+        int x0, rho, j0, j1;
+        decode(q, img0, x0, rho, j0, j1);
+        // the first row's three input rows (chain rows j0 - 1 .. j0 + 1), then its MMAs; every
+        // earlier MMA of this CTA has completed (each row's wait precedes its epilogue)
+        for (int i = j0 - 1; i <= j0 + 1; ++i) stage_row(img0, x0, rho + i * dil, (i + 4) & 3);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) issue(j0, k & 1, tmem);
+        for (int j = j0; j < j1; ++j, ++k) {
+            const int b = k & 1;
+            // the input row the next output row adds (chain row j + 2, into the slot of j - 2)
+            if (j + 1 < j1) stage_row(img0, x0, rho + (j + 2) * dil, (j + 2) & 3);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            uint32_t done = 0;
+            const uint32_t parity = (uint32_t)(k >> 1) & 1u;
+            for (int it = 0; it < (1 << 18) && !done; ++it)
+                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                             : "=r"(done) : "r"(smem_u32(s_bar + b)), "r"(parity) : "memory");
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (done) {
+                const int y = rho + j * dil;
+                uint32_t v[CO];
+                tmem_ld_32x32b<CO>(tmem + 32u * b + ((uint32_t)(32 * warp) << 16), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int64_t pix = img0 + (int64_t)y * W + x0 + 32 * warp + lane;
+                if (EPI == kEpiLinearF32) {
+                    static_cast<float *>(out)[pix] = __uint_as_float(v[0]) + bias[0];
+                } else {
+                    uint4 o[CO / 8];
+                    uint4 mk[CO / 8];
+                    if (EPI == kEpiMaskBf16) {
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int ky = tap / 3, kx = tap % 3;
-#pragma unroll
-            for (int c0 = 0; c0 < CI; c0 += 16) {
-                const uint32_t a = smem_u32(s_in + ((size_t)(ky * C8 + c0 / 8) * cols + kx * dil) * 8);
-                const uint32_t bb = smem_u32(s_w + ((size_t)(tap * C8 + c0 / 8) * CO) * 8);
-                umma_bf16(tmem, umma_smem_desc(a, (uint32_t)cols * 16u, 128u), umma_smem_desc(bb, CO * 16u, 128u), idesc,
-                          accumulate);
-                accumulate = 1;
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(smem_u32(s_bar)) : "memory");
-    }
-    // wait for the MMAs (phase 0 of the barrier), with an iteration limit
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 18) && !done; ++it)
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(smem_u32(s_bar)) : "memory");
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (done) {
-        uint32_t v[CO];
-        tmem_ld_32x32b<CO>(tmem + ((uint32_t)(32 * warp) << 16), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int64_t pix = img0 + (int64_t)y * W + x0 + 32 * warp + lane;
-        if (EPI == kEpiLinearF32) {
-            static_cast<float *>(out)[pix] = __uint_as_float(v[0]) + bias[0];
-        } else {
-            uint4 o[CO / 8];
-            uint4 mk[CO / 8];
-            if (EPI == kEpiMaskBf16) {
-#pragma unroll
-                for (int q = 0; q < CO / 8; ++q) mk[q] = reinterpret_cast<const uint4 *>(mask + pix * CO)[q];
-            }
-#pragma unroll
-            for (int q = 0; q < CO / 8; ++q) {
-                uint32_t packed[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int ch = 8 * q + 2 * e;
-                    float v0 = __uint_as_float(v[ch]), v1 = __uint_as_float(v[ch + 1]);
-                    if (EPI == kEpiReluBf16) {
-                        v0 = fmaxf(v0 + bias[ch], 0.f);
-                        v1 = fmaxf(v1 + bias[ch + 1], 0.f);
-                    } else {
-                        const uint32_t mw = e == 0 ? mk[q].x : e == 1 ? mk[q].y : e == 2 ? mk[q].z : mk[q].w;
-                        const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw);
-                        v0 = __bfloat162float(m2.x) > 0.f ? v0 : 0.f;
-                        v1 = __bfloat162float(m2.y) > 0.f ? v1 : 0.f;
+                        for (int qq = 0; qq < CO / 8; ++qq) mk[qq] = reinterpret_cast<const uint4 *>(mask + pix * CO)[qq];
                     }
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-                    packed[e] = *reinterpret_cast<const uint32_t *>(&h2);
-                }
-                o[q] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-            }
 #pragma unroll
-            for (int q = 0; q < CO / 8; ++q) reinterpret_cast<uint4 *>(static_cast<bf16 *>(out) + pix * CO)[q] = o[q];
+                    for (int qq = 0; qq < CO / 8; ++qq) {
+                        uint32_t packed[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int ch = 8 * qq + 2 * e;
+                            float v0 = __uint_as_float(v[ch]), v1 = __uint_as_float(v[ch + 1]);
+                            if (EPI == kEpiReluBf16) {
+                                v0 = fmaxf(v0 + bias[ch], 0.f);
+                                v1 = fmaxf(v1 + bias[ch + 1], 0.f);
+                            } else {
+                                const uint32_t mw = e == 0 ? mk[qq].x : e == 1 ? mk[qq].y : e == 2 ? mk[qq].z : mk[qq].w;
+                                const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162 *>(&mw);
+                                v0 = __bfloat162float(m2.x) > 0.f ? v0 : 0.f;
+                                v1 = __bfloat162float(m2.y) > 0.f ? v1 : 0.f;
+                            }
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                            packed[e] = *reinterpret_cast<const uint32_t *>(&h2);
+                        }
+                        o[qq] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    }
+#pragma unroll
+                    for (int qq = 0; qq < CO / 8; ++qq) reinterpret_cast<uint4 *>(static_cast<bf16 *>(out) + pix * CO)[qq] = o[qq];
+                }
+            }
+            // the next row's input has landed and this row's accumulator has been read
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            const int all_done = __syncthreads_and((int)done);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!all_done) {                    // a wait gave up: report and stop this CTA
+                if (tid == 0) atomicExch(&g_tc_timeout, 1);
+                ok = false;
+                break;
+            }
+            if (tid == 0 && j + 1 < j1) issue(j + 1, (k + 1) & 1, tmem);
         }
-    } else if (lane == 0) {
-        atomicExch(&g_tc_timeout, 1);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" :: "r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" :: "r"(tmem) : "memory");
 }
 
 // Weight gradient partials: CTA c sums rows [c*rows, (c+1)*rows) of the B*H image rows.
@@ -561,12 +631,16 @@ cudaError_t launch_conv(const void *in, const void *w, const float *bias, const 
     return cudaGetLastError();
 }
 
-// The tensor-memory variant: one CTA per 128-pixel row segment (W a multiple of 128).
+// The tensor-memory variant (W a multiple of 128): persistent CTAs over segments of
+// dilation-strided row chains.  Each CTA holds 64 TMEM columns; its shared-memory request is
+// at least 30 KB, so that at most 7 CTAs share an SM (448 of its 512 columns: an
+// allocation never waits).
 template <int CI, int CO, int EPI>
 cudaError_t launch_conv_tc(const void *in, const void *w, const float *bias, const void *mask, void *out, int B,
                            int H, int W, int dil, cudaStream_t st) {
     auto bytes = [](int d) {
-        return sizeof(ddk::bf16) * ((size_t)9 * CI * CO + (size_t)3 * CI * (ddk::kTW5 + 2 * d)) + 16;
+        const size_t b = sizeof(ddk::bf16) * ((size_t)9 * CI * CO + (size_t)4 * CI * (ddk::kTW5 + 2 * d)) + 32;
+        return std::max<size_t>(b, 30 * 1024);
     };
     static bool configured = false;     // allow the largest dilation's staging area once
     if (!configured) {
@@ -575,9 +649,23 @@ cudaError_t launch_conv_tc(const void *in, const void *w, const float *bias, con
         if (err != cudaSuccess) return err;
         configured = true;
     }
-    const unsigned grid = (unsigned)(B * H * (W / ddk::kTW5));
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ddk::conv3x3_tc_kernel<CI, CO, EPI>, 128, bytes(dil));
+    if (err != cudaSuccess) return err;
+    // items per (image, column tile): the segments of every residue chain rho < dil
+    int per_strip = 0;
+    for (int rho = 0; rho < dil; ++rho) {
+        const int J = (H - rho + dil - 1) / dil;
+        per_strip += (J + ddk::kSeg - 1) / ddk::kSeg;
+    }
+    const int n_items = B * (W / ddk::kTW5) * per_strip;
+    const int grid = std::max(1, std::min(n_items, sms * std::min(per, 7)));
     ddk::conv3x3_tc_kernel<CI, CO, EPI><<<grid, 128, bytes(dil), st>>>((const ddk::bf16 *)in, (const ddk::bf16 *)w, bias,
-                                                                        (const ddk::bf16 *)mask, out, H, W, dil);
+                                                                        (const ddk::bf16 *)mask, out, H, W, dil,
+                                                                        per_strip, n_items);
     return cudaGetLastError();
 }
 
@@ -604,7 +692,7 @@ dd_status dd_sur_conv3x3(const void *in, const void *w, const float *bias, const
     const char *name = epilogue == 2 ? "conv3x3_dgrad" : "conv3x3_fwd";
     dd::ProfScope ps(name, st);
     cudaError_t err = cudaSuccess;
-    // rows of 128 pixels: one tcgen05 MMA tile per CTA; otherwise 64-pixel tiles on mma.sync
+    // rows of 128 pixels: tcgen05 MMA tiles of 128 pixels; otherwise 64-pixel tiles on mma.sync
     const bool tc = W % ddk::kTW5 == 0;
 #define DD_CONV(CI, CO)                                                                                   \
     if (cin == CI && cout == CO) {                                                                        \
