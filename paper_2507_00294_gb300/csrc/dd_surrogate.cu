@@ -211,7 +211,7 @@ template <int CI, int CO, int EPI>
 __global__ void __launch_bounds__(128)
 conv3x3_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const float *__restrict__ bias,
                   const bf16 *__restrict__ mask, void *__restrict__ out, int H, int W, int dil, int items_per_strip,
-                  int n_items) {
+                  int n_items, int withhold_mma) {
     constexpr int C8 = CI / 8;
     static_assert(CI % 16 == 0 && (CO == 16 || CO == 32), "K steps of 16; 16 or 32 accumulator columns");
     // dynamic shared memory: weights [9][C8][CO][8], the ring of 4 input rows
@@ -310,16 +310,18 @@ conv3x3_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) issue(j0, k & 1, tmem);
+        if (tid == 0 && !withhold_mma) issue(j0, k & 1, tmem);
         for (int j = j0; j < j1; ++j, ++k) {
             const int b = k & 1;
             // the input row the next output row adds (chain row j + 2, into the slot of j - 2)
             if (j + 1 < j1) stage_row(img0, x0, rho + (j + 2) * dil, (j + 2) & 3);
             asm volatile("cp.async.commit_group;" ::: "memory");
+            // at most 2^18 tries of at most 1 us each (the suspend-time hint): a quarter second
             uint32_t done = 0;
             const uint32_t parity = (uint32_t)(k >> 1) & 1u;
             for (int it = 0; it < (1 << 18) && !done; ++it)
-                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
+                             " selp.u32 %0, 1, 0, p;\n}\n"
                              : "=r"(done) : "r"(smem_u32(s_bar + b)), "r"(parity) : "memory");
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (done) {
@@ -373,7 +375,7 @@ conv3x3_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ w, const
                 ok = false;
                 break;
             }
-            if (tid == 0 && j + 1 < j1) issue(j + 1, (k + 1) & 1, tmem);
+            if (tid == 0 && j + 1 < j1 && !withhold_mma) issue(j + 1, (k + 1) & 1, tmem);
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -663,9 +665,12 @@ cudaError_t launch_conv_tc(const void *in, const void *w, const float *bias, con
     }
     const int n_items = B * (W / ddk::kTW5) * per_strip;
     const int grid = std::max(1, std::min(n_items, sms * std::min(per, 7)));
+    // DD_FAULT=tc_wait (tests): no MMA is issued, so every completion wait runs out and the
+    // timeout path (flag, no output, TMEM released) is exercised without a GPU fault
+    const int withhold = dd::fault_injected("tc_wait") ? 1 : 0;
     ddk::conv3x3_tc_kernel<CI, CO, EPI><<<grid, 128, bytes(dil), st>>>((const ddk::bf16 *)in, (const ddk::bf16 *)w, bias,
                                                                         (const ddk::bf16 *)mask, out, H, W, dil,
-                                                                        per_strip, n_items);
+                                                                        per_strip, n_items, withhold);
     return cudaGetLastError();
 }
 

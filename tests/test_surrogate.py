@@ -58,6 +58,27 @@ def test_conv_data_gradient(cuda, ci, co, dil):
     np.testing.assert_allclose(r64(out), ref, rtol=8e-3, atol=1e-3 * np.abs(ref).max())
 
 
+def test_tensor_core_wait_timeout_is_reported(cuda, monkeypatch):
+    """Failure detection without a GPU fault: with DD_FAULT=tc_wait no MMA is issued, the
+    tensor-memory convolution's completion wait runs out (bounded), the CTA releases its
+    TMEM and returns, and dd_sur_check reports DD_ETIMEOUT; the next call runs normally."""
+    rng = np.random.default_rng(77)
+    x = bf(rng.standard_normal((1, 8, 128, 32))).to(cuda)
+    wt = bf(rng.standard_normal((32, 9, 32)) * 0.2).to(cuda)
+    bias = torch.from_numpy(rng.standard_normal(32).astype(np.float32)).to(cuda)
+    out = torch.empty((1, 8, 128, 32), dtype=torch.bfloat16, device=cuda)
+    monkeypatch.setenv("DD_FAULT", "tc_wait")
+    b.dd_sur_conv3x3(x, wt, bias, None, out, 0, 1)
+    with pytest.raises(b.DDError) as e:
+        b.dd_sur_check()
+    assert e.value.status == b.DD_ETIMEOUT
+    monkeypatch.delenv("DD_FAULT")
+    b.dd_sur_conv3x3(x, wt, bias, None, out, 0, 1)
+    b.dd_sur_check()
+    ref = conv_ref.conv3x3(r64(x), r64(wt).reshape(32, 3, 3, 32), bias.double().cpu().numpy(), 1)
+    np.testing.assert_allclose(r64(out), np.maximum(ref, 0), rtol=8e-3, atol=1e-3 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("ci,co,dil", [(32, 32, 2), (16, 16, 32)])
 def test_conv_forward_64_pixel_tiles(cuda, ci, co, dil):
     """Rows that are not a multiple of 128 pixels (W = 192) take the 64-pixel mma.sync
