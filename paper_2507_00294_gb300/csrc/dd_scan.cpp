@@ -421,10 +421,16 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         s->kappa = d->D_m2s * tref / (p * p);
         s->pref = d->Q0 / (4.0 * 3.14159265358979323846 * d->D_m2s);
         s->X.resize((size_t)n); s->Y.resize((size_t)n); s->T.resize((size_t)n); s->TAU.resize((size_t)n);
+        // grid row and column of each visit: g / nx from a double reciprocal, corrected to
+        // the exact quotient (g < 2^26, so the product is off by less than one), instead of
+        // an integer division per visit
+        const double inv_nx = 1.0 / (double)nx;
         for (int64_t k = 0; k < n; ++k) {
-            const int32_t g = seq[(size_t)k];
-            s->X[(size_t)k] = (double)(g % nx);
-            s->Y[(size_t)k] = (double)(g / nx);
+            const int64_t g = seq[(size_t)k];
+            int64_t q = (int64_t)((double)g * inv_nx), r = g - q * nx;
+            if (r < 0) { --q; r += nx; } else if (r >= nx) { ++q; r -= nx; }
+            s->X[(size_t)k] = (double)r;
+            s->Y[(size_t)k] = (double)q;
             s->T[(size_t)k] = s->uniform ? (double)k : s->t_start[(size_t)k] / tref;
             s->TAU[(size_t)k] = s->uniform ? 1.0 : s->tau[(size_t)k] / tref;
         }
