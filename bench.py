@@ -71,35 +71,49 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 100 ms while running."""
+    """nvidia-smi clock / throttle samples every 25 ms, each stamped with the host clock.
+
+    The timed region of a short run lasts tens of milliseconds, so the sampler is started
+    first and the region opens only once a sample has arrived; `mark()` brackets the region
+    (after the closing synchronise, so it covers the device work) and `summary()` keeps the
+    samples inside it."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 25
 
     def __init__(self, index):
         self.index = index
         self.rows = []
         self.proc = None
+        self.window = None
+        self.first = threading.Event()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            self.first.wait(timeout=10.0)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([c.strip() for c in line.split(",")])
+            self.rows.append((time.monotonic(), [c.strip() for c in line.split(",")]))
+            self.first.set()
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *exc):
         if self.proc is not None:
+            time.sleep(2.0 * self.PERIOD_MS / 1e3)   # the sample that closes the window
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -108,11 +122,22 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = self.rows
+        where = "inside the timed region"
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if inside:
+                rows = inside
+            else:
+                # no sample fell inside: keep the ones nearest either edge of the region
+                near = sorted(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))[:2]
+                rows, where = near, "nearest the timed region (none fell inside it)"
         sm = []
         mx = None
         reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for _, r in rows:
             try:
                 sm.append(float(r[0]))
                 mx = float(r[1])
@@ -124,7 +149,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "period_ms": self.PERIOD_MS, "window": where}
 
 
 def whole_job(pairs_per_rank_step, steps, rank_total_ms, dist=None, device=None):
@@ -414,12 +439,14 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     with ClockSampler(local_rank) as clocks:
+        t_open = time.monotonic()
         for k in range(args.steps):
             flush.fill_(float(k))                    # evict L2 between steps (untimed)
             ev[k][0].record(stream)
             step("mixed")
             ev[k][1].record(stream)
         torch.cuda.synchronize(dev)
+        clocks.mark(t_open, time.monotonic())
     b.dd_profile_enable(False)
     prof = b.dd_profile_read()
     step_ms = [a.elapsed_time(z) for a, z in ev]

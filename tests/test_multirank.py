@@ -47,3 +47,18 @@ def test_weak_scaling_reduction_two_ranks():
 def test_single_rank_without_process_group():
     value, total_ms, w = bench.whole_job(10, 3, 2.0)
     assert w == 1 and total_ms == 2.0 and value == pytest.approx(15000.0)
+
+
+def test_clock_summary_keeps_the_timed_window():
+    """Samples outside the timed region are dropped; throttle reasons inside it are kept."""
+    c = bench.ClockSampler(0)
+    row = lambda mhz, cap: [str(mhz), "2070", "900", "Not Active", "Not Active", "Not Active", cap]
+    c.rows = [(0.0, row(1000, "Not Active")), (1.0, row(2070, "Active")),
+              (1.1, row(2060, "Not Active")), (2.0, row(500, "Not Active"))]
+    c.mark(0.9, 1.2)
+    s = c.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == 2065.0 and s["reasons"] == ["sw_power_cap"]
+    assert s["window"] == "inside the timed region"
+    c.mark(1.5, 1.6)                       # no sample inside: the two nearest, labelled so
+    s = c.summary()
+    assert s["samples"] == 2 and s["window"].startswith("nearest")
