@@ -18,6 +18,21 @@ def oracle_sources(spec):
     return oracle.Sources(xs, ys, ts, taus)
 
 
+def raster_sources(spec):
+    """Sources of a full raster scan with a uniform dwell, from the definition (visit k is
+    grid index k and starts at k * dwell) in vectorised form, for grids too large for the
+    oracle's list-based scan builder; equal to oracle_sources on such specs (checked in
+    test_oracle_scan.py)."""
+    assert spec.order == oscan.RASTER and spec.keep_fraction == 1.0 and spec.mask is None
+    assert spec.flyback_s == 0.0 and spec.dwell_per_visit is None
+    n = spec.nx * spec.ny
+    g = np.arange(n, dtype=np.int64)
+    ts = np.arange(n, dtype=np.int64).astype(np.float64) * spec.dwell_s
+    return oracle.Sources((g % spec.nx).astype(np.float64) * spec.pitch_m,
+                          (g // spec.nx).astype(np.float64) * spec.pitch_m, ts,
+                          np.full(n, spec.dwell_s, dtype=np.float64))
+
+
 def oracle_field(spec, pts, times):
     return oracle.field(oracle_sources(spec), spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
                         pts[:, 0], pts[:, 1], times)

@@ -5,7 +5,7 @@ import pytest
 from paper_2507_00294_gb300 import binding as b
 from paper_2507_00294_gb300 import workloads as w
 from parity_util import (assert_fp64, assert_mixed, oracle_field, oracle_pairs,
-                         peak_lower_bound)
+                         peak_lower_bound, raster_sources)
 
 pytestmark = pytest.mark.gpu
 
@@ -254,3 +254,48 @@ def test_series_class_limits_swept(cuda, prec):
         assert_fp64(got, ref, "class limits fp64")
     else:
         assert_mixed(got, ref, ref.max(axis=1), "class limits mixed")
+
+
+def test_maximum_grid_2_26_visits(cuda):
+    """The largest scan the library accepts: an 8192 x 8192 raster, 2^26 visits (coefficient
+    tables of 5-19 GB, byte offsets past 2^32, 131,072 visit blocks).  Slow diffusion
+    (D tau / pitch^2 = 1e-6) keeps every region's dose distinct.  Snapshots on the dwell
+    lattice (half-way, when visit 2^25 starts, and the end: one lag table of 2^26 + 1
+    records) and off it (0.37 dwell into visit 2^25, and 2.5 dwells after the end: one
+    record per (snapshot, visit)); 16 points at the beam, behind it, ahead of it, at the
+    first probe and off the grid, in both precisions; 64 pairs against the oracle over all
+    2^26 visits."""
+    import oracle
+    nx = 8192
+    spec = w.ScanSpec(nx, nx, D_m2s=1e-6 * w.PITCH ** 2 / w.DWELL)
+    p, tau, n = spec.pitch_m, spec.dwell_s, nx * nx
+    half = n // 2                                   # visit 2^25 starts row 4096 at x = 0
+    pts = p * np.array([[8191, 8191], [8190.5, 8191], [8191, 8190], [4000, 8191],
+                        [0, 0], [4096.3, 4095.7], [8191, 4095], [8190, 4095],
+                        [0, 4096], [1, 4096], [0, 4095], [0.5, 4095.5],
+                        [100, 5000], [8191, 8000], [-3, -3], [8194.2, 8191]], dtype=np.float64)
+    calls = {"lattice": np.array([half * tau, n * tau]),
+             "off lattice": np.array([(half + 0.37) * tau, (n + 2.5) * tau])}
+    ip = np.tile(np.arange(len(pts)), 2)
+    it = np.repeat(np.arange(2), len(pts))
+    src = raster_sources(spec)
+    t_all = np.concatenate([ts[it] for ts in calls.values()])
+    ref_all = oracle.field_pairs(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
+                                 np.tile(pts[ip, 0], 2), np.tile(pts[ip, 1], 2), t_all)
+    del src
+    scan = b.Scan(spec)
+    import torch
+    pd = torch.from_numpy(pts).cuda()
+    for c, (name, times) in enumerate(calls.items()):
+        ref = ref_all[c * len(ip):(c + 1) * len(ip)].reshape(2, len(pts))
+        assert np.all(ref[1] > 0.0) and np.all(ref[0, 4:12] > 0.0)
+        for prec in ("fp64", "mixed"):
+            got = b.dd_field_at_times(scan, pd, times, prec)
+            torch.cuda.synchronize()
+            got = got.cpu().numpy()
+            if prec == "fp64":
+                assert_fp64(got, ref, "2^26 visits, %s, fp64" % name)
+            else:
+                # the largest sampled value bounds each map's peak from below
+                assert_mixed(got, ref, ref.max(axis=1), "2^26 visits, %s, mixed" % name)
+    scan.close()
