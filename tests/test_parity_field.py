@@ -264,10 +264,18 @@ def test_maximum_grid_2_26_visits(cuda):
     records) and off it (0.37 dwell into visit 2^25, and 2.5 dwells after the end: one
     record per (snapshot, visit)); 16 points at the beam, behind it, ahead of it, at the
     first probe and off the grid, in both precisions; 64 pairs against the oracle over all
-    2^26 visits."""
+    2^26 visits.
+
+    Pitch 2^-31 m (0.47 nm) and dwell 2^-20 s (0.95 us) are powers of two, so that every
+    coordinate, start time and time difference is exact in FP64 on both sides.  With a
+    decimal dwell, times near 33 s carry an FP64 rounding of 7e-15 s, i.e. 7e-9 relative
+    to a one-dwell lag: the field at the beam is then fixed by its inputs only to a few
+    1e-9, above the FP64 tolerance (the library, which works in dwells on the lattice, and
+    the oracle, which subtracts seconds, differed by 2.5e-9 there)."""
     import oracle
     nx = 8192
-    spec = w.ScanSpec(nx, nx, D_m2s=1e-6 * w.PITCH ** 2 / w.DWELL)
+    pitch, dwell = 2.0 ** -31, 2.0 ** -20
+    spec = w.ScanSpec(nx, nx, pitch_m=pitch, dwell_s=dwell, D_m2s=1e-6 * pitch ** 2 / dwell)
     p, tau, n = spec.pitch_m, spec.dwell_s, nx * nx
     half = n // 2                                   # visit 2^25 starts row 4096 at x = 0
     pts = p * np.array([[8191, 8191], [8190.5, 8191], [8191, 8190], [4000, 8191],
