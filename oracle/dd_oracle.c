@@ -195,10 +195,12 @@ double ddo_phi(double rho2, double dt, double tau, double Ds, double D, double Q
                    : 2.0 * Ds + 4.0 * D * (dt - tau);  /* Eq. 2: 2Ds + 4D(t - (t_i + tau_i)) */
     if (rho2 == 0.0) {
         /* Eq. 3 / Eq. 4: ln((Ds + 2D(t-t_i)) / Ds) and
-           ln((Ds + 2D(t-t_i)) / (Ds + 2D(t-t_i-tau))) */
-        double num = Ds + 2.0 * D * dt;
+           ln((Ds + 2D(t-t_i)) / (Ds + 2D(t-t_i-tau))), as ln(1 + (num - den)/den)
+           with num - den = 2D min(t - t_i, tau_i) taken directly: long after the dwell
+           the ratio is 1 + O(tau/(t - t_i)), and rounding it first would cost
+           u / (num/den - 1) of relative accuracy */
         double den = on ? Ds : Ds + 2.0 * D * (dt - tau);
-        return pref * log(num / den);
+        return pref * log1p(2.0 * D * (on ? dt : tau) / den);
     }
     /* ln(b/a) = ln(w1/w0), with w1 - w0 = 4D min(t - t_i, tau_i) taken directly */
     double ell = log1p(4.0 * D * (on ? dt : tau) / w0);

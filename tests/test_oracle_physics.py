@@ -66,6 +66,20 @@ def test_phi_equals_green_function_time_integral(r, dt, tau):
     assert abs(got / ref - 1.0) < 1e-12, (r, dt, tau, got, ref)
 
 
+@pytest.mark.parametrize("r", [0.0, 0.15e-9])
+@pytest.mark.parametrize("lag", [0.5, 1e3, 1e5, 1e7, 6.7e7])
+def test_phi_long_after_the_dwell_slow_diffusion(r, lag):
+    """Eq. 3/4 (rho = 0) and Eq. 2 long after the dwell, with slow diffusion
+    (D tau / pitch^2 = 1e-6 at a 0.5 nm pitch): the logarithm's argument is then
+    1 + O(1e-8), where forming the ratio before the logarithm would lose ~1e-8 of relative
+    accuracy; against the Green's-function time integral at 40 digits."""
+    D_slow = 1e-6 * (0.5e-9) ** 2 / TAU
+    dt = lag * TAU
+    ref = float(green_time_integral(r * r, dt, TAU, Ds, D_slow, Q0, dps=40))
+    got = float(oracle.phi(r * r, dt, TAU, Ds, D_slow, Q0))
+    assert abs(got / ref - 1.0) < 1e-13, (r, lag, got, ref)
+
+
 def test_phi_causal_and_continuous_at_rho0():
     assert oracle.phi(1e-20, 0.0, TAU, Ds, D, Q0) == 0.0          # t = t_i
     assert oracle.phi(1e-20, -1e-7, TAU, Ds, D, Q0) == 0.0        # not started
