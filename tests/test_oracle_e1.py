@@ -66,3 +66,15 @@ def test_quadrature_agrees_with_value_difference_where_well_conditioned():
     q = oracle.e1_diff_quad(a, b)
     d = oracle.e1(a) - oracle.e1(b)
     assert np.max(np.abs(q / d - 1.0)) < 1e-13
+
+
+def test_tabulated_values():
+    """The oracle's E1 against tabulated values (tests/golden/e1_table.txt, 10 significant
+    digits): agreement to the table's last digit."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "e1_table.txt")
+    rows = np.loadtxt(path, comments="#")
+    assert rows.shape == (9, 2)
+    for x, v in rows:
+        got = float(oracle.e1(x))
+        assert abs(got / v - 1.0) <= 5e-10, (x, got, v)
