@@ -59,7 +59,10 @@ def assert_fp64(got, ref, what=""):
     m = np.abs(ref) >= 1e-290
     rel = np.abs(got[m] - ref[m]) / np.abs(ref[m])
     worst = rel.max() if rel.size else 0.0
-    assert worst <= FP64_RTOL, "%s: FP64 max rel err %.3e" % (what, worst)
+    if worst > FP64_RTOL:
+        k = np.argwhere(m)[np.argmax(rel)]
+        raise AssertionError("%s: FP64 max rel err %.3e at index %s (got %.17g, oracle %.17g)"
+                             % (what, worst, tuple(int(i) for i in k), got[tuple(k)], ref[tuple(k)]))
     return worst
 
 
@@ -74,5 +77,9 @@ def assert_mixed(got, ref, peak, what=""):
     assert m.sum() > 0
     rel = np.abs(got[m] - ref[m]) / ref[m]
     worst = rel.max()
-    assert worst <= MIXED_RTOL, "%s: mixed max rel err %.3e (median %.3e)" % (what, worst, np.median(rel))
+    if worst > MIXED_RTOL:
+        k = np.argwhere(m)[np.argmax(rel)]
+        raise AssertionError("%s: mixed max rel err %.3e (median %.3e) at index %s (got %.9g, oracle %.9g)"
+                             % (what, worst, np.median(rel), tuple(int(i) for i in k), got[tuple(k)],
+                                ref[tuple(k)]))
     return worst
