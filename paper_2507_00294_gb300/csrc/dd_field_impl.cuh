@@ -280,15 +280,25 @@ __device__ __forceinline__ void box_rho2(float sx, float sy, float bx0, float bx
     r2min = (dx0 * dx0 + dy0 * dy0) * 0.9999f;
 }
 
-// rho^2 of PPT points (in pairs: px[m] = (x_2m, x_2m+1)) to the visit nxy = (-x, -x, -y, -y)
-// on f32x2 instructions.
+// Points in a tile are held as an integer offset from the tile's integer origin plus a
+// fraction (|f| <= 1/2 pitch): P.i = (x_2m, x_2m+1) - origin (exact integers), P.f the
+// fractions, and likewise in y.  Visits sit on the integer probe grid, so visit minus
+// origin is an exact integer too: dx = (P.i - visit) + P.f is exact up to the final
+// rounding, i.e. within 2^-24 |dx| wherever the points lie.  (One FP32 offset per point
+// would carry an error of 2^-24 times the distance to the tile origin instead, which at a
+// few thousand pitches and a sub-pitch probe is a 1e-3 error in e^-a.)
+struct PointPair {
+    float2 xi, xf, yi, yf;
+};
+
+// rho^2 of PPT points (pairs m: points 2m, 2m+1) to the visit nxy = (-x, -x, -y, -y)
+// (integer, relative to the tile origin) on f32x2 instructions.
 template <int PPT>
-__device__ __forceinline__ void rho2_points(const float2 (&px)[PPT / 2], const float2 (&py)[PPT / 2],
-                                            const float4 &nxy, float (&r2)[PPT]) {
+__device__ __forceinline__ void rho2_points(const PointPair (&P)[PPT / 2], const float4 &nxy, float (&r2)[PPT]) {
 #pragma unroll
     for (int m = 0; m < PPT / 2; ++m) {
-        const float2 dx = __fadd2_rn(px[m], f2(nxy.x, nxy.y));
-        const float2 dy = __fadd2_rn(py[m], f2(nxy.z, nxy.w));
+        const float2 dx = __fadd2_rn(__fadd2_rn(P[m].xi, f2(nxy.x, nxy.y)), P[m].xf);
+        const float2 dy = __fadd2_rn(__fadd2_rn(P[m].yi, f2(nxy.z, nxy.w)), P[m].yf);
         const float2 q = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
         r2[2 * m] = q.x;
         r2[2 * m + 1] = q.y;
@@ -311,17 +321,23 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     static_assert(PPT % 2 == 0, "points are processed in pairs");
     const int tid = threadIdx.x, lane = tid & 31;
 
-    // coordinates relative to the tile's first point (keeps FP32 differences precise far
-    // from the origin); points k = 2m, 2m+1 in one pair
+    // coordinates relative to the integer grid position nearest the tile's first point:
+    // integer offset + fraction per point (PointPair), exact integers for the visits;
+    // points k = 2m, 2m+1 in one pair
     const float4 org = ptsF[tile0];
-    float2 px[PPT / 2], py[PPT / 2];
+    const float ox = rintf(org.x), oy = rintf(org.z);
+    PointPair P[PPT / 2];
     float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int64_t p = tile0 + k * NT + tid;
-        const float2 d = p < n_pts ? ff_diff(ptsF[p], org) : make_float2(0.0f, 0.0f);
-        const float x = d.x, y = d.y;
-        if (k & 1) { px[k >> 1].y = x; py[k >> 1].y = y; } else { px[k >> 1].x = x; py[k >> 1].x = y; }
+        const float4 q = p < n_pts ? ptsF[p] : org;
+        const float ix = rintf(q.x), iy = rintf(q.z);
+        const float fx = (q.x - ix) + q.y, fy = (q.z - iy) + q.w;     // q.x - ix is exact
+        const float xi = ix - ox, yi = iy - oy;                        // exact integers
+        if (k & 1) { P[k >> 1].xi.y = xi; P[k >> 1].xf.y = fx; P[k >> 1].yi.y = yi; P[k >> 1].yf.y = fy; }
+        else       { P[k >> 1].xi.x = xi; P[k >> 1].xf.x = fx; P[k >> 1].yi.x = yi; P[k >> 1].yf.x = fy; }
+        const float x = xi + fx, y = yi + fy;
         bx0 = fminf(bx0, x); bx1 = fmaxf(bx1, x);
         by0 = fminf(by0, y); by1 = fmaxf(by1, y);
     }
@@ -353,8 +369,10 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
         const int cnt = min(STILE, s_end - s0);
         __syncthreads();
         for (int i = tid; i < cnt; i += NT) {
-            const float2 d = ff_diff(srcF[s0 + i], org);
-            sm.xy[i] = make_float4(-d.x, -d.x, -d.y, -d.y);
+            // probe positions are integers in pitch units: visit - origin is exact
+            const float4 v = srcF[s0 + i];
+            const float dx = (v.x - ox) + v.y, dy = (v.z - oy) + v.w;
+            sm.xy[i] = make_float4(-dx, -dx, -dy, -dy);
         }
         // records; a snapshot for which the visit has not started gets the zero record,
         // whose terms are 0
@@ -443,7 +461,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const float4 g2 = sm.gm[0][s];
                     const float2 g2p[2] = {f2(g2.x, g2.y), f2(g2.z, g2.w)};
                     float r2[PPT];
-                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+                    rho2_points<PPT>(P, sm.xy[s], r2);
 #pragma unroll
                     for (int P = 0; P < NP; ++P)
 #pragma unroll
@@ -464,7 +482,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const float2 g3p[2] = {f2(g3.x, g3.y), f2(g3.z, g3.w)};
                     const float2 g4p[2] = {f2(g4.x, g4.y), f2(g4.z, g4.w)};
                     float r2[PPT];
-                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+                    rho2_points<PPT>(P, sm.xy[s], r2);
 #pragma unroll
                     for (int P = 0; P < NP; ++P)
 #pragma unroll
@@ -483,7 +501,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const int b = __ffs(m) - 1, s = cw * 32 + b;
                     const uint32_t word = __shfl_sync(0xffffffffu, my_word[cw], b);
                     float r2[PPT];
-                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+                    rho2_points<PPT>(P, sm.xy[s], r2);
 #pragma unroll
                     for (int jc = 0; jc < TCH; ++jc) {
                         const uint32_t c = (word >> (kCodeBits * jc)) & kCodeMask;
@@ -515,7 +533,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const float4 v0 = sm.lo[0][s];                     // (g_0, g_1x, g_2x, g_3x)
                     const float g4 = d4 ? sm.hi[0][s].x : 0.0f;
                     float r2[PPT];
-                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+                    rho2_points<PPT>(P, sm.xy[s], r2);
 #pragma unroll
                     for (int mm = 0; mm < PPT / 2; ++mm) {
                         const float2 r = f2(r2[2 * mm], r2[2 * mm + 1]);
@@ -537,7 +555,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const uint32_t c = __shfl_sync(0xffffffffu, my_word[cw], b) & kCodeMask;
                     if (c == kCodeSkip) continue;
                     float r2[PPT];
-                    rho2_points<PPT>(px, py, sm.xy[s], r2);
+                    rho2_points<PPT>(P, sm.xy[s], r2);
                     const RecF32 &Rs = sm.rec[s];
                     if (c == kCodeD8) {
                         point_pass_h2<8, PPT>(acc[0], r2, Rs);
