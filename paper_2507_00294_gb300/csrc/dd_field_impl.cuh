@@ -292,14 +292,28 @@ struct PointPair {
 };
 
 // rho^2 of PPT points (pairs m: points 2m, 2m+1) to the visit nxy = (-x, -x, -y, -y)
-// (integer, relative to the tile origin) on f32x2 instructions.
+// (integer, relative to the tile origin) on f32x2 instructions.  split (uniform over the
+// CTA): add the fractions; otherwise P.xi, P.yi hold the whole offsets, which are then exact
+// in FP32 (points on the probe grid, its halves, quarters, ...), and the two adds are skipped.
 template <int PPT>
-__device__ __forceinline__ void rho2_points(const PointPair (&P)[PPT / 2], const float4 &nxy, float (&r2)[PPT]) {
+__device__ __forceinline__ void rho2_points(const PointPair (&P)[PPT / 2], const float4 &nxy, bool split,
+                                            float (&r2)[PPT]) {
+    float2 dx[PPT / 2], dy[PPT / 2];
 #pragma unroll
     for (int m = 0; m < PPT / 2; ++m) {
-        const float2 dx = __fadd2_rn(__fadd2_rn(P[m].xi, f2(nxy.x, nxy.y)), P[m].xf);
-        const float2 dy = __fadd2_rn(__fadd2_rn(P[m].yi, f2(nxy.z, nxy.w)), P[m].yf);
-        const float2 q = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        dx[m] = __fadd2_rn(P[m].xi, f2(nxy.x, nxy.y));
+        dy[m] = __fadd2_rn(P[m].yi, f2(nxy.z, nxy.w));
+    }
+    if (split) {
+#pragma unroll
+        for (int m = 0; m < PPT / 2; ++m) {
+            dx[m] = __fadd2_rn(dx[m], P[m].xf);
+            dy[m] = __fadd2_rn(dy[m], P[m].yf);
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < PPT / 2; ++m) {
+        const float2 q = __ffma2_rn(dx[m], dx[m], __fmul2_rn(dy[m], dy[m]));
         r2[2 * m] = q.x;
         r2[2 * m + 1] = q.y;
     }
@@ -326,8 +340,9 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
     // points k = 2m, 2m+1 in one pair
     const float4 org = ptsF[tile0];
     const float ox = rintf(org.x), oy = rintf(org.z);
-    PointPair P[PPT / 2];
+    PointPair pp[PPT / 2];
     float bx0 = 3.0e38f, bx1 = -3.0e38f, by0 = 3.0e38f, by1 = -3.0e38f;
+    bool exact = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int64_t p = tile0 + k * NT + tid;
@@ -335,11 +350,23 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
         const float ix = rintf(q.x), iy = rintf(q.z);
         const float fx = (q.x - ix) + q.y, fy = (q.z - iy) + q.w;     // q.x - ix is exact
         const float xi = ix - ox, yi = iy - oy;                        // exact integers
-        if (k & 1) { P[k >> 1].xi.y = xi; P[k >> 1].xf.y = fx; P[k >> 1].yi.y = yi; P[k >> 1].yf.y = fy; }
-        else       { P[k >> 1].xi.x = xi; P[k >> 1].xf.x = fx; P[k >> 1].yi.x = yi; P[k >> 1].yf.x = fy; }
+        if (k & 1) { pp[k >> 1].xi.y = xi; pp[k >> 1].xf.y = fx; pp[k >> 1].yi.y = yi; pp[k >> 1].yf.y = fy; }
+        else       { pp[k >> 1].xi.x = xi; pp[k >> 1].xf.x = fx; pp[k >> 1].yi.x = yi; pp[k >> 1].yf.x = fy; }
         const float x = xi + fx, y = yi + fy;
+        // (x - xi) is computed exactly (|fx| <= 1/2, xi an integer), so it equals fx only
+        // when x lost no bit of xi + fx
+        exact = exact && (x - xi) == fx && (y - yi) == fy;
         bx0 = fminf(bx0, x); bx1 = fmaxf(bx1, x);
         by0 = fminf(by0, y); by1 = fmaxf(by1, y);
+    }
+    // one vote of the CTA: split offsets only where some point of the tile needs them
+    const bool split = __syncthreads_or(!exact) != 0;
+    if (!split) {
+#pragma unroll
+        for (int m = 0; m < PPT / 2; ++m) {
+            pp[m].xi = __fadd2_rn(pp[m].xi, pp[m].xf);
+            pp[m].yi = __fadd2_rn(pp[m].yi, pp[m].yf);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -461,7 +488,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const float4 g2 = sm.gm[0][s];
                     const float2 g2p[2] = {f2(g2.x, g2.y), f2(g2.z, g2.w)};
                     float r2[PPT];
-                    rho2_points<PPT>(P, sm.xy[s], r2);
+                    rho2_points<PPT>(pp, sm.xy[s], split, r2);
 #pragma unroll
                     for (int P = 0; P < NP; ++P)
 #pragma unroll
@@ -482,7 +509,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const float2 g3p[2] = {f2(g3.x, g3.y), f2(g3.z, g3.w)};
                     const float2 g4p[2] = {f2(g4.x, g4.y), f2(g4.z, g4.w)};
                     float r2[PPT];
-                    rho2_points<PPT>(P, sm.xy[s], r2);
+                    rho2_points<PPT>(pp, sm.xy[s], split, r2);
 #pragma unroll
                     for (int P = 0; P < NP; ++P)
 #pragma unroll
@@ -501,7 +528,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const int b = __ffs(m) - 1, s = cw * 32 + b;
                     const uint32_t word = __shfl_sync(0xffffffffu, my_word[cw], b);
                     float r2[PPT];
-                    rho2_points<PPT>(P, sm.xy[s], r2);
+                    rho2_points<PPT>(pp, sm.xy[s], split, r2);
 #pragma unroll
                     for (int jc = 0; jc < TCH; ++jc) {
                         const uint32_t c = (word >> (kCodeBits * jc)) & kCodeMask;
@@ -533,7 +560,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const float4 v0 = sm.lo[0][s];                     // (g_0, g_1x, g_2x, g_3x)
                     const float g4 = d4 ? sm.hi[0][s].x : 0.0f;
                     float r2[PPT];
-                    rho2_points<PPT>(P, sm.xy[s], r2);
+                    rho2_points<PPT>(pp, sm.xy[s], split, r2);
 #pragma unroll
                     for (int mm = 0; mm < PPT / 2; ++mm) {
                         const float2 r = f2(r2[2 * mm], r2[2 * mm + 1]);
@@ -555,7 +582,7 @@ __device__ __forceinline__ void field_tile_mixed(TileSmemMixed<Cfg, TCH> &sm, co
                     const uint32_t c = __shfl_sync(0xffffffffu, my_word[cw], b) & kCodeMask;
                     if (c == kCodeSkip) continue;
                     float r2[PPT];
-                    rho2_points<PPT>(P, sm.xy[s], r2);
+                    rho2_points<PPT>(pp, sm.xy[s], split, r2);
                     const RecF32 &Rs = sm.rec[s];
                     if (c == kCodeD8) {
                         point_pass_h2<8, PPT>(acc[0], r2, Rs);

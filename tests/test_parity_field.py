@@ -307,3 +307,19 @@ def test_maximum_grid_2_26_visits(cuda):
                 # the largest sampled value bounds each map's peak from below
                 assert_mixed(got, ref, ref.max(axis=1), "2^26 visits, %s, mixed" % name)
     scan.close()
+
+
+def test_off_grid_points_far_from_the_tile_origin(cuda):
+    """A dense grid of points off the probe lattice (pitch/3 spacing shifted by 0.1 pitch,
+    so no offset from a tile origin is exact in FP32) over a 32 x 32 raster with slow
+    diffusion (D tau / pitch^2 = 1e-4, so e^-a falls steeply near recent visits): every
+    point and both snapshots against the oracle, in both precisions.  Tiles span up to 32
+    pitches; a single FP32 offset per point would put ~1e-5 errors into rho^2 there."""
+    spec = w.ScanSpec(32, 32, D_m2s=1e-4 * w.PITCH ** 2 / w.DWELL)
+    g = (np.arange(96) / 3.0 + 0.1) * spec.pitch_m
+    xx, yy = np.meshgrid(g, g)
+    pts = np.column_stack([xx.ravel(), yy.ravel()])
+    times = np.array([600.5, 1024.0]) * spec.dwell_s
+    ref = oracle_field(spec, pts, times)
+    assert_fp64(gpu_field(spec, pts, times, "fp64"), ref, "off-grid fp64")
+    assert_mixed(gpu_field(spec, pts, times, "mixed"), ref, ref.max(axis=1), "off-grid mixed")
