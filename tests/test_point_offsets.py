@@ -1,0 +1,34 @@
+"""The FP32-mixed tile's test of whether a point's offset from the tile origin is exact in
+one FP32 value: with xi an integer (|xi| < 2^24) and f a fraction (|f| <= 1/2, itself
+FP32), x = fl(xi + f) lost no bit exactly when fl(x - xi) == f.  Checked here in FP32
+arithmetic against the exact sum in FP64 (which holds xi + f exactly)."""
+import numpy as np
+
+
+def _exact_by_test(xi, f):
+    x = (xi + f).astype(np.float32)                      # FP32 add, one rounding
+    return (x - xi).astype(np.float32) == f
+
+
+def _exact_truth(xi, f):
+    x = (xi + f).astype(np.float32)
+    return x.astype(np.float64) == xi.astype(np.float64) + f.astype(np.float64)
+
+
+def test_exactness_test_matches_the_exact_sum():
+    rng = np.random.default_rng(7)
+    n = 2_000_000
+    xi = rng.integers(-8192, 8193, n).astype(np.float32)
+    # fractions: grid-like (k/2, k/4, k/3, k/10 + 0.1 style) and random FP32 values
+    kinds = [rng.integers(-2, 3, n) / 4.0, rng.integers(-1, 2, n) / 3.0,
+             rng.uniform(-0.5, 0.5, n), (rng.integers(0, 3, n) / 3.0 + 0.1) % 1.0 - 0.5]
+    for f in kinds:
+        f = np.asarray(f, dtype=np.float32)
+        assert np.array_equal(_exact_by_test(xi, f), _exact_truth(xi, f))
+    # halves and quarters of the grid are always exact; generic fractions far from the
+    # origin are not
+    q = (rng.integers(-2, 3, n) / 4.0).astype(np.float32)
+    assert _exact_by_test(xi, q).all()
+    g = rng.uniform(-0.5, 0.5, n).astype(np.float32)
+    far = np.abs(xi) >= 4096
+    assert not _exact_by_test(xi[far], g[far]).all()
