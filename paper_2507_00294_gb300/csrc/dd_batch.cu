@@ -82,9 +82,17 @@ __global__ void batch_coef_kernel(const BScan *__restrict__ sc, const int64_t *_
     rec[g] = out;
 }
 
+// Resident CTAs per SM each variant is compiled for (register cap 65536 / (threads x
+// blocks)); 0 leaves the register count to the compiler.
+template <typename Cfg>
+struct BatchMinBlocks { static constexpr int value = 0; };
+struct CfgMixed64x12;
+template <> struct BatchMinBlocks<CfgMixed64x12> { static constexpr int value = 12; };
+template <> struct BatchMinBlocks<CfgMixed> { static constexpr int value = 9; };
+
 // Persistent CTAs: claim item indices from *counter until the list is exhausted.
 template <typename Cfg>
-__global__ void __launch_bounds__(Cfg::kThreads)
+__global__ void __launch_bounds__(Cfg::kThreads, BatchMinBlocks<Cfg>::value)
 batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items, int n_items,
                    unsigned *__restrict__ counter, const double *__restrict__ X, const double *__restrict__ Y,
                    const float4 *__restrict__ F, const typename Cfg::Rec *__restrict__ rec, int sb,
@@ -135,6 +143,8 @@ struct CfgMixed256 : CfgMixed {
 struct CfgMixed64 : CfgMixed {
     static constexpr int kThreads = 64, kPPT = 8, kSTILE = 64;
 };
+// the same, held to 80 registers (12 CTAs per SM, a few spilled values) instead of 96
+struct CfgMixed64x12 : CfgMixed64 {};
 struct CfgF64x256 : CfgF64 {
     static constexpr int kThreads = 256, kPPT = 1;
 };
@@ -170,11 +180,13 @@ struct dd_batch {
 namespace {
 
 constexpr int kTile = 512;
-constexpr int kVariants = 3;
+constexpr int kVariants = 4;
 
 const char *variant_name(dd_precision prec, int v) {
-    static const char *mixed[kVariants] = {"batch_field_mixed_128x4", "batch_field_mixed_256x2", "batch_field_mixed_64x8"};
-    static const char *f64[kVariants] = {"batch_field_fp64_128x4", "batch_field_fp64_256x2", "batch_field_fp64_64x8"};
+    static const char *mixed[kVariants] = {"batch_field_mixed_128x4", "batch_field_mixed_256x2", "batch_field_mixed_64x8",
+                                           "batch_field_mixed_64x8_r80"};
+    static const char *f64[kVariants] = {"batch_field_fp64_128x4", "batch_field_fp64_256x2", "batch_field_fp64_64x8",
+                                         "batch_field_fp64_64x8"};
     return prec == DD_MIXED ? mixed[v] : f64[v];
 }
 
@@ -213,7 +225,8 @@ dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cuda
         if (b->prec == DD_MIXED) {
             if (variant == 0) launch_field<ddk::CfgMixed>(b, g, st);
             else if (variant == 1) launch_field<ddk::CfgMixed256>(b, g, st);
-            else launch_field<ddk::CfgMixed64>(b, g, st);
+            else if (variant == 2) launch_field<ddk::CfgMixed64>(b, g, st);
+            else launch_field<ddk::CfgMixed64x12>(b, g, st);
         } else {
             if (variant == 0) launch_field<ddk::CfgF64>(b, g, st);   // 128 x 2 (256-point tile)
             else if (variant == 1) launch_field<ddk::CfgF64x256>(b, g, st);
@@ -351,9 +364,11 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
     if (!it.empty()) DD_CUDA_TRY(cudaMemcpy(b->d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
     DD_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     if (prec == DD_MIXED)
-        b->grid = {persistent_grid<ddk::CfgMixed>(), persistent_grid<ddk::CfgMixed256>(), persistent_grid<ddk::CfgMixed64>()};
+        b->grid = {persistent_grid<ddk::CfgMixed>(), persistent_grid<ddk::CfgMixed256>(), persistent_grid<ddk::CfgMixed64>(),
+                   persistent_grid<ddk::CfgMixed64x12>()};
     else
-        b->grid = {persistent_grid<ddk::CfgF64>(), persistent_grid<ddk::CfgF64x256>(), persistent_grid<ddk::CfgF64>()};
+        b->grid = {persistent_grid<ddk::CfgF64>(), persistent_grid<ddk::CfgF64x256>(), persistent_grid<ddk::CfgF64>(),
+                   persistent_grid<ddk::CfgF64>()};
     // tuning key: device name, precision and a log2 bucket of the pair count
     cudaDeviceProp prop;
     DD_CUDA_TRY(cudaGetDeviceProperties(&prop, b->device));

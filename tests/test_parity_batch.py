@@ -70,7 +70,7 @@ def test_tuned_variants_agree(cuda):
     dp = torch.from_numpy(allp).cuda()
     base = plan.run(dp).cpu().numpy()
     v = plan.tune(dp)
-    assert v in (0, 1, 2) and plan.info()["variant"] == v
+    assert v in (0, 1, 2, 3) and plan.info()["variant"] == v
     tuned = plan.run(dp).cpu().numpy()
     # a fixed variant is bit-reproducible; another tile shape groups points into warps
     # differently and may pick another (equally accurate) polynomial degree per warp
