@@ -99,3 +99,22 @@ def test_batched_512_scans_sampled(cuda):
         ip = np.concatenate([ip, [g_last]])
         ref = oracle_pairs(j.scan, j.pts_xy, j.times, ip, np.zeros(len(ip), int))
         assert_mixed(out[offs[k] + ip], ref, ref[-1], "batch512 scan %d" % k)
+
+
+def test_off_grid_points_batch(cuda):
+    """Batch tiles (one snapshot each) on points off the probe lattice (pitch/3 spacing
+    shifted by 0.11 pitch: no offset from a tile origin is exact in FP32, so every tile
+    takes the split point offsets): every point of every scan against the oracle."""
+    import torch
+    specs, _, times = small_batch(seed=31, n_scans=12)
+    pts = [w.grid_points(3 * max(s.nx, s.ny), s.pitch_m / 3) + 0.11 * s.pitch_m for s in specs]
+    offs, allp = flat(pts)
+    scans = [b.Scan(s) for s in specs]
+    out = b.Batch(scans, offs, times, "mixed").run(torch.from_numpy(allp).cuda()).cpu().numpy()
+    for k, s in enumerate(specs):
+        got = out[offs[k]:offs[k + 1]]
+        if times[k] == 0.0:
+            assert np.all(got == 0.0)
+            continue
+        ref = oracle_field(s, pts[k], times[k:k + 1])[0]
+        assert_mixed(got, ref, ref.max(), "off-grid batch scan %d" % k)
