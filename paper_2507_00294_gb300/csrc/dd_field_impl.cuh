@@ -283,8 +283,9 @@ __device__ __forceinline__ void box_rho2(float sx, float sy, float bx0, float bx
 // Points in a tile are held as an integer offset from the tile's integer origin plus a
 // fraction (|f| <= 1/2 pitch): P.i = (x_2m, x_2m+1) - origin (exact integers), P.f the
 // fractions, and likewise in y.  Visits sit on the integer probe grid, so visit minus
-// origin is an exact integer too: dx = (P.i - visit) + P.f is exact up to the final
-// rounding, i.e. within 2^-24 |dx| wherever the points lie.  (One FP32 offset per point
+// origin is an exact integer too: dx = (P.i - visit) + P.f is within 2^-24 |dx| + 2^-25
+// pitch of the exact difference (the final rounding and the fraction's own) wherever the
+// points lie.  (One FP32 offset per point
 // would carry an error of 2^-24 times the distance to the tile origin instead, which at a
 // few thousand pitches and a sub-pitch probe is a 1e-3 error in e^-a.)
 struct PointPair {

@@ -32,3 +32,30 @@ def test_exactness_test_matches_the_exact_sum():
     g = rng.uniform(-0.5, 0.5, n).astype(np.float32)
     far = np.abs(xi) >= 4096
     assert not _exact_by_test(xi[far], g[far]).all()
+
+
+def test_split_offset_error_bound():
+    """dx from the split point offsets, emulated step by step in FP32 (point as float-float
+    (hi, lo) of x in pitch units, rint, integer offsets from an integer origin, one add for
+    the fraction), within 2^-24 |dx| + 2^-25 pitch of the exact difference, for points
+    anywhere on an 8192-pitch grid; the single FP32 offset from the tile origin is not."""
+    rng = np.random.default_rng(3)
+    n = 1_000_000
+    x = rng.uniform(-2.0, 8194.0, n)                          # point, pitch units (FP64)
+    v = rng.integers(0, 8192, n).astype(np.float64)           # visit on the probe grid
+    org = rng.uniform(0.0, 8192.0, n)                         # tile's first point
+    f32 = np.float32
+    hi = x.astype(f32)
+    lo = (x - hi.astype(np.float64)).astype(f32)
+    ox = np.rint(org.astype(f32)).astype(f32)
+    ix = np.rint(hi).astype(f32)
+    fx = ((hi - ix).astype(f32) + lo).astype(f32)
+    xi = (ix - ox).astype(f32)
+    nv = (-(v.astype(f32) - ox)).astype(f32)
+    dx = (((xi + nv).astype(f32)) + fx).astype(f32).astype(np.float64)
+    exact = x - v
+    err = np.abs(dx - exact)
+    assert np.all(err <= 2.0 ** -24 * np.abs(exact) + 2.0 ** -25), err.max()
+    # one FP32 offset per point from the tile origin: errors grow with the distance to it
+    single = ((x - org).astype(f32) - (v - org).astype(f32)).astype(np.float64)
+    assert np.max(np.abs(single - exact)) > 1e-4
