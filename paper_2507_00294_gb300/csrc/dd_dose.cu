@@ -504,6 +504,18 @@ dd_status noalloc_scratch(char **addr) {
     return DD_OK;
 }
 
+// Float-float copy (hi, lo, hi, lo) of FP64 coordinates: hi = x rounded to FP32, lo = the
+// FP64 remainder x - hi (exact) rounded to FP32 -- the same values as the scan's cached
+// float-float copy, which is built on the host by the same two roundings.
+__global__ void ff_coords_kernel(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+                                 float4 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double xv = x[i], yv = y[i];
+    const float xh = __double2float_rn(xv), yh = __double2float_rn(yv);
+    out[i] = make_float4(xh, __double2float_rn(xv - (double)xh), yh, __double2float_rn(yv - (double)yh));
+}
+
 template <typename Cfg>
 dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream, char *scratch) {
     using Rec = typename Cfg::Rec;
@@ -550,14 +562,6 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     double *d_x = (double *)(scratch + o_x);
     double *d_y = d_x + n;
     float4 *d_f = (float4 *)(scratch + o_f);
-    // float-float copy of the coordinates (host staging reused by the next call)
-    static thread_local std::vector<float4> ffh;
-    ffh.resize((size_t)n);
-    for (int64_t i = 0; i < n; ++i) {
-        const float xh = (float)scan->X[(size_t)i], yh = (float)scan->Y[(size_t)i];
-        ffh[(size_t)i] = make_float4(xh, (float)(scan->X[(size_t)i] - (double)xh), yh,
-                                     (float)(scan->Y[(size_t)i] - (double)yh));
-    }
     Rec *d_rec = (Rec *)(scratch + o_rec);
     Part *d_part = (Part *)(scratch + o_part);
     int2 *d_items = (int2 *)(scratch + o_items);
@@ -565,7 +569,9 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     // nothing left by a previous call can leak into the result
     DD_CUDA_TRY(cudaMemcpyAsync(d_x, scan->X.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
     DD_CUDA_TRY(cudaMemcpyAsync(d_y, scan->Y.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, stream));
-    DD_CUDA_TRY(cudaMemcpyAsync(d_f, ffh.data(), (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, stream));
+    // float-float copy of the coordinates, built on the device from the FP64 ones
+    ff_coords_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(d_x, d_y, n, d_f);
+    DD_CUDA_TRY(cudaGetLastError());
     if (n >= 2) {
         ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 31) / 32), 32, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
         DD_CUDA_TRY(cudaGetLastError());
@@ -575,7 +581,8 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
     }
     ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);
     DD_CUDA_TRY(cudaGetLastError());
-    // the host staging above is reused by the next call on this thread
+    // the work list above lives in this thread's fixed host storage, which the next call
+    // on this thread rewrites: wait until the stream has copied it
     DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
 }

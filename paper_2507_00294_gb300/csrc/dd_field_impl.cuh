@@ -56,7 +56,8 @@ template <typename Rec>
 struct RecTraits;
 
 // Largest h of each FP32 class: the truncated exponent series of degree d stays within
-// 2.5e-7 of ln(P(h)/c_0) for every r in [1e-12, 1e6] (checked against 30-digit quadrature;
+// 2.5e-7 of ln(P(h)/c_0) for every r in [1e-12, 1e6] (checked against FP64 adaptive
+// quadrature of P(h), relative 1e-13, at half-decade steps of r: worst 2.49e-7 at degree 2;
 // about four FP32 roundings of the term, below the exponent's own rounding for all but the
 // largest terms): degree 2 up to h = 0.04, 4 up to 0.33, 8 up to 1.25 and 12 up to 2.0.
 // FP64: the moment polynomial of degree 15 up to h = 1/2 (1.2e-18).

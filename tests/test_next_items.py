@@ -32,11 +32,34 @@ def test_live_mode_snapshot_stream(cuda):
     assert_mixed(got, ref, ref.max(axis=1), "live mode")
 
 
+def _levels_from_definition(field, decades=6.0):
+    """Grey levels restated from their definition (log10 of the field over its maximum,
+    six decades onto 0..255), and the unrounded level, for the comparison below."""
+    top = float(np.max(field))
+    lv = 255.0 * (1.0 + np.log10(np.maximum(field, top * 10.0 ** -decades) / top) / decades)
+    return np.clip(np.floor(lv + 0.5), 0, 255).astype(np.uint8), lv
+
+
 def test_headless_maps(cuda, tmp_path):
+    """Fig. 1-style maps: the field behind each PGM matches the oracle's (mixed tolerance),
+    and each image equals the oracle field quantised the same way, except by one grey level
+    where the oracle's unrounded level lies within the field tolerance of a rounding edge."""
     from paper_2507_00294_gb300 import figures
-    paths = figures.fig1_maps(w.ScanSpec(16, 16, order=w.INTERLEAVED, interleave_stride=4), str(tmp_path))
-    for p in paths:
+    spec = w.ScanSpec(16, 16, order=w.INTERLEAVED, interleave_stride=4)
+    pts, times, field = figures.fig1_field(spec)
+    ref = oracle_field(spec, pts, times).reshape(field.shape)
+    for i in range(2):
+        assert_mixed(field[i], ref[i], ref[i].max(), "fig1 map %d" % i)
+    paths = figures.fig1_maps(spec, str(tmp_path))
+    head = b"P5\n32 32\n255\n"
+    for i, p in enumerate(paths):
         data = open(p, "rb").read()
-        assert data.startswith(b"P5\n32 32\n255\n") and len(data) == len(b"P5\n32 32\n255\n") + 32 * 32
-        img = np.frombuffer(data[-32 * 32:], np.uint8)
+        assert data.startswith(head) and len(data) == len(head) + 32 * 32
+        img = np.frombuffer(data[len(head):], np.uint8).reshape(32, 32)
+        want, lv = _levels_from_definition(ref[i])
         assert img.max() == 255 and img.min() < 255
+        # a 1e-5 relative field error moves a level by at most 255 * 2 * 4.4e-6 / 6 = 4e-4
+        edge = np.abs((lv - np.floor(lv)) - 0.5) < 1e-3
+        diff = np.abs(img.astype(int) - want.astype(int))
+        assert np.all(diff[~edge] == 0), "grey levels differ away from a rounding edge"
+        assert np.all(diff <= 1)

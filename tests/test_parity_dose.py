@@ -32,20 +32,6 @@ def test_dose_full(cuda, spec):
         assert_mixed(gm[1:], ref[1:], ref.max(), "dose mixed")
 
 
-def test_dose_grid256_sampled(cuda):
-    job = w.precision_study(w.INTERLEAVED, 0)
-    spec = job.scan
-    rng = np.random.default_rng(31)
-    targets = np.sort(rng.choice(np.arange(1, 256 * 256), 128, replace=False))
-    targets = np.concatenate([[1, 2, 255, 256, 65535], targets])
-    src = oracle_sources(spec)
-    ref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0, targets=targets)
-    g64 = gpu_dose(spec, "fp64")
-    assert_fp64(g64[targets], ref, "dose256 fp64")
-    gm = gpu_dose(spec, "mixed")
-    assert_mixed(gm[targets], ref, ref.max(), "dose256 mixed")
-
-
 @pytest.mark.parametrize("spec", [
     w.ScanSpec(12, 9, flyback_s=2.5e-6),
     w.ScanSpec(10, 10, order=w.SERPENTINE, flyback_s=4e-7, D_m2s=1e-12),

@@ -145,21 +145,48 @@ def test_deterministic_repeat(cuda):
     np.testing.assert_array_equal(a, c)
 
 
+# Seeded oracle samples per 256x256 run: 4096 (point, snapshot) pairs of the field (2048 at
+# the end of the scan, 2048 at 16x that time) and 2048 dwell-start dose targets plus the
+# edge targets (the first visits, a row change, the last visit).
+GRID256_FIELD_SAMPLES = 4096
+GRID256_DOSE_SAMPLES = 2048
+
+
 @pytest.mark.parametrize("order,d_index", [(w.RASTER, 0), (w.INTERLEAVED, 7), (w.SERPENTINE, 3), (w.RANDOM, 5)])
 def test_grid256_precision_study_sampled(cuda, order, d_index):
     """256x256 scans, the four orders, D from the seeded log-uniform draws, the end of the
-    scan and 16x later (t >> tau): oracle at 160 seeded points per snapshot."""
+    scan and 16x later (t >> tau, where the E1 differences cancel): the field in FP64 and
+    FP32-mixed on the whole probe grid, and the dwell-start dose of all 65,536 visits, each
+    against the oracle on seeded samples."""
+    import oracle
+    from parity_util import oracle_sources
     job = w.precision_study(order, d_index)
+    spec = job.scan
+    src = oracle_sources(spec)
     rng = np.random.default_rng(100 + d_index)
-    ip = rng.choice(len(job.pts_xy), 160, replace=False)
-    it = np.repeat([0, 1], 80)
-    ref = oracle_pairs(job.scan, job.pts_xy, job.times, ip, it)
-    peak = peak_lower_bound(job.scan, job.times)
-    gm = gpu_field(job.scan, job.pts_xy, job.times, "mixed")
-    assert_mixed(gm[it, ip], ref, peak[it], "grid256 mixed")
-    if order == w.RASTER:
-        g64 = gpu_field(job.scan, job.pts_xy, job.times, "fp64")
-        assert_fp64(g64[it, ip], ref, "grid256 fp64")
+    half = GRID256_FIELD_SAMPLES // 2
+    ip = np.concatenate([rng.choice(len(job.pts_xy), half, replace=False) for _ in range(2)])
+    it = np.repeat([0, 1], half)
+    ref = oracle.field_pairs(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0, job.pts_xy[ip, 0],
+                             job.pts_xy[ip, 1], job.times[it])
+    peak = peak_lower_bound(spec, job.times)
+    gm = gpu_field(spec, job.pts_xy, job.times, "mixed")
+    assert_mixed(gm[it, ip], ref, peak[it], "grid256 %s mixed" % w.ORDER_NAMES[order])
+    g64 = gpu_field(spec, job.pts_xy, job.times, "fp64")
+    assert_fp64(g64[it, ip], ref, "grid256 %s fp64" % w.ORDER_NAMES[order])
+
+    n = src.n
+    targets = np.sort(rng.choice(np.arange(1, n), GRID256_DOSE_SAMPLES, replace=False))
+    targets = np.unique(np.concatenate([[1, 2, 3, 255, 256, 257, n - 1], targets]))
+    dref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0, targets=targets)
+    scan = b.Scan(spec)
+    d64 = b.dd_per_probe_dose(scan, "fp64", device=cuda).cpu().numpy()
+    assert d64[0] == 0.0
+    assert_fp64(d64[targets], dref, "dose256 %s fp64" % w.ORDER_NAMES[order])
+    dmx = b.dd_per_probe_dose(scan, "mixed", device=cuda).cpu().numpy()
+    assert dmx[0] == 0.0
+    assert_mixed(dmx[targets], dref, dref.max(), "dose256 %s mixed" % w.ORDER_NAMES[order])
+    scan.close()
 
 
 def test_allocation_failure_is_reported_and_recoverable(cuda, monkeypatch):

@@ -20,7 +20,7 @@ import pytest
 integrate = pytest.importorskip("scipy.integrate")
 
 HEADER = os.path.join(os.path.dirname(__file__), "..", "paper_2507_00294_gb300", "csrc", "dd_field_impl.cuh")
-BOUND = 2.6e-7          # the header states 2.5e-7; the quadrature itself is good to ~1e-13
+BOUND = 2.5e-7          # as the header states; the quadrature itself is good to ~1e-13
 
 
 def class_limits():
