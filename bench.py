@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--surrogate-maps", type=int, default=20000)
     ap.add_argument("--surrogate-epochs", type=int, default=20)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--leg", choices=["all", "batched", "surrogate-infer"], default="all",
+                    help="run one leg alone (for profiling): the 512-scan batch, or the surrogate "
+                         "network's inference at batch 256 (random weights)")
     return ap.parse_args()
 
 
@@ -225,7 +228,8 @@ def ops_per_pair(job, samples=400_000, seed=5):
                                             np.where(h <= 2.0, FLOPS_SERIES[12], FLOPS_GENERAL)))))
     m = np.where(zero, 0.0, np.where(h <= 2.0, MUFU_SERIES, MUFU_GENERAL))
     wgt = nact[np.arange(samples)]               # pairs are sampled per snapshot: weight by n_active
-    return float(np.sum(f * wgt) / np.sum(wgt)), float(np.sum(m * wgt) / np.sum(wgt))
+    return (float(np.sum(f * wgt) / np.sum(wgt)), float(np.sum(m * wgt) / np.sum(wgt)),
+            float(np.sum(zero * wgt) / np.sum(wgt)))
 
 
 def workload():
@@ -238,22 +242,23 @@ def workload():
     return job, n, field_pairs, dose_pairs
 
 
-def cpu_oracle_sample(job, seconds, seed=11):
-    """Time the oracle on seeded (point, time) samples of the workload for ~`seconds`."""
+def cpu_oracle_sample(job, seconds, seed=11, threads=0):
+    """Time the oracle on seeded (point, time) samples of the workload for ~`seconds`, on
+    `threads` host threads (0: all the cores the process may use)."""
     import oracle
     from oracle import scan as oscan
     from paper_2507_00294_gb300 import workloads as w
     s = job.scan
     xs, ys, ts, taus, _ = oscan.sources(s.nx, s.ny, s.pitch_m, s.dwell_s, order=s.order)
     src = oracle.Sources(xs, ys, ts, taus)
-    cores = oracle.max_threads()
+    cores = threads if threads > 0 else oracle.max_threads()
 
     def run(count, sd):
         ip, it = w.sample_pairs(len(job.pts_xy), len(job.times), count, seed=sd)
         pairs = int(np.searchsorted(ts, job.times[it], side="left").sum())
         t0 = time.perf_counter()
         oracle.field_pairs(src, s.sigma_m ** 2, s.D_m2s, s.Q0, job.pts_xy[ip, 0], job.pts_xy[ip, 1],
-                           job.times[it])
+                           job.times[it], threads=threads)
         return pairs, time.perf_counter() - t0
     p0, t0 = run(64, seed)
     rate = p0 / max(t0, 1e-6)
@@ -370,6 +375,40 @@ def bench_surrogate(dev, maps, epochs):
                      "(estimated from 64 exact spot points per map)"}
 
 
+def bench_surrogate_inference(dev, maps=256, reps=5):
+    """The surrogate network alone at batch `maps` (random weights; the throughput does not
+    depend on them): maps/s of the six convolutions on the 128 x 128 canvas."""
+    import torch
+    from paper_2507_00294_gb300 import surrogate as sur
+    specs = sur.draw_scans(maps, seed=7)
+    tmap, scal = sur.scan_inputs(specs)
+    tmap, scal = torch.from_numpy(tmap).to(dev), torch.from_numpy(scal).to(dev)
+    net = sur.Net(dev, seed=0)
+    sur.predict(net, tmap, scal, batch=maps)
+    torch.cuda.synchronize(dev)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        sur.predict(net, tmap, scal, batch=maps)
+    z.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(z) / reps
+    return {"maps_per_s_network": maps / (ms / 1e3), "ms_per_batch": ms, "batch": maps}
+
+
+def run_leg(args):
+    import torch
+    from paper_2507_00294_gb300 import binding as b
+    dev = torch.device("cuda", 0)
+    b.load()
+    if args.leg == "batched":
+        res = bench_batched(dev, torch.cuda.current_stream(dev), runs=3)
+    else:
+        res = bench_surrogate_inference(dev)
+    print(json.dumps({"leg": args.leg, **res}), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -457,7 +496,7 @@ def run_ours(args):
     # roofline of the dominant kernel (field_mixed), from its own events in the timed region
     fl, fms = prof.get("field_mixed", (0, 0.0))
     avg_ms = fms / max(1, fl)
-    fpp, mpp = ops_per_pair(job)
+    fpp, mpp, culled = ops_per_pair(job)
     rate = field_pairs / (avg_ms / 1e3) if fl else None
     traffic = recorded_traffic("field_mixed")
     # the pair term needs FP32 issue and one MUFU ex2: report the pipe this algorithm's mix
@@ -475,6 +514,9 @@ def run_ours(args):
                 "achieved": bind["achieved"], "peak": bind["peak"], "unit": bind["unit"], "frac": bind["frac"],
                 "traffic": traffic, "avg_launch_ms": avg_ms, "pairs_per_launch": field_pairs,
                 "kernel_pairs_per_s": rate, "ops_per_pair": bind["per_pair"], "peak_note": bind["peak_note"],
+                "culled_pair_fraction": round(culled, 5),
+                "culled_note": "pair-terms with a >= 87 (below the FP32 normal range) are counted in the "
+                               "pair-terms but skipped per warp; their share of the workload's pairs",
                 "other_pipe": {"pipe": "fp32" if bind is mufu else "mufu", **other}}
     launches = int(sum(v[0] for v in prof.values()))
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
@@ -542,10 +584,14 @@ def run_ours(args):
         if rank == 0 and world == 1:
             run, rate, count, cores = cpu_oracle_sample(job, args.cpu_seconds)
             p, t = run(count, 7)
+            run1, _, count1, _ = cpu_oracle_sample(job, args.cpu_seconds / 3, threads=1)
+            p1, t1 = run1(count1, 8)
             line["cpu_baseline"] = {
                 "value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": "%d seeded (point, snapshot) pairs of the workload, %d pair-terms, "
-                          "%.1f s, field only" % (count, p, t)}
+                          "%.1f s, field only" % (count, p, t),
+                "single_thread": {"value": p1 / t1, "unit": UNIT, "cores": 1,
+                                  "sample": "%d seeded pairs, %d pair-terms, %.1f s" % (count1, p1, t1)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -557,6 +603,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg != "all":
+        return run_leg(args)
     return run_ours(args)
 
 

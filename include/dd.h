@@ -94,12 +94,20 @@ typedef struct {
     int32_t n_custom;
     const double *dwell_per_visit;/* host, optional per-visit dwell tau_i [s] (Eq. 1/2 allow a
                                      different tau_i per probe); NULL = dwell_s for all */
+    double blank_s;               /* beam-blanker travel: dead time [s] before a visit whose
+                                     position lies more than one pitch from the previous
+                                     visit's (random, interleaved, masked or subsampled scans,
+                                     Sec. 1), >= 0; 0 = none */
+    double blank_s_per_m;         /* further dead time per metre of such a jump [s/m], >= 0 */
 } dd_scan_desc;
 
 /* Build a scan: the visit list in visit order and each visit's start time
-   t_k = k*dwell (uniform dwell, no flyback), otherwise t_{k+1} = t_k + tau_k
-   (+ flyback_s when a raster/serpentine scan changes row).  Host-only; touches
-   no GPU.  *out is set to a new scan owned by the caller (free with dd_destroy).
+   t_k = k*dwell (uniform dwell, no flyback, no blanker travel), otherwise
+   t_{k+1} = t_k + tau_k (+ flyback_s when a raster/serpentine scan changes row)
+   (+ blank_s + blank_s_per_m * |r_{k+1} - r_k| when that jump is longer than one pitch;
+   flyback and travel add up at a row change).  The beam deposits nothing during either
+   dead time.  Host-only; touches no GPU.  *out is set to a new scan owned by the caller
+   (free with dd_destroy).
    Errors: DD_EINVAL (bad description; *out untouched), DD_ENOMEM. */
 dd_status dd_create_scan(const dd_scan_desc *desc, dd_scan **out);
 

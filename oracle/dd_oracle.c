@@ -209,6 +209,17 @@ double ddo_phi(double rho2, double dt, double tau, double Ds, double D, double Q
 
 /* --------------------------------------------------- cumulative field, Eq. 5 */
 
+/* Threads of one call: `threads` if positive, else every thread OpenMP offers (the
+   request applies to that call only). */
+static int oracle_threads(int threads) {
+#ifdef _OPENMP
+    return threads > 0 ? threads : omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
+}
+
 /* out[it * n_pts + ip] = sum_{i} phi_i(|p - r_i|^2, t - t_i), summed in visit order.
    Sources: xs, ys [m], ts start times [s], taus dwell [s] (n_src each). */
 void ddo_field(int64_t n_src, const double *xs, const double *ys, const double *ts,
@@ -216,11 +227,9 @@ void ddo_field(int64_t n_src, const double *xs, const double *ys, const double *
                int64_t n_pts, const double *px, const double *py,
                int64_t n_t, const double *times, double *out, int threads) {
     if (!gl_ready) gl_init();
-#ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#endif
+    const int nt = oracle_threads(threads);
     int64_t total = n_t * n_pts;
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
     for (int64_t k = 0; k < total; ++k) {
         int64_t it = k / n_pts, ip = k % n_pts;
         double t = times[it], acc = 0.0;
@@ -238,10 +247,8 @@ void ddo_field_pairs(int64_t n_src, const double *xs, const double *ys, const do
                      int64_t n_pairs, const double *px, const double *py, const double *pt,
                      double *out, int threads) {
     if (!gl_ready) gl_init();
-#ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#endif
-#pragma omp parallel for schedule(dynamic, 4)
+    const int nt = oracle_threads(threads);
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
     for (int64_t k = 0; k < n_pairs; ++k) {
         double acc = 0.0;
         for (int64_t i = 0; i < n_src; ++i) {
@@ -258,10 +265,8 @@ void ddo_dose(int64_t n_src, const double *xs, const double *ys, const double *t
               const double *taus, double Ds, double D, double Q0,
               int64_t n_targets, const int64_t *targets, double *out, int threads) {
     if (!gl_ready) gl_init();
-#ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#endif
-#pragma omp parallel for schedule(dynamic, 4)
+    const int nt = oracle_threads(threads);
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
     for (int64_t k = 0; k < n_targets; ++k) {
         int64_t j = targets[k];
         double acc = 0.0;

@@ -17,9 +17,14 @@ Readings used here (they are restated in the design notes):
     seeded permutation; the random order visits them in permutation order, the
     other orders visit them in their own sequence;
   * an explicit mask removes positions whose mask entry is 0;
-  * visit k starts at t_k = k * tau with a uniform dwell and no flyback; otherwise
-    t_{k+1} = t_k + tau_k (+ flyback when raster/serpentine visits change row).
+  * visit k starts at t_k = k * tau with a uniform dwell and no dead time; otherwise
+    t_{k+1} = t_k + tau_k (+ flyback when raster/serpentine visits change row)
+    (+ the blanker's travel time, blank + blank_per_m * jump length in metres, when the
+    beam jumps more than one pitch to the next visit: the blanker of Sec. 1 keeps the beam
+    off while the probe moves over positions it does not visit).
 """
+import math
+
 import numpy as np
 
 RASTER, SERPENTINE, INTERLEAVED, RANDOM, CUSTOM = 0, 1, 2, 3, 4
@@ -90,10 +95,11 @@ def visit_order(nx, ny, order, stride=1, seed=0, keep_fraction=1.0, mask=None, c
     return seq
 
 
-def visit_times(visits, nx, order, dwell, flyback=0.0, dwell_per_visit=None):
+def visit_times(visits, nx, order, dwell, flyback=0.0, dwell_per_visit=None, pitch=0.0,
+                blank=0.0, blank_per_m=0.0):
     """Start time t_k [s] and dwell tau_k [s] of each visit."""
     n = len(visits)
-    if dwell_per_visit is None and flyback == 0.0:
+    if dwell_per_visit is None and flyback == 0.0 and blank == 0.0 and blank_per_m == 0.0:
         ts = [k * dwell for k in range(n)]
         return np.array(ts, dtype=np.float64), np.full(n, dwell, dtype=np.float64)
     taus = (np.full(n, dwell, dtype=np.float64) if dwell_per_visit is None
@@ -102,18 +108,25 @@ def visit_times(visits, nx, order, dwell, flyback=0.0, dwell_per_visit=None):
     t = 0.0
     for k in range(n):
         ts[k] = t
-        t = t + taus[k]
-        if flyback != 0.0 and order in (RASTER, SERPENTINE) and k + 1 < n:
-            if visits[k] // nx != visits[k + 1] // nx:
-                t = t + flyback
+        t = t + float(taus[k])
+        if k + 1 == n:
+            break
+        here, there = int(visits[k]), int(visits[k + 1])
+        if flyback != 0.0 and order in (RASTER, SERPENTINE) and here // nx != there // nx:
+            t = t + flyback
+        if blank != 0.0 or blank_per_m != 0.0:
+            jx = there % nx - here % nx
+            jy = there // nx - here // nx
+            if jx * jx + jy * jy > 1:                  # not the neighbouring position
+                t = t + (blank + blank_per_m * (pitch * math.sqrt(jx * jx + jy * jy)))
     return ts, taus
 
 
 def sources(nx, ny, pitch, dwell, order=RASTER, stride=1, seed=0, keep_fraction=1.0,
-            mask=None, custom=None, flyback=0.0, dwell_per_visit=None):
+            mask=None, custom=None, flyback=0.0, dwell_per_visit=None, blank=0.0, blank_per_m=0.0):
     """Probe visits as (xs, ys, ts, taus) arrays in SI units, plus the visit list."""
     v = visit_order(nx, ny, order, stride, seed, keep_fraction, mask, custom)
-    ts, taus = visit_times(v, nx, order, dwell, flyback, dwell_per_visit)
+    ts, taus = visit_times(v, nx, order, dwell, flyback, dwell_per_visit, pitch, blank, blank_per_m)
     g = np.asarray(v, dtype=np.int64)
     xs = (g % nx).astype(np.float64) * pitch
     ys = (g // nx).astype(np.float64) * pitch

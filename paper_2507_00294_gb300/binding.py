@@ -34,6 +34,7 @@ class dd_scan_desc(ctypes.Structure):
         ("mask", ctypes.POINTER(ctypes.c_uint8)),
         ("custom_visit", ctypes.POINTER(ctypes.c_int32)), ("n_custom", ctypes.c_int32),
         ("dwell_per_visit", ctypes.POINTER(ctypes.c_double)),
+        ("blank_s", ctypes.c_double), ("blank_s_per_m", ctypes.c_double),
     ]
 
 
@@ -145,6 +146,8 @@ class Scan:
         d.Q0, d.dwell_s, d.flyback_s = spec.Q0, spec.dwell_s, spec.flyback_s
         d.order, d.interleave_stride = int(spec.order), int(spec.interleave_stride)
         d.seed, d.keep_fraction = int(spec.seed) & ((1 << 64) - 1), float(spec.keep_fraction)
+        d.blank_s = float(getattr(spec, "blank_s", 0.0))
+        d.blank_s_per_m = float(getattr(spec, "blank_s_per_m", 0.0))
         self._keep = []
         if spec.mask is not None:
             m = np.ascontiguousarray(np.asarray(spec.mask, dtype=np.uint8).reshape(-1))

@@ -18,7 +18,7 @@
 // and the arguments rho^2 / w are unchanged by the scaling.
 struct dd_scan {
     int32_t nx = 0, ny = 0;
-    double pitch = 0, sigma = 0, D = 0, Q0 = 0, dwell = 0, flyback = 0;
+    double pitch = 0, sigma = 0, D = 0, Q0 = 0, dwell = 0, flyback = 0, blank = 0, blank_per_m = 0;
     int32_t order = 0, stride = 1;
     uint64_t seed = 0;
     double keep_fraction = 1.0;
@@ -26,7 +26,7 @@ struct dd_scan {
     int64_t n = 0;                       // visits
     std::vector<int32_t> visit;          // grid index per visit
     std::vector<double> t_start, tau;    // SI seconds
-    bool uniform = false;                // t_k = k * dwell and tau_k = dwell for all k
+    bool uniform = false;                // t_k = k * dwell and tau_k = dwell for all k (no dead time)
 
     double s = 0, kappa = 0, pref = 0;   // dimensionless Ds, D, and Q0/(4 pi D) [u/m^2]
     std::vector<double> X, Y, T, TAU;    // dimensionless, visit order

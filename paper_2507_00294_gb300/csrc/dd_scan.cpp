@@ -302,6 +302,9 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         return dd::fail(DD_EINVAL, "dd_create_scan: pitch, sigma, D, dwell must be finite and > 0; Q0 finite");
     if (!std::isfinite(d->flyback_s) || d->flyback_s < 0.0)
         return dd::fail(DD_EINVAL, "dd_create_scan: flyback must be finite and >= 0");
+    if (!std::isfinite(d->blank_s) || d->blank_s < 0.0 || !std::isfinite(d->blank_s_per_m) ||
+        d->blank_s_per_m < 0.0)
+        return dd::fail(DD_EINVAL, "dd_create_scan: blanker travel times must be finite and >= 0");
     if (d->order < DD_RASTER || d->order > DD_CUSTOM)
         return dd::fail(DD_EINVAL, "dd_create_scan: unknown order");
     if (d->flyback_s != 0.0 && d->order != DD_RASTER && d->order != DD_SERPENTINE)
@@ -387,6 +390,7 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         s->D = d->D_m2s; s->Q0 = d->Q0; s->dwell = d->dwell_s; s->flyback = d->flyback_s;
         s->order = d->order; s->stride = d->interleave_stride; s->seed = d->seed;
         s->keep_fraction = d->keep_fraction;
+        s->blank = d->blank_s; s->blank_per_m = d->blank_s_per_m;
         s->n = n;
         s->visit = seq;
         s->t_start.resize((size_t)n);
@@ -403,7 +407,8 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         } else {
             for (int64_t k = 0; k < n; ++k) s->tau[(size_t)k] = d->dwell_s;
         }
-        s->uniform = !d->dwell_per_visit && d->flyback_s == 0.0;
+        const bool travel = d->blank_s != 0.0 || d->blank_s_per_m != 0.0;
+        s->uniform = !d->dwell_per_visit && d->flyback_s == 0.0 && !travel;
         if (s->uniform) {
             for (int64_t k = 0; k < n; ++k) s->t_start[(size_t)k] = (double)k * d->dwell_s;
         } else {
@@ -411,8 +416,16 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
             for (int64_t k = 0; k < n; ++k) {
                 s->t_start[(size_t)k] = t;
                 t = t + s->tau[(size_t)k];
-                if (d->flyback_s != 0.0 && k + 1 < n && seq[(size_t)k] / nx != seq[(size_t)k + 1] / nx)
-                    t = t + d->flyback_s;
+                if (k + 1 == n) break;
+                const int64_t g0 = seq[(size_t)k], g1 = seq[(size_t)k + 1];
+                const int64_t r0 = g0 / nx, r1 = g1 / nx;
+                if (d->flyback_s != 0.0 && r0 != r1) t = t + d->flyback_s;
+                if (travel) {
+                    // blanker travel over a jump longer than one pitch
+                    const int64_t dx = g1 - r1 * nx - (g0 - r0 * nx), dy = r1 - r0;
+                    const int64_t d2 = dx * dx + dy * dy;
+                    if (d2 > 1) t = t + (d->blank_s + d->blank_s_per_m * (d->pitch_m * std::sqrt((double)d2)));
+                }
             }
         }
         // dimensionless form

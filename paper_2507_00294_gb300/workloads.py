@@ -41,6 +41,8 @@ class ScanSpec:
     mask: Optional[np.ndarray] = None
     custom_visit: Optional[np.ndarray] = None
     dwell_per_visit: Optional[np.ndarray] = None
+    blank_s: float = 0.0          # blanker dead time before a jump longer than one pitch [s]
+    blank_s_per_m: float = 0.0    # and per metre of that jump [s/m]
 
     def with_(self, **kw):
         return replace(self, **kw)

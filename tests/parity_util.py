@@ -9,20 +9,32 @@ FP64_RTOL = 1e-12          # GPU FP64 vs oracle, every point with |psi| >= 1e-29
 MIXED_RTOL = 1e-5          # GPU FP32-mixed vs oracle where psi >= 1e-6 of the map's peak
 
 
-def oracle_sources(spec):
+def oracle_problem(spec):
+    """The scan as the oracle evaluates it, with time measured in dwells.
+
+    Eq. 1/2 depend on time only through D (t - t_i), D tau_i and Q0 / D, so measuring
+    time in units of the dwell tau (t' = t / tau, D' = D tau, Q0' = Q0 tau) leaves every
+    field value unchanged, in u/m^2.  It does change the oracle's rounding: in seconds a
+    start time t_k = k tau carries an FP64 rounding of ulp(t_k), which long into a scan is
+    no longer small against a one-dwell lag (1.4e-11 of it at t = 65 ms, tau = 1 us: the
+    dose of a 256 x 256 scan at its last visits then moves by 3e-12), whereas in dwells
+    t'_k = k and every lag on the dwell lattice are exact.  Returns (sources with times in
+    dwells, Ds, D', Q0')."""
+    tau = spec.dwell_s
+    dpv = None if spec.dwell_per_visit is None else np.asarray(spec.dwell_per_visit, np.float64) / tau
     xs, ys, ts, taus, _ = oscan.sources(
-        spec.nx, spec.ny, spec.pitch_m, spec.dwell_s, order=spec.order,
+        spec.nx, spec.ny, spec.pitch_m, 1.0, order=spec.order,
         stride=spec.interleave_stride, seed=spec.seed, keep_fraction=spec.keep_fraction,
-        mask=spec.mask, custom=spec.custom_visit, flyback=spec.flyback_s,
-        dwell_per_visit=spec.dwell_per_visit)
-    return oracle.Sources(xs, ys, ts, taus)
+        mask=spec.mask, custom=spec.custom_visit, flyback=spec.flyback_s / tau,
+        dwell_per_visit=dpv, blank=spec.blank_s / tau, blank_per_m=spec.blank_s_per_m / tau)
+    return oracle.Sources(xs, ys, ts, taus), spec.sigma_m ** 2, spec.D_m2s * tau, spec.Q0 * tau
 
 
 def raster_sources(spec):
     """Sources of a full raster scan with a uniform dwell, from the definition (visit k is
-    grid index k and starts at k * dwell) in vectorised form, for grids too large for the
-    oracle's list-based scan builder; equal to oracle_sources on such specs (checked in
-    test_oracle_scan.py)."""
+    grid index k and starts at k * dwell) in vectorised form, in SI units, for grids too
+    large for the oracle's list-based scan builder; equal to the oracle's SI sources on such
+    specs (checked in test_oracle_scan.py)."""
     assert spec.order == oscan.RASTER and spec.keep_fraction == 1.0 and spec.mask is None
     assert spec.flyback_s == 0.0 and spec.dwell_per_visit is None
     n = spec.nx * spec.ny
@@ -33,22 +45,27 @@ def raster_sources(spec):
                           np.full(n, spec.dwell_s, dtype=np.float64))
 
 
-def oracle_field(spec, pts, times):
-    return oracle.field(oracle_sources(spec), spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
-                        pts[:, 0], pts[:, 1], times)
+def oracle_field(spec, pts, times, problem=None):
+    src, Ds, D, Q0 = problem or oracle_problem(spec)
+    return oracle.field(src, Ds, D, Q0, pts[:, 0], pts[:, 1], np.asarray(times) / spec.dwell_s)
 
 
-def oracle_pairs(spec, pts, times, ip, it):
-    return oracle.field_pairs(oracle_sources(spec), spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
-                              pts[ip, 0], pts[ip, 1], times[it])
+def oracle_pairs(spec, pts, times, ip, it, problem=None):
+    src, Ds, D, Q0 = problem or oracle_problem(spec)
+    return oracle.field_pairs(src, Ds, D, Q0, pts[ip, 0], pts[ip, 1], np.asarray(times)[it] / spec.dwell_s)
 
 
-def peak_lower_bound(spec, times):
+def oracle_dose(spec, targets=None, problem=None):
+    src, Ds, D, Q0 = problem or oracle_problem(spec)
+    return oracle.dose(src, Ds, D, Q0, targets=targets)
+
+
+def peak_lower_bound(spec, times, problem=None):
     """Oracle field at the probe visited last before each time: <= that map's peak."""
-    src = oracle_sources(spec)
-    idx = np.clip(np.searchsorted(src.ts, times, side="left") - 1, 0, src.n - 1)
-    return oracle.field_pairs(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0,
-                              src.xs[idx], src.ys[idx], times)
+    src, Ds, D, Q0 = problem or oracle_problem(spec)
+    tt = np.asarray(times) / spec.dwell_s
+    idx = np.clip(np.searchsorted(src.ts, tt, side="left") - 1, 0, src.n - 1)
+    return oracle.field_pairs(src, Ds, D, Q0, src.xs[idx], src.ys[idx], tt)
 
 
 def assert_fp64(got, ref, what=""):

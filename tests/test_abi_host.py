@@ -36,7 +36,7 @@ def _compare_with_oracle(spec):
         spec.nx, spec.ny, spec.pitch_m, spec.dwell_s, order=spec.order,
         stride=spec.interleave_stride, seed=spec.seed, keep_fraction=spec.keep_fraction,
         mask=spec.mask, custom=spec.custom_visit, flyback=spec.flyback_s,
-        dwell_per_visit=spec.dwell_per_visit)
+        dwell_per_visit=spec.dwell_per_visit, blank=spec.blank_s, blank_per_m=spec.blank_s_per_m)
     np.testing.assert_array_equal(g, og)
     np.testing.assert_array_equal(t, ts)      # same FP64 recipe on both sides: bit-exact
     np.testing.assert_array_equal(tau, taus)
@@ -58,6 +58,32 @@ def test_scan_subsets_flyback_and_dwell_match_oracle():
     _compare_with_oracle(w.ScanSpec(10, 6, order=w.SERPENTINE, flyback_s=1e-7, mask=mask[:6, :10]))
     rng = np.random.default_rng(3)
     _compare_with_oracle(w.ScanSpec(8, 8, dwell_per_visit=10 ** rng.uniform(-7, -5, 64)))
+
+
+def test_scan_blanker_travel_matches_oracle():
+    """Blanker dead time before jumps longer than one pitch: random, subsampled, masked,
+    interleaved and raster-with-flyback scans, constant and distance-proportional parts."""
+    mask = (np.arange(12 * 9).reshape(9, 12) % 5 != 2).astype(np.uint8)
+    rng = np.random.default_rng(4)
+    for spec in (w.ScanSpec(16, 16, order=w.RANDOM, seed=7, blank_s=2e-7),
+                 w.ScanSpec(20, 20, order=w.RANDOM, seed=8, keep_fraction=0.3, blank_s_per_m=300.0),
+                 w.ScanSpec(12, 9, order=w.RASTER, mask=mask, blank_s=1e-7, blank_s_per_m=50.0),
+                 w.ScanSpec(12, 12, order=w.INTERLEAVED, interleave_stride=3, blank_s=5e-8),
+                 w.ScanSpec(10, 6, order=w.SERPENTINE, flyback_s=3e-7, blank_s=1e-7,
+                            keep_fraction=0.6, seed=2),
+                 w.ScanSpec(9, 9, order=w.RANDOM, seed=3, blank_s=1e-7,
+                            dwell_per_visit=10 ** rng.uniform(-7, -5, 81))):
+        _compare_with_oracle(spec)
+    s = b.Scan(w.ScanSpec(4, 4, order=w.RANDOM, seed=1, blank_s=1e-7))
+    _, t, tau = s.visits()
+    assert np.all(np.diff(t) >= tau[:-1] * (1 - 1e-12))    # dead time only adds
+
+
+def test_scan_rejects_negative_blanker_time():
+    for kw in ({"blank_s": -1e-9}, {"blank_s_per_m": -1.0}, {"blank_s": float("nan")}):
+        with pytest.raises(b.DDError) as e:
+            b.Scan(w.ScanSpec(4, 4, **kw))
+        assert e.value.status == b.DD_EINVAL
     _compare_with_oracle(w.ScanSpec(5, 5, order=w.CUSTOM, custom_visit=np.array([24, 0, 12, 3, 3, 7])))
 
 

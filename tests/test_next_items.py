@@ -2,10 +2,9 @@
 import numpy as np
 import pytest
 
-import oracle
 from paper_2507_00294_gb300 import binding as b
 from paper_2507_00294_gb300 import workloads as w
-from parity_util import assert_fp64, assert_mixed, oracle_field, oracle_sources
+from parity_util import assert_fp64, assert_mixed, oracle_dose, oracle_field
 
 pytestmark = pytest.mark.gpu
 
@@ -20,7 +19,7 @@ def test_multi_frame_field_and_dose(cuda, frames):
     ref = oracle_field(spec, pts, times)
     assert_fp64(b.dd_field_at_times(b.Scan(spec), pts, times, "fp64"), ref, "multi-frame fp64")
     assert_mixed(b.dd_field_at_times(b.Scan(spec), pts, times, "mixed"), ref, ref.max(axis=1), "multi-frame")
-    dref = oracle.dose(oracle_sources(spec), spec.sigma_m ** 2, spec.D_m2s, spec.Q0)
+    dref = oracle_dose(spec)
     assert_fp64(b.dd_per_probe_dose(b.Scan(spec), "fp64"), dref, "multi-frame dose")
 
 
@@ -63,3 +62,32 @@ def test_headless_maps(cuda, tmp_path):
         diff = np.abs(img.astype(int) - want.astype(int))
         assert np.all(diff[~edge] == 0), "grey levels differ away from a rounding edge"
         assert np.all(diff <= 1)
+
+
+@pytest.mark.parametrize("spec", [
+    w.ScanSpec(12, 12, order=w.RANDOM, seed=21, blank_s=3e-7),
+    w.ScanSpec(16, 16, order=w.RANDOM, seed=22, keep_fraction=0.4, blank_s=1e-7, blank_s_per_m=400.0,
+               D_m2s=2e-13),
+    w.ScanSpec(10, 10, order=w.RASTER, mask=(np.arange(100).reshape(10, 10) % 7 != 3).astype(np.uint8),
+               blank_s_per_m=1000.0, flyback_s=5e-7),
+    w.ScanSpec(12, 12, order=w.INTERLEAVED, interleave_stride=3, blank_s=2e-7, D_m2s=1e-15),
+])
+def test_blanker_travel_field_and_dose(cuda, spec):
+    """Random, subsampled, masked and interleaved scans with the blanker's dead time before
+    every jump longer than one pitch (constant and distance-proportional): field and dose,
+    both precisions, against the oracle."""
+    assert not np.allclose(np.diff(b.Scan(spec).visits()[1]), spec.dwell_s)   # dead time present
+    pts = w.grid_points(2 * spec.nx, spec.pitch_m / 2)
+    _, ts, taus = b.Scan(spec).visits()
+    end = ts[-1] + taus[-1]
+    times = np.array([0.4 * end, end, 3 * end])
+    ref = oracle_field(spec, pts, times)
+    assert_fp64(b.dd_field_at_times(b.Scan(spec), pts, times, "fp64"), ref, "blanker field fp64")
+    assert_mixed(b.dd_field_at_times(b.Scan(spec), pts, times, "mixed"), ref, ref.max(axis=1),
+                 "blanker field mixed")
+    dref = oracle_dose(spec)
+    d64 = b.dd_per_probe_dose(b.Scan(spec), "fp64")
+    assert d64[0] == 0.0
+    assert_fp64(d64, dref, "blanker dose fp64")
+    dmx = b.dd_per_probe_dose(b.Scan(spec), "mixed")
+    assert_mixed(dmx[1:], dref[1:], dref.max(), "blanker dose mixed")

@@ -194,3 +194,42 @@ def test_field_is_sum_over_visits_and_dose_matches_field():
     whole = oracle.field(src, Ds, D, Q0, px, py, times)
     part = lambda sl: oracle.field(oracle.Sources(xs[sl], ys[sl], ts[sl], taus[sl]), Ds, D, Q0, px, py, times)
     assert np.max(np.abs((part(slice(0, 7)) + part(slice(7, None))) / whole - 1.0)) < 1e-14
+
+
+@pytest.mark.parametrize("r,lag", [(0.0, 1.0), (0.5e-9, 1.0), (0.5e-9, 2.0), (1.1e-9, 37.0), (3e-9, 65015.0),
+                                   (0.7e-9, 0.4)])
+def test_phi_in_dwell_units(r, lag):
+    """Time measured in dwells (t' = t / tau, D' = D tau, Q0' = Q0 tau), the form the parity
+    tests hand to the oracle, gives phi unchanged: Eq. 1/2 see time only through D (t - t_i),
+    D tau and Q0 / D."""
+    si = float(oracle.phi(r * r, lag * TAU, TAU, Ds, D, Q0))
+    dw = float(oracle.phi(r * r, lag, 1.0, Ds, D * TAU, Q0 * TAU))
+    assert dw == pytest.approx(si, rel=2e-14)
+
+
+def test_dose_late_in_a_long_scan_against_40_digits():
+    """Dwell-start dose of visit 65016 of a 256 x 256 serpentine scan (D = 5.58e-14 m^2/s,
+    0.065 s into the scan): the oracle fed with time in dwells against a 40-digit mpmath
+    sum of Eq. 2 over all 65016 earlier visits.  With start times in seconds, each lag
+    carries the rounding of t_k (1.4e-11 of a dwell here), and the oracle was off by
+    3.3e-12 -- beyond the FP64 parity tolerance."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from parity_util import oracle_dose
+    from paper_2507_00294_gb300 import workloads as w
+    spec = w.precision_study(w.SERPENTINE, 3).scan
+    j = 65016
+    got = float(oracle_dose(spec, np.array([j]))[0])
+    order = scan.visit_order(spec.nx, spec.ny, spec.order)
+    mp.mp.dps = 40
+    p, Dm, Dsm, tau = mp.mpf(spec.pitch_m), mp.mpf(spec.D_m2s), mp.mpf(spec.sigma_m) ** 2, mp.mpf(spec.dwell_s)
+    gj = order[j]
+    acc = mp.mpf(0)
+    for i in range(j):
+        gi = order[i]
+        r2 = ((gj % spec.nx - gi % spec.nx) ** 2 + (gj // spec.nx - gi // spec.nx) ** 2) * p * p
+        lag = j - i                       # beam of visit i off since (lag - 1) dwells (Eq. 2)
+        acc += mp.e1(r2 / (2 * Dsm + 4 * Dm * lag * tau)) - mp.e1(r2 / (2 * Dsm + 4 * Dm * (lag - 1) * tau))
+    want = float(acc * spec.Q0 / (4 * mp.pi * Dm))
+    assert got == pytest.approx(want, rel=2e-14)

@@ -60,6 +60,24 @@ def test_visit_times():
     np.testing.assert_allclose(ts, [0, 1e-6, 3e-6], rtol=1e-15)
 
 
+def test_visit_times_with_blanker_travel():
+    """Dead time of the blanker before a jump longer than one pitch (worked by hand on a
+    4-wide grid): 0 -> 1 and 1 -> 5 are neighbours (no dead time), 5 -> 2 is a diagonal
+    jump of sqrt(2) pitches, 2 -> 15 jumps (1, 3) pitches = sqrt(10)."""
+    tau, blank, per_m, p = 1e-6, 0.3e-6, 200.0, 0.5e-9
+    v = [0, 1, 5, 2, 15]
+    ts, taus = scan.visit_times(v, 4, scan.CUSTOM, tau, pitch=p, blank=blank, blank_per_m=per_m)
+    d1 = 0.3e-6 + 200.0 * 0.5e-9 * 1.4142135623730951
+    d2 = 0.3e-6 + 200.0 * 0.5e-9 * 3.1622776601683795
+    np.testing.assert_allclose(ts, [0.0, 1e-6, 2e-6, 3e-6 + d1, 4e-6 + d1 + d2], rtol=1e-15)
+    assert np.all(taus == tau)
+    # with a flyback too, a raster row change pays both
+    v = scan.visit_order(3, 2, scan.RASTER)
+    ts, _ = scan.visit_times(v, 3, scan.RASTER, tau, flyback=0.25e-6, pitch=p, blank=blank)
+    np.testing.assert_allclose(ts, [0, tau, 2 * tau, 3 * tau + 0.25e-6 + blank,
+                                    4 * tau + 0.25e-6 + blank, 5 * tau + 0.25e-6 + blank], rtol=1e-15)
+
+
 def test_sources_positions():
     xs, ys, ts, taus, g = scan.sources(3, 2, 0.5e-9, 1e-6, order=scan.SERPENTINE)
     assert list(g) == [0, 1, 2, 5, 4, 3]

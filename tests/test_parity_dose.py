@@ -2,10 +2,9 @@
 import numpy as np
 import pytest
 
-import oracle
 from paper_2507_00294_gb300 import binding as b
 from paper_2507_00294_gb300 import workloads as w
-from parity_util import assert_fp64, assert_mixed, oracle_sources
+from parity_util import assert_fp64, assert_mixed, oracle_dose
 
 pytestmark = pytest.mark.gpu
 
@@ -22,8 +21,7 @@ def gpu_dose(spec, prec):
                                   w.ScanSpec(23, 19, order=w.RANDOM, seed=8, keep_fraction=0.7),
                                   w.ScanSpec(1, 1), w.ScanSpec(2, 1)])
 def test_dose_full(cuda, spec):
-    src = oracle_sources(spec)
-    ref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0)
+    ref = oracle_dose(spec)
     g64 = gpu_dose(spec, "fp64")
     assert g64[0] == 0.0
     assert_fp64(g64, ref, "dose fp64")
@@ -39,8 +37,7 @@ def test_dose_full(cuda, spec):
                dwell_per_visit=10 ** np.random.default_rng(1).uniform(-7, -5, 81)),
 ])
 def test_dose_general_timing(cuda, spec):
-    src = oracle_sources(spec)
-    ref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0)
+    ref = oracle_dose(spec)
     g64 = gpu_dose(spec, "fp64")
     assert g64[0] == 0.0
     assert_fp64(g64, ref, "general dose fp64")

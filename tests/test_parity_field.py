@@ -158,27 +158,25 @@ def test_grid256_precision_study_sampled(cuda, order, d_index):
     scan and 16x later (t >> tau, where the E1 differences cancel): the field in FP64 and
     FP32-mixed on the whole probe grid, and the dwell-start dose of all 65,536 visits, each
     against the oracle on seeded samples."""
-    import oracle
-    from parity_util import oracle_sources
+    from parity_util import oracle_dose, oracle_problem
     job = w.precision_study(order, d_index)
     spec = job.scan
-    src = oracle_sources(spec)
+    problem = oracle_problem(spec)
     rng = np.random.default_rng(100 + d_index)
     half = GRID256_FIELD_SAMPLES // 2
     ip = np.concatenate([rng.choice(len(job.pts_xy), half, replace=False) for _ in range(2)])
     it = np.repeat([0, 1], half)
-    ref = oracle.field_pairs(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0, job.pts_xy[ip, 0],
-                             job.pts_xy[ip, 1], job.times[it])
-    peak = peak_lower_bound(spec, job.times)
+    ref = oracle_pairs(spec, job.pts_xy, job.times, ip, it, problem)
+    peak = peak_lower_bound(spec, job.times, problem)
     gm = gpu_field(spec, job.pts_xy, job.times, "mixed")
     assert_mixed(gm[it, ip], ref, peak[it], "grid256 %s mixed" % w.ORDER_NAMES[order])
     g64 = gpu_field(spec, job.pts_xy, job.times, "fp64")
     assert_fp64(g64[it, ip], ref, "grid256 %s fp64" % w.ORDER_NAMES[order])
 
-    n = src.n
+    n = problem[0].n
     targets = np.sort(rng.choice(np.arange(1, n), GRID256_DOSE_SAMPLES, replace=False))
     targets = np.unique(np.concatenate([[1, 2, 3, 255, 256, 257, n - 1], targets]))
-    dref = oracle.dose(src, spec.sigma_m ** 2, spec.D_m2s, spec.Q0, targets=targets)
+    dref = oracle_dose(spec, targets, problem)
     scan = b.Scan(spec)
     d64 = b.dd_per_probe_dose(scan, "fp64", device=cuda).cpu().numpy()
     assert d64[0] == 0.0

@@ -13,10 +13,9 @@ at the first failure has already run every other test.
 import numpy as np
 import pytest
 
-import oracle
 from paper_2507_00294_gb300 import binding as b
 from paper_2507_00294_gb300 import workloads as w
-from parity_util import assert_fp64, assert_mixed, oracle_sources
+from parity_util import assert_fp64, assert_mixed, oracle_dose
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +56,7 @@ def test_noalloc_dose_at_the_limit_against_the_oracle(cuda, prec):
     rng = np.random.default_rng(41)
     targets = np.unique(np.concatenate([[1, 2, 127, 128, 129, n - 1],
                                         rng.choice(np.arange(1, n), 1024, replace=False)]))
-    ref = oracle.dose(oracle_sources(spec), spec.sigma_m ** 2, spec.D_m2s, spec.Q0, targets=targets)
+    ref = oracle_dose(spec, targets)
     assert got[0] == 0.0
     if prec == "fp64":
         assert_fp64(got[targets], ref, "noalloc dose 128x128 fp64")
