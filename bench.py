@@ -10,9 +10,10 @@ with t_i < t.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (oracle/, plain C FP64) on a bounded sample of the
-same workload on the host cores.  Under torchrun every rank runs its own copy of the
-workload on its own GPU (weak scaling; no collective on the data path) and rank 0 prints
-one JSON line with the whole-job throughput.
+same workload on the host cores.  Under torchrun the step is split across the ranks
+(strong scaling): each GPU evaluates a range of point tiles at every snapshot and a
+cost-balanced range of dose targets, the outputs are all-gathered once per step, and
+rank 0 prints one JSON line with the whole-job throughput (MAX of the ranks' times).
 """
 import argparse
 import hashlib
@@ -155,10 +156,10 @@ class ClockSampler:
                 "samples": len(sm), "period_ms": self.PERIOD_MS, "window": where}
 
 
-def whole_job(pairs_per_rank_step, steps, rank_total_ms, dist=None, device=None):
-    """Whole-job throughput under weak scaling: every rank evaluates its own copy of the
-    workload; the job's time is the slowest rank's (MAX over ranks), the job's work the
-    sum over ranks.  No collective touches the data path -- only this timing reduction."""
+def whole_job(job_pairs_per_step, steps, rank_total_ms, dist=None, device=None):
+    """Whole-job throughput: the job's work is the whole workload (split across the ranks
+    when there are several: strong scaling), its time the slowest rank's (MAX over ranks).
+    Only this timing reduction and the output gather run as collectives."""
     world = 1
     total_ms = float(rank_total_ms)
     if dist is not None and dist.is_initialized():
@@ -167,7 +168,7 @@ def whole_job(pairs_per_rank_step, steps, rank_total_ms, dist=None, device=None)
         t = torch.tensor([total_ms], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    return pairs_per_rank_step * steps * world / (total_ms / 1e3), total_ms, world
+    return job_pairs_per_step * steps / (total_ms / 1e3), total_ms, world
 
 
 def kernel_source_sha():
@@ -266,12 +267,19 @@ def cpu_oracle_sample(job, seconds, seed=11, threads=0):
     return run, rate, count, cores
 
 
-def bench_batched(dev, stream, runs=10):
-    """The 512-scan batched workload through one tuned, graph-replayed plan (FP32-mixed)."""
+def bench_batched(dev, stream, runs=10, rank=0, world=1, dist=None):
+    """The 512-scan batched workload through one tuned, graph-replayed plan (FP32-mixed).
+    With several ranks the scans are dealt out longest-first by pair count (LPT), each rank
+    runs a plan of its own scans, and the fields are gathered once per run."""
     import torch
     from paper_2507_00294_gb300 import binding as b
+    from paper_2507_00294_gb300 import shard
     from paper_2507_00294_gb300 import workloads as w
-    jobs = w.batched_scans()
+    jobs_all = w.batched_scans()
+    costs = [w.n_visits(j.scan) * len(j.pts_xy) for j in jobs_all]     # one snapshot at the end
+    total_pairs = int(sum(costs))
+    mine = shard.lpt_assign(costs, world)[rank]
+    jobs = [jobs_all[k] for k in mine]
     offs = np.concatenate([[0], np.cumsum([len(j.pts_xy) for j in jobs])]).astype(np.int64)
     pts = torch.from_numpy(np.ascontiguousarray(np.concatenate([j.pts_xy for j in jobs]))).to(dev)
     times = np.array([j.times[0] for j in jobs])
@@ -279,26 +287,41 @@ def bench_batched(dev, stream, runs=10):
     plan = b.Batch(scans, offs, times, "mixed")
     variant = plan.tune(pts)
     out = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
-    for _ in range(2):
+    sizes = None
+    if world > 1:
+        n_out = torch.tensor([int(offs[-1])], device=dev)
+        allsz = [torch.zeros_like(n_out) for _ in range(world)]
+        dist.all_gather(allsz, n_out)
+        sizes = [int(x.item()) for x in allsz]
+        ranges = [(0, sz) for sz in sizes]
+
+    def run():
         plan.run(pts, out=out, stream=stream)
+        if world > 1:
+            shard.gather_vector(out, ranges, rank, dist)
+
+    for _ in range(2):
+        run()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ev = []
     for k in range(runs):
         flush.fill_(float(k))
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        plan.run(pts, out=out, stream=stream)
+        run()
         z.record(stream)
         ev.append((a, z))
     torch.cuda.synchronize(dev)
-    ms = sum(a.elapsed_time(z) for a, z in ev) / runs
+    value, ms_total, _ = whole_job(total_pairs, runs, sum(a.elapsed_time(z) for a, z in ev), dist, dev)
     info = plan.info()
     plan.close()
-    return {"value": info["pairs"] / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "runs": runs,
-            "pairs_per_run": info["pairs"], "scans": len(jobs), "work_items": info["items"],
-            "tuned_variant": variant, "workload": "512 scans, n ~ U{32..128}, D log-U[1e-15,1e-12], "
+    return {"value": value, "unit": UNIT, "ms_per_run": ms_total / runs, "runs": runs,
+            "pairs_per_run": total_pairs, "rank_pairs_per_run": info["pairs"], "scans": len(jobs_all),
+            "rank_scans": len(jobs), "work_items": info["items"], "tuned_variant": variant,
+            "workload": "512 scans, n ~ U{32..128}, D log-U[1e-15,1e-12], "
             "dwell log-U[1e-7,1e-5] s, sigma U[0.05,0.2] nm, keep U[0.1,1], random order, final field on the n x n grid",
-            "launch": "persistent kernel, atomic work claim, CUDA graph replay"}
+            "launch": "persistent kernel, atomic work claim, CUDA graph replay" +
+                      (", scans split over %d GPUs longest-first, one gather per run" % world if world > 1 else "")}
 
 
 def bench_runtime_curve(dev, stream, sizes=(8, 16, 20, 32, 64), frames=(1e-6, 10e-6), reps=5):
@@ -430,7 +453,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": job.name, "points": len(job.pts_xy), "snapshots": len(job.times),
                    "visits": n},
@@ -445,6 +468,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     from paper_2507_00294_gb300 import binding as b
+    from paper_2507_00294_gb300 import shard
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
@@ -457,16 +481,27 @@ def run_ours(args):
     job, n, field_pairs, dose_pairs = workload()
     pairs_step = field_pairs + dose_pairs
     scan = b.Scan(job.scan)
-    pts = torch.from_numpy(job.pts_xy).to(dev)
     times = np.ascontiguousarray(job.times)
-    out = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, device=dev)
-    dose = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # Under torchrun the step is split (strong scaling): each rank evaluates a contiguous
+    # range of whole point tiles at every snapshot and a cost-balanced range of dose
+    # targets, then one all-gather of the output rows (the only collective on the path).
+    n_pts = len(job.pts_xy)
+    pr, dr = shard.point_ranges(n_pts, world), shard.dose_ranges(n, world)
+    (p0, p1), (j0, j1) = pr[rank], dr[rank]
+    pts = torch.from_numpy(np.ascontiguousarray(job.pts_xy[p0:p1])).to(dev)
+    out = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
+    dose = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
+    rank_field_pairs = field_pairs // n_pts * (p1 - p0)     # every point has the same pair count
 
     def step(prec):
         b.dd_field_at_times(scan, pts, times, prec, out=out, stream=stream)
-        b.dd_per_probe_dose(scan, prec, out=dose, stream=stream)
+        if world == 1:
+            b.dd_per_probe_dose(scan, prec, out=dose, stream=stream)
+            return out, dose
+        b.dd_per_probe_dose_range(scan, j0, j1, prec, out=dose, stream=stream)
+        return shard.gather_columns(out, pr, rank, dist), shard.gather_vector(dose, dr, rank, dist)
 
     for _ in range(args.warmup):
         step("mixed")
@@ -497,7 +532,7 @@ def run_ours(args):
     fl, fms = prof.get("field_mixed", (0, 0.0))
     avg_ms = fms / max(1, fl)
     fpp, mpp, culled = ops_per_pair(job)
-    rate = field_pairs / (avg_ms / 1e3) if fl else None
+    rate = rank_field_pairs / (avg_ms / 1e3) if fl else None
     traffic = recorded_traffic("field_mixed")
     # the pair term needs FP32 issue and one MUFU ex2: report the pipe this algorithm's mix
     # binds (the larger fraction), with the other beside it
@@ -512,7 +547,7 @@ def run_ours(args):
     bind, other = (mufu, fp32) if (mufu["frac"] or 0) >= (fp32["frac"] or 0) else (fp32, mufu)
     roofline = {"bound": "alu", "kernel": "field_mixed", "pipe": "mufu" if bind is mufu else "fp32",
                 "achieved": bind["achieved"], "peak": bind["peak"], "unit": bind["unit"], "frac": bind["frac"],
-                "traffic": traffic, "avg_launch_ms": avg_ms, "pairs_per_launch": field_pairs,
+                "traffic": traffic, "avg_launch_ms": avg_ms, "pairs_per_launch": rank_field_pairs,
                 "kernel_pairs_per_s": rate, "ops_per_pair": bind["per_pair"], "peak_note": bind["peak_note"],
                 "culled_pair_fraction": round(culled, 5),
                 "culled_note": "pair-terms with a >= 87 (below the FP32 normal range) are counted in the "
@@ -524,13 +559,14 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32-mixed", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32-mixed", "data": "synthetic",
         "config": {"workload": job.name, "scan": "64x64 raster, pitch 0.5 nm, sigma 0.1 nm, "
-                   "D 6e-14 m^2/s, Q0 1 u/s, dwell 1 us", "points": len(job.pts_xy),
+                   "D 6e-14 m^2/s, Q0 1 u/s, dwell 1 us", "points": n_pts,
                    "snapshots": len(times), "visits": n, "pairs_per_step": pairs_step,
                    "field_pairs": field_pairs, "dose_pairs": dose_pairs, "precision": "mixed",
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
-                   "parallelism": "replica per GPU" if world > 1 else "single GPU"},
+                   "parallelism": ("points and dose targets split over %d GPUs, one all-gather per step"
+                                   % world) if world > 1 else "single GPU"},
         "roofline": roofline, "gpu_launches": launches, "kernel_time_share": shares,
         "clocks": clocks.summary(),
     }
@@ -549,54 +585,75 @@ def run_ours(args):
             z.record(stream)
             e64.append((a, z))
         torch.cuda.synchronize(dev)
-        ms64 = sum(a.elapsed_time(z) for a, z in e64) / len(e64)
-        v64 = pairs_step / (ms64 / 1e3)
-        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": len(e64)}
-        line["mixed_over_fp64"] = (value / world) / v64
-
-        # end to end through the public API with pinned host buffers: scan build, H2D of
-        # the points and the visit list, both kernel chains, D2H of the field and the dose,
-        # both calls on one stream that the step synchronises once at its end (with a
-        # stream and page-locked buffers the field's D2H overlaps the dose's work)
-        pts_h = torch.from_numpy(np.ascontiguousarray(job.pts_xy)).pin_memory().numpy()
-        out_h = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True).numpy()
-        dose_h = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-        e2e_stream = torch.cuda.Stream(dev)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            s2 = b.Scan(job.scan)
-            b.dd_field_at_times(s2, pts_h, times, "mixed", out=out_h, stream=e2e_stream)
-            b.dd_per_probe_dose(s2, "mixed", out=dose_h, stream=e2e_stream)
-            e2e_stream.synchronize()
-            s2.close()
-        e2e_s = time.perf_counter() - t0
-        line["e2e"] = {"value": pairs_step * args.steps / e2e_s * world, "unit": UNIT,
-                       "h2d_bytes_per_step": int(pts_h.nbytes + 4 * n * 8),
-                       "d2h_bytes_per_step": int(out_h.nbytes + dose_h.nbytes),
-                       "ms_per_step": e2e_s / args.steps * 1e3}
-
-        line["batched"] = bench_batched(dev, stream)
-        line["runtime_curve"] = bench_runtime_curve(dev, stream)
-        if not args.no_surrogate:
-            line["surrogate"] = bench_surrogate(dev, args.surrogate_maps, args.surrogate_epochs)
+        v64, _, _ = whole_job(pairs_step, len(e64), sum(a.elapsed_time(z) for a, z in e64), dist, dev)
+        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": pairs_step / v64 * 1e3, "steps": len(e64)}
+        line["mixed_over_fp64"] = value / v64
+        line["e2e"] = bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, pr, dr)
+        line["batched"] = bench_batched(dev, stream, rank=rank, world=world, dist=dist)
+        if world == 1:
+            line["runtime_curve"] = bench_runtime_curve(dev, stream)
+            if not args.no_surrogate:
+                line["surrogate"] = bench_surrogate(dev, args.surrogate_maps, args.surrogate_epochs)
 
         if rank == 0 and world == 1:
             run, rate, count, cores = cpu_oracle_sample(job, args.cpu_seconds)
             p, t = run(count, 7)
             run1, _, count1, _ = cpu_oracle_sample(job, args.cpu_seconds / 3, threads=1)
-            p1, t1 = run1(count1, 8)
+            p1_, t1_ = run1(count1, 8)
             line["cpu_baseline"] = {
                 "value": p / t, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": "%d seeded (point, snapshot) pairs of the workload, %d pair-terms, "
                           "%.1f s, field only" % (count, p, t),
-                "single_thread": {"value": p1 / t1, "unit": UNIT, "cores": 1,
-                                  "sample": "%d seeded pairs, %d pair-terms, %.1f s" % (count1, p1, t1)}}
+                "single_thread": {"value": p1_ / t1_, "unit": UNIT, "cores": 1,
+                                  "sample": "%d seeded pairs, %d pair-terms, %.1f s" % (count1, p1_, t1_)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, pr, dr):
+    """End to end through the public API with pinned host buffers: scan build, H2D of the
+    points and the visit list, both kernel chains, D2H of the field and the dose.  One GPU:
+    both calls on one stream, synchronised once per step (with a stream and page-locked
+    buffers the field's D2H overlaps the dose's work).  Several: each rank copies in its
+    own points, the device results are gathered, and rank 0 copies out the whole field and
+    dose."""
+    import torch
+    (p0, p1), (j0, j1) = pr[rank], dr[rank]
+    pts_h = torch.from_numpy(np.ascontiguousarray(job.pts_xy[p0:p1])).pin_memory().numpy()
+    out_h = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True)
+    dose_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    e2e_stream = torch.cuda.Stream(dev)
+    if world > 1:
+        out_d = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
+        dose_d = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s2 = b.Scan(job.scan)
+        if world == 1:
+            b.dd_field_at_times(s2, pts_h, times, "mixed", out=out_h.numpy(), stream=e2e_stream)
+            b.dd_per_probe_dose(s2, "mixed", out=dose_h.numpy(), stream=e2e_stream)
+        else:
+            with torch.cuda.stream(e2e_stream):
+                b.dd_field_at_times(s2, pts_h, times, "mixed", out=out_d, stream=e2e_stream)
+                b.dd_per_probe_dose_range(s2, j0, j1, "mixed", out=dose_d, stream=e2e_stream)
+                f = shard.gather_columns(out_d, pr, rank, dist)
+                d = shard.gather_vector(dose_d, dr, rank, dist)
+                if rank == 0:
+                    out_h.copy_(f, non_blocking=True)
+                    dose_h.copy_(d, non_blocking=True)
+        e2e_stream.synchronize()
+        s2.close()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    v, ms, _ = whole_job(pairs_step, args.steps, e2e_ms, dist, dev)
+    return {"value": v, "unit": UNIT, "h2d_bytes_per_step": int(len(job.pts_xy) * 16 + world * 4 * n * 8),
+            "d2h_bytes_per_step": int(out_h.numel() * 8 + dose_h.numel() * 8),
+            "ms_per_step": ms / args.steps}
 
 
 def main():

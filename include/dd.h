@@ -143,6 +143,18 @@ dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy_m, int64_t
 dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, double *out,
                             void *cuda_stream);
 
+/* Dwell-start dose of the visits j0 <= j < j1 only (0 <= j0 <= j1 <= n_visits):
+     out[j - j0] = psi_{j-1}(r_j, t_j)   (as dd_per_probe_dose, Eq. 5 at r_j, t_j)
+   The paper partitions the sum into independent tasks over subsets of the probe positions
+   (Sec. 3); this is that partition for the dose, so that several GPUs (or processes)
+   can each evaluate a range of targets.  Visit j's dose costs about j pair terms, so equal
+   work needs ranges that shrink towards the end of the scan.  out: host or device,
+   j1 - j0 doubles; j1 == j0 is a no-op.  Results agree with dd_per_probe_dose within the
+   precision's rounding (the lag blocks are sized for the range, so the summation order
+   may differ).  Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA. */
+dd_status dd_per_probe_dose_range(const dd_scan *scan, dd_precision prec, int64_t j0, int64_t j1,
+                                  double *out, void *cuda_stream);
+
 /* Allocation-free variant of dd_per_probe_dose (the paper has no counterpart: this
    entry point exists for callers that cannot allocate device memory while they run,
    e.g. an acquisition loop that reserves its whole GPU memory budget before the scan

@@ -62,6 +62,8 @@ def load(build_if_missing=True):
     lib.dd_field_at_times.argtypes = [_VP, _VP, _I64, _VP, _I64, ctypes.c_int, _VP, _VP]
     lib.dd_per_probe_dose.argtypes = [_VP, ctypes.c_int, _VP, _VP]
     lib.dd_field_batch.argtypes = [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
+    lib.dd_per_probe_dose_range.argtypes = [_VP, ctypes.c_int, _I64, _I64, _VP, _VP]
+    lib.dd_per_probe_dose_range.restype = ctypes.c_int
     lib.dd_per_probe_dose_noalloc.argtypes = [_VP, ctypes.c_int, _VP, _VP]
     lib.dd_per_probe_dose_noalloc.restype = ctypes.c_int
     lib.dd_batch_create.argtypes = [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)]
@@ -245,6 +247,21 @@ def dd_per_probe_dose(scan, prec="mixed", out=None, stream=None, device=None):
     o, ko = _ptr(out, np.float64)
     _check(load().dd_per_probe_dose(scan.handle, PRECISIONS[prec], o, _stream(stream, out)),
            "dd_per_probe_dose")
+    return out
+
+
+def dd_per_probe_dose_range(scan, j0, j1, prec="mixed", out=None, stream=None, device=None):
+    """Dwell-start dose of visits j0 <= j < j1 (out[j - j0])."""
+    m = int(j1) - int(j0)
+    if out is None:
+        if device is not None:
+            import torch
+            out = torch.empty(m, dtype=torch.float64, device=device)
+        else:
+            out = np.empty(m, dtype=np.float64)
+    o, ko = _ptr(out, np.float64)
+    _check(load().dd_per_probe_dose_range(scan.handle, PRECISIONS[prec], int(j0), int(j1), o,
+                                           _stream(stream, out)), "dd_per_probe_dose_range")
     return out
 
 

@@ -218,16 +218,17 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
 // before the CTA's last target are staged through shared memory in visit order.
 template <typename Cfg>
 __global__ void __launch_bounds__(128)
-dose_general_kernel(const double *__restrict__ src, int64_t n, double s, double kappa,
-                    double *__restrict__ out_partial) {
+dose_general_kernel(const double *__restrict__ src, int64_t n, int64_t j0, int64_t j1, double s,
+                    double kappa, double *__restrict__ out_partial) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
     constexpr int TILE = 64;
     __shared__ double s_x[TILE], s_y[TILE], s_t[TILE], s_tau[TILE];
     const double *X = src, *Y = src + n, *T = src + 2 * n, *TAU = src + 3 * n;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t j_last = min(n, (int64_t)(blockIdx.x + 1) * blockDim.x) - 1;
-    const bool live = j < n;
+    // targets j0 + [blockIdx.x * blockDim.x, ...) of the range [j0, j1)
+    const int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j_last = min(j1, j0 + (int64_t)(blockIdx.x + 1) * blockDim.x) - 1;
+    const bool live = j < j1;
     const double xj = live ? X[j] : 0.0, yj = live ? Y[j] : 0.0, tj = live ? T[j] : 0.0;
     double tot = 0.0;
     for (int64_t i0 = 0; i0 < j_last; i0 += TILE) {
@@ -249,7 +250,7 @@ dose_general_kernel(const double *__restrict__ src, int64_t n, double s, double 
         }
         tot += (double)acc;
     }
-    if (live) out_partial[j] = tot;
+    if (live) out_partial[j - j0] = tot;
 }
 
 __global__ void scale_kernel(const double *__restrict__ v, int64_t n, double pref, double *__restrict__ out) {
@@ -257,20 +258,20 @@ __global__ void scale_kernel(const double *__restrict__ v, int64_t n, double pre
     if (j < n) out[j] = pref * v[j];
 }
 
-// out[j] = pref * sum over the lag blocks of target j.  A block of 256 threads serves 32
+// out[j - j0] = pref * sum over the lag blocks of target j, j in [j0, j1).  A block of 256 threads serves 32
 // targets: lane t of warp q sums the blocks b = q, q + 8, q + 16, ... of target t (in
 // order), and warp 0 adds the eight results in q order -- a fixed association, so the
 // result is deterministic, with eight times the loads in flight of one thread per target.
 constexpr int kDoseReduceSplit = 8;
 template <typename Part>
 __global__ void __launch_bounds__(32 * kDoseReduceSplit)
-dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int tile, int lb, double pref,
-                   double *__restrict__ out) {
+dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int64_t j0, int64_t j1, int tile, int lb,
+                   double pref, double *__restrict__ out) {
     __shared__ double s_sum[kDoseReduceSplit][32];
     const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t j = j0 + (int64_t)blockIdx.x * 32 + lane;
     double v = 0.0;
-    if (j < n) {
+    if (j < j1) {
         // blocks written for target j: every lag block that starts below the tile's last target
         const int64_t tile_last = min(n, (j / tile + 1) * tile) - 1;
         const int64_t nb = dose_blocks(tile_last + 1, lb);
@@ -281,11 +282,11 @@ dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int tile, int lb
     }
     s_sum[q][lane] = v;
     __syncthreads();
-    if (q == 0 && j < n) {
+    if (q == 0 && j < j1) {
         double t = 0.0;
 #pragma unroll
         for (int k = 0; k < kDoseReduceSplit; ++k) t += s_sum[k][lane];
-        out[j] = pref * t;
+        out[j - j0] = pref * t;
     }
 }
 
@@ -297,7 +298,7 @@ namespace {
 // kDoseLBMin lags, that still gives at least 8 items per SM (the triangle of a few
 // thousand visits is otherwise cut into too few CTAs to fill the GPU).
 template <typename Cfg>
-int dose_lag_block(int64_t n) {
+int dose_lag_block(int64_t n, int64_t tile_lo, int64_t tile_hi) {
     constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -308,8 +309,8 @@ int dose_lag_block(int64_t n) {
     int lb = Cfg::kDoseLB;
     while (lb > Cfg::kDoseLBMin) {
         int64_t items = 0;
-        for (int64_t t0 = 0; t0 < n; t0 += TILE) {
-            const int64_t t1 = std::min(n, t0 + TILE);
+        for (int64_t t = tile_lo; t < tile_hi; ++t) {
+            const int64_t t1 = std::min(n, t * TILE + TILE);
             items += ddk::dose_blocks(t1, lb);
         }
         if (items >= 8 * (int64_t)sms) break;
@@ -327,28 +328,31 @@ inline int64_t dose_item_pairs(int64_t t0, int64_t t1, int64_t k0, int64_t k1) {
     return full + (a <= b ? (b - a + 1) * t1 - (a + b) * (b - a + 1) / 2 : 0);
 }
 
+// Dose of the targets [j0, j1): the target tiles that overlap the range are evaluated
+// whole, and only the range is reduced and written (out[j - j0]).
 template <typename Cfg>
-dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
+dd_status run_dose(const dd_scan *scan, int64_t j0, int64_t j1, double *out, cudaStream_t stream) {
     using Rec = typename Cfg::Rec;
     const int64_t n = scan->n;
+    const int64_t m = j1 - j0;
     const dd::MemKind out_kind = dd::memory_kind(out);
     const bool out_host = out_kind != dd::MemKind::Device;
     const bool out_copy = out_host;
     constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
-    const int lb = dose_lag_block<Cfg>(n);
-    const int64_t n_tiles = (n + TILE - 1) / TILE;
+    const int64_t tile_lo = j0 / TILE, tile_hi = (j1 + TILE - 1) / TILE;
+    const int lb = dose_lag_block<Cfg>(n, tile_lo, tile_hi);
     int64_t n_items = 0;
-    for (int64_t t = 0; t < n_tiles; ++t) {
+    for (int64_t t = tile_lo; t < tile_hi; ++t) {
         const int64_t t1 = std::min(n, t * TILE + TILE);
         n_items += ddk::dose_blocks(t1, lb);                          // lags 1 .. t1-1
     }
-    const int64_t nblk = ddk::dose_blocks(n, lb);
+    const int64_t nblk = ddk::dose_blocks(std::min(n, tile_hi * TILE), lb);
     size_t bytes = 0;
     auto add = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
     add((size_t)std::max<int64_t>(n, 1) * sizeof(Rec));
     add((size_t)n_items * sizeof(int2) + 16);
     add((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(typename Cfg::Real));
-    if (out_copy) add((size_t)n * sizeof(double));
+    if (out_copy) add((size_t)m * sizeof(double));
     bytes += 256;
 
     dd_status st = DD_OK;
@@ -369,7 +373,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
     int2 *d_items = (int2 *)take((size_t)n_items * sizeof(int2) + 16);
     using Part = typename Cfg::Real;
     Part *d_part = (Part *)take((size_t)std::max<int64_t>(nblk, 1) * n * sizeof(Part));
-    double *out_dev = out_copy ? (double *)take((size_t)n * sizeof(double)) : out;
+    double *out_dev = out_copy ? (double *)take((size_t)m * sizeof(double)) : out;
 
     // work list, kept until the stream has consumed its upload (pinned staging when available)
     struct Keep {
@@ -384,7 +388,7 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         DD_CUDA_TRY(cudaGetLastError());
         std::vector<std::pair<int64_t, int2>> its;
         its.reserve((size_t)n_items);
-        for (int64_t t = 0; t < n_tiles; ++t) {
+        for (int64_t t = tile_lo; t < tile_hi; ++t) {
             const int64_t t0 = t * TILE, t1 = std::min(n, t0 + TILE);
             if (t1 - 1 < 1) continue;                                // target 0 has no source
             const int64_t nb = ddk::dose_blocks(t1, lb);             // lags 1 .. t1-1
@@ -406,10 +410,10 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
         DD_CUDA_TRY(cudaGetLastError());
     }
     DD_PROFILED("dose_reduce", stream,
-                (ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out_dev)));
+                (ddk::dose_reduce_kernel<Part><<<(unsigned)((m + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, j0, j1, TILE, lb, scan->pref, out_dev)));
     DD_CUDA_TRY(cudaGetLastError());
     if (out_copy)
-        DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
     DD_CUDA_TRY(dd::defer_release(stream, keep, [](void *p) { delete static_cast<Keep *>(p); }));
     if (dd::host_sync_needed(stream, {out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
@@ -417,15 +421,16 @@ dd_status run_dose(const dd_scan *scan, double *out, cudaStream_t stream) {
 }
 
 template <typename Cfg>
-dd_status run_dose_general(const dd_scan *scan, double *out, cudaStream_t stream) {
+dd_status run_dose_general(const dd_scan *scan, int64_t j0, int64_t j1, double *out, cudaStream_t stream) {
     const int64_t n = scan->n;
+    const int64_t m = j1 - j0;
     const dd::MemKind out_kind = dd::memory_kind(out);
     const bool out_host = out_kind != dd::MemKind::Device;
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
     void *ws = nullptr;
-    const size_t bytes = (size_t)n * sizeof(double) * (out_host ? 2 : 1) + 512;
+    const size_t bytes = (size_t)m * sizeof(double) * (out_host ? 2 : 1) + 512;
     cudaError_t err = dd::workspace_alloc(&ws, bytes, stream);
     if (err != cudaSuccess) {
         cudaGetLastError();
@@ -433,19 +438,35 @@ dd_status run_dose_general(const dd_scan *scan, double *out, cudaStream_t stream
                         std::string("dose workspace allocation: ") + cudaGetErrorString(err));
     }
     double *sums = (double *)ws;
-    double *out_dev = out_host ? sums + n : out;
+    double *out_dev = out_host ? sums + m : out;
     DD_PROFILED(Cfg::kDoseName, stream,
-                (ddk::dose_general_kernel<Cfg><<<(unsigned)((n + 127) / 128), 128, 0, stream>>>(
-                    src, n, scan->s, scan->kappa, sums)));
+                (ddk::dose_general_kernel<Cfg><<<(unsigned)((m + 127) / 128), 128, 0, stream>>>(
+                    src, n, j0, j1, scan->s, scan->kappa, sums)));
     DD_CUDA_TRY(cudaGetLastError());
     DD_PROFILED("dose_scale", stream,
-                (ddk::scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sums, n, scan->pref, out_dev)));
+                (ddk::scale_kernel<<<(unsigned)((m + 255) / 256), 256, 0, stream>>>(sums, m, scan->pref, out_dev)));
     DD_CUDA_TRY(cudaGetLastError());
     if (out_host)
-        DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, stream));
     DD_CUDA_TRY(cudaFreeAsync(ws, stream));
     if (dd::host_sync_needed(stream, {out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
+}
+
+}  // namespace
+
+namespace {
+
+dd_status dose_range(const dd_scan *scan, dd_precision prec, int64_t j0, int64_t j1, double *out,
+                     void *cuda_stream) {
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    if (!scan->uniform) {
+        // per-visit dwells, flyback or blanker travel: no lag table, coefficients per pair
+        if (prec == DD_MIXED) return run_dose_general<ddk::CfgMixed>(scan, j0, j1, out, stream);
+        return run_dose_general<ddk::CfgF64>(scan, j0, j1, out, stream);
+    }
+    if (prec == DD_MIXED) return run_dose<ddk::CfgMixed>(scan, j0, j1, out, stream);
+    return run_dose<ddk::CfgF64>(scan, j0, j1, out, stream);
 }
 
 }  // namespace
@@ -454,14 +475,20 @@ extern "C" dd_status dd_per_probe_dose(const dd_scan *scan, dd_precision prec, d
     dd::clear_error();
     if (!scan || !out) return dd::fail(DD_EINVAL, "dd_per_probe_dose: NULL argument");
     if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_per_probe_dose: unknown precision");
-    cudaStream_t stream = (cudaStream_t)cuda_stream;
-    if (!scan->uniform) {
-        // per-visit dwells or flyback: no lag table, coefficients per pair
-        if (prec == DD_MIXED) return run_dose_general<ddk::CfgMixed>(scan, out, stream);
-        return run_dose_general<ddk::CfgF64>(scan, out, stream);
-    }
-    if (prec == DD_MIXED) return run_dose<ddk::CfgMixed>(scan, out, stream);
-    return run_dose<ddk::CfgF64>(scan, out, stream);
+    return dose_range(scan, prec, 0, scan->n, out, cuda_stream);
+}
+
+extern "C" dd_status dd_per_probe_dose_range(const dd_scan *scan, dd_precision prec, int64_t j0, int64_t j1,
+                                             double *out, void *cuda_stream) {
+    dd::clear_error();
+    if (!scan) return dd::fail(DD_EINVAL, "dd_per_probe_dose_range: NULL scan");
+    if (prec != DD_FP64 && prec != DD_MIXED)
+        return dd::fail(DD_EINVAL, "dd_per_probe_dose_range: unknown precision");
+    if (j0 < 0 || j1 < j0 || j1 > scan->n)
+        return dd::fail(DD_EINVAL, "dd_per_probe_dose_range: need 0 <= j0 <= j1 <= n_visits");
+    if (j1 == j0) return DD_OK;
+    if (!out) return dd::fail(DD_EINVAL, "dd_per_probe_dose_range: NULL output");
+    return dose_range(scan, prec, j0, j1, out, cuda_stream);
 }
 
 // ---------------------------------------------------------------------------------
@@ -579,7 +606,7 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
         ddk::dose_kernel<Cfg><<<(unsigned)count, Cfg::kThreads, 0, stream>>>(d_x, d_y, n, d_rec, d_items, lb, d_part, d_f);
         DD_CUDA_TRY(cudaGetLastError());
     }
-    ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, TILE, lb, scan->pref, out);
+    ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, 0, n, TILE, lb, scan->pref, out);
     DD_CUDA_TRY(cudaGetLastError());
     // the work list above lives in this thread's fixed host storage, which the next call
     // on this thread rewrites: wait until the stream has copied it
