@@ -43,6 +43,17 @@ FLOPS_SERIES = {2: 6.25, 4: 10.25, 8: 19.25, 12: 27.25}
 FLOPS_GENERAL = 56.25
 FLOPS_ZERO = 1.25
 MUFU_SERIES, MUFU_GENERAL = 1.0, 4.0
+# The same on a grid tile (128 columns x 4 rows x 4 snapshots, dd_field_on_grid): dx and
+# dx^2 cost 2 flops per (column, visit), shared by 16 pairs (0.125); rho^2 = dx^2 + dy^2 one
+# FMA per (point, visit), shared by 4 snapshots (0.5).  A degree-2 pair is X Y (+ A B):
+# the column factor X = 2^(g_0 + g_1x dx^2 + g_2x dx^4) costs 2 FMAs and one ex2 per
+# (column, visit, snapshot), shared by the 4 rows (1 flop, 0.25 ex2 per pair); the row
+# factor Y is shared by 128 columns (~0.02 flops, 0.008 ex2); the pair itself one FMA (2
+# flops); where the cross term is needed, A = X (2 ln2 g_2x) dx^2 (3 multiplies per
+# column, visit and snapshot: 0.75) and one more FMA (2).  Higher degrees as above with
+# the grid's rho^2 (0.625 instead of 1.25).
+GRID_FLOPS_SEP1, GRID_FLOPS_SEP2, GRID_MUFU_SEP = 3.17, 5.92, 0.258
+GRID_FLOPS_RHO, GRID_FLOPS_ZERO = 0.625, 0.125
 # FP32 peak from the unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # MUFU ex2 peak: 32 per clock per SM (GB300 doubles the SFU exponential rate of B200; a
@@ -171,9 +182,18 @@ def whole_job(job_pairs_per_step, steps, rank_total_ms, dist=None, device=None):
     return job_pairs_per_step * steps / (total_ms / 1e3), total_ms, world
 
 
-def kernel_source_sha():
+# Per kernel: the ncu summary under profiles/ that records its DRAM traffic, and the
+# sources whose text fixes its code (the summary's source_sha is their hash).
+PROFILED = {
+    "field_mixed": ("field_mixed_raster64.md", ("dd_field_impl.cuh", "dd_e1.cuh", "dd_coef.cuh")),
+    "field_grid_mixed": ("field_grid_mixed_raster64.md",
+                         ("dd_field_grid.cuh", "dd_field_impl.cuh", "dd_e1.cuh", "dd_coef.cuh")),
+}
+
+
+def kernel_source_sha(kernel):
     h = hashlib.sha256()
-    for name in ("dd_field_impl.cuh", "dd_e1.cuh", "dd_coef.cuh", "dd_field.cu"):
+    for name in PROFILED[kernel][1]:
         with open(os.path.join(ROOT, "paper_2507_00294_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -181,7 +201,7 @@ def kernel_source_sha():
 
 def recorded_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
-    path = os.path.join(ROOT, "profiles", "field_mixed_raster64.md")
+    path = os.path.join(ROOT, "profiles", PROFILED[kernel][0])
     if not os.path.exists(path):
         return None
     vals = {}
@@ -189,7 +209,7 @@ def recorded_traffic(kernel):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel") != kernel or vals.get("source_sha") != kernel_source_sha():
+    if vals.get("kernel") != kernel or vals.get("source_sha") != kernel_source_sha(kernel):
         return None
     try:
         return int(vals["dram_bytes_per_launch"])
@@ -197,11 +217,28 @@ def recorded_traffic(kernel):
         return None
 
 
-def ops_per_pair(job, samples=400_000, seed=5):
+def cumulant_l2(r):
+    """l_2 of the FP32 record's exponent series (half the variance of s under the weight
+    r / (1 + r s) on [0, 1]), by a 2000-node midpoint rule: enough to place a pair in the
+    degree-2 class with or without the cross term."""
+    sg = (np.arange(2000) + 0.5) / 2000
+    out = np.empty(len(r))
+    for k0 in range(0, len(r), 4096):
+        rr = r[k0:k0 + 4096, None]
+        wgt = rr / (1 + rr * sg[None, :])
+        m0 = wgt.mean(1)
+        m1 = (wgt * sg).mean(1) / m0
+        m2 = (wgt * sg ** 2).mean(1) / m0
+        out[k0:k0 + 4096] = 0.5 * (m2 - m1 ** 2)
+    return out
+
+
+def ops_per_pair(job, samples=400_000, seed=5, grid=False):
     """Algorithmic FP32 FLOPs and MUFU operations per pair-term of the field kernel on this
     workload: the cost of the cheapest path that meets the FP32 accuracy target for each
-    pair (series degree from that pair's own h, zero when a >= 87), averaged over seeded
-    pairs."""
+    pair (series degree from that pair's own h, zero when a >= 87; on a grid, the degree-2
+    pairs in their separable form, with the cross term where its size 2 g_2x dx^2 dy^2
+    exceeds the 2.5e-7 budget), averaged over seeded pairs."""
     from paper_2507_00294_gb300 import workloads as w
     s = job.scan
     rng = np.random.default_rng(seed)
@@ -228,15 +265,32 @@ def ops_per_pair(job, samples=400_000, seed=5):
                                    np.where(h <= 1.25, FLOPS_SERIES[8],
                                             np.where(h <= 2.0, FLOPS_SERIES[12], FLOPS_GENERAL)))))
     m = np.where(zero, 0.0, np.where(h <= 2.0, MUFU_SERIES, MUFU_GENERAL))
+    if grid:
+        # grid tile: rho^2 shared more widely, degree 2 in the separable form
+        dqp = (1.0 / w0 - 1.0 / w1) * s.pitch_m ** 2                     # dq in pitch units
+        rr = np.where(dt <= tau, 4 * D * dt, 4 * D * tau) / w0             # r = w1 / w0 - 1
+        d2 = h <= 0.04
+        cross = np.zeros(samples)
+        cross[d2] = (2 * 1.4426950408889634 * cumulant_l2(rr[d2]) * dqp[d2] ** 2
+                     * (dx[d2] / s.pitch_m) ** 2 * (dy[d2] / s.pitch_m) ** 2)
+        sep = np.where(cross <= 2.5e-7, GRID_FLOPS_SEP1, GRID_FLOPS_SEP2)
+        f = np.where(zero, GRID_FLOPS_ZERO, np.where(d2, sep, f - FLOPS_ZERO + GRID_FLOPS_RHO))
+        m = np.where(zero, 0.0, np.where(d2, GRID_MUFU_SEP, m))
     wgt = nact[np.arange(samples)]               # pairs are sampled per snapshot: weight by n_active
     return (float(np.sum(f * wgt) / np.sum(wgt)), float(np.sum(m * wgt) / np.sum(wgt)),
             float(np.sum(zero * wgt) / np.sum(wgt)))
 
 
 def workload():
+    """The 64x64 raster job, its evaluation grid (x0, y0, dx, dy, columns, rows) -- the
+    job's 128 x 128 points at pitch / 2 are that grid in row-major order -- and the pair
+    counts of the field and the dose."""
     from paper_2507_00294_gb300 import workloads as w
     job = w.raster_64_supersampled()
     n = w.n_visits(job.scan)
+    half = job.scan.pitch_m / 2
+    job.extra["grid"] = (0.0, 0.0, half, half, 128, 128)
+    assert np.array_equal(w.grid_points(128, half), job.pts_xy)
     ts = np.arange(n, dtype=np.float64) * job.scan.dwell_s
     field_pairs = w.causal_pairs(ts, job.times, len(job.pts_xy))
     dose_pairs = n * (n - 1) // 2
@@ -484,19 +538,21 @@ def run_ours(args):
     times = np.ascontiguousarray(job.times)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    # Under torchrun the step is split (strong scaling): each rank evaluates a contiguous
-    # range of whole point tiles at every snapshot and a cost-balanced range of dose
-    # targets, then one all-gather of the output rows (the only collective on the path).
+    # The field is evaluated on the job's grid of points (dd_field_on_grid).  Under torchrun
+    # the step is split (strong scaling): each rank evaluates a contiguous range of whole
+    # grid-tile rows at every snapshot and a cost-balanced range of dose targets, then one
+    # all-gather of the output rows (the only collective on the path).
     n_pts = len(job.pts_xy)
-    pr, dr = shard.point_ranges(n_pts, world), shard.dose_ranges(n, world)
-    (p0, p1), (j0, j1) = pr[rank], dr[rank]
-    pts = torch.from_numpy(np.ascontiguousarray(job.pts_xy[p0:p1])).to(dev)
+    x0, y0, gdx, gdy, W, H = job.extra["grid"]
+    rr, dr = shard.row_ranges(H, world), shard.dose_ranges(n, world)
+    pr = [(r0 * W, r1 * W) for r0, r1 in rr]
+    (r0, r1), (p0, p1), (j0, j1) = rr[rank], pr[rank], dr[rank]
     out = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
     dose = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
     rank_field_pairs = field_pairs // n_pts * (p1 - p0)     # every point has the same pair count
 
     def step(prec):
-        b.dd_field_at_times(scan, pts, times, prec, out=out, stream=stream)
+        b.dd_field_on_grid(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, prec, out=out, stream=stream)
         if world == 1:
             b.dd_per_probe_dose(scan, prec, out=dose, stream=stream)
             return out, dose
@@ -528,12 +584,12 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
 
-    # roofline of the dominant kernel (field_mixed), from its own events in the timed region
-    fl, fms = prof.get("field_mixed", (0, 0.0))
+    # roofline of the dominant kernel (field_grid_mixed), from its own events in the timed region
+    fl, fms = prof.get("field_grid_mixed", (0, 0.0))
     avg_ms = fms / max(1, fl)
-    fpp, mpp, culled = ops_per_pair(job)
+    fpp, mpp, culled = ops_per_pair(job, grid=True)
     rate = rank_field_pairs / (avg_ms / 1e3) if fl else None
-    traffic = recorded_traffic("field_mixed")
+    traffic = recorded_traffic("field_grid_mixed")
     # the pair term needs FP32 issue and one MUFU ex2: report the pipe this algorithm's mix
     # binds (the larger fraction), with the other beside it
     fp32 = {"achieved": fpp * rate / 1e12 if rate else None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -545,7 +601,7 @@ def run_ours(args):
     for x in (fp32, mufu):
         x["frac"] = x["achieved"] / x["peak"] if x["achieved"] else None
     bind, other = (mufu, fp32) if (mufu["frac"] or 0) >= (fp32["frac"] or 0) else (fp32, mufu)
-    roofline = {"bound": "alu", "kernel": "field_mixed", "pipe": "mufu" if bind is mufu else "fp32",
+    roofline = {"bound": "alu", "kernel": "field_grid_mixed", "pipe": "mufu" if bind is mufu else "fp32",
                 "achieved": bind["achieved"], "peak": bind["peak"], "unit": bind["unit"], "frac": bind["frac"],
                 "traffic": traffic, "avg_launch_ms": avg_ms, "pairs_per_launch": rank_field_pairs,
                 "kernel_pairs_per_s": rate, "ops_per_pair": bind["per_pair"], "peak_note": bind["peak_note"],
@@ -588,7 +644,9 @@ def run_ours(args):
         v64, _, _ = whole_job(pairs_step, len(e64), sum(a.elapsed_time(z) for a, z in e64), dist, dev)
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": pairs_step / v64 * 1e3, "steps": len(e64)}
         line["mixed_over_fp64"] = value / v64
-        line["e2e"] = bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, pr, dr)
+        line["e2e"] = bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, rr, pr, dr)
+        if world == 1:
+            line["field_point_list"] = bench_point_list(b, job, times, scan, dev, stream, flush, field_pairs)
         line["batched"] = bench_batched(dev, stream, rank=rank, world=world, dist=dist)
         if world == 1:
             line["runtime_curve"] = bench_runtime_curve(dev, stream)
@@ -613,16 +671,16 @@ def run_ours(args):
     return 0
 
 
-def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, pr, dr):
-    """End to end through the public API with pinned host buffers: scan build, H2D of the
-    points and the visit list, both kernel chains, D2H of the field and the dose.  One GPU:
+def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, rr, pr, dr):
+    """End to end through the public API with page-locked host outputs: scan build (its
+    visit list uploaded on first use), the grid field and the dose, D2H of both.  One GPU:
     both calls on one stream, synchronised once per step (with a stream and page-locked
-    buffers the field's D2H overlaps the dose's work).  Several: each rank copies in its
-    own points, the device results are gathered, and rank 0 copies out the whole field and
-    dose."""
+    buffers the field's D2H overlaps the dose's work).  Several: each rank evaluates its
+    rows and dose targets, the device results are gathered, and rank 0 copies out the
+    whole field and dose."""
     import torch
-    (p0, p1), (j0, j1) = pr[rank], dr[rank]
-    pts_h = torch.from_numpy(np.ascontiguousarray(job.pts_xy[p0:p1])).pin_memory().numpy()
+    x0, y0, gdx, gdy, W, H = job.extra["grid"]
+    (r0, r1), (p0, p1), (j0, j1) = rr[rank], pr[rank], dr[rank]
     out_h = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True)
     dose_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
     e2e_stream = torch.cuda.Stream(dev)
@@ -636,11 +694,12 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
     for k in range(args.steps):
         s2 = b.Scan(job.scan)
         if world == 1:
-            b.dd_field_at_times(s2, pts_h, times, "mixed", out=out_h.numpy(), stream=e2e_stream)
+            b.dd_field_on_grid(s2, x0, y0, gdx, gdy, W, H, times, "mixed", out=out_h.numpy(), stream=e2e_stream)
             b.dd_per_probe_dose(s2, "mixed", out=dose_h.numpy(), stream=e2e_stream)
         else:
             with torch.cuda.stream(e2e_stream):
-                b.dd_field_at_times(s2, pts_h, times, "mixed", out=out_d, stream=e2e_stream)
+                b.dd_field_on_grid(s2, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, "mixed", out=out_d,
+                                   stream=e2e_stream)
                 b.dd_per_probe_dose_range(s2, j0, j1, "mixed", out=dose_d, stream=e2e_stream)
                 f = shard.gather_columns(out_d, pr, rank, dist)
                 d = shard.gather_vector(dose_d, dr, rank, dist)
@@ -651,9 +710,39 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
         s2.close()
     e2e_ms = (time.perf_counter() - t0) * 1e3
     v, ms, _ = whole_job(pairs_step, args.steps, e2e_ms, dist, dev)
-    return {"value": v, "unit": UNIT, "h2d_bytes_per_step": int(len(job.pts_xy) * 16 + world * 4 * n * 8),
+    # host -> device per step and rank: the scan's visit cache (6 doubles per visit) and the
+    # snapshot times; device -> host: the whole field and dose
+    return {"value": v, "unit": UNIT, "h2d_bytes_per_step": int(world * (6 * n * 8 + len(times) * 8)),
             "d2h_bytes_per_step": int(out_h.numel() * 8 + dose_h.numel() * 8),
-            "ms_per_step": ms / args.steps}
+            "ms_per_step": ms / args.steps,
+            "api": "dd_create_scan + dd_field_on_grid + dd_per_probe_dose (host outputs)"}
+
+
+def bench_point_list(b, job, times, scan, dev, stream, flush, field_pairs, reps=10):
+    """The same field through dd_field_at_times (the points as an explicit list, general
+    tiles of 512 consecutive points): its kernel's event time and roofline."""
+    import torch
+    pts = torch.from_numpy(np.ascontiguousarray(job.pts_xy)).to(dev)
+    out = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        b.dd_field_at_times(scan, pts, times, "mixed", out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    b.dd_profile_reset()
+    b.dd_profile_enable(True)
+    for k in range(reps):
+        flush.fill_(float(k))
+        b.dd_field_at_times(scan, pts, times, "mixed", out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    b.dd_profile_enable(False)
+    prof = b.dd_profile_read()
+    fl, fms = prof.get("field_mixed", (0, 0.0))
+    avg_ms = fms / max(1, fl)
+    fpp, mpp, _ = ops_per_pair(job)
+    rate = field_pairs / (avg_ms / 1e3)
+    return {"kernel": "field_mixed", "avg_launch_ms": avg_ms, "kernel_pairs_per_s": rate,
+            "mufu_frac": mpp * rate / 1e12 / MUFU_PEAK_TOPS, "fp32_frac": fpp * rate / 1e12 / FP32_PEAK_TFLOPS,
+            "ops_per_pair": {"flops": round(fpp, 3), "mufu": round(mpp, 4)},
+            "traffic": recorded_traffic("field_mixed")}
 
 
 def main():

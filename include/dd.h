@@ -132,6 +132,23 @@ dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy_m, int64_t
                             const double *times_s, int64_t n_t, dd_precision prec,
                             double *out, void *cuda_stream);
 
+/* Cumulative field psi (Eq. 5) on a rectilinear grid of evaluation points (the paper's
+   simulation grid of pixel side delta_s, Sec. 3): point (c, r) sits at
+   (x0_m + c * dx_m, y0_m + r * dy_m) for c < n_cols, r < n_rows (each product and sum
+   rounded once in FP64, no fused multiply-add), and
+     out[it * n_cols * n_rows + r * n_cols + c] = psi(point (c, r), times_s[it])   [u/m^2]
+   -- the result of dd_field_at_times on those points in row-major order, without a point
+   buffer.  In FP32-mixed precision the grid lets a tile of 128 columns x 4 rows split the
+   low-degree pair terms into column and row factors (fewer exponentials per pair); the
+   result then differs from dd_field_at_times by the FP32 rounding, within the same error
+   budget.  times_s and out as in dd_field_at_times.  A grid with no columns, rows or
+   snapshots is a no-op.
+   Errors: DD_EINVAL (NULL scan/buffer, negative sizes, non-finite origin or spacing, more
+   than 2^31 points), DD_ENOMEM, DD_ECUDA. */
+dd_status dd_field_on_grid(const dd_scan *scan, double x0_m, double y0_m, double dx_m, double dy_m,
+                           int64_t n_cols, int64_t n_rows, const double *times_s, int64_t n_t,
+                           dd_precision prec, double *out, void *cuda_stream);
+
 /* Dwell-start dose of every visit: the field at the probe's own position when
    its dwell starts, from the visits before it,
      out[j] = psi_{j-1}(r_j, t_j) = sum_{i<j} phi_i(r_j, t_j)   (Eq. 5 at r_j, t_j)

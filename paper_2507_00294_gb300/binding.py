@@ -61,6 +61,9 @@ def load(build_if_missing=True):
     lib.dd_scan_visits.argtypes = [_VP, _VP, _VP, _VP]
     lib.dd_field_at_times.argtypes = [_VP, _VP, _I64, _VP, _I64, ctypes.c_int, _VP, _VP]
     lib.dd_per_probe_dose.argtypes = [_VP, ctypes.c_int, _VP, _VP]
+    lib.dd_field_on_grid.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     _I64, _I64, _VP, _I64, ctypes.c_int, _VP, _VP]
+    lib.dd_field_on_grid.restype = ctypes.c_int
     lib.dd_field_batch.argtypes = [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, _VP, _VP]
     lib.dd_per_probe_dose_range.argtypes = [_VP, ctypes.c_int, _I64, _I64, _VP, _VP]
     lib.dd_per_probe_dose_range.restype = ctypes.c_int
@@ -232,6 +235,26 @@ def dd_field_at_times(scan, pts_xy_m, times_s, prec="mixed", out=None, stream=No
     st = load().dd_field_at_times(scan.handle, p, n_pts, t, n_t, PRECISIONS[prec], o,
                                   _stream(stream, pts_xy_m, out))
     _check(st, "dd_field_at_times")
+    return out
+
+
+def dd_field_on_grid(scan, x0, y0, dx, dy, n_cols, n_rows, times_s, prec="mixed", out=None, stream=None,
+                     device=None):
+    """Field on the grid (x0 + c dx, y0 + r dy), c < n_cols, r < n_rows: out [n_t, n_rows * n_cols]
+    (row-major points).  times_s: numpy or torch; out: host numpy unless `device` is given."""
+    t, kt = _ptr(times_s, np.float64)
+    n_t = int(times_s.shape[0]) if _is_torch(times_s) else len(np.asarray(times_s).reshape(-1))
+    n_pts = int(n_cols) * int(n_rows)
+    if out is None:
+        if device is not None:
+            import torch
+            out = torch.empty((n_t, n_pts), dtype=torch.float64, device=device)
+        else:
+            out = np.empty((n_t, n_pts), dtype=np.float64)
+    o, ko = _ptr(out, np.float64)
+    _check(load().dd_field_on_grid(scan.handle, float(x0), float(y0), float(dx), float(dy), int(n_cols),
+                                   int(n_rows), t, n_t, PRECISIONS[prec], o, _stream(stream, out)),
+           "dd_field_on_grid")
     return out
 
 

@@ -25,25 +25,45 @@
 
 #include "dd_coef.cuh"
 #include "dd_e1.cuh"
+#include "dd_field_grid.cuh"
 #include "dd_field_impl.cuh"
 #include "dd_internal.h"
 
 namespace ddk {
 
+// A rectilinear grid of evaluation points: point k = r W + c at (x0 + c dx, y0 + r dy)
+// (SI); W = 0 for an explicit point list.
+struct GridDesc {
+    double x0 = 0, y0 = 0, dx = 0, dy = 0;
+    int64_t W = 0, H = 0;
+};
+
 // Points in pitch units: FP64 X, Y, and float-float (x_hi, x_lo, y_hi, y_lo) for the FP32
 // tile, so that the FP32 kernels form coordinate differences without FP64 arithmetic.
-__device__ __forceinline__ void prep_point(int64_t k, const double *__restrict__ xy, int64_t n, double inv_p,
-                                           double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
+// A grid point is formed in SI as x0 + c dx (one product, one sum, no fused multiply-add:
+// the values a caller's point list of the same grid holds).
+__device__ __forceinline__ void prep_point(int64_t k, const double *__restrict__ xy, const GridDesc &g, int64_t n,
+                                           double inv_p, double *__restrict__ X, double *__restrict__ Y,
+                                           float4 *__restrict__ F) {
     if (k >= n) return;
-    const double x = xy[2 * k] * inv_p, y = xy[2 * k + 1] * inv_p;
+    double xs, ys;
+    if (g.W > 0) {
+        const int64_t r = k / g.W, c = k - r * g.W;
+        xs = __dadd_rn(__dmul_rn((double)c, g.dx), g.x0);
+        ys = __dadd_rn(__dmul_rn((double)r, g.dy), g.y0);
+    } else {
+        xs = xy[2 * k];
+        ys = xy[2 * k + 1];
+    }
+    const double x = xs * inv_p, y = ys * inv_p;
     X[k] = x;
     Y[k] = y;
     const float xh = (float)x, yh = (float)y;
     F[k] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
 }
-__global__ void prep_points_kernel(const double *__restrict__ xy, int64_t n, double inv_p,
+__global__ void prep_points_kernel(const double *__restrict__ xy, GridDesc g, int64_t n, double inv_p,
                                    double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
-    prep_point((int64_t)blockIdx.x * blockDim.x + threadIdx.x, xy, n, inv_p, X, Y, F);
+    prep_point((int64_t)blockIdx.x * blockDim.x + threadIdx.x, xy, g, n, inv_p, X, Y, F);
 }
 
 // The reversed lag table (blocks [0, nb_lag), one record per thread: a long serial chain,
@@ -51,12 +71,12 @@ __global__ void prep_points_kernel(const double *__restrict__ xy, int64_t n, dou
 // launch: the field's two preparation steps cost one launch instead of two.
 template <typename Rec>
 __global__ void prep_points_lag_kernel(int nb_lag, int64_t M, double s, double kappa, Rec *__restrict__ rev,
-                                       const double *__restrict__ xy, int64_t n, double inv_p,
+                                       const double *__restrict__ xy, GridDesc g, int64_t n, double inv_p,
                                        double *__restrict__ X, double *__restrict__ Y, float4 *__restrict__ F) {
     if ((int)blockIdx.x < nb_lag)
         rev_lag_record<Rec>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, M, s, kappa, rev);
     else
-        prep_point((int64_t)(blockIdx.x - nb_lag) * blockDim.x + threadIdx.x, xy, n, inv_p, X, Y, F);
+        prep_point((int64_t)(blockIdx.x - nb_lag) * blockDim.x + threadIdx.x, xy, g, n, inv_p, X, Y, F);
 }
 
 // out[row[j] * n_pts + p] = pref * sum_{k < nblk[chunk(j)]} partial[(k * n_tg + j) * n_pts + p]
@@ -149,30 +169,45 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
 // array), set once per device: the FP32-mixed tile's 8 CTAs of 13 KB fit in 132 KB and
 // the rest stays L1 for the minority classes' record reads (about 1 % faster than the
 // whole array as shared memory); the FP64 tile takes the whole array.
-template <typename Cfg>
+// The grid tile (dd_field_grid.cuh) keeps 4 KB of row tables beside the general tile's
+// 12 KB: 8 CTAs of 17.3 KB (with the per-CTA reserve) need a 66 % carveout.
+constexpr int kGridCarveout = 66;
+
+template <typename Cfg, bool kGrid>
+struct TileKernel {
+    static constexpr auto fn() { return ddk::field_kernel<Cfg>; }
+    static constexpr int carveout = Cfg::kCarveout;
+};
+template <>
+struct TileKernel<ddk::CfgMixed, true> {
+    static constexpr auto fn() { return ddk::field_grid_kernel<ddk::CfgMixed>; }
+    static constexpr int carveout = kGridCarveout;
+};
+
+template <typename Cfg, bool kGrid = false>
 cudaError_t prefer_shared() {
     static std::atomic<uint64_t> done{0};
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess || dev >= 64) return err;
     if (done.load() & (uint64_t(1) << dev)) return cudaSuccess;
-    err = cudaFuncSetAttribute(ddk::field_kernel<Cfg>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               Cfg::kCarveout);
+    err = cudaFuncSetAttribute(TileKernel<Cfg, kGrid>::fn(), cudaFuncAttributePreferredSharedMemoryCarveout,
+                               TileKernel<Cfg, kGrid>::carveout);
     if (err == cudaSuccess) done.fetch_or(uint64_t(1) << dev);
     return err;
 }
 
-// CTAs of field_kernel<Cfg> resident on the whole device at once (0 if unknown).
-template <typename Cfg>
+// CTAs of the tile kernel resident on the whole device at once (0 if unknown).
+template <typename Cfg, bool kGrid = false>
 int64_t resident_ctas() {
     static std::atomic<int64_t> cached[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 0;
     int64_t v = cached[dev].load();
     if (v > 0) return v;
-    if (prefer_shared<Cfg>() != cudaSuccess) cudaGetLastError();   // occupancy at the carveout used
+    if (prefer_shared<Cfg, kGrid>() != cudaSuccess) cudaGetLastError();   // occupancy at the carveout used
     int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ddk::field_kernel<Cfg>, Cfg::kThreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, TileKernel<Cfg, kGrid>::fn(), Cfg::kThreads, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -182,13 +217,19 @@ int64_t resident_ctas() {
     return v;
 }
 
+// pts_xy_m == NULL: the points are the grid `grid` (row-major, n_pts = W H), formed on
+// the device; the FP32-mixed path then runs the grid tile kernel.
 template <typename Cfg>
-dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
+dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, const ddk::GridDesc &grid,
                     const std::vector<double> &times, double *out, cudaStream_t stream) {
     using Rec = typename Cfg::Rec;
+    constexpr bool kMixed = std::is_same<typename Cfg::Real, float>::value;
+    const bool on_grid = grid.W > 0;
+    const bool grid_tiles = kMixed && on_grid;
     const int64_t n_src = scan->n;
     const int n_t = (int)times.size();
-    const dd::MemKind pts_kind = dd::memory_kind(pts_xy_m), out_kind = dd::memory_kind(out);
+    const dd::MemKind pts_kind = on_grid ? dd::MemKind::Device : dd::memory_kind(pts_xy_m);
+    const dd::MemKind out_kind = dd::memory_kind(out);
     const bool pts_host = pts_kind != dd::MemKind::Device;
     const bool out_host = out_kind != dd::MemKind::Device;
     // host buffers go through a workspace copy (a pinned output written in place by the
@@ -221,7 +262,9 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
 
     // visit block size and snapshot groups bound the partial and record buffers
     const int tile = Cfg::kThreads * Cfg::kPPT;
-    const int64_t n_tiles = (n_pts + tile - 1) / tile;
+    // grid tiles: 128 columns x 4 rows (kThreads x kPPT); otherwise 512 consecutive points
+    const int64_t n_tc = grid_tiles ? (grid.W + Cfg::kThreads - 1) / Cfg::kThreads : 0;
+    const int64_t n_tiles = grid_tiles ? n_tc * ((grid.H + Cfg::kPPT - 1) / Cfg::kPPT) : (n_pts + tile - 1) / tile;
     int sb = Cfg::kSB;
     int group = n_t;
     const size_t budget = size_t(1) << 30;
@@ -234,7 +277,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
     // resident CTAs, so that the last wave's stragglers cost little
     {
         constexpr int kWaves = 4;
-        const int64_t waves4 = kWaves * resident_ctas<Cfg>();
+        const int64_t waves4 = kWaves * (grid_tiles ? resident_ctas<Cfg, true>() : resident_ctas<Cfg>());
         const int n_groups = (n_t + group - 1) / group;
         auto items_per_launch = [&](int b) {
             int64_t blocks = 0;
@@ -290,7 +333,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
 
     if (!lattice) {
         DD_PROFILED("prep_points", stream,
-                    (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, n_pts, 1.0 / scan->pitch, X, Y, PF)));
+                    (ddk::prep_points_kernel<<<(unsigned)((n_pts + 255) / 256), 256, 0, stream>>>(pts_dev, grid, n_pts, 1.0 / scan->pitch, X, Y, PF)));
         DD_CUDA_TRY(cudaGetLastError());
     }
 
@@ -304,7 +347,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
         const int64_t nb_pts = (n_pts + 31) / 32;
         DD_PROFILED(Cfg::kCoefName, stream,
                     (ddk::prep_points_lag_kernel<Rec><<<(unsigned)(nb_lag + nb_pts), 32, 0, stream>>>(
-                        nb_lag, M, scan->s, scan->kappa, d_rec, pts_dev, n_pts, 1.0 / scan->pitch, X, Y, PF)));
+                        nb_lag, M, scan->s, scan->kappa, d_rec, pts_dev, grid, n_pts, 1.0 / scan->pitch, X, Y, PF)));
         DD_CUDA_TRY(cudaGetLastError());
     }
     for (int g0 = 0; g0 < n_t; g0 += group) {
@@ -365,13 +408,24 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts,
             DD_CUDA_TRY(cudaGetLastError());
         }
         if (!it.empty()) {
-            DD_CUDA_TRY(prefer_shared<Cfg>());
+            if (grid_tiles) DD_CUDA_TRY((prefer_shared<Cfg, true>()));
+            else DD_CUDA_TRY(prefer_shared<Cfg>());
             // one CTA per item, in launches of at most 2^31 - 1 CTAs (the grid's x limit)
             const int64_t n_items = (int64_t)it.size() * n_tiles, kMaxGrid = (int64_t(1) << 31) - 1;
             for (int64_t item0 = 0; item0 < n_items; item0 += kMaxGrid) {
-                const unsigned grid = (unsigned)std::min(kMaxGrid, n_items - item0);
+                const unsigned nctas = (unsigned)std::min(kMaxGrid, n_items - item0);
+                if constexpr (kMixed) {
+                    if (grid_tiles) {
+                        DD_PROFILED("field_grid_mixed", stream,
+                                    (ddk::field_grid_kernel<Cfg><<<nctas, Cfg::kThreads, 0, stream>>>(
+                                        grid.W, grid.H, n_tc, d_rec, d_roff, d_nact, d_desc, n_tiles, item0, ng, sb,
+                                        d_part, pstride, srcF, PF)));
+                        DD_CUDA_TRY(cudaGetLastError());
+                        continue;
+                    }
+                }
                 DD_PROFILED(Cfg::kFieldName, stream,
-                            (ddk::field_kernel<Cfg><<<grid, Cfg::kThreads, 0, stream>>>(
+                            (ddk::field_kernel<Cfg><<<nctas, Cfg::kThreads, 0, stream>>>(
                                 srcX, srcY, X, Y, n_pts, d_rec, d_roff, d_nact, d_desc, n_tiles, item0, ng, sb, d_part,
                                 pstride, srcF, PF)));
                 DD_CUDA_TRY(cudaGetLastError());
@@ -417,6 +471,38 @@ extern "C" dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy
     }
     for (double t : times)
         if (!std::isfinite(t)) return dd::fail(DD_EINVAL, "dd_field_at_times: non-finite time");
-    if (prec == DD_MIXED) return run_field<ddk::CfgMixed>(scan, pts_xy_m, n_pts, times, out, stream);
-    return run_field<ddk::CfgF64>(scan, pts_xy_m, n_pts, times, out, stream);
+    const ddk::GridDesc list;                                     // an explicit point list
+    if (prec == DD_MIXED) return run_field<ddk::CfgMixed>(scan, pts_xy_m, n_pts, list, times, out, stream);
+    return run_field<ddk::CfgF64>(scan, pts_xy_m, n_pts, list, times, out, stream);
+}
+
+extern "C" dd_status dd_field_on_grid(const dd_scan *scan, double x0_m, double y0_m, double dx_m, double dy_m,
+                                      int64_t n_cols, int64_t n_rows, const double *times_s, int64_t n_t,
+                                      dd_precision prec, double *out, void *cuda_stream) {
+    dd::clear_error();
+    if (!scan) return dd::fail(DD_EINVAL, "dd_field_on_grid: NULL scan");
+    if (n_cols < 0 || n_rows < 0 || n_t < 0) return dd::fail(DD_EINVAL, "dd_field_on_grid: negative size");
+    if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_field_on_grid: unknown precision");
+    if (!std::isfinite(x0_m) || !std::isfinite(y0_m) || !std::isfinite(dx_m) || !std::isfinite(dy_m))
+        return dd::fail(DD_EINVAL, "dd_field_on_grid: grid origin and spacing must be finite");
+    if (n_cols == 0 || n_rows == 0 || n_t == 0) return DD_OK;
+    if (!times_s || !out) return dd::fail(DD_EINVAL, "dd_field_on_grid: NULL buffer");
+    if (n_t > (int64_t(1) << 24) || n_cols > (int64_t(1) << 31) || n_rows > (int64_t(1) << 31) ||
+        n_cols * n_rows > (int64_t(1) << 31))
+        return dd::fail(DD_EINVAL, "dd_field_on_grid: too many points or snapshots");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    std::vector<double> times((size_t)n_t);
+    if (dd::is_device_pointer(times_s)) {
+        DD_CUDA_TRY(cudaMemcpyAsync(times.data(), times_s, n_t * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        DD_CUDA_TRY(cudaStreamSynchronize(stream));
+    } else {
+        std::memcpy(times.data(), times_s, n_t * sizeof(double));
+    }
+    for (double t : times)
+        if (!std::isfinite(t)) return dd::fail(DD_EINVAL, "dd_field_on_grid: non-finite time");
+    ddk::GridDesc g;
+    g.x0 = x0_m; g.y0 = y0_m; g.dx = dx_m; g.dy = dy_m; g.W = n_cols; g.H = n_rows;
+    const int64_t n_pts = n_cols * n_rows;
+    if (prec == DD_MIXED) return run_field<ddk::CfgMixed>(scan, nullptr, n_pts, g, times, out, stream);
+    return run_field<ddk::CfgF64>(scan, nullptr, n_pts, g, times, out, stream);
 }

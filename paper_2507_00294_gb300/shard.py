@@ -32,6 +32,12 @@ def point_ranges(n_pts, world, align=POINT_TILE):
     return out
 
 
+def row_ranges(n_rows, world, align=4):
+    """Contiguous row ranges [r0, r1) of a point grid per rank, whole blocks of `align`
+    rows (the grid tile's height), as even as the blocks allow."""
+    return point_ranges(n_rows, world, align)
+
+
 def dose_ranges(n_visits, world, align=DOSE_TILE):
     """Contiguous [j0, j1) per rank with about equal pair counts: the dose of visit j sums
     j earlier visits, so the work below j grows as j^2 / 2 and rank r's range ends at

@@ -80,10 +80,12 @@ def test_blanker_travel_field_and_dose(cuda, spec):
     pts = w.grid_points(2 * spec.nx, spec.pitch_m / 2)
     _, ts, taus = b.Scan(spec).visits()
     end = ts[-1] + taus[-1]
-    # off the visits' dwell boundaries: there the field's derivative in t is large at the
-    # beam, and start times that are not on the dwell lattice round differently in seconds
-    # (library) and in dwells (oracle)
-    times = np.array([0.4 * end, 1.0001 * end, 3 * end])
+    # half a dwell away from every visit boundary: there the field's derivative in t is
+    # large at the beam, and start times off the dwell lattice carry different roundings
+    # in seconds (library) and in dwells (oracle), some 1e-13 of a dwell after a hundred
+    # dead times -- 5e-12 of a lag of 0.02 dwell
+    k = len(ts) // 3
+    times = np.array([ts[k] + 0.5 * taus[k], end + 0.5 * spec.dwell_s, 3 * end])
     ref = oracle_field(spec, pts, times)
     assert_fp64(b.dd_field_at_times(b.Scan(spec), pts, times, "fp64"), ref, "blanker field fp64")
     assert_mixed(b.dd_field_at_times(b.Scan(spec), pts, times, "mixed"), ref, ref.max(axis=1),

@@ -56,7 +56,7 @@ def test_dose_ranges_against_the_oracle(cuda, spec):
     scan = b.Scan(spec)
     n = len(scan)
     ref = oracle_dose(spec)
-    for j0, j1 in ((0, n), (0, 1), (1, 2), (100, 300), (257, 811), (n - 1, n), (5, 5)):
+    for j0, j1 in ((0, n), (0, 1), (1, 2), (100, 300), (257, min(n, 811)), (n - 1, n), (5, 5)):
         for prec in ("fp64", "mixed"):
             got = b.dd_per_probe_dose_range(scan, j0, j1, prec, device=cuda).cpu().numpy()
             assert got.shape == (j1 - j0,)
@@ -66,8 +66,10 @@ def test_dose_ranges_against_the_oracle(cuda, spec):
                 assert_fp64(got, ref[j0:j1], "dose range fp64")
             else:
                 keep = np.arange(j0, j1) > 0
-                if keep.any():
+                if np.any(ref[j0:j1][keep] >= 1e-6 * ref.max()):
                     assert_mixed(got[keep], ref[j0:j1][keep], ref.max(), "dose range mixed")
+                else:                                       # below the tolerance's floor
+                    assert np.all(np.abs(got[keep]) <= 1e-6 * ref.max())
     with pytest.raises(b.DDError) as e:
         b.dd_per_probe_dose_range(scan, 3, n + 1, "mixed", device=cuda)
     assert e.value.status == b.DD_EINVAL
