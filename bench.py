@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--surrogate-maps", type=int, default=20000)
     ap.add_argument("--surrogate-epochs", type=int, default=20)
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--leg", choices=["all", "batched", "surrogate-infer"], default="all",
+    ap.add_argument("--leg", choices=["all", "batched", "surrogate-infer", "surrogate"], default="all",
                     help="run one leg alone (for profiling): the 512-scan batch, or the surrogate "
                          "network's inference at batch 256 (random weights)")
     return ap.parse_args()
@@ -407,49 +407,91 @@ def bench_runtime_curve(dev, stream, sizes=(8, 16, 20, 32, 64), frames=(1e-6, 10
 
 
 def bench_surrogate(dev, maps, epochs):
-    """Train the surrogate on `maps` exact fields and compare it with the exact path."""
+    """Train the surrogate on `maps` exact fields and compare it with the exact path, both
+    as kernels on device-resident inputs and end to end from the scan descriptions."""
     import torch
+    from paper_2507_00294_gb300 import binding as b
     from paper_2507_00294_gb300 import surrogate as sur
     t0 = time.perf_counter()
     specs, tmap, scal, target = sur.build_dataset(maps, seed=5, device=dev)
+    weight = sur.loss_weights(target)
     torch.cuda.synchronize(dev)
     t_data = time.perf_counter() - t0
     n_test = max(64, maps // 20)
     n_train = maps - 2 * n_test
     net = sur.Net(dev, seed=0)
     t0 = time.perf_counter()
-    losses = sur.train(net, tmap[:n_train], scal[:n_train], target[:n_train], epochs=epochs, batch=32)
+    losses = sur.train(net, tmap[:n_train], scal[:n_train], target[:n_train], epochs=epochs, batch=32,
+                       weight=weight[:n_train])
     torch.cuda.synchronize(dev)
     t_train = time.perf_counter() - t0
     te = slice(maps - n_test, maps)
     te_specs = specs[te]
-    # exact path on the test maps (full canvas, batched)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return r, time.perf_counter() - t
+
+    # exact path end to end (scans, plans, kernels) on the test maps, full canvas
     sur.exact_fields(te_specs[:64], dev)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    exact = sur.exact_fields(te_specs, dev).view(n_test, -1)
-    torch.cuda.synchronize(dev)
-    t_exact = time.perf_counter() - t0
-    # network alone, batch 256
+    exact, t_exact = timed(lambda: sur.exact_fields(te_specs, dev).view(n_test, -1))
+    pts = torch.from_numpy(np.ascontiguousarray(np.concatenate([sur.canvas_points(s) for s in te_specs]))).to(dev)
+    offs = np.arange(n_test + 1, dtype=np.int64) * sur.CANVAS * sur.CANVAS
+    out = torch.empty(n_test * sur.CANVAS * sur.CANVAS, dtype=torch.float64, device=dev)
+
+    def kernel_time(spec_list, times):
+        """One plan of the scans on the canvas, replayed: the kernels alone."""
+        scans = [b.Scan(s) for s in spec_list]
+        plan = b.Batch(scans, offs, np.asarray(times), "mixed")
+        plan.run(pts, out=out)
+        _, t = timed(lambda: plan.run(pts, out=out))
+        plan.close()
+        return t
+    t_exact_kernel = kernel_time(te_specs, [w_nv(s) * s.dwell_s for s in te_specs])
+    parts = [sur.split_scan(s) for s in te_specs]
+    t_near_kernel = kernel_time([p_[2] for p_ in parts], [p_[3] for p_ in parts])
+    # network alone, batch 256, device-resident input descriptors
     sur.predict(net, tmap[te], scal[te])
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    pred = sur.predict(net, tmap[te], scal[te], batch=256)
-    torch.cuda.synchronize(dev)
-    t_net = time.perf_counter() - t0
-    err = sur.map_errors(sur.fields_from_prediction(pred, te_specs), exact)
+    _, t_net = timed(lambda: sur.predict(net, tmap[te], scal[te], batch=256))
+    # surrogate end to end: input planes from the scan descriptions (host), upload, network,
+    # and the exact field of each scan's last visits
+    def net_e2e():
+        tm, sc = sur.scan_inputs(te_specs)
+        return sur.surrogate_fields(net, te_specs, torch.from_numpy(tm).to(dev), torch.from_numpy(sc).to(dev), dev)[0]
+    fields_sur, t_net_e2e = timed(net_e2e)
+    err = sur.map_errors(fields_sur, exact)
     fields, fell, est, t_fb = sur.infer_with_fallback(net, te_specs, tmap[te], scal[te], dev)
     err_after = sur.map_errors(fields, exact)
-    return {"maps_per_s_network": n_test / t_net, "maps_per_s_with_fallback": n_test / t_fb,
-            "maps_per_s_exact": n_test / t_exact, "unit": "maps/s",
-            "gain_network_over_exact": t_exact / t_net, "gain_with_fallback_over_exact": t_exact / t_fb,
+    est_ok = np.abs(np.log10(np.maximum(est, 1e-12) / np.maximum(err, 1e-12)))
+    return {"maps_per_s_network": n_test / t_net, "maps_per_s_exact_kernel": n_test / t_exact_kernel,
+            "maps_per_s_surrogate_kernels": n_test / (t_net + t_near_kernel),
+            "maps_per_s_surrogate_end_to_end": n_test / t_net_e2e, "maps_per_s_exact_end_to_end": n_test / t_exact,
+            "maps_per_s_with_fallback": n_test / t_fb, "unit": "maps/s",
+            "gain_network_over_exact_kernel": t_exact_kernel / t_net,
+            "gain_surrogate_over_exact_kernels": t_exact_kernel / (t_net + t_near_kernel),
+            "gain_surrogate_over_exact_end_to_end": t_exact / t_net_e2e,
+            "exact_last_visits": sur.K_EXACT,
+            "gain_with_fallback_over_exact_end_to_end": t_exact / t_fb,
             "median_rel_err": float(np.median(err)), "p90_rel_err": float(np.percentile(err, 90)),
+            "share_below_1e-2": float(np.mean(err <= 1e-2)),
             "fallback_fraction": float(np.mean(fell)), "max_rel_err_after_fallback": float(err_after.max()),
+            "spot_estimate_within_2x": float(np.mean(est_ok <= np.log10(2.0))),
             "train_maps": n_train, "test_maps": n_test, "epochs": epochs, "final_train_loss": losses[-1],
             "seconds": {"dataset": t_data, "train": t_train},
-            "net": "6 x conv3x3 (4->32->32->32->32->32->1, padded 16/32/16), BF16 tcgen05.mma (forward, data gradient) and mma.sync (weight gradient), FP32 accum, Adam",
+            "net": "6 x conv3x3 (4->32->32->32->32->32->1, padded 16/32/16), dilations 1..32, BF16 tcgen05.mma "
+                   "(forward, data gradient) and mma.sync (weight gradient), FP32 accum, Adam",
+            "loss": "squared log10 error weighted by each pixel's share of the map's squared field "
+                    "(alpha %.2f) plus a uniform part" % sur.LOSS_ALPHA,
             "error": "relative L2 of the linear field over the 128x128 canvas; fallback above 1e-2 "
-                     "(estimated from 64 exact spot points per map)"}
+                     "(estimated from 64 exact spot points per map: the last 32 visits and 32 others)"}
+
+
+def w_nv(spec):
+    from paper_2507_00294_gb300 import workloads as w
+    return w.n_visits(spec)
 
 
 def bench_surrogate_inference(dev, maps=256, reps=5):
@@ -480,6 +522,8 @@ def run_leg(args):
     b.load()
     if args.leg == "batched":
         res = bench_batched(dev, torch.cuda.current_stream(dev), runs=3)
+    elif args.leg == "surrogate":
+        res = bench_surrogate(dev, args.surrogate_maps, args.surrogate_epochs)
     else:
         res = bench_surrogate_inference(dev)
     print(json.dumps({"leg": args.leg, **res}), flush=True)

@@ -259,13 +259,20 @@ const char *dd_last_error(void);
    when w_bf16 is given also writes the BF16 copy and the flipped copy [cin][8-tap][cout].
    dd_sur_planes: x [B,H,W,16] BF16 from tmap [B,H,W] (visit time / total scan time,
    < 0 where not visited) and scal [B][2] (standardised log D, log dwell).
+   dd_sur_wmse: the same with per-element weights weight[n] (FP32): loss_sum[0] =
+   sum w (pred - target)^2, dz = (2 w (pred - target) / n, 0, ..., 0).
+   dd_sur_weights: w [n_maps*hw] FP32 = alpha hw f_p^2 / sum_q f_q^2 + (1 - alpha) per map,
+   f = 10^(target sigma + mu) from normalised targets (alpha in [0, 1]): the squared log
+   error weighted so, summed over a map and divided by hw, approximates (relative L2 error of
+   the linear map / ln 10)^2, the measure the surrogate is judged by.
    dd_sur_targets: out [n_maps*hw] FP32 = (log10(max(f, peak * 10^floor_rel_log10)) - mu)
    / sigma with f = psi*scale[map] and peak = max of f over the map (floor_rel_log10 < 0):
    the network's normalised target from exact fields psi [n_maps*hw] (u/m^2, FP64) and
    per-map scale[] = 4 pi D / Q0 (the dimensionless field).
    dd_sur_fields: psi [n_maps*hw] (u/m^2, FP64) = 10^(pred*sigma + mu) / scale[map].
    dd_sur_spot_error: err[m] = relative L2 error over k spot points of map m between the
-   field of pred [n_maps][hw] and exact [n_maps][k] (u/m^2) at canvas indices idx [n_maps][k].
+   field of pred [n_maps][hw] plus add [n_maps][hw] (u/m^2, FP64; an exactly computed part
+   of the field, or NULL) and exact [n_maps][k] (u/m^2) at canvas indices idx [n_maps][k].
    dd_sur_check: synchronises the device and returns DD_ETIMEOUT (clearing the flag) if a
    tensor-memory convolution since the last check gave up waiting for its MMAs (an
    iteration-limited wait; its output is then not written), DD_OK otherwise. */
@@ -282,13 +289,17 @@ dd_status dd_sur_adam(float *param, const float *grad, float *m, float *v, int64
                       void *w_flip_bf16, int32_t cin, int32_t cout, void *cuda_stream);
 dd_status dd_sur_planes(const float *tmap, const float *scal, int32_t B, int32_t H, int32_t W, void *x,
                         void *cuda_stream);
+dd_status dd_sur_wmse(const float *pred, const float *target, const float *weight, int64_t n, void *dz,
+                      double *block_sums, double *loss_sum, void *cuda_stream);
+dd_status dd_sur_weights(const float *target, int64_t n_maps, int64_t hw, float mu, float sigma, float alpha,
+                         float *w, void *cuda_stream);
 dd_status dd_sur_targets(const double *psi, const double *scale, int64_t n_maps, int64_t hw,
                          double floor_rel_log10, float mu, float sigma, float *out, void *cuda_stream);
 dd_status dd_sur_fields(const float *pred, const double *scale, int64_t n_maps, int64_t hw, float mu,
                         float sigma, double *psi, void *cuda_stream);
 dd_status dd_sur_spot_error(const float *pred, const int32_t *idx, const double *exact,
-                            const double *scale, int32_t n_maps, int32_t hw, int32_t k, float mu,
-                            float sigma, double *err, void *cuda_stream);
+                            const double *scale, const double *add, int32_t n_maps, int32_t hw, int32_t k,
+                            float mu, float sigma, double *err, void *cuda_stream);
 dd_status dd_sur_check(void);
 
 /* Tracing (no counterpart in the paper): per-kernel device time of this library's

@@ -81,14 +81,17 @@ def load(build_if_missing=True):
     lib.dd_sur_conv3x3.argtypes = [_VP, _VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, _VP]
     lib.dd_sur_wgrad.argtypes = [_VP, _VP, i32, i32, i32, i32, i32, i32, _VP, _I64, _VP, _VP]
     lib.dd_sur_mse.argtypes = [_VP, _VP, _I64, _VP, _VP, _VP, _VP]
+    lib.dd_sur_wmse.argtypes = [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]
+    lib.dd_sur_weights.argtypes = [_VP, _I64, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP, _VP]
     lib.dd_sur_adam.argtypes = [_VP, _VP, _VP, _VP, _I64, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, ctypes.c_float, i32, _VP, _VP, i32, i32, _VP]
     lib.dd_sur_planes.argtypes = [_VP, _VP, i32, i32, i32, _VP, _VP]
     lib.dd_sur_targets.argtypes = [_VP, _VP, _I64, _I64, ctypes.c_double, ctypes.c_float, ctypes.c_float, _VP, _VP]
     lib.dd_sur_fields.argtypes = [_VP, _VP, _I64, _I64, ctypes.c_float, ctypes.c_float, _VP, _VP]
-    lib.dd_sur_spot_error.argtypes = [_VP, _VP, _VP, _VP, i32, i32, i32, ctypes.c_float, ctypes.c_float, _VP, _VP]
+    lib.dd_sur_spot_error.argtypes = [_VP, _VP, _VP, _VP, _VP, i32, i32, i32, ctypes.c_float, ctypes.c_float, _VP, _VP]
     lib.dd_sur_check.argtypes = []
-    for name in ("dd_sur_conv3x3", "dd_sur_wgrad", "dd_sur_mse", "dd_sur_adam", "dd_sur_planes",
+    for name in ("dd_sur_conv3x3", "dd_sur_wgrad", "dd_sur_mse", "dd_sur_wmse", "dd_sur_weights", "dd_sur_adam",
+                 "dd_sur_planes",
                  "dd_sur_targets", "dd_sur_fields", "dd_sur_spot_error", "dd_sur_check"):
         getattr(lib, name).restype = ctypes.c_int
     lib.dd_profile_enable.argtypes = [ctypes.c_int32]
@@ -419,6 +422,16 @@ def dd_sur_planes(tmap, scal, x, stream=None):
     return x
 
 
+def dd_sur_wmse(pred, target, weight, dz, block_sums, loss_sum, stream=None):
+    _check(load().dd_sur_wmse(_dp(pred), _dp(target), _dp(weight), pred.numel(), _dp(dz), _dp(block_sums),
+                              _dp(loss_sum), _cs(stream, pred)), "dd_sur_wmse")
+
+
+def dd_sur_weights(target, n_maps, hw, mu, sigma, alpha, out, stream=None):
+    _check(load().dd_sur_weights(_dp(target), n_maps, hw, mu, sigma, alpha, _dp(out), _cs(stream, target)),
+           "dd_sur_weights")
+
+
 def dd_sur_targets(psi, scale, n_maps, hw, floor_rel_log10, mu, sigma, out, stream=None):
     _check(load().dd_sur_targets(_dp(psi), _dp(scale), n_maps, hw, floor_rel_log10, mu, sigma, _dp(out),
                                  _cs(stream, psi)), "dd_sur_targets")
@@ -431,9 +444,9 @@ def dd_sur_fields(pred, scale, n_maps, hw, mu, sigma, psi, stream=None):
     return psi
 
 
-def dd_sur_spot_error(pred, idx, exact, scale, n_maps, hw, k, mu, sigma, err, stream=None):
-    _check(load().dd_sur_spot_error(_dp(pred), _dp(idx), _dp(exact), _dp(scale), n_maps, hw, k, mu, sigma,
-                                    _dp(err), _cs(stream, pred)), "dd_sur_spot_error")
+def dd_sur_spot_error(pred, idx, exact, scale, n_maps, hw, k, mu, sigma, err, stream=None, add=None):
+    _check(load().dd_sur_spot_error(_dp(pred), _dp(idx), _dp(exact), _dp(scale), None if add is None else _dp(add),
+                                    n_maps, hw, k, mu, sigma, _dp(err), _cs(stream, pred)), "dd_sur_spot_error")
     return err
 
 

@@ -481,17 +481,20 @@ __global__ void reduce_partials_kernel(const float *__restrict__ part, int n_par
     out[i] = s;
 }
 
-// dz[p][0] = 2 (pred[p] - target[p]) / n, dz[p][1..15] = 0; per-block squared-error sums.
-__global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ target, int64_t n,
-                           bf16 *__restrict__ dz, double *__restrict__ block_sums) {
+// dz[p][0] = 2 w[p] (pred[p] - target[p]) / n, dz[p][1..15] = 0; per-block sums of
+// w[p] (pred[p] - target[p])^2 (w = 1 when weight is NULL).
+__global__ void mse_kernel(const float *__restrict__ pred, const float *__restrict__ target,
+                           const float *__restrict__ weight, int64_t n, bf16 *__restrict__ dz,
+                           double *__restrict__ block_sums) {
     __shared__ double s[256];
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double e = 0.0;
     if (p < n) {
         const float d = pred[p] - target[p];
-        e = (double)d * d;
+        const float wp = weight ? weight[p] : 1.0f;
+        e = (double)wp * d * d;
         uint4 z = make_uint4(0, 0, 0, 0);
-        __nv_bfloat162 g = __floats2bfloat162_rn(2.0f * d / (float)n, 0.0f);
+        __nv_bfloat162 g = __floats2bfloat162_rn(2.0f * wp * d / (float)n, 0.0f);
         z.x = *reinterpret_cast<uint32_t *>(&g);
         uint4 *o = reinterpret_cast<uint4 *>(dz + p * 16);
         o[0] = z;
@@ -540,7 +543,7 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     }
 }
 
-// Input planes [B,H,W,16]: time map (t_i / total time where visited), visited mask,
+// Input planes [B,H,W,16]: the time map value where visited (its encoding is the caller's), visited mask,
 // standardised log D and log dwell; channels 4..15 zero.  tmap < 0 marks unvisited.
 __global__ void planes_kernel(const float *__restrict__ tmap, const float *__restrict__ scal, int HW, int64_t n,
                               bf16 *__restrict__ x) {
@@ -578,6 +581,34 @@ __global__ void targets_kernel(const double *__restrict__ psi, const double *__r
         out[m * hw + p] = (float)((log10(fmax(psi[m * hw + p] * sc, lo)) - (double)mu) * (double)inv_sigma);
 }
 
+// Per-pixel loss weights of one map per CTA, from its normalised log targets:
+//   f_p = 10^(target_p sigma + mu),  w_p = alpha hw f_p^2 / sum_q f_q^2 + (1 - alpha).
+// With alpha = 1 the weighted squared log error sum_p w_p (log10 error_p)^2 / hw is, to
+// first order, (relative L2 error of the linear map / ln 10)^2: a pixel weighs as much as
+// its share of the map's squared norm; 1 - alpha keeps every pixel in the loss.
+__global__ void weights_kernel(const float *__restrict__ target, int64_t hw, float mu, float sigma, float alpha,
+                               float *__restrict__ w) {
+    __shared__ double s[256];
+    const int64_t m = blockIdx.x;
+    const float *t = target + m * hw;
+    double acc = 0.0;
+    for (int64_t p = threadIdx.x; p < hw; p += blockDim.x) {
+        const double f = pow(10.0, (double)t[p] * sigma + mu);
+        acc += f * f;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+        __syncthreads();
+    }
+    const double norm = s[0] > 0.0 ? (double)alpha * (double)hw / s[0] : 0.0;
+    for (int64_t p = threadIdx.x; p < hw; p += blockDim.x) {
+        const double f = pow(10.0, (double)t[p] * sigma + mu);
+        w[m * hw + p] = (float)(norm * f * f + (1.0 - (double)alpha));
+    }
+}
+
 // psi[m][p] = 10^(pred[m][p] * sigma + mu) / scale[m]  (back to u/m^2)
 __global__ void fields_kernel(const float *__restrict__ pred, const double *__restrict__ scale, int64_t hw,
                               int64_t n, float mu, float sigma, double *__restrict__ psi) {
@@ -586,17 +617,20 @@ __global__ void fields_kernel(const float *__restrict__ pred, const double *__re
     psi[i] = pow(10.0, (double)pred[i] * sigma + mu) / scale[i / hw];
 }
 
-// err[m] = || psi_pred(spots) - exact ||_2 / || exact ||_2 over the k spot points of map m
+// err[m] = || psi_pred(spots) + add(spots) - exact ||_2 / || exact ||_2 over the k spot
+// points of map m (add: an exactly computed part of the field, or NULL)
 __global__ void spot_error_kernel(const float *__restrict__ pred, const int32_t *__restrict__ idx,
-                                  const double *__restrict__ exact, const double *__restrict__ scale, int hw, int k,
-                                  float mu, float sigma, double *__restrict__ err) {
+                                  const double *__restrict__ exact, const double *__restrict__ scale,
+                                  const double *__restrict__ add, int hw, int k, float mu, float sigma,
+                                  double *__restrict__ err) {
     const int m = blockIdx.x;
     __shared__ double sn[128], sd[128];
     double num = 0.0, den = 0.0;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         const int p = idx[(int64_t)m * k + j];
         const double e = exact[(int64_t)m * k + j];
-        const double v = pow(10.0, (double)pred[(int64_t)m * hw + p] * sigma + mu) / scale[m];
+        const double v = pow(10.0, (double)pred[(int64_t)m * hw + p] * sigma + mu) / scale[m] +
+                         (add ? add[(int64_t)m * hw + p] : 0.0);
         num += (v - e) * (v - e);
         den += e * e;
     }
@@ -648,6 +682,13 @@ cudaError_t launch_conv_tc(const void *in, const void *w, const float *bias, con
     if (!configured) {
         cudaError_t err = cudaFuncSetAttribute(ddk::conv3x3_tc_kernel<CI, CO, EPI>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(ddk::kMaxDil));
+        // the whole L1/shared array as shared memory: without this preference the occupancy
+        // query below counts a small shared-memory carveout and allows one CTA (4 warps) per
+        // SM, leaving the tensor pipe idle behind each CTA's copy and MMA waits
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(ddk::conv3x3_tc_kernel<CI, CO, EPI>,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
         if (err != cudaSuccess) return err;
         configured = true;
     }
@@ -764,8 +805,31 @@ dd_status dd_sur_mse(const float *pred, const float *target, int64_t n, void *dz
     if (!pred || !target || !dz || !block_sums || !loss_sum || n < 1) return dd::fail(DD_EINVAL, "dd_sur_mse: bad arguments");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int nb = (int)((n + 255) / 256);
-    ddk::mse_kernel<<<nb, 256, 0, st>>>(pred, target, n, (ddk::bf16 *)dz, block_sums);
+    ddk::mse_kernel<<<nb, 256, 0, st>>>(pred, target, nullptr, n, (ddk::bf16 *)dz, block_sums);
     ddk::sum_doubles_kernel<<<1, 256, 0, st>>>(block_sums, nb, loss_sum);
+    DD_CUDA_TRY(cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status dd_sur_wmse(const float *pred, const float *target, const float *weight, int64_t n, void *dz,
+                      double *block_sums, double *loss_sum, void *cuda_stream) {
+    dd::clear_error();
+    if (!pred || !target || !weight || !dz || !block_sums || !loss_sum || n < 1)
+        return dd::fail(DD_EINVAL, "dd_sur_wmse: bad arguments");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int nb = (int)((n + 255) / 256);
+    ddk::mse_kernel<<<nb, 256, 0, st>>>(pred, target, weight, n, (ddk::bf16 *)dz, block_sums);
+    ddk::sum_doubles_kernel<<<1, 256, 0, st>>>(block_sums, nb, loss_sum);
+    DD_CUDA_TRY(cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status dd_sur_weights(const float *target, int64_t n_maps, int64_t hw, float mu, float sigma, float alpha,
+                         float *w, void *cuda_stream) {
+    dd::clear_error();
+    if (!target || !w || n_maps < 1 || hw < 1 || !(alpha >= 0.f && alpha <= 1.f))
+        return dd::fail(DD_EINVAL, "dd_sur_weights: bad arguments");
+    ddk::weights_kernel<<<(unsigned)n_maps, 256, 0, (cudaStream_t)cuda_stream>>>(target, hw, mu, sigma, alpha, w);
     DD_CUDA_TRY(cudaGetLastError());
     return DD_OK;
 }
@@ -817,12 +881,13 @@ dd_status dd_sur_fields(const float *pred, const double *scale, int64_t n_maps, 
 }
 
 dd_status dd_sur_spot_error(const float *pred, const int32_t *idx, const double *exact, const double *scale,
-                            int32_t n_maps, int32_t hw, int32_t k, float mu, float sigma, double *err,
-                            void *cuda_stream) {
+                            const double *add, int32_t n_maps, int32_t hw, int32_t k, float mu, float sigma,
+                            double *err, void *cuda_stream) {
     dd::clear_error();
     if (!pred || !idx || !exact || !scale || !err || n_maps < 1 || hw < 1 || k < 1)
         return dd::fail(DD_EINVAL, "dd_sur_spot_error: bad arguments");
-    ddk::spot_error_kernel<<<n_maps, 128, 0, (cudaStream_t)cuda_stream>>>(pred, idx, exact, scale, hw, k, mu, sigma, err);
+    ddk::spot_error_kernel<<<n_maps, 128, 0, (cudaStream_t)cuda_stream>>>(pred, idx, exact, scale, add, hw, k, mu,
+                                                                          sigma, err);
     DD_CUDA_TRY(cudaGetLastError());
     return DD_OK;
 }

@@ -1,18 +1,26 @@
 """Learned surrogate of the final damage map, trained on the exact batched path.
 
 A small convolutional network maps four input planes of a scan -- the visit-time map
-(t_i / total scan time where visited), the visited mask, standardised log10 D and log10
-dwell -- on a 128 x 128 canvas at the probe pitch to the log10 of the dimensionless final
-field (psi * 4 pi D / Q0), floored six decades below the map's own peak: values below
-that floor change a map's relative L2 error by less than 1e-6, so the loss does not spend
-capacity on them.  Six 3x3 convolutions, 32 channels, ReLU,
+(log10 of each visit's age at the end of the scan, in dwells, / 4.5, where visited), the
+visited mask, standardised log10 D and log10 dwell -- on a 128 x 128 canvas at the probe
+pitch to the log10 of the dimensionless final field (psi * 4 pi D / Q0), floored six
+decades below the map's own peak: values below that floor change a map's relative L2
+error by less than 1e-6, so the loss does not spend capacity on them.  The probe sigma is
+fixed (0.1 nm) for the surrogate's scans: it is not an input plane, and near the last
+visits the field depends on it.  The loss is the squared log error weighted per pixel by
+the pixel's share of the map's squared norm (plus a small uniform part), which to first
+order is the squared relative L2 error of the linear map, the measure the surrogate is
+judged by.  Six 3x3 convolutions, 32 channels, ReLU,
 BF16 activations, FP32 accumulation and FP32 master weights; every layer, the loss, the
 weight and data gradients and Adam run in the library's CUDA kernels (dd_sur_* in
 include/dd.h).  This module only allocates buffers and sequences those calls.
 
-The exact path (dd_batch_*) generates the training fields and is also the fallback: at
-inference every map gets k exact spot values, and a map whose estimated relative L2 error
-exceeds the threshold is recomputed exactly.
+The network learns the field of all but the last K_EXACT visits (the "background"); the
+last K_EXACT visits, whose sharp, recent deposits carry most of a map's squared norm, are
+added by the exact path (K_EXACT x 128^2 pair terms per map, against the full map's
+n_visits x 128^2).  The exact path (dd_batch_*) generates the training fields and is also
+the fallback: at inference every map gets k exact spot values, and a map whose estimated
+relative L2 error exceeds the threshold is recomputed exactly.
 """
 import math
 import time
@@ -31,6 +39,10 @@ REAL_IN, REAL_OUT = 4, 1
 FLOOR_REL = -6.0          # target floor: log10 of the fraction of the map's peak
 # fixed affine normalisation of the target log10 field: (log10 psi - MU) / SIGMA
 MU, SIGMA = -3.0, 3.0
+PROBE_SIGMA = 0.1e-9      # probe sigma of every surrogate scan [m]
+LAG_SCALE = 4.5           # time plane: log10(age in dwells) / LAG_SCALE (ages up to 16384)
+LOSS_ALPHA = 0.9          # share of the loss weight that follows the pixel's squared field
+K_EXACT = 64              # the last visits of a scan, added exactly to the network's background
 
 
 def _torch():
@@ -93,9 +105,13 @@ class Net:
         b.dd_sur_conv3x3(self.acts[5], self.wb[5], bias, None, self.pred, 1, self.dil[5])
         return self.pred
 
-    def backward(self, target):
-        """MSE against target (FP32 [B,H,W]); fills self.grads; returns the loss tensor."""
-        b.dd_sur_mse(self.pred, target, self.dz6, self.block_sums, self.loss_sum)
+    def backward(self, target, weight=None):
+        """(Weighted) squared error against target (FP32 [B,H,W]); fills self.grads; returns
+        the loss tensor."""
+        if weight is None:
+            b.dd_sur_mse(self.pred, target, self.dz6, self.block_sums, self.loss_sum)
+        else:
+            b.dd_sur_wmse(self.pred, target, weight, self.dz6, self.block_sums, self.loss_sum)
         b.dd_sur_wgrad(self.acts[5], self.dz6, self.part, self.grads[5], self.dil[5])
         b.dd_sur_conv3x3(self.dz6, self.wf[5], None, self.acts[5], self.dzs[0], 2, self.dil[5])
         cur = 0
@@ -147,8 +163,10 @@ class Net:
 # ----------------------------------------------------------------------- dataset
 
 def draw_scans(n_maps, seed, n_min=32, n_max=128):
-    """Scans with the batched workload's distributions (seeded)."""
-    return w.batched_specs(n_scans=n_maps, seed=seed, n_min=n_min, n_max=n_max)
+    """Scans with the batched workload's distributions (seeded), the probe sigma fixed at
+    PROBE_SIGMA (it is not an input of the network)."""
+    return [s.with_(sigma_m=PROBE_SIGMA)
+            for s in w.batched_specs(n_scans=n_maps, seed=seed, n_min=n_min, n_max=n_max)]
 
 
 def canvas_points(spec):
@@ -165,7 +183,8 @@ def scan_inputs(specs):
         g, _, _ = sc.visits()
         nv = len(g)
         iy, ix = g // s.nx, g % s.nx
-        tmap[k, iy, ix] = np.arange(nv, dtype=np.float32) / nv
+        # age of visit k at the end of the scan, in dwells: nv - k (the last visit: 1)
+        tmap[k, iy, ix] = np.log10(nv - np.arange(nv, dtype=np.float64)).astype(np.float32) / LAG_SCALE
         scal[k] = [(math.log10(s.D_m2s) + 13.5) / 1.5, math.log10(s.dwell_s) + 6.0]
         sc.close()
     return tmap, scal
@@ -177,9 +196,27 @@ def field_scales(specs, device):
     return torch.tensor([4 * math.pi * s.D_m2s / s.Q0 for s in specs], dtype=torch.float64, device=device)
 
 
-def exact_fields(specs, device, prec="mixed", chunk=512, pts_index=None):
-    """Exact final fields psi [u/m^2] (FP64, device) on the canvas by the batched path,
-    `chunk` scans per plan; with pts_index ([N, k] canvas indices) only those points."""
+def split_scan(spec, k=K_EXACT):
+    """The scan's first n - k visits and its last k, as two custom-order scans of the same
+    grid positions and dwell: (background spec, its snapshot time, near spec, its
+    snapshot time).  The background is seen at the scan's end, n dwells; the near scan's
+    visits start (n - k) dwells early in its own clock, so it is seen at k dwells (the field
+    depends on t - t_i only).  Uniform dwell, no dead time (the surrogate's scans)."""
+    sc = b.Scan(spec)
+    g, _, _ = sc.visits()
+    sc.close()
+    n = len(g)
+    k = max(1, min(k, n - 1))
+    kw = dict(order=w.CUSTOM, keep_fraction=1.0, mask=None)
+    bg = spec.with_(custom_visit=np.ascontiguousarray(g[:n - k]), **kw)
+    near = spec.with_(custom_visit=np.ascontiguousarray(g[n - k:]), **kw)
+    return bg, n * spec.dwell_s, near, k * spec.dwell_s
+
+
+def exact_fields(specs, device, prec="mixed", chunk=512, pts_index=None, times=None):
+    """Exact fields psi [u/m^2] (FP64, device) on the canvas by the batched path, `chunk`
+    scans per plan, at times[k] (default: the end of scan k); with pts_index ([N, k]
+    canvas indices) only those points."""
     torch = _torch()
     outs = []
     for c0 in range(0, len(specs), chunk):
@@ -192,8 +229,9 @@ def exact_fields(specs, device, prec="mixed", chunk=512, pts_index=None):
             idx = pts_index[c0:c0 + chunk]
             allp = np.concatenate([canvas_points(s)[ix] for s, ix in zip(sub, idx)])
             offs = np.concatenate([[0], np.cumsum([len(ix) for ix in idx])]).astype(np.int64)
-        times = np.array([w.n_visits(s) * s.dwell_s for s in sub])
-        plan = b.Batch(scans, offs, times, prec)
+        tt = (np.array([w.n_visits(s) * s.dwell_s for s in sub]) if times is None
+              else np.asarray(times[c0:c0 + chunk], dtype=np.float64))
+        plan = b.Batch(scans, offs, tt, prec)
         outs.append(plan.run(torch.from_numpy(np.ascontiguousarray(allp)).to(device)))
         plan.close()
         for s in scans:
@@ -201,14 +239,29 @@ def exact_fields(specs, device, prec="mixed", chunk=512, pts_index=None):
     return torch.cat(outs) if outs else None
 
 
+def loss_weights(target):
+    """Per-pixel loss weights [N,H,W] (FP32, device) of normalised targets (dd_sur_weights)."""
+    torch = _torch()
+    wt = torch.empty_like(target)
+    b.dd_sur_weights(target, target.shape[0], CANVAS * CANVAS, MU, SIGMA, LOSS_ALPHA, wt)
+    return wt
+
+
+def near_fields(specs, device, pts_index=None):
+    """Exact field of each scan's last K_EXACT visits at its end [N, points] (u/m^2)."""
+    parts = [split_scan(s) for s in specs]
+    return exact_fields([p[2] for p in parts], device, pts_index=pts_index, times=[p[3] for p in parts])
+
+
 def build_dataset(n_maps, seed, device):
     """(specs, tmap [N,H,W] f32, scal [N,2] f32, normalised target [N,H,W] f32) on the device;
-    the target is (log10 of the dimensionless exact field, floored at 1e-6 of the map's
-    peak, - MU) / SIGMA."""
+    the target is (log10 of the dimensionless exact background field -- all visits but the
+    last K_EXACT, at the scan's end -- floored at 1e-6 of the map's peak, - MU) / SIGMA."""
     torch = _torch()
     specs = draw_scans(n_maps, seed)
     tmap, scal = scan_inputs(specs)
-    psi = exact_fields(specs, device)
+    parts = [split_scan(s) for s in specs]
+    psi = exact_fields([p[0] for p in parts], device, times=[p[1] for p in parts])
     target = torch.empty((n_maps, CANVAS, CANVAS), dtype=torch.float32, device=device)
     b.dd_sur_targets(psi, field_scales(specs, device), n_maps, CANVAS * CANVAS, FLOOR_REL, MU, SIGMA, target)
     return specs, torch.from_numpy(tmap).to(device), torch.from_numpy(scal).to(device), target
@@ -216,8 +269,9 @@ def build_dataset(n_maps, seed, device):
 
 # ---------------------------------------------------------------------- training
 
-def train(net, tmap, scal, target, epochs, batch=32, lr=2e-3, seed=0, log=None):
-    """Adam on the MSE of the log10 field; returns the per-epoch mean losses."""
+def train(net, tmap, scal, target, epochs, batch=32, lr=2e-3, seed=0, log=None, weight=None):
+    """Adam on the squared error of the normalised log10 field (weighted per pixel when
+    `weight` [N,H,W] is given); returns the per-epoch mean losses."""
     torch = _torch()
     N = tmap.shape[0]
     net.buffers(batch)
@@ -231,7 +285,7 @@ def train(net, tmap, scal, target, epochs, batch=32, lr=2e-3, seed=0, log=None):
             idx = torch.from_numpy(order[s0:s0 + batch]).to(tmap.device)
             b.dd_sur_planes(tmap[idx].contiguous(), scal[idx].contiguous(), net.x)
             net.forward()
-            loss = net.backward(target[idx].contiguous())
+            loss = net.backward(target[idx].contiguous(), None if weight is None else weight[idx].contiguous())
             net.adam(lr_ep)
             tot += float(loss.item()) / (batch * CANVAS * CANVAS)
             cnt += 1
@@ -269,6 +323,30 @@ def map_errors(fields, exact):
     return (torch.linalg.norm(fields - exact, dim=1) / torch.linalg.norm(exact, dim=1)).cpu().numpy()
 
 
+def spot_points(specs, k_spot, seed=0):
+    """Canvas indices [N, k_spot] of the exact spot checks: the positions of the last
+    k_spot / 2 visits (near them sits most of a map's squared norm) and k_spot / 2 seeded
+    canvas points."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((len(specs), k_spot), np.int32)
+    for m, s in enumerate(specs):
+        sc = b.Scan(s)
+        g, _, _ = sc.visits()
+        sc.close()
+        last = ((g // s.nx) * CANVAS + g % s.nx)[::-1][:k_spot // 2]
+        out[m, :len(last)] = last
+        out[m, len(last):] = rng.integers(0, CANVAS * CANVAS, k_spot - len(last))
+    return out
+
+
+def surrogate_fields(net, specs, tmap, scal, device, batch=256):
+    """Fields [N, H*W] (u/m^2, FP64): the network's background plus the exact field of each
+    scan's last K_EXACT visits; also returns the prediction and that exact part."""
+    pred = predict(net, tmap, scal, batch)
+    near = near_fields(specs, device).view(len(specs), -1)
+    return fields_from_prediction(pred, specs) + near, pred, near
+
+
 def infer_with_fallback(net, specs, tmap, scal, device, k_spot=64, threshold=1e-2, batch=256, seed=0):
     """Surrogate fields with exact spot checks; maps whose estimated relative L2 error
     exceeds `threshold` are recomputed by the exact batched path.  Returns
@@ -276,14 +354,12 @@ def infer_with_fallback(net, specs, tmap, scal, device, k_spot=64, threshold=1e-
     torch = _torch()
     t0 = time.perf_counter()
     N = len(specs)
-    pred = predict(net, tmap, scal, batch)
-    rng = np.random.default_rng(seed)
-    spot = np.stack([rng.choice(CANVAS * CANVAS, k_spot, replace=False) for _ in range(N)]).astype(np.int32)
+    fields, pred, near = surrogate_fields(net, specs, tmap, scal, device, batch)
+    spot = spot_points(specs, k_spot, seed)
     ex_spot = exact_fields(specs, device, pts_index=spot)
     est = torch.empty(N, dtype=torch.float64, device=device)
     b.dd_sur_spot_error(pred, torch.from_numpy(spot).to(device), ex_spot, field_scales(specs, device), N,
-                        CANVAS * CANVAS, k_spot, MU, SIGMA, est)
-    fields = fields_from_prediction(pred, specs)
+                        CANVAS * CANVAS, k_spot, MU, SIGMA, est, add=near)
     est = est.cpu().numpy()
     bad = np.nonzero(~(est <= threshold))[0]
     if len(bad):

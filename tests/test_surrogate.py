@@ -230,3 +230,47 @@ def test_checkpoint_resume_continues_identically(cuda, tmp_path):
     assert la == lc
     for pa, pc in zip(a.state(), c.state()):
         np.testing.assert_array_equal(pa, pc)
+
+
+def test_weighted_loss_kernels(cuda):
+    """dd_sur_weights and dd_sur_wmse against their definitions in numpy."""
+    import torch
+    rng = np.random.default_rng(3)
+    n_maps, hw = 3, 128 * 128
+    t = rng.uniform(-1.0, 1.2, (n_maps, hw)).astype(np.float32)
+    mu, sg, alpha = -3.0, 3.0, 0.9
+    wt = torch.empty((n_maps, hw), dtype=torch.float32, device=cuda)
+    b.dd_sur_weights(torch.from_numpy(t).to(cuda), n_maps, hw, mu, sg, alpha, wt)
+    f = 10.0 ** (t.astype(np.float64) * sg + mu)
+    want = alpha * hw * f ** 2 / np.sum(f ** 2, axis=1, keepdims=True) + (1 - alpha)
+    np.testing.assert_allclose(wt.cpu().numpy(), want, rtol=1e-5)
+    assert np.allclose(wt.cpu().numpy().mean(axis=1), 1.0, rtol=1e-4)     # mean weight 1 per map
+    pred = (t + rng.normal(0, 0.01, t.shape)).astype(np.float32)
+    n = pred.size
+    dz = torch.zeros((n, 16), dtype=torch.bfloat16, device=cuda)
+    bs = torch.zeros((n + 255) // 256, dtype=torch.float64, device=cuda)
+    ls = torch.zeros(1, dtype=torch.float64, device=cuda)
+    b.dd_sur_wmse(torch.from_numpy(pred).to(cuda), torch.from_numpy(t).to(cuda), wt, dz, bs, ls)
+    d = pred.astype(np.float64) - t
+    w64 = wt.cpu().numpy().astype(np.float64)
+    assert float(ls.item()) == pytest.approx(np.sum(w64 * d * d), rel=1e-6)
+    g = dz.float().cpu().numpy()
+    np.testing.assert_allclose(g[:, 0], (2 * w64 * d / n).reshape(-1), rtol=1e-2, atol=1e-12)
+    assert np.all(g[:, 1:] == 0)
+
+
+def test_background_plus_last_visits_is_the_whole_field(cuda):
+    """The surrogate's split of a scan: the exact field of its first n - K visits at the
+    scan's end plus that of its last K visits, each seen in its own clock, equals the whole
+    scan's field (FP64, to its tolerance), on the canvas."""
+    from paper_2507_00294_gb300 import surrogate as sur
+    specs = sur.draw_scans(6, seed=31)
+    parts = [sur.split_scan(s) for s in specs]
+    whole = sur.exact_fields(specs, cuda, prec="fp64").view(6, -1).cpu().numpy()
+    bg = sur.exact_fields([p[0] for p in parts], cuda, prec="fp64", times=[p[1] for p in parts]).view(6, -1)
+    near = sur.exact_fields([p[2] for p in parts], cuda, prec="fp64", times=[p[3] for p in parts]).view(6, -1)
+    total = (bg + near).cpu().numpy()
+    m = whole > 1e-12 * whole.max(axis=1, keepdims=True)
+    assert np.max(np.abs(total[m] / whole[m] - 1.0)) <= 1e-12
+    for s, (b_, _, n_, _) in zip(specs, parts):
+        assert b.Scan(b_).visits()[0].size + b.Scan(n_).visits()[0].size == b.Scan(s).visits()[0].size
