@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64/e2e/CPU/batch/surrogate legs")
     ap.add_argument("--surrogate-maps", type=int, default=20000)
-    ap.add_argument("--surrogate-epochs", type=int, default=20)
+    ap.add_argument("--surrogate-epochs", type=int, default=60)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--leg", choices=["all", "batched", "surrogate-infer", "surrogate"], default="all",
                     help="run one leg alone (for profiling): the 512-scan batch, or the surrogate "
@@ -459,6 +459,7 @@ def bench_surrogate(dev, maps, epochs):
     # surrogate end to end: input planes from the scan descriptions (host), upload, network,
     # and the exact field of each scan's last visits
     def net_e2e():
+        sur._VISITS.clear()                  # every scan's visit list built inside the timing
         tm, sc = sur.scan_inputs(te_specs)
         return sur.surrogate_fields(net, te_specs, torch.from_numpy(tm).to(dev), torch.from_numpy(sc).to(dev), dev)[0]
     fields_sur, t_net_e2e = timed(net_e2e)

@@ -1,7 +1,7 @@
 """Learned surrogate of the final damage map, trained on the exact batched path.
 
 A small convolutional network maps four input planes of a scan -- the visit-time map
-(log10 of each visit's age at the end of the scan, in dwells, / 4.5, where visited), the
+(the inverse of each visit's age at the end of the scan, in dwells, where visited), the
 visited mask, standardised log10 D and log10 dwell -- on a 128 x 128 canvas at the probe
 pitch to the log10 of the dimensionless final field (psi * 4 pi D / Q0), floored six
 decades below the map's own peak: values below that floor change a map's relative L2
@@ -40,7 +40,6 @@ FLOOR_REL = -6.0          # target floor: log10 of the fraction of the map's pea
 # fixed affine normalisation of the target log10 field: (log10 psi - MU) / SIGMA
 MU, SIGMA = -3.0, 3.0
 PROBE_SIGMA = 0.1e-9      # probe sigma of every surrogate scan [m]
-LAG_SCALE = 4.5           # time plane: log10(age in dwells) / LAG_SCALE (ages up to 16384)
 LOSS_ALPHA = 0.9          # share of the loss weight that follows the pixel's squared field
 K_EXACT = 64              # the last visits of a scan, added exactly to the network's background
 
@@ -48,6 +47,23 @@ K_EXACT = 64              # the last visits of a scan, added exactly to the netw
 def _torch():
     import torch
     return torch
+
+
+_VISITS = {}
+
+
+def visit_list(spec):
+    """Grid indices of the scan's visits in visit order (built once per spec object)."""
+    hit = _VISITS.get(id(spec))
+    if hit is not None and hit[0] is spec:
+        return hit[1]
+    sc = b.Scan(spec)
+    g, _, _ = sc.visits()
+    sc.close()
+    if len(_VISITS) > 100_000:
+        _VISITS.clear()
+    _VISITS[id(spec)] = (spec, g)
+    return g
 
 
 class Net:
@@ -179,14 +195,14 @@ def scan_inputs(specs):
     tmap = np.full((N, CANVAS, CANVAS), -1.0, np.float32)
     scal = np.zeros((N, 2), np.float32)
     for k, s in enumerate(specs):
-        sc = b.Scan(s)
-        g, _, _ = sc.visits()
+        g = visit_list(s)
         nv = len(g)
         iy, ix = g // s.nx, g % s.nx
-        # age of visit k at the end of the scan, in dwells: nv - k (the last visit: 1)
-        tmap[k, iy, ix] = np.log10(nv - np.arange(nv, dtype=np.float64)).astype(np.float32) / LAG_SCALE
+        # inverse age of visit k at the end of the scan, in dwells: 1 / (nv - k) (the last
+        # visit: 1).  Long after its dwell a visit's own dose falls as 1 / age, and BF16
+        # keeps 1 / age to 0.2 % (a log of the age would lose ln(age) times more)
+        tmap[k, iy, ix] = (1.0 / (nv - np.arange(nv, dtype=np.float64))).astype(np.float32)
         scal[k] = [(math.log10(s.D_m2s) + 13.5) / 1.5, math.log10(s.dwell_s) + 6.0]
-        sc.close()
     return tmap, scal
 
 
@@ -202,9 +218,7 @@ def split_scan(spec, k=K_EXACT):
     snapshot time).  The background is seen at the scan's end, n dwells; the near scan's
     visits start (n - k) dwells early in its own clock, so it is seen at k dwells (the field
     depends on t - t_i only).  Uniform dwell, no dead time (the surrogate's scans)."""
-    sc = b.Scan(spec)
-    g, _, _ = sc.visits()
-    sc.close()
+    g = visit_list(spec)
     n = len(g)
     k = max(1, min(k, n - 1))
     kw = dict(order=w.CUSTOM, keep_fraction=1.0, mask=None)
@@ -330,9 +344,7 @@ def spot_points(specs, k_spot, seed=0):
     rng = np.random.default_rng(seed)
     out = np.empty((len(specs), k_spot), np.int32)
     for m, s in enumerate(specs):
-        sc = b.Scan(s)
-        g, _, _ = sc.visits()
-        sc.close()
+        g = visit_list(s)
         last = ((g // s.nx) * CANVAS + g % s.nx)[::-1][:k_spot // 2]
         out[m, :len(last)] = last
         out[m, len(last):] = rng.integers(0, CANVAS * CANVAS, k_spot - len(last))
