@@ -692,12 +692,14 @@ cudaError_t launch_conv_tc(const void *in, const void *w, const float *bias, con
         if (err != cudaSuccess) return err;
         configured = true;
     }
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0, smem_sm = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (err == cudaSuccess)
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ddk::conv3x3_tc_kernel<CI, CO, EPI>, 128, bytes(dil));
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (err != cudaSuccess) return err;
+    // CTAs that fit one SM's shared memory (each also costs the runtime's 1 KB reserve);
+    // the occupancy query was seen to answer 1 here, which left 4 warps per SM
+    const int per = (int)((size_t)smem_sm / (bytes(dil) + 1024));
     // items per (image, column tile): the segments of every residue chain rho < dil
     int per_strip = 0;
     for (int rho = 0; rho < dil; ++rho) {
