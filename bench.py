@@ -321,10 +321,11 @@ def cpu_oracle_sample(job, seconds, seed=11, threads=0):
     return run, rate, count, cores
 
 
-def bench_batched(dev, stream, runs=10, rank=0, world=1, dist=None):
-    """The 512-scan batched workload through one tuned, graph-replayed plan (FP32-mixed).
-    With several ranks the scans are dealt out longest-first by pair count (LPT), each rank
-    runs a plan of its own scans, and the fields are gathered once per run."""
+def bench_batched(dev, stream, runs=10, rank=0, world=1, dist=None, grid=True):
+    """The 512-scan batched workload through one tuned, graph-replayed plan (FP32-mixed),
+    each scan on its probe grid (dd_batch_create_grid; grid=False: the same points as
+    lists).  With several ranks the scans are dealt out longest-first by pair count (LPT),
+    each rank runs a plan of its own scans, and the fields are gathered once per run."""
     import torch
     from paper_2507_00294_gb300 import binding as b
     from paper_2507_00294_gb300 import shard
@@ -335,10 +336,15 @@ def bench_batched(dev, stream, runs=10, rank=0, world=1, dist=None):
     mine = shard.lpt_assign(costs, world)[rank]
     jobs = [jobs_all[k] for k in mine]
     offs = np.concatenate([[0], np.cumsum([len(j.pts_xy) for j in jobs])]).astype(np.int64)
-    pts = torch.from_numpy(np.ascontiguousarray(np.concatenate([j.pts_xy for j in jobs]))).to(dev)
     times = np.array([j.times[0] for j in jobs])
     scans = [b.Scan(j.scan) for j in jobs]
-    plan = b.Batch(scans, offs, times, "mixed")
+    if grid:
+        pts = None
+        plan = b.Batch(scans, None, times, "mixed",
+                       grids=[(0.0, 0.0, j.scan.pitch_m, j.scan.pitch_m, j.scan.nx, j.scan.ny) for j in jobs])
+    else:
+        pts = torch.from_numpy(np.ascontiguousarray(np.concatenate([j.pts_xy for j in jobs]))).to(dev)
+        plan = b.Batch(scans, offs, times, "mixed")
     variant = plan.tune(pts)
     out = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
     sizes = None
@@ -374,6 +380,8 @@ def bench_batched(dev, stream, runs=10, rank=0, world=1, dist=None):
             "rank_scans": len(jobs), "work_items": info["items"], "tuned_variant": variant,
             "workload": "512 scans, n ~ U{32..128}, D log-U[1e-15,1e-12], "
             "dwell log-U[1e-7,1e-5] s, sigma U[0.05,0.2] nm, keep U[0.1,1], random order, final field on the n x n grid",
+            "points": "each scan's probe grid, dd_batch_create_grid (32 x 32 grid tiles)" if grid
+                      else "each scan's probe grid as a point list (512-point tiles)",
             "launch": "persistent kernel, atomic work claim, CUDA graph replay" +
                       (", scans split over %d GPUs longest-first, one gather per run" % world if world > 1 else "")}
 
@@ -438,16 +446,15 @@ def bench_surrogate(dev, maps, epochs):
     # exact path end to end (scans, plans, kernels) on the test maps, full canvas
     sur.exact_fields(te_specs[:64], dev)
     exact, t_exact = timed(lambda: sur.exact_fields(te_specs, dev).view(n_test, -1))
-    pts = torch.from_numpy(np.ascontiguousarray(np.concatenate([sur.canvas_points(s) for s in te_specs]))).to(dev)
-    offs = np.arange(n_test + 1, dtype=np.int64) * sur.CANVAS * sur.CANVAS
     out = torch.empty(n_test * sur.CANVAS * sur.CANVAS, dtype=torch.float64, device=dev)
 
     def kernel_time(spec_list, times):
-        """One plan of the scans on the canvas, replayed: the kernels alone."""
+        """One plan of the scans on the canvas grid, replayed: the kernels alone."""
         scans = [b.Scan(s) for s in spec_list]
-        plan = b.Batch(scans, offs, np.asarray(times), "mixed")
-        plan.run(pts, out=out)
-        _, t = timed(lambda: plan.run(pts, out=out))
+        plan = b.Batch(scans, None, np.asarray(times), "mixed",
+                       grids=[(0.0, 0.0, s.pitch_m, s.pitch_m, sur.CANVAS, sur.CANVAS) for s in spec_list])
+        plan.run(out=out)
+        _, t = timed(lambda: plan.run(out=out))
         plan.close()
         return t
     t_exact_kernel = kernel_time(te_specs, [w_nv(s) * s.dwell_s for s in te_specs])
@@ -693,6 +700,10 @@ def run_ours(args):
         if world == 1:
             line["field_point_list"] = bench_point_list(b, job, times, scan, dev, stream, flush, field_pairs)
         line["batched"] = bench_batched(dev, stream, rank=rank, world=world, dist=dist)
+        if world == 1:
+            lst = bench_batched(dev, stream, grid=False)
+            line["batched"]["point_list"] = {"value": lst["value"], "ms_per_run": lst["ms_per_run"],
+                                             "tuned_variant": lst["tuned_variant"]}
         if world == 1:
             line["runtime_curve"] = bench_runtime_curve(dev, stream)
             if not args.no_surrogate:

@@ -216,6 +216,19 @@ dd_status dd_field_batch(const dd_scan *const *scans, int32_t n_scans, const int
    dd_batch_info: work items, causal pair-terms per run and the kernel variant.
    dd_batch_destroy synchronises the device and frees the plan (NULL is a no-op). */
 typedef struct dd_batch dd_batch;
+/* dd_batch_create_grid: the same plan with each scan evaluated on a rectilinear grid of
+   points instead of a point list: grid_xy[4k..4k+3] = (x0, y0, dx, dy) [m] and
+   grid_wh[2k], grid_wh[2k+1] = (columns W_k, rows H_k) of scan k; point (c, r) of scan k
+   sits at (x0 + c dx, y0 + r dy) (one product and one sum each, no fused multiply-add) and
+   its field goes to out[off_k + r W_k + c], off_k = sum over the earlier scans of W H.
+   dd_batch_run and dd_batch_tune then take pts_xy_m = NULL.  In FP32-mixed precision the
+   grid lets tiles of 32 x 32 points split the low-degree pair terms into column and row
+   factors (as dd_field_on_grid does); the result differs from the point-list plan by FP32
+   rounding only.  Errors: DD_EINVAL (sizes, non-finite origin or spacing, more than 2^31
+   points), DD_ENOMEM, DD_ECUDA. */
+dd_status dd_batch_create_grid(const dd_scan *const *scans, int32_t n_scans, const double *grid_xy,
+                               const int64_t *grid_wh, const double *times_s, dd_precision prec,
+                               dd_batch **out);
 dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
                           const double *times_s, dd_precision prec, dd_batch **out);
 dd_status dd_batch_run(dd_batch *batch, const double *pts_xy_m, double *out, void *cuda_stream);

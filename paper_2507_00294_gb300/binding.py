@@ -70,6 +70,8 @@ def load(build_if_missing=True):
     lib.dd_per_probe_dose_noalloc.argtypes = [_VP, ctypes.c_int, _VP, _VP]
     lib.dd_per_probe_dose_noalloc.restype = ctypes.c_int
     lib.dd_batch_create.argtypes = [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)]
+    lib.dd_batch_create_grid.argtypes = [_VP, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(_VP)]
+    lib.dd_batch_create_grid.restype = ctypes.c_int
     lib.dd_batch_run.argtypes = [_VP, _VP, _VP, _VP]
     lib.dd_batch_tune.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32)]
     lib.dd_batch_info.argtypes = [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32)]
@@ -322,26 +324,40 @@ def dd_field_batch(scans, pt_offsets, pts_xy_m, times_s, prec="mixed", out=None,
 
 
 class Batch:
-    """A dd_batch plan: many scans, each at its own points and one time, one graph launch."""
+    """A dd_batch plan: many scans, each at its own points and one time, one graph launch.
+    With grids ([n_scans, 6]: x0, y0, dx, dy [m], columns, rows) the points are each scan's
+    grid (dd_batch_create_grid) and run() takes pts_xy_m=None."""
 
-    def __init__(self, scans, pt_offsets, times_s, prec="mixed"):
+    def __init__(self, scans, pt_offsets, times_s, prec="mixed", grids=None):
         lib = load()
         self.scans = list(scans)                  # the plan reads them: keep them alive
         n = len(self.scans)
         self._handles = (ctypes.c_void_p * n)(*[s.handle.value for s in self.scans])
-        self.offsets = np.ascontiguousarray(np.asarray(pt_offsets, dtype=np.int64))
         times = np.ascontiguousarray(np.asarray(times_s, dtype=np.float64))
         h = ctypes.c_void_p()
-        _check(lib.dd_batch_create(self._handles, n, self.offsets.ctypes.data, times.ctypes.data,
-                                   PRECISIONS[prec], ctypes.byref(h)), "dd_batch_create")
+        if grids is None:
+            self.offsets = np.ascontiguousarray(np.asarray(pt_offsets, dtype=np.int64))
+            _check(lib.dd_batch_create(self._handles, n, self.offsets.ctypes.data, times.ctypes.data,
+                                       PRECISIONS[prec], ctypes.byref(h)), "dd_batch_create")
+        else:
+            g = np.asarray(grids, dtype=np.float64).reshape(n, 6)
+            xy = np.ascontiguousarray(g[:, :4])
+            wh = np.ascontiguousarray(g[:, 4:].astype(np.int64))
+            self.offsets = np.concatenate([[0], np.cumsum(wh[:, 0] * wh[:, 1])]).astype(np.int64)
+            _check(lib.dd_batch_create_grid(self._handles, n, xy.ctypes.data, wh.ctypes.data, times.ctypes.data,
+                                            PRECISIONS[prec], ctypes.byref(h)), "dd_batch_create_grid")
+        self.on_grid = grids is not None
         self.handle = h
         self.total = int(self.offsets[-1])
 
-    def run(self, pts_xy_m, out=None, stream=None):
+    def run(self, pts_xy_m=None, out=None, stream=None, device=None):
         if out is None:
             if _is_torch(pts_xy_m) and pts_xy_m.is_cuda:
                 import torch
                 out = torch.empty(self.total, dtype=torch.float64, device=pts_xy_m.device)
+            elif device is not None:
+                import torch
+                out = torch.empty(self.total, dtype=torch.float64, device=device)
             else:
                 out = np.empty(self.total, dtype=np.float64)
         p, kp = _ptr(pts_xy_m, np.float64)
@@ -349,7 +365,7 @@ class Batch:
         _check(load().dd_batch_run(self.handle, p, o, _stream(stream, pts_xy_m, out)), "dd_batch_run")
         return out
 
-    def tune(self, pts_xy_m):
+    def tune(self, pts_xy_m=None):
         p, kp = _ptr(pts_xy_m, np.float64)
         v = ctypes.c_int32()
         _check(load().dd_batch_tune(self.handle, p, ctypes.byref(v)), "dd_batch_tune")

@@ -26,6 +26,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "dd_batch_grid.cuh"
 #include "dd_coef.cuh"
 #include "dd_e1.cuh"
 #include "dd_field_impl.cuh"
@@ -42,6 +43,10 @@ struct BScan {
     int64_t part_off;           // first partial of the scan (nblk * n_pts of them)
     double s, kappa, pref, tdim, inv_pitch;
     int nact, nblk;
+    // a grid of points (dd_batch_create_grid): point r W + c at (x0 + c dx, y0 + r dy) [m];
+    // W = 0 for an explicit point list
+    double gx0, gy0, gdx, gdy;
+    int64_t gW, gH, n_tc;
 };
 
 __device__ __forceinline__ int find_segment(const int64_t *__restrict__ offs, int n, int64_t g) {
@@ -59,8 +64,18 @@ __global__ void batch_prep_kernel(const BScan *__restrict__ sc, const int64_t *_
                                   double *__restrict__ Y, float4 *__restrict__ F) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
-    const double ip = sc[find_segment(pt_offs, n_scans, g)].inv_pitch;
-    const double x = xy[2 * g] * ip, y = xy[2 * g + 1] * ip;
+    const BScan &S = sc[find_segment(pt_offs, n_scans, g)];
+    const double ip = S.inv_pitch;
+    double xs, ys;
+    if (S.gW > 0) {                     // grid point: one product and one sum, no fused multiply-add
+        const int64_t p = g - S.pt_off, r = p / S.gW, c = p - r * S.gW;
+        xs = __dadd_rn(__dmul_rn((double)c, S.gdx), S.gx0);
+        ys = __dadd_rn(__dmul_rn((double)r, S.gdy), S.gy0);
+    } else {
+        xs = xy[2 * g];
+        ys = xy[2 * g + 1];
+    }
+    const double x = xs * ip, y = ys * ip;
     X[g] = x;
     Y[g] = y;
     const float xh = (float)x, yh = (float)y;
@@ -125,6 +140,28 @@ batch_field_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items,
     }
 }
 
+// Persistent CTAs over grid tiles of 32 x 32 points (FP32-mixed): item (scan, tile, block).
+__global__ void __launch_bounds__(kBgThreads, 8)
+batch_grid_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items, int n_items,
+                  unsigned *__restrict__ counter, const float4 *__restrict__ F, const RecF32 *__restrict__ rec,
+                  int sb, double *__restrict__ partial) {
+    __shared__ BGridSmem sm;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const int4 item = items[it];
+        const BScan &S = sc[item.x];
+        const int s_begin = item.z * sb;
+        const int s_end = min(s_begin + sb, S.nact);
+        field_tile_bgrid(sm, S.srcF, F + S.pt_off, S.gW, S.gH, item.y % S.n_tc, item.y / S.n_tc,
+                         rec + S.rec_off, s_begin, s_end, partial + S.part_off + (int64_t)item.z * S.n_pts);
+    }
+}
+
 __global__ void batch_reduce_kernel(const BScan *__restrict__ sc, const int64_t *__restrict__ pt_offs, int n_scans,
                                     int64_t total, const double *__restrict__ partial, double *__restrict__ out) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -171,6 +208,8 @@ struct dd_batch {
     double *d_pts = nullptr, *d_out = nullptr;   // staging for host buffers
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool on_grid = false;               // points formed from per-scan grids (no point buffer)
+    bool grid_tiles = false;            // ... and evaluated by the grid tile kernel (FP32-mixed)
     const double *g_pts = nullptr;
     double *g_out = nullptr;
     int g_variant = -1;
@@ -220,7 +259,11 @@ dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cuda
             ddk::batch_coef_kernel<ddk::RecF64><<<nb, 128, 0, st>>>(b->d_sc, b->d_rec_offs, b->n_scans, b->total_rec,
                                                                   (ddk::RecF64 *)b->d_rec);
     }
-    if (b->n_items > 0) {
+    if (b->n_items > 0 && b->grid_tiles) {
+        ddk::batch_grid_kernel<<<b->grid[0], ddk::kBgThreads, 0, st>>>(b->d_sc, b->d_items, b->n_items, b->d_counter,
+                                                                      b->d_F, (const ddk::RecF32 *)b->d_rec, b->sb,
+                                                                      b->d_part);
+    } else if (b->n_items > 0) {
         const int g = b->grid[variant];
         if (b->prec == DD_MIXED) {
             if (variant == 0) launch_field<ddk::CfgMixed>(b, g, st);
@@ -266,16 +309,39 @@ void tune_cache_store() {
     f << "}\n";
 }
 
-}  // namespace
+int grid_kernel_ctas() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(ddk::batch_grid_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        cudaGetLastError();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ddk::batch_grid_kernel, ddk::kBgThreads, 0);
+    return std::max(1, sms * std::max(1, std::min(per, 8)));
+}
 
-extern "C" {
-
-dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
-                          const double *times_s, dd_precision prec, dd_batch **out) {
-    dd::clear_error();
-    if (!scans || !pt_offsets || !times_s || !out || n_scans < 1)
-        return dd::fail(DD_EINVAL, "dd_batch_create: NULL argument or no scans");
-    if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_batch_create: unknown precision");
+// Plan of a batch: explicit points (grid_xy == NULL, pt_offsets given) or per-scan grids
+// (grid_xy: x0, y0, dx, dy per scan [m]; grid_wh: columns, rows per scan).
+dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets_in,
+                      const double *grid_xy, const int64_t *grid_wh, const double *times_s, dd_precision prec,
+                      dd_batch **out) {
+    std::vector<int64_t> offs_grid;
+    const int64_t *pt_offsets = pt_offsets_in;
+    if (grid_xy) {
+        offs_grid.assign((size_t)n_scans + 1, 0);
+        for (int k = 0; k < n_scans; ++k) {
+            const int64_t W = grid_wh[2 * k], H = grid_wh[2 * k + 1];
+            if (W < 0 || H < 0 || W > (int64_t(1) << 31) || H > (int64_t(1) << 31))
+                return dd::fail(DD_EINVAL, "dd_batch_create_grid: grid sizes must be in [0, 2^31]");
+            for (int q = 0; q < 4; ++q)
+                if (!std::isfinite(grid_xy[4 * k + q]))
+                    return dd::fail(DD_EINVAL, "dd_batch_create_grid: grid origin and spacing must be finite");
+            offs_grid[(size_t)k + 1] = offs_grid[(size_t)k] + W * H;
+            if (offs_grid[(size_t)k + 1] > (int64_t(1) << 31))
+                return dd::fail(DD_EINVAL, "dd_batch_create_grid: more than 2^31 points");
+        }
+        pt_offsets = offs_grid.data();
+    }
     if (pt_offsets[0] != 0) return dd::fail(DD_EINVAL, "dd_batch_create: pt_offsets[0] must be 0");
     for (int k = 0; k < n_scans; ++k) {
         if (!scans[k]) return dd::fail(DD_EINVAL, "dd_batch_create: NULL scan");
@@ -285,6 +351,8 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
     std::unique_ptr<dd_batch> b(new dd_batch());
     b->prec = prec;
     b->n_scans = n_scans;
+    b->on_grid = grid_xy != nullptr;
+    b->grid_tiles = b->on_grid && prec == DD_MIXED;
     DD_CUDA_TRY(cudaGetDevice(&b->device));
     const int tile = prec == DD_MIXED ? kTile : ddk::CfgF64::kThreads * ddk::CfgF64::kPPT;
     std::vector<ddk::BScan> sc((size_t)n_scans);
@@ -309,15 +377,32 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
         S.nblk = (S.nact + b->sb - 1) / b->sb;
         S.rec_off = rec;
         S.part_off = part;
+        S.gx0 = S.gy0 = S.gdx = S.gdy = 0.0;
+        S.gW = S.gH = S.n_tc = 0;
+        if (grid_xy) {
+            S.gx0 = grid_xy[4 * k]; S.gy0 = grid_xy[4 * k + 1];
+            S.gdx = grid_xy[4 * k + 2]; S.gdy = grid_xy[4 * k + 3];
+            S.gW = grid_wh[2 * k]; S.gH = grid_wh[2 * k + 1];
+            S.n_tc = (S.gW + ddk::kBgCols - 1) / ddk::kBgCols;
+        }
         pt_offs[(size_t)k] = S.pt_off;
         rec_offs[(size_t)k] = rec;
         rec += S.nact;
         part += (int64_t)S.nblk * S.n_pts;
-        const int64_t tiles = (S.n_pts + tile - 1) / tile;
+        // grid tiles of 32 x 32 points (items cost by their valid points), else point tiles
+        const int64_t n_tr = b->grid_tiles ? (S.gH + ddk::kBgRows - 1) / ddk::kBgRows : 0;
+        const int64_t tiles = S.n_pts == 0 ? 0 : b->grid_tiles ? S.n_tc * n_tr : (S.n_pts + tile - 1) / tile;
         for (int blk = 0; blk < S.nblk; ++blk) {
             const int64_t nsrc = std::min<int64_t>(S.nact, (int64_t)(blk + 1) * b->sb) - (int64_t)blk * b->sb;
             for (int64_t t = 0; t < tiles; ++t) {
-                const int64_t npt = std::min<int64_t>(tile, S.n_pts - t * tile);
+                int64_t npt;
+                if (b->grid_tiles) {
+                    const int64_t tc = t % S.n_tc, tr = t / S.n_tc;
+                    npt = std::min<int64_t>(ddk::kBgCols, S.gW - tc * ddk::kBgCols) *
+                          std::min<int64_t>(ddk::kBgRows, S.gH - tr * ddk::kBgRows);
+                } else {
+                    npt = std::min<int64_t>(tile, S.n_pts - t * tile);
+                }
                 items.push_back({nsrc * npt, make_int4(k, (int)t, blk, 0)});
             }
         }
@@ -363,7 +448,9 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
     DD_CUDA_TRY(cudaMemcpy(b->d_rec_offs, rec_offs.data(), rec_offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     if (!it.empty()) DD_CUDA_TRY(cudaMemcpy(b->d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
     DD_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
-    if (prec == DD_MIXED)
+    if (b->grid_tiles)
+        b->grid = {grid_kernel_ctas(), grid_kernel_ctas(), grid_kernel_ctas(), grid_kernel_ctas()};
+    else if (prec == DD_MIXED)
         b->grid = {persistent_grid<ddk::CfgMixed>(), persistent_grid<ddk::CfgMixed256>(), persistent_grid<ddk::CfgMixed64>(),
                    persistent_grid<ddk::CfgMixed64x12>()};
     else
@@ -378,7 +465,8 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
     int bucket = 0;
     while ((int64_t(1) << bucket) < pairs && bucket < 62) ++bucket;
     std::ostringstream key;
-    key << prop.name << "/sm" << prop.major << prop.minor << "/" << (prec == DD_MIXED ? "mixed" : "fp64") << "/2^" << bucket;
+    key << prop.name << "/sm" << prop.major << prop.minor << "/" << (prec == DD_MIXED ? "mixed" : "fp64")
+        << (b->on_grid ? "/grid" : "") << "/2^" << bucket;
     b->tune_key = key.str();
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -386,14 +474,39 @@ dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const in
         auto f = g_tune.find(b->tune_key);
         b->variant = f != g_tune.end() ? std::min(std::max(f->second, 0), kVariants - 1) : 0;
     }
+    if (b->grid_tiles) b->variant = 0;                  // one kernel for grid tiles
     *out = b.release();
     return DD_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+dd_status dd_batch_create(const dd_scan *const *scans, int32_t n_scans, const int64_t *pt_offsets,
+                          const double *times_s, dd_precision prec, dd_batch **out) {
+    dd::clear_error();
+    if (!scans || !pt_offsets || !times_s || !out || n_scans < 1)
+        return dd::fail(DD_EINVAL, "dd_batch_create: NULL argument or no scans");
+    if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_batch_create: unknown precision");
+    return create_plan(scans, n_scans, pt_offsets, nullptr, nullptr, times_s, prec, out);
+}
+
+dd_status dd_batch_create_grid(const dd_scan *const *scans, int32_t n_scans, const double *grid_xy,
+                               const int64_t *grid_wh, const double *times_s, dd_precision prec, dd_batch **out) {
+    dd::clear_error();
+    if (!scans || !grid_xy || !grid_wh || !times_s || !out || n_scans < 1)
+        return dd::fail(DD_EINVAL, "dd_batch_create_grid: NULL argument or no scans");
+    if (prec != DD_FP64 && prec != DD_MIXED) return dd::fail(DD_EINVAL, "dd_batch_create_grid: unknown precision");
+    return create_plan(scans, n_scans, nullptr, grid_xy, grid_wh, times_s, prec, out);
+}
+
 dd_status dd_batch_tune(dd_batch *b, const double *pts_xy_m, int32_t *chosen) {
     dd::clear_error();
-    if (!b || !pts_xy_m) return dd::fail(DD_EINVAL, "dd_batch_tune: NULL argument");
-    if (!dd::is_device_pointer(pts_xy_m)) return dd::fail(DD_EINVAL, "dd_batch_tune: points must be on the device");
+    if (!b || (!pts_xy_m && !b->on_grid)) return dd::fail(DD_EINVAL, "dd_batch_tune: NULL argument");
+    if (b->on_grid) pts_xy_m = nullptr;                  // grid plans form their points
+    else if (!dd::is_device_pointer(pts_xy_m))
+        return dd::fail(DD_EINVAL, "dd_batch_tune: points must be on the device");
     double *tmp = nullptr;
     DD_CUDA_TRY(cudaMalloc(&tmp, (size_t)std::max<int64_t>(1, b->total_pts) * sizeof(double)));
     cudaEvent_t e0, e1;
@@ -401,7 +514,7 @@ dd_status dd_batch_tune(dd_batch *b, const double *pts_xy_m, int32_t *chosen) {
     DD_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_v = 0;
-    const int nv = b->prec == DD_MIXED ? kVariants : 2;
+    const int nv = b->grid_tiles ? 1 : b->prec == DD_MIXED ? kVariants : 2;
     for (int v = 0; v < nv; ++v) {
         dd_status st = enqueue(b, pts_xy_m, tmp, v, b->cap);           // warm
         if (st != DD_OK) { cudaFree(tmp); return st; }
@@ -428,9 +541,10 @@ dd_status dd_batch_tune(dd_batch *b, const double *pts_xy_m, int32_t *chosen) {
 
 dd_status dd_batch_run(dd_batch *b, const double *pts_xy_m, double *out, void *cuda_stream) {
     dd::clear_error();
-    if (!b || !pts_xy_m || !out) return dd::fail(DD_EINVAL, "dd_batch_run: NULL argument");
+    if (!b || (!pts_xy_m && !b->on_grid) || !out) return dd::fail(DD_EINVAL, "dd_batch_run: NULL argument");
     cudaStream_t stream = (cudaStream_t)cuda_stream;
-    const bool pts_host = !dd::is_device_pointer(pts_xy_m);
+    if (b->on_grid) pts_xy_m = nullptr;                  // grid plans form their points
+    const bool pts_host = pts_xy_m && !dd::is_device_pointer(pts_xy_m);
     const bool out_host = !dd::is_device_pointer(out);
     const size_t npt = (size_t)std::max<int64_t>(1, b->total_pts);
     if ((pts_host && !b->d_pts) || (out_host && !b->d_out)) {
@@ -461,7 +575,7 @@ dd_status dd_batch_run(dd_batch *b, const double *pts_xy_m, double *out, void *c
         b->g_variant = b->variant;
     }
     {
-        dd::ProfScope ps(variant_name(b->prec, b->variant), stream);
+        dd::ProfScope ps(b->grid_tiles ? "batch_grid_mixed_32x32" : variant_name(b->prec, b->variant), stream);
         DD_CUDA_TRY(cudaGraphLaunch(b->exec, stream));
     }
     if (out_host)

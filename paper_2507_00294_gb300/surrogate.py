@@ -236,17 +236,19 @@ def exact_fields(specs, device, prec="mixed", chunk=512, pts_index=None, times=N
     for c0 in range(0, len(specs), chunk):
         sub = specs[c0:c0 + chunk]
         scans = [b.Scan(s) for s in sub]
+        tt = (np.array([w.n_visits(s) * s.dwell_s for s in sub]) if times is None
+              else np.asarray(times[c0:c0 + chunk], dtype=np.float64))
         if pts_index is None:
-            allp = np.concatenate([canvas_points(s) for s in sub])
-            offs = np.arange(len(sub) + 1, dtype=np.int64) * CANVAS * CANVAS
+            # the canvas as each scan's grid of points (dd_batch_create_grid)
+            plan = b.Batch(scans, None, tt, prec,
+                           grids=[(0.0, 0.0, s.pitch_m, s.pitch_m, CANVAS, CANVAS) for s in sub])
+            outs.append(plan.run(device=device))
         else:
             idx = pts_index[c0:c0 + chunk]
             allp = np.concatenate([canvas_points(s)[ix] for s, ix in zip(sub, idx)])
             offs = np.concatenate([[0], np.cumsum([len(ix) for ix in idx])]).astype(np.int64)
-        tt = (np.array([w.n_visits(s) * s.dwell_s for s in sub]) if times is None
-              else np.asarray(times[c0:c0 + chunk], dtype=np.float64))
-        plan = b.Batch(scans, offs, tt, prec)
-        outs.append(plan.run(torch.from_numpy(np.ascontiguousarray(allp)).to(device)))
+            plan = b.Batch(scans, offs, tt, prec)
+            outs.append(plan.run(torch.from_numpy(np.ascontiguousarray(allp)).to(device)))
         plan.close()
         for s in scans:
             s.close()
