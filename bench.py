@@ -56,6 +56,9 @@ GRID_FLOPS_SEP1, GRID_FLOPS_SEP2, GRID_MUFU_SEP = 3.17, 5.92, 0.258
 GRID_FLOPS_RHO, GRID_FLOPS_ZERO = 0.625, 0.125
 # FP32 peak from the unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 FMA peak: 1.6 per clock per SM (a microbenchmark on this GPU: 0.50 T DFMA/s at
+# 1.995 GHz) x 152 x 2.07 GHz.
+FP64_PEAK_TDFMA = 152 * 1.6 * 2.07e9 / 1e12
 # MUFU ex2 peak: 32 per clock per SM (GB300 doubles the SFU exponential rate of B200; a
 # microbenchmark on this GPU measured 30.6 per clock per SM at 1.995 GHz) x 152 x 2.07 GHz.
 MUFU_PEAK_TOPS = 152 * 32 * 2.07e9 / 1e12
@@ -96,7 +99,7 @@ class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
-    PERIOD_MS = 25
+    PERIOD_MS = 10
 
     def __init__(self, index):
         self.index = index
@@ -279,6 +282,35 @@ def ops_per_pair(job, samples=400_000, seed=5, grid=False):
     wgt = nact[np.arange(samples)]               # pairs are sampled per snapshot: weight by n_active
     return (float(np.sum(f * wgt) / np.sum(wgt)), float(np.sum(m * wgt) / np.sum(wgt)),
             float(np.sum(zero * wgt) / np.sum(wgt)))
+
+
+def dfma_per_pair_fp64(job, samples=200_000, seed=6):
+    """Algorithmic FP64 operations (DFMA-equivalents) per pair of the FP64 field kernel on
+    this workload: rho^2 shared by the 4 snapshots of a chunk (1), the moment polynomial of
+    the cheapest degree whose range holds the pair's h (4, 8, 11, 15 up to h = 1e-3, 0.052,
+    0.19, 0.5: D + 1 with the final product), exp(-a) as 15, the two-E1 path as 60, a pair
+    with a >= 745 its rho^2 only."""
+    from paper_2507_00294_gb300 import workloads as w
+    s = job.scan
+    rng = np.random.default_rng(seed)
+    n = w.n_visits(s)
+    ts = np.arange(n) * s.dwell_s
+    it = rng.integers(0, len(job.times), samples)
+    t = job.times[it]
+    nact = np.searchsorted(ts, t, side="left")
+    i = (rng.random(samples) * nact).astype(np.int64)
+    ip = rng.integers(0, len(job.pts_xy), samples)
+    dx = job.pts_xy[ip, 0] - (i % s.nx) * s.pitch_m
+    dy = job.pts_xy[ip, 1] - (i // s.nx) * s.pitch_m
+    rho2 = dx * dx + dy * dy
+    dt = t - ts[i]
+    Ds, D, tau = s.sigma_m ** 2, s.D_m2s, s.dwell_s
+    w1 = 2 * Ds + 4 * D * dt
+    w0 = np.where(dt <= tau, 2 * Ds, 2 * Ds + 4 * D * (dt - tau))
+    a, h = rho2 / w1, rho2 / w0 - rho2 / w1
+    c = np.where(a >= 745, 1.0, np.where(h <= 1e-3, 1 + 5 + 15, np.where(h <= 0.052, 1 + 9 + 15,
+                 np.where(h <= 0.19, 1 + 12 + 15, np.where(h <= 0.5, 1 + 16 + 15, 1 + 60)))))
+    return float(np.sum(c * nact) / np.sum(nact))
 
 
 def workload():
@@ -684,6 +716,8 @@ def run_ours(args):
         b.dd_profile_enable(False)
         step("fp64")
         torch.cuda.synchronize(dev)
+        b.dd_profile_reset()
+        b.dd_profile_enable(True)
         e64 = []
         for k in range(args.fp64_steps):
             flush.fill_(float(k))
@@ -693,8 +727,23 @@ def run_ours(args):
             z.record(stream)
             e64.append((a, z))
         torch.cuda.synchronize(dev)
+        b.dd_profile_enable(False)
+        prof64 = b.dd_profile_read()
         v64, _, _ = whole_job(pairs_step, len(e64), sum(a.elapsed_time(z) for a, z in e64), dist, dev)
         line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": pairs_step / v64 * 1e3, "steps": len(e64)}
+        l64, ms64 = prof64.get("field_fp64", (0, 0.0))
+        if l64:
+            dpp = dfma_per_pair_fp64(job)
+            rate64 = rank_field_pairs / (ms64 / l64 / 1e3)
+            line["fp64"]["roofline"] = {
+                "bound": "alu", "kernel": "field_fp64", "pipe": "fp64", "achieved": dpp * rate64 / 1e12,
+                "peak": FP64_PEAK_TDFMA, "unit": "T DFMA-equivalents/s", "frac": dpp * rate64 / 1e12 / FP64_PEAK_TDFMA,
+                "avg_launch_ms": ms64 / l64, "kernel_pairs_per_s": rate64, "ops_per_pair": round(dpp, 2),
+                "peak_note": "FP64 FMA: 1.6 per clock per SM measured by a microbenchmark on this GPU (0.50 T/s "
+                             "at 1.995 GHz), x 152 SMs x 2070 MHz",
+                "ops_note": "per pair: rho^2 shared by 4 snapshots (1), the moment polynomial of the warp's "
+                            "degree (4 / 8 / 11 / 15 from the pair's own h: D + 1), exp(-a) counted as 15 "
+                            "DFMA-equivalents, 60 for a two-E1 pair"}
         line["mixed_over_fp64"] = value / v64
         line["e2e"] = bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, rr, pr, dr)
         if world == 1:
