@@ -169,8 +169,11 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
 // array), set once per device: the FP32-mixed tile's 8 CTAs of 13 KB fit in 132 KB and
 // the rest stays L1 for the minority classes' record reads (about 1 % faster than the
 // whole array as shared memory); the FP64 tile takes the whole array.
-// The grid tile (dd_field_grid.cuh) keeps 4 KB of row tables beside the general tile's
-// 12 KB: 8 CTAs of 17.3 KB (with the per-CTA reserve) need a 66 % carveout.
+// The grid tile (dd_field_grid.cuh): 128 columns x GridCfg::kPPT = 4 rows (a tile of 8 rows
+// per thread, 80 registers and 6 CTAs per SM, measured 8 % slower).  Its row tables sit
+// beside the general tile's 12 KB: 8 CTAs of 17.3 KB (with the per-CTA reserve) need a 66 %
+// carveout.
+using GridCfg = ddk::CfgMixed;
 constexpr int kGridCarveout = 66;
 
 template <typename Cfg, bool kGrid>
@@ -180,7 +183,7 @@ struct TileKernel {
 };
 template <>
 struct TileKernel<ddk::CfgMixed, true> {
-    static constexpr auto fn() { return ddk::field_grid_kernel<ddk::CfgMixed>; }
+    static constexpr auto fn() { return ddk::field_grid_kernel<GridCfg>; }
     static constexpr int carveout = kGridCarveout;
 };
 
@@ -264,7 +267,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     const int tile = Cfg::kThreads * Cfg::kPPT;
     // grid tiles: 128 columns x 4 rows (kThreads x kPPT); otherwise 512 consecutive points
     const int64_t n_tc = grid_tiles ? (grid.W + Cfg::kThreads - 1) / Cfg::kThreads : 0;
-    const int64_t n_tiles = grid_tiles ? n_tc * ((grid.H + Cfg::kPPT - 1) / Cfg::kPPT) : (n_pts + tile - 1) / tile;
+    const int64_t n_tiles = grid_tiles ? n_tc * ((grid.H + GridCfg::kPPT - 1) / GridCfg::kPPT)
+                                       : (n_pts + tile - 1) / tile;
     int sb = Cfg::kSB;
     int group = n_t;
     const size_t budget = size_t(1) << 30;
@@ -417,7 +421,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                 if constexpr (kMixed) {
                     if (grid_tiles) {
                         DD_PROFILED("field_grid_mixed", stream,
-                                    (ddk::field_grid_kernel<Cfg><<<nctas, Cfg::kThreads, 0, stream>>>(
+                                    (ddk::field_grid_kernel<GridCfg><<<nctas, Cfg::kThreads, 0, stream>>>(
                                         grid.W, grid.H, n_tc, d_rec, d_roff, d_nact, d_desc, n_tiles, item0, ng, sb,
                                         d_part, pstride, srcF, PF)));
                         DD_CUDA_TRY(cudaGetLastError());
