@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--surrogate-maps", type=int, default=20000)
     ap.add_argument("--surrogate-epochs", type=int, default=60)
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--leg", choices=["all", "batched", "surrogate-infer", "surrogate"], default="all",
+    ap.add_argument("--leg", choices=["all", "batched", "surrogate-infer", "surrogate", "dose"], default="all",
                     help="run one leg alone (for profiling): the 512-scan batch, or the surrogate "
                          "network's inference at batch 256 (random weights)")
     return ap.parse_args()
@@ -313,6 +313,117 @@ def dfma_per_pair_fp64(job, samples=200_000, seed=6):
     return float(np.sum(c * nact) / np.sum(nact))
 
 
+# Batch grid tile (32 x 32 points, one snapshot, 8 rows per thread): a degree-2 pair is one
+# FMA (2 flops) plus its share of the column factor X (2 FMAs and one ex2 per column and
+# visit, shared by 8 rows: 0.5 flops, 0.125 ex2) and of dx, dx^2 (0.25); with the cross term
+# A = X (2 ln2 g_2x) dx^2 (3 multiplies / 8 = 0.375) and one more FMA (2); degree 4 and above
+# per point with rho^2 = dx^2 + dy^2 (one FMA, 2 flops).
+# per class: zero (a >= 87), degree 2 without / with the cross term, degree 4, 8, 12, two E1
+BATCH_FLOPS = np.array([0.25, 2.75, 5.125, 2.0 + 8.0 + 1.0, 2.0 + 17.0 + 1.0, 2.0 + 25.0 + 1.0, 2.0 + 55.0])
+BATCH_MUFU = np.array([0.0, 0.125, 0.125, 1.0, 1.0, 1.0, 4.0])
+
+
+def batch_ops_per_pair(jobs, samples=200_000, seed=7):
+    """Algorithmic FP32 flops and ex2 per pair-term of the batch grid kernel on the 512-scan
+    workload (each pair at the cheapest class its own h allows, degree 2 with the cross term
+    where 2 g_2x dx^2 dy^2 exceeds 2.5e-7), pairs sampled in proportion to each scan's."""
+    from paper_2507_00294_gb300 import binding as b
+    from paper_2507_00294_gb300 import workloads as w
+    rng = np.random.default_rng(seed)
+    pairs = np.array([w.n_visits(j.scan) * len(j.pts_xy) for j in jobs], dtype=np.float64)
+    ks = rng.choice(len(jobs), samples, p=pairs / pairs.sum())
+    code = np.empty(samples, dtype=np.int64)
+    for k in np.unique(ks):
+        sel = np.nonzero(ks == k)[0]
+        j = jobs[k]
+        s = j.scan
+        sc = b.Scan(s)
+        g = sc.visits()[0].astype(np.int64)
+        sc.close()
+        nv = len(g)
+        i = rng.integers(0, nv, len(sel))
+        ip = rng.integers(0, len(j.pts_xy), len(sel))
+        dx = j.pts_xy[ip, 0] / s.pitch_m - g[i] % s.nx
+        dy = j.pts_xy[ip, 1] / s.pitch_m - g[i] // s.nx
+        rho2 = dx * dx + dy * dy
+        kap, ss = s.D_m2s * s.dwell_s / s.pitch_m ** 2, (s.sigma_m / s.pitch_m) ** 2
+        L = (nv - i).astype(np.float64)                  # lag of visit i at the scan's end
+        w1 = 2 * ss + 4 * kap * L
+        w0 = 2 * ss + 4 * kap * (L - 1)
+        dq = 1 / w0 - 1 / w1
+        a, h = rho2 / w1, rho2 * dq
+        cross = 2 * 1.4426950408889634 * cumulant_l2(4 * kap / w0) * dq ** 2 * dx ** 2 * dy ** 2
+        code[sel] = np.where(a >= 87, 0, np.where(h <= 0.04, np.where(cross <= 2.5e-7, 1, 2),
+                             np.where(h <= 0.33, 3, np.where(h <= 1.25, 4, np.where(h <= 2.0, 5, 6)))))
+    return float(BATCH_FLOPS[code].mean()), float(BATCH_MUFU[code].mean())
+
+
+def dose_ops_per_pair(spec, samples=200_000, seed=9):
+    """Algorithmic FP32 flops and MUFU operations per pair of the dwell-start dose on a
+    uniform scan: target j, source i = j - k seen k dwells later at distance rho_jk, each
+    pair at the cheapest class its own h allows; rho^2 is per pair here (about 4 flops: two
+    differences and one multiply-add)."""
+    from paper_2507_00294_gb300 import binding as b
+    rng = np.random.default_rng(seed)
+    sc = b.Scan(spec)
+    g = sc.visits()[0].astype(np.int64)
+    sc.close()
+    n = len(g)
+    # pairs (j, k) uniform over the triangle k < j: j with weight j, then k uniform
+    j = np.floor(np.sqrt(rng.random(samples)) * (n - 1)).astype(np.int64) + 1
+    k = np.floor(rng.random(samples) * j).astype(np.int64) + 1
+    i = j - k
+    dx = (g[j] % spec.nx - g[i] % spec.nx).astype(np.float64)
+    dy = (g[j] // spec.nx - g[i] // spec.nx).astype(np.float64)
+    rho2 = dx * dx + dy * dy
+    kap, ss = spec.D_m2s * spec.dwell_s / spec.pitch_m ** 2, (spec.sigma_m / spec.pitch_m) ** 2
+    w1 = 2 * ss + 4 * kap * k
+    w0 = 2 * ss + 4 * kap * (k - 1)
+    a, h = rho2 / w1, rho2 * (1 / w0 - 1 / w1)
+    rho = 4.0 - FLOPS_ZERO                               # the per-pair rho^2 in place of the shared one
+    f = np.where(a >= 87, 4.0, np.where(h <= 0.04, FLOPS_SERIES[2] + rho, np.where(h <= 0.33, FLOPS_SERIES[4] + rho,
+                 np.where(h <= 1.25, FLOPS_SERIES[8] + rho, np.where(h <= 2.0, FLOPS_SERIES[12] + rho,
+                                                                     FLOPS_GENERAL + rho)))))
+    m = np.where(a >= 87, 0.0, np.where(h <= 2.0, MUFU_SERIES, MUFU_GENERAL))
+    return float(f.mean()), float(m.mean())
+
+
+def bench_dose(b, dev, stream, job, n, reps=10):
+    """The dwell-start dose alone: the bench workload's 4096 visits and the 256 x 256
+    precision study's 65,536 (2.1e9 pairs), FP32-mixed, kernels on the device."""
+    import torch
+    from paper_2507_00294_gb300 import workloads as w
+    out = {}
+    for name, spec in (("raster64", job.scan), ("grid256_raster", w.precision_study(w.RASTER, 0).scan)):
+        scan = b.Scan(spec)
+        nv = len(scan)
+        dose = torch.empty(nv, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            b.dd_per_probe_dose(scan, "mixed", out=dose, stream=stream)
+        torch.cuda.synchronize(dev)
+        b.dd_profile_reset()
+        b.dd_profile_enable(True)
+        for _ in range(reps):
+            b.dd_per_probe_dose(scan, "mixed", out=dose, stream=stream)
+        torch.cuda.synchronize(dev)
+        b.dd_profile_enable(False)
+        prof = b.dd_profile_read()
+        ms = sum(v[1] for v in prof.values()) / reps
+        kl, kms = prof.get("dose_mixed", (0, 0.0))
+        pairs = nv * (nv - 1) // 2
+        fpp, mpp = dose_ops_per_pair(spec)
+        krate = pairs / (kms / max(1, kl) / 1e3) if kl else None
+        out[name] = {"visits": nv, "pairs": pairs, "ms": ms, "value": pairs / (ms / 1e3), "unit": UNIT,
+                     "roofline": {"bound": "alu", "kernel": "dose_mixed", "pipe": "fp32",
+                                  "achieved": fpp * krate / 1e12 if krate else None, "peak": FP32_PEAK_TFLOPS,
+                                  "unit": "TFLOP/s", "frac": fpp * krate / 1e12 / FP32_PEAK_TFLOPS if krate else None,
+                                  "mufu_frac": mpp * krate / 1e12 / MUFU_PEAK_TOPS if krate else None,
+                                  "ops_per_pair": round(fpp, 2), "mufu_per_pair": round(mpp, 3),
+                                  "avg_launch_ms": kms / max(1, kl)}}
+        scan.close()
+    return out
+
+
 def workload():
     """The 64x64 raster job, its evaluation grid (x0, y0, dx, dy, columns, rows) -- the
     job's 128 x 128 points at pitch / 2 are that grid in row-major order -- and the pair
@@ -407,7 +518,16 @@ def bench_batched(dev, stream, runs=10, rank=0, world=1, dist=None, grid=True):
     value, ms_total, _ = whole_job(total_pairs, runs, sum(a.elapsed_time(z) for a, z in ev), dist, dev)
     info = plan.info()
     plan.close()
-    return {"value": value, "unit": UNIT, "ms_per_run": ms_total / runs, "runs": runs,
+    roof = None
+    if grid and world == 1:
+        fpp, mpp = batch_ops_per_pair(jobs_all)
+        rate = total_pairs / (ms_total / runs / 1e3)
+        roof = {"bound": "alu", "kernel": "batch_grid_mixed_32x32", "pipe": "fp32", "achieved": fpp * rate / 1e12,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fpp * rate / 1e12 / FP32_PEAK_TFLOPS,
+                "ops_per_pair": round(fpp, 3), "mufu_per_pair": round(mpp, 4),
+                "mufu_frac": mpp * rate / 1e12 / MUFU_PEAK_TOPS,
+                "note": "event time of the whole graph (coefficients, kernel, reduce) per run"}
+    return {"value": value, "unit": UNIT, "ms_per_run": ms_total / runs, "runs": runs, "roofline": roof,
             "pairs_per_run": total_pairs, "rank_pairs_per_run": info["pairs"], "scans": len(jobs_all),
             "rank_scans": len(jobs), "work_items": info["items"], "tuned_variant": variant,
             "workload": "512 scans, n ~ U{32..128}, D log-U[1e-15,1e-12], "
@@ -564,6 +684,9 @@ def run_leg(args):
         res = bench_batched(dev, torch.cuda.current_stream(dev), runs=3)
     elif args.leg == "surrogate":
         res = bench_surrogate(dev, args.surrogate_maps, args.surrogate_epochs)
+    elif args.leg == "dose":
+        job, n, _, _ = workload()
+        res = bench_dose(b, dev, torch.cuda.current_stream(dev), job, n)
     else:
         res = bench_surrogate_inference(dev)
     print(json.dumps({"leg": args.leg, **res}), flush=True)
@@ -750,6 +873,7 @@ def run_ours(args):
             line["field_point_list"] = bench_point_list(b, job, times, scan, dev, stream, flush, field_pairs)
         line["batched"] = bench_batched(dev, stream, rank=rank, world=world, dist=dist)
         if world == 1:
+            line["dose"] = bench_dose(b, dev, stream, job, n)
             lst = bench_batched(dev, stream, grid=False)
             line["batched"]["point_list"] = {"value": lst["value"], "ms_per_run": lst["ms_per_run"],
                                              "tuned_variant": lst["tuned_variant"]}
