@@ -142,13 +142,18 @@ def test_cumulative_field_brute_force_tiny_scans():
         pts = np.array([[0.0, 0.0], [0.25e-9, 0.1e-9], [1.0e-9, 0.5e-9], [3e-9, -1e-9]])
         times = np.array([0.5e-6, 1.0e-6, 2.5e-6, 7e-6])
         got = oracle.field(src, Ds, D, Q0, pts[:, 0], pts[:, 1], times)
+        # the (point, time) pair list form, on every pair, against the same brute force
+        ip_all, it_all = np.meshgrid(np.arange(len(pts)), np.arange(len(times)))
+        pairs = oracle.field_pairs(src, Ds, D, Q0, pts[ip_all.ravel(), 0], pts[ip_all.ravel(), 1],
+                                   times[it_all.ravel()]).reshape(len(times), len(pts))
         for it, t in enumerate(times):
             for ip in range(len(pts)):
                 ref = brute_field(xs, ys, ts, taus, pts[ip, 0], pts[ip, 1], t)
-                if ref < 1e-250:
-                    assert got[it, ip] < 1e-240
-                else:
-                    assert abs(got[it, ip] / ref - 1.0) < 1e-12
+                for val in (got[it, ip], pairs[it, ip]):
+                    if ref < 1e-250:
+                        assert val < 1e-240
+                    else:
+                        assert abs(val / ref - 1.0) < 1e-12
 
 
 def test_raster_field_mirror_symmetry():
