@@ -758,12 +758,25 @@ def run_ours(args):
     dose = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
     rank_field_pairs = field_pairs // n_pts * (p1 - p0)     # every point has the same pair count
 
+    # The field and the dose are independent calls: the dose goes on a side stream that forks
+    # from the step's stream and joins it again, so that its short kernels run beside the
+    # field kernel's CTAs instead of after them; the step's events on `stream` bracket both.
+    side = torch.cuda.Stream(dev)
+
     def step(prec):
-        b.dd_field_on_grid(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, prec, out=out, stream=stream)
+        fork = torch.cuda.Event()
+        fork.record(stream)
+        side.wait_event(fork)
         if world == 1:
-            b.dd_per_probe_dose(scan, prec, out=dose, stream=stream)
+            b.dd_per_probe_dose(scan, prec, out=dose, stream=side)
+        else:
+            b.dd_per_probe_dose_range(scan, j0, j1, prec, out=dose, stream=side)
+        b.dd_field_on_grid(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, prec, out=out, stream=stream)
+        join = torch.cuda.Event()
+        join.record(side)
+        stream.wait_event(join)
+        if world == 1:
             return out, dose
-        b.dd_per_probe_dose_range(scan, j0, j1, prec, out=dose, stream=stream)
         return shard.gather_columns(out, pr, rank, dist), shard.gather_vector(dose, dr, rank, dist)
 
     for _ in range(args.warmup):
@@ -817,6 +830,8 @@ def run_ours(args):
                                "pair-terms but skipped per warp; their share of the workload's pairs",
                 "other_pipe": {"pipe": "fp32" if bind is mufu else "mufu", **other}}
     launches = int(sum(v[0] for v in prof.values()))
+    # shares of the summed per-launch event time (the dose's kernels run beside the field's,
+    # so their events overlap and the shares do not add up to wall time)
     shares = {k: round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4) for k, v in prof.items()}
 
     line = {
@@ -903,8 +918,8 @@ def run_ours(args):
 def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, rr, pr, dr):
     """End to end through the public API with page-locked host outputs: scan build (its
     visit list uploaded on first use), the grid field and the dose, D2H of both.  One GPU:
-    both calls on one stream, synchronised once per step (with a stream and page-locked
-    buffers the field's D2H overlaps the dose's work).  Several: each rank evaluates its
+    the two calls on two streams, each synchronised once per step (with a stream and
+    page-locked buffers the calls leave their copies enqueued).  Several: each rank evaluates its
     rows and dose targets, the device results are gathered, and rank 0 copies out the
     whole field and dose."""
     import torch
@@ -913,6 +928,7 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
     out_h = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True)
     dose_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
     e2e_stream = torch.cuda.Stream(dev)
+    e2e_side = torch.cuda.Stream(dev)
     if world > 1:
         out_d = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
         dose_d = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
@@ -923,8 +939,11 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
     for k in range(args.steps):
         s2 = b.Scan(job.scan)
         if world == 1:
+            # the field first (its kernels start while the host prepares the dose), the
+            # dose on a second stream beside it, each leaving its copies enqueued
             b.dd_field_on_grid(s2, x0, y0, gdx, gdy, W, H, times, "mixed", out=out_h.numpy(), stream=e2e_stream)
-            b.dd_per_probe_dose(s2, "mixed", out=dose_h.numpy(), stream=e2e_stream)
+            b.dd_per_probe_dose(s2, "mixed", out=dose_h.numpy(), stream=e2e_side)
+            e2e_side.synchronize()
         else:
             with torch.cuda.stream(e2e_stream):
                 b.dd_field_on_grid(s2, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, "mixed", out=out_d,
