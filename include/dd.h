@@ -139,15 +139,25 @@ dd_status dd_field_at_times(const dd_scan *scan, const double *pts_xy_m, int64_t
      out[it * n_cols * n_rows + r * n_cols + c] = psi(point (c, r), times_s[it])   [u/m^2]
    -- the result of dd_field_at_times on those points in row-major order, without a point
    buffer.  In FP32-mixed precision the grid lets a tile of 128 columns x 4 rows split the
-   low-degree pair terms into column and row factors (fewer exponentials per pair); the
+   low-degree pair terms into column and row factors (fewer exponentials per pair); and on
+   grids of at least 64 x 64 points, the visits whose pair terms are on the degree-2 series
+   at every point of the grid (the older ones) are summed as a matrix product of those
+   factors on the tensor cores (BF16 pieces of the FP32 factors, FP32 accumulation); the
    result then differs from dd_field_at_times by the FP32 rounding, within the same error
    budget.  times_s and out as in dd_field_at_times.  A grid with no columns, rows or
    snapshots is a no-op.
    Errors: DD_EINVAL (NULL scan/buffer, negative sizes, non-finite origin or spacing, more
-   than 2^31 points), DD_ENOMEM, DD_ECUDA. */
+   than 2^31 points), DD_ENOMEM, DD_ECUDA.  A tensor-core wait that gave up (an
+   iteration-limited wait for the MMAs' completion) leaves NaN in the affected points and
+   is reported by dd_field_check. */
 dd_status dd_field_on_grid(const dd_scan *scan, double x0_m, double y0_m, double dx_m, double dy_m,
                            int64_t n_cols, int64_t n_rows, const double *times_s, int64_t n_t,
                            dd_precision prec, double *out, void *cuda_stream);
+
+/* Synchronise the device and return DD_ETIMEOUT (clearing the flag) if a tensor-core
+   contraction of dd_field_on_grid gave up waiting for its MMAs since the last check,
+   DD_OK otherwise. */
+dd_status dd_field_check(void);
 
 /* Dwell-start dose of every visit: the field at the probe's own position when
    its dwell starts, from the visits before it,

@@ -92,6 +92,8 @@ def load(build_if_missing=True):
     lib.dd_sur_fields.argtypes = [_VP, _VP, _I64, _I64, ctypes.c_float, ctypes.c_float, _VP, _VP]
     lib.dd_sur_spot_error.argtypes = [_VP, _VP, _VP, _VP, _VP, i32, i32, i32, ctypes.c_float, ctypes.c_float, _VP, _VP]
     lib.dd_sur_check.argtypes = []
+    lib.dd_field_check.argtypes = []
+    lib.dd_field_check.restype = ctypes.c_int
     for name in ("dd_sur_conv3x3", "dd_sur_wgrad", "dd_sur_mse", "dd_sur_wmse", "dd_sur_weights", "dd_sur_adam",
                  "dd_sur_planes",
                  "dd_sur_targets", "dd_sur_fields", "dd_sur_spot_error", "dd_sur_check"):
@@ -405,6 +407,12 @@ def dd_sur_conv3x3(x, w, bias, mask, out, epilogue, dilation=1, stream=None):
     _check(load().dd_sur_conv3x3(_dp(x), _dp(w), _dp(bias), _dp(mask), _dp(out), B, H, W, cin, cout,
                                  int(dilation), int(epilogue), _cs(stream, x)), "dd_sur_conv3x3")
     return out
+
+
+def dd_field_check():
+    """Synchronise the device; raise DDError (DD_ETIMEOUT) if a tensor-core contraction of
+    dd_field_on_grid gave up waiting for its MMAs since the last check."""
+    _check(load().dd_field_check(), "dd_field_check")
 
 
 def dd_sur_check():

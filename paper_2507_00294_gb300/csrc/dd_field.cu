@@ -17,6 +17,7 @@
 //      Q0/(4 pi D), into out[snapshot][point] (reduce_kernel).
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -27,6 +28,7 @@
 #include "dd_e1.cuh"
 #include "dd_field_grid.cuh"
 #include "dd_field_impl.cuh"
+#include "dd_field_tc.cuh"
 #include "dd_internal.h"
 
 namespace ddk {
@@ -79,20 +81,31 @@ __global__ void prep_points_lag_kernel(int nb_lag, int64_t M, double s, double k
         prep_point((int64_t)(blockIdx.x - nb_lag) * blockDim.x + threadIdx.x, xy, g, n, inv_p, X, Y, F);
 }
 
-// out[row[j] * n_pts + p] = pref * sum_{k < nblk[chunk(j)]} partial[(k * n_tg + j) * n_pts + p]
-// out[row[j]][p] = pref * sum over the visit blocks of snapshot j, in block order
-// (deterministic); four points per thread, so that each load moves 16 bytes or more.
+// out[row[j]][p] = pref * (sum_{q < nq[j]} tpart[(q * n_tg + j) * pstride + p]
+//                          + sum_{kb0[j] <= k < nblk[j]} partial[(k * n_tg + j) * pstride + p]):
+// the tensor-core chunks of snapshot j (the older visits), then its visit blocks, in that
+// order (deterministic); four points per thread, so that each load moves 16 bytes or more.
+// kb0 and nq NULL: every block from 0, no tensor-core chunks.
 template <typename Part>
 __global__ void reduce_kernel(const Part *__restrict__ partial, const int *__restrict__ nblk_of_snap,
-                              const int *__restrict__ row, int n_tg, int64_t n_pts, int64_t pstride,
-                              double pref, double *__restrict__ out) {
+                              const int *__restrict__ kb0_of_snap, const Part *__restrict__ tpart,
+                              const int *__restrict__ nq_of_snap, const int *__restrict__ row, int n_tg,
+                              int64_t n_pts, int64_t pstride, double pref, double *__restrict__ out) {
     const int j = blockIdx.y;
     const int64_t p0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (p0 >= n_pts) return;
     const int nb = nblk_of_snap[j];
+    const int kb0 = kb0_of_snap ? kb0_of_snap[j] : 0;
+    const int nq = nq_of_snap ? nq_of_snap[j] : 0;
     BlockSum<Part> acc[4];
+    for (int k = 0; k < nq; ++k) {
+        Part v[4];
+        load4_cg(tpart + ((int64_t)k * n_tg + j) * pstride + p0, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q].add(v[q]);
+    }
 #pragma unroll 4
-    for (int k = 0; k < nb; ++k) {
+    for (int k = kb0; k < nb; ++k) {
         Part v[4];
         load4_cg(partial + ((int64_t)k * n_tg + j) * pstride + p0, v);
 #pragma unroll
@@ -146,7 +159,7 @@ struct HostTables {
 // Sizes of the workspace a call needs (the same function drives the carve).
 template <typename Cfg>
 size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out_host, bool pts_host,
-                       int n_t, int64_t n_rec) {
+                       int n_t, int64_t n_rec, int nq_max, int64_t n_titems) {
     using Rec = typename Cfg::Rec;
     const int nblk_max = (int)((n_src + sb - 1) / sb);
     const int n_chunks = (group + Cfg::kTCH - 1) / Cfg::kTCH;
@@ -157,11 +170,13 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
     add(2 * (size_t)n_pts * sizeof(double));                  // X, Y in pitch units
     add((size_t)n_pts * sizeof(float4));                      // the same as float-float
     add((size_t)group * sizeof(double));                      // snapshot times
-    add((size_t)group * sizeof(int) * 3);                     // nact, row, nblk per snapshot
+    add((size_t)group * sizeof(int) * 6);                     // nact, row, nblk, kst, kb0, nq per snapshot
     add((size_t)group * sizeof(int64_t));                     // record row offset per snapshot
     add((size_t)n_chunks * nblk_max * sizeof(int2));          // (chunk, block) descriptors
+    add((size_t)n_titems * sizeof(ddk::TcItem));              // tensor-core work items
     add((size_t)n_rec * sizeof(Rec));                         // coefficient records
     add((size_t)nblk_max * group * ((n_pts + 3) / 4 * 4) * sizeof(typename Cfg::Real));   // partial sums
+    add((size_t)nq_max * group * ((n_pts + 3) / 4 * 4) * sizeof(float));                  // tensor-core partials
     return b + 256;
 }
 
@@ -220,6 +235,106 @@ int64_t resident_ctas() {
     return v;
 }
 
+// ---- the tensor-core part of the grid field (dd_field_tc.cuh)
+//
+// A visit is handed to the contraction for snapshot j when its pair term is on the degree-2
+// series at every point of the grid: h = rho^2 dq <= kL2H for rho^2 up to R2, the largest
+// squared distance between the grid's box and the box of the visits.  With c = 4 kappa
+// tau_max, dq = 1/w0 - 1/w1 <= c / ((w1 - c) w1) for every visit of the scan (dq grows with
+// the dwell at a fixed w1 = 2s + 4 kappa (t - T_i)), so every visit with w1 at or above the
+// root w1* of (w1 - c) w1 = c R2 / kL2H (and its dwell over) qualifies: the prefix of the
+// visits that started by t_j - dT*, dT* = (w1* - 2s) / (4 kappa), found by bisection of the
+// start times.  The contraction takes that prefix, the CUDA-core tile the rest.
+struct TcPlan {
+    bool on = false;
+    int chunk = ddk::kTcMaxChunk;
+    int64_t n_tile_cols = 0, n_tiles = 0;
+    std::vector<int> K;          // per snapshot (time order): the contraction's visits [0, K)
+};
+
+TcPlan plan_tc(const dd_scan *scan, const ddk::GridDesc &grid, const std::vector<double> &tdim,
+               const std::vector<int> &nact) {
+    TcPlan tp;
+    const int n_t = (int)tdim.size();
+    tp.K.assign(n_t, 0);
+    // tiles of 128 x 128 points: only grids that fill them reasonably
+    if (grid.W < ddk::kTcTile / 2 || grid.H < ddk::kTcTile / 2 || scan->n == 0) return tp;
+    const double ip = 1.0 / scan->pitch;
+    const double xa = grid.x0 * ip, xb = (grid.x0 + (double)(grid.W - 1) * grid.dx) * ip;
+    const double ya = grid.y0 * ip, yb = (grid.y0 + (double)(grid.H - 1) * grid.dy) * ip;
+    const double ex = std::max(std::max(xa, xb) - scan->x_lo, scan->x_hi - std::min(xa, xb));
+    const double ey = std::max(std::max(ya, yb) - scan->y_lo, scan->y_hi - std::min(ya, yb));
+    // margins for the points' own rounding and the records' rounding to FP32
+    const double R2 = (ex * ex + ey * ey) * (1.0 + 1e-6) + 1e-6;
+    const double dq_max = (double)ddk::kL2H * (1.0 - 1e-4) / R2;
+    const double c = 4.0 * scan->kappa * scan->tau_max;
+    if (!(c > 0.0) || !(dq_max > 0.0) || !std::isfinite(dq_max)) return tp;
+    double w1s = 0.5 * (c + std::sqrt(c * c + 4.0 * c / dq_max));
+    w1s = std::max(w1s, (2.0 * scan->s + c) * (1.0 + 1e-9));        // the dwell is over
+    const double dTs = (w1s - 2.0 * scan->s) / (4.0 * scan->kappa) * (1.0 + 1e-9);
+    int64_t any = 0;
+    for (int k = 0; k < n_t; ++k) {
+        const int64_t Kk = std::upper_bound(scan->T.begin(), scan->T.end(), tdim[k] - dTs) - scan->T.begin();
+        tp.K[k] = (int)std::min<int64_t>(Kk, nact[k]);
+        any += tp.K[k];
+    }
+    if (any == 0) return tp;
+    tp.n_tile_cols = (grid.W + ddk::kTcTile - 1) / ddk::kTcTile;
+    tp.n_tiles = tp.n_tile_cols * ((grid.H + ddk::kTcTile - 1) / ddk::kTcTile);
+    tp.on = true;
+    return tp;
+}
+
+// dynamic shared memory above 48 KB and the whole L1/shared array as shared memory, set
+// once per device
+cudaError_t prepare_tc_kernel() {
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess || dev >= 64) return err;
+    if (done.load() & (uint64_t(1) << dev)) return cudaSuccess;
+    err = cudaFuncSetAttribute(ddk::field_grid_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ddk::kTcSmemBytes);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(ddk::field_grid_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
+    if (err == cudaSuccess) done.fetch_or(uint64_t(1) << dev);
+    return err;
+}
+
+// Tensor-core CTAs resident on the whole device at once: kTcCtasPerSm per SM (their
+// shared memory and tensor memory bound it; 0 if unknown).
+int64_t tc_resident_ctas() {
+    static std::atomic<int64_t> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 0;
+    int64_t v = cached[dev].load();
+    if (v > 0) return v;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    v = (int64_t)ddk::kTcCtasPerSm * sms;
+    cached[dev].store(v);
+    return v;
+}
+
+// Visits per tensor-core work item: the candidate (a multiple of the 16-visit stage) with
+// the shortest estimated makespan, whole waves of resident CTAs times (chunk + a fixed
+// cost per item of about three stages for the staging and the epilogue).
+int choose_tc_chunk(const TcPlan &tp, int n_t) {
+    const int64_t slots = std::max<int64_t>(1, tc_resident_ctas());
+    int best = ddk::kTcMaxChunk;
+    int64_t best_cost = INT64_MAX;
+    for (int c = 64; c <= ddk::kTcMaxChunk; c += 64) {
+        int64_t items = 0;
+        for (int j = 0; j < n_t; ++j) items += (int64_t)((tp.K[j] + c - 1) / c) * tp.n_tiles;
+        const int64_t cost = (items + slots - 1) / slots * (c + 48);
+        if (cost < best_cost) { best_cost = cost; best = c; }
+    }
+    return best;
+}
+
 // pts_xy_m == NULL: the points are the grid `grid` (row-major, n_pts = W H), formed on
 // the device; the FP32-mixed path then runs the grid tile kernel.
 template <typename Cfg>
@@ -262,6 +377,10 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
         for (int k = 0; k < n_t; ++k) tdim[k] = std::nearbyint(tdim[k]);
     for (int k = 0; k < n_t; ++k)
         nact[k] = (int)(std::lower_bound(scan->T.begin(), scan->T.end(), tdim[k]) - scan->T.begin());
+    // the degree-2 prefixes that the tensor-core contraction takes (grid tiles only)
+    TcPlan tp;
+    tp.K.assign(n_t, 0);
+    if (grid_tiles) tp = plan_tc(scan, grid, tdim, nact);
 
     // visit block size and snapshot groups bound the partial and record buffers
     const int tile = Cfg::kThreads * Cfg::kPPT;
@@ -286,9 +405,12 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
         auto items_per_launch = [&](int b) {
             int64_t blocks = 0;
             for (int j0 = 0; j0 < n_t; j0 += Cfg::kTCH) {
-                int cmax = 0;
-                for (int j = j0; j < std::min(n_t, j0 + Cfg::kTCH); ++j) cmax = std::max(cmax, nact[j]);
-                blocks += (cmax + b - 1) / b;
+                int cmax = 0, kmin = INT_MAX;
+                for (int j = j0; j < std::min(n_t, j0 + Cfg::kTCH); ++j) {
+                    cmax = std::max(cmax, nact[j]);
+                    kmin = std::min(kmin, tp.K[j] / b);
+                }
+                blocks += std::max(0, (cmax + b - 1) / b - kmin);
             }
             return blocks * n_tiles / std::max(1, n_groups);
         };
@@ -298,9 +420,32 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     }
     const int nblk_max = (int)((n_src + sb - 1) / sb);
     const int n_chunks_max = (group + Cfg::kTCH - 1) / Cfg::kTCH;
+    // tensor-core chunks: rows of partial sums per snapshot and work items per group, within
+    // the partial-sum budget (else the CUDA-core tile takes every visit)
+    int nq_max = 0;
+    int64_t n_titems_max = 0;
+    if (tp.on) {
+        tp.chunk = choose_tc_chunk(tp, n_t);
+        for (int g0 = 0; g0 < n_t; g0 += group) {
+            int64_t ni = 0;
+            for (int j = g0; j < std::min(n_t, g0 + group); ++j) {
+                const int nq = (tp.K[j] + tp.chunk - 1) / tp.chunk;
+                nq_max = std::max(nq_max, nq);
+                ni += (int64_t)nq * tp.n_tiles;
+            }
+            n_titems_max = std::max(n_titems_max, ni);
+        }
+        if ((size_t)nq_max * group * ((n_pts + 3) / 4 * 4) * sizeof(float) > budget || n_titems_max > (int64_t(1) << 24)) {
+            tp.on = false;
+            std::fill(tp.K.begin(), tp.K.end(), 0);
+            nq_max = 0;
+            n_titems_max = 0;
+        }
+    }
 
     const int64_t n_rec = lattice ? M + 1 : (int64_t)group * n_src;
-    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_copy, pts_copy, n_t, n_rec);
+    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_copy, pts_copy, n_t, n_rec, nq_max,
+                                                 n_titems_max);
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
@@ -325,15 +470,20 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     double *Y = X + n_pts;
     float4 *PF = cv.take<float4>((size_t)n_pts);
     double *d_t = cv.take<double>(group);
-    int *d_nact = cv.take<int>(3 * (size_t)group);
+    int *d_nact = cv.take<int>(6 * (size_t)group);
     int *d_row = d_nact + group;
     int *d_nblk = d_row + group;
+    int *d_kst = d_nblk + group;
+    int *d_kb0 = d_kst + group;
+    int *d_nq = d_kb0 + group;
     int64_t *d_roff = cv.take<int64_t>(group);
     int2 *d_desc = cv.take<int2>((size_t)n_chunks_max * nblk_max);
+    ddk::TcItem *d_titems = cv.take<ddk::TcItem>((size_t)n_titems_max);
     Rec *d_rec = cv.take<Rec>((size_t)n_rec);
     using Part = typename Cfg::Real;
     const int64_t pstride = (n_pts + 3) / 4 * 4;            // 16-byte aligned partial rows
     Part *d_part = cv.take<Part>((size_t)nblk_max * group * pstride);
+    float *d_tpart = cv.take<float>((size_t)nq_max * group * pstride);
 
     if (!lattice) {
         DD_PROFILED("prep_points", stream,
@@ -357,7 +507,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     for (int g0 = 0; g0 < n_t; g0 += group) {
         const int ng = std::min(group, n_t - g0);
         const int n_chunks = (ng + Cfg::kTCH - 1) / Cfg::kTCH;
-        std::vector<int> tabs(3 * (size_t)ng);
+        std::vector<int> tabs(6 * (size_t)ng);
         std::vector<double> tg(ng);
         std::vector<int64_t> roff(ng);
         int max_nact = 0;
@@ -365,43 +515,68 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
             tg[j] = tdim[g0 + j];
             tabs[j] = nact[g0 + j];
             tabs[ng + j] = order[g0 + j];
+            tabs[3 * ng + j] = tp.K[g0 + j];                               // kst
+            tabs[4 * ng + j] = tp.K[g0 + j] / sb;                          // kb0
+            tabs[5 * ng + j] = (tp.K[g0 + j] + tp.chunk - 1) / tp.chunk;   // nq
             max_nact = std::max(max_nact, nact[g0 + j]);
             // lattice: snapshot t reads lag t - i at rev[M - t + i]; otherwise row j of the
             // per-(snapshot, visit) records
             roff[j] = lattice ? (tdim[g0 + j] > 0 ? M - (int64_t)tdim[g0 + j] : M) : (int64_t)j * n_src;
         }
         // work items: (tile, chunk, block) for every block below the chunk's largest
-        // n_active, longest first.  Every tile of a (chunk, block) costs the same, so the
-        // (chunk, block) descriptors are sorted (stable: ties keep chunk, block order) and
-        // the kernel expands each into its tiles in tile order.
+        // n_active (from the first block that holds a visit past some snapshot's
+        // tensor-core prefix), longest first.  Every tile of a (chunk, block) costs the
+        // same, so the (chunk, block) descriptors are sorted (stable: ties keep chunk, block
+        // order) and the kernel expands each into its tiles in tile order.
         std::vector<std::pair<int64_t, int2>> blocks;
         for (int c = 0; c < n_chunks; ++c) {
             const int j0 = c * Cfg::kTCH, j1 = std::min(ng, j0 + Cfg::kTCH);
-            int cmax = 0;
-            for (int j = j0; j < j1; ++j) cmax = std::max(cmax, nact[g0 + j]);
+            int cmax = 0, kbmin = INT_MAX;
+            for (int j = j0; j < j1; ++j) {
+                cmax = std::max(cmax, nact[g0 + j]);
+                kbmin = std::min(kbmin, tp.K[g0 + j] / sb);
+            }
             const int nb = (cmax + sb - 1) / sb;
             for (int j = j0; j < j1; ++j) tabs[2 * ng + j] = nb;
-            for (int k = 0; k < nb; ++k) {
+            for (int k = kbmin; k < nb; ++k) {
                 int64_t cost = 0;
                 for (int j = j0; j < j1; ++j)
-                    cost += std::max(0, std::min(nact[g0 + j], (k + 1) * sb) - k * sb);
+                    cost += std::max(0, std::min(nact[g0 + j], (k + 1) * sb) - std::max(k * sb, tp.K[g0 + j]));
                 blocks.push_back({cost, make_int2(c, k)});
             }
+        }
+        // tensor-core items: (snapshot, chunk of its prefix, tile), whole chunks first
+        std::vector<ddk::TcItem> titems;
+        if (tp.on) {
+            for (int pass = 0; pass < 2; ++pass)
+                for (int j = 0; j < ng; ++j) {
+                    const int K = tp.K[g0 + j];
+                    for (int q = 0; q * tp.chunk < K; ++q) {
+                        const int v_end = std::min(K, (q + 1) * tp.chunk);
+                        if ((v_end - q * tp.chunk == tp.chunk) != (pass == 0)) continue;
+                        for (int64_t t = 0; t < tp.n_tiles; ++t) titems.push_back({j, q, (int)t, v_end, roff[j], 0});
+                    }
+                }
         }
         std::stable_sort(blocks.begin(), blocks.end(),
                          [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
         std::vector<int2> it(blocks.size());
         for (size_t q = 0; q < blocks.size(); ++q) it[q] = blocks[q].second;
 
-        // the group's tables in one copy: a host image of the device span d_t .. descriptors end
+        // the group's tables in one copy: a host image of the device span d_t .. the end of
+        // the descriptors (of the tensor-core items, if any)
         {
             char *const d0 = reinterpret_cast<char *>(d_t);
-            const size_t span = reinterpret_cast<char *>(d_desc + it.size()) - d0;
+            const size_t span = titems.empty() ? reinterpret_cast<char *>(d_desc + it.size()) - d0
+                                               : reinterpret_cast<char *>(d_titems + titems.size()) - d0;
             std::vector<char> img(span);
             std::memcpy(img.data(), tg.data(), ng * sizeof(double));
-            std::memcpy(img.data() + (reinterpret_cast<char *>(d_nact) - d0), tabs.data(), 3 * (size_t)ng * sizeof(int));
+            std::memcpy(img.data() + (reinterpret_cast<char *>(d_nact) - d0), tabs.data(), 6 * (size_t)ng * sizeof(int));
             std::memcpy(img.data() + (reinterpret_cast<char *>(d_roff) - d0), roff.data(), ng * sizeof(int64_t));
             std::memcpy(img.data() + (reinterpret_cast<char *>(d_desc) - d0), it.data(), it.size() * sizeof(int2));
+            if (!titems.empty())
+                std::memcpy(img.data() + (reinterpret_cast<char *>(d_titems) - d0), titems.data(),
+                            titems.size() * sizeof(ddk::TcItem));
             DD_CUDA_TRY(keep->staging.upload(d0, img.data(), span, stream));
             keep->images.push_back(std::move(img));
         }
@@ -410,6 +585,23 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
             DD_PROFILED(Cfg::kCoefName, stream,
                         (ddk::coef_kernel<Rec><<<cg, 128, 0, stream>>>(srcT, srcTAU, d_t, d_nact, scan->s, scan->kappa, d_rec, n_src)));
             DD_CUDA_TRY(cudaGetLastError());
+        }
+        if constexpr (kMixed) {
+            if (!titems.empty()) {
+                DD_CUDA_TRY(prepare_tc_kernel());
+                // DD_FAULT=field_tc_wait (tests): no MMA is issued, so the completion waits
+                // run out and the kernel reports it (dd_field_check)
+                const int withhold = dd::fault_injected("field_tc_wait") ? 1 : 0;
+                // persistent CTAs: as many as are resident at once, at most one per item
+                const int64_t resident = tc_resident_ctas();
+                const unsigned n_cta = (unsigned)std::min<int64_t>((int64_t)titems.size(),
+                                                                   resident > 0 ? resident : 2 * 148);
+                DD_PROFILED("field_grid_tc", stream,
+                            (ddk::field_grid_tc_kernel<<<n_cta, ddk::kTcThreads, ddk::kTcSmemBytes, stream>>>(
+                                grid.W, grid.H, tp.n_tile_cols, d_rec, d_titems, (int)titems.size(), tp.chunk, ng,
+                                d_tpart, pstride, srcF, PF, withhold)));
+                DD_CUDA_TRY(cudaGetLastError());
+            }
         }
         if (!it.empty()) {
             if (grid_tiles) DD_CUDA_TRY((prefer_shared<Cfg, true>()));
@@ -422,8 +614,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                     if (grid_tiles) {
                         DD_PROFILED("field_grid_mixed", stream,
                                     (ddk::field_grid_kernel<GridCfg><<<nctas, Cfg::kThreads, 0, stream>>>(
-                                        grid.W, grid.H, n_tc, d_rec, d_roff, d_nact, d_desc, n_tiles, item0, ng, sb,
-                                        d_part, pstride, srcF, PF)));
+                                        grid.W, grid.H, n_tc, d_rec, d_roff, d_nact, tp.on ? d_kst : nullptr, d_desc,
+                                        n_tiles, item0, ng, sb, d_part, pstride, srcF, PF)));
                         DD_CUDA_TRY(cudaGetLastError());
                         continue;
                     }
@@ -437,7 +629,9 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
         }
         dim3 rg((unsigned)((n_pts + 1023) / 1024), (unsigned)ng);
         DD_PROFILED("field_reduce", stream,
-                    (ddk::reduce_kernel<Part><<<rg, 256, 0, stream>>>(d_part, d_nblk, d_row, ng, n_pts, pstride, scan->pref, out_dev)));
+                    (ddk::reduce_kernel<Part><<<rg, 256, 0, stream>>>(
+                        d_part, d_nblk, tp.on ? d_kb0 : nullptr, reinterpret_cast<const Part *>(d_tpart),
+                        tp.on ? d_nq : nullptr, d_row, ng, n_pts, pstride, scan->pref, out_dev)));
         DD_CUDA_TRY(cudaGetLastError());
         keep->items.push_back(std::move(it));
         keep->ints.push_back(std::move(tabs));
@@ -509,4 +703,15 @@ extern "C" dd_status dd_field_on_grid(const dd_scan *scan, double x0_m, double y
     const int64_t n_pts = n_cols * n_rows;
     if (prec == DD_MIXED) return run_field<ddk::CfgMixed>(scan, nullptr, n_pts, g, times, out, stream);
     return run_field<ddk::CfgF64>(scan, nullptr, n_pts, g, times, out, stream);
+}
+
+extern "C" dd_status dd_field_check(void) {
+    dd::clear_error();
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    int flag = 0;
+    DD_CUDA_TRY(cudaMemcpyFromSymbol(&flag, ddk::g_field_tc_timeout, sizeof(int)));
+    if (!flag) return DD_OK;
+    const int zero = 0;
+    DD_CUDA_TRY(cudaMemcpyToSymbol(ddk::g_field_tc_timeout, &zero, sizeof(int)));
+    return dd::fail(DD_ETIMEOUT, "dd_field_check: a tensor-core contraction of the grid field gave up waiting for its MMAs");
 }

@@ -20,6 +20,7 @@
 // rho^2 = dx^2 + dy^2 from the column's dx and the row's dy^2 -- the same roundings as
 // the general tile's rho^2.
 #pragma once
+#include <climits>
 #include <cstdint>
 
 #include "dd_field_impl.cuh"
@@ -52,14 +53,15 @@ struct TileSmemGrid {
 
 // srcF: visit coordinates, ptsF: point coordinates (float-float, pitch units, row-major
 // grid of W columns and H rows); the tile covers columns [128 tc, 128 tc + 128) and rows
-// [4 tr, 4 tr + 4).  partial[jc * part_stride + r W + c] receives the sum over visits
-// [s_begin, s_end) of snapshot jc < nj.
+// [4 tr, 4 tr + 4).  partial[jc * part_stride + r W + c] receives, for each snapshot jc of
+// write_mask, the sum over visits i in [s_begin, s_end) with ks[jc] <= i < na[jc].
 template <typename Cfg>
 __device__ __forceinline__ void field_tile_grid_mixed(TileSmemGrid<Cfg> &sm, const float4 *__restrict__ srcF,
                                                       const float4 *__restrict__ ptsF, int64_t W, int64_t H,
                                                       int64_t tc, int64_t tr, const RecF32 *const (&rows)[4],
-                                                      const int (&na)[4], int nj, int s_begin, int s_end,
-                                                      float *__restrict__ partial, int64_t part_stride) {
+                                                      const int (&na)[4], const int (&ks)[4], uint32_t write_mask,
+                                                      int s_begin, int s_end, float *__restrict__ partial,
+                                                      int64_t part_stride) {
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kPPT, STILE = Cfg::kSTILE, TCH = 4, NP = 2;
     static_assert(NT == 128 && PPT == 4 && STILE == 32, "grid tile: 128 columns x 4 rows, 32-visit stages");
     const int tid = threadIdx.x, lane = tid & 31;
@@ -126,10 +128,11 @@ __device__ __forceinline__ void field_tile_grid_mixed(TileSmemGrid<Cfg> &sm, con
 #pragma unroll
         for (int jc = 0; jc < TCH; ++jc) {
             const float4 *row = reinterpret_cast<const float4 *>(rows[jc] + s0);
-            const int lim = na[jc] - s0;
+            const int lim = na[jc] - s0, lo = ks[jc] - s0;
             for (int v = tid; v < cnt * 2; v += NT) {
                 const int i = v >> 1, q = v & 1;
-                const float4 r = i < lim ? row[i * RV + q] : (q == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
+                const float4 r = (i < lim && i >= lo) ? row[i * RV + q]
+                                                      : (q == 0 ? zero_rec_v0() : make_float4(0.f, 0.f, 0.f, 0.f));
                 if (q == 0) {
                     float *a = reinterpret_cast<float *>(&sm.pa[jc >> 1][i]) + (jc & 1);
                     a[0] = r.x; a[2] = r.y;
@@ -179,7 +182,7 @@ __device__ __forceinline__ void field_tile_grid_mixed(TileSmemGrid<Cfg> &sm, con
 #pragma unroll
             for (int jc = 0; jc < TCH; ++jc) {
                 uint32_t cl = kCodeD2, code = kCodeSkip;
-                if (s0 + lane < na[jc]) {
+                if (s0 + lane < na[jc] && s0 + lane >= ks[jc]) {
                     const float2 h = sm.cls[jc][lane];
                     cl = code = series_class(r2max * h.x, r2min * h.y, h.x);
                     any = any || cl != kCodeSkip;
@@ -308,7 +311,7 @@ __device__ __forceinline__ void field_tile_grid_mixed(TileSmemGrid<Cfg> &sm, con
     }
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc) {
-        if (jc >= nj) continue;
+        if (!((write_mask >> jc) & 1u)) continue;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
             const int64_t r = r0 + k;
@@ -320,34 +323,44 @@ __device__ __forceinline__ void field_tile_grid_mixed(TileSmemGrid<Cfg> &sm, con
 // One work item per CTA, as field_kernel, over grid tiles: CTA item0 + blockIdx.x takes
 // descriptor (item0 + blockIdx.x) / n_tiles and grid tile (item0 + blockIdx.x) % n_tiles,
 // tile q covering column block q % n_tc and row block q / n_tc.
+// kst (NULL: none): snapshot j's visits below kst[j] are summed by the tensor-core
+// contraction (dd_field_tc.cuh); this kernel takes visits [kst[j], nact[j]) and writes the
+// partial row of block k only where the block reaches past kst[j] ((k + 1) sb > kst[j]).
 template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads, Cfg::kMinBlocks)
 field_grid_kernel(int64_t W, int64_t H, int64_t n_tc, const RecF32 *__restrict__ rec,
-                  const int64_t *__restrict__ row_off, const int *__restrict__ nact, const int2 *__restrict__ desc,
-                  int64_t n_tiles, int64_t item0, int n_tg, int sb, float *__restrict__ partial, int64_t pstride,
-                  const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF) {
+                  const int64_t *__restrict__ row_off, const int *__restrict__ nact, const int *__restrict__ kst,
+                  const int2 *__restrict__ desc, int64_t n_tiles, int64_t item0, int n_tg, int sb,
+                  float *__restrict__ partial, int64_t pstride, const float4 *__restrict__ srcF,
+                  const float4 *__restrict__ ptsF) {
     constexpr int TCH = Cfg::kTCH;
     static_assert(TCH == 4, "grid tile: four snapshots");
     const int64_t q = item0 + blockIdx.x;
     const int2 dc = desc[q / n_tiles];                     // (chunk, block)
     const int64_t tile = q % n_tiles;
     const int j0 = dc.x * TCH;
-    int na[TCH];
+    const int s_begin = dc.y * sb;
+    int na[TCH], ks[TCH];
     const RecF32 *rows[TCH];
-    int nmax = 0;
+    int nmax = 0, kmin = INT_MAX;
+    uint32_t write_mask = 0;
 #pragma unroll
     for (int jc = 0; jc < TCH; ++jc) {
         const bool live = j0 + jc < n_tg;
         na[jc] = live ? nact[j0 + jc] : 0;
+        ks[jc] = live && kst ? kst[j0 + jc] : 0;
         rows[jc] = live ? rec + row_off[j0 + jc] : rec;
         nmax = max(nmax, na[jc]);
+        if (live) {
+            kmin = min(kmin, ks[jc]);
+            if (s_begin + sb > ks[jc]) write_mask |= 1u << jc;
+        }
     }
-    const int s_begin = dc.y * sb;
     const int s_end = min(s_begin + sb, nmax);
     float *part = partial + ((int64_t)dc.y * n_tg + j0) * pstride;
     __shared__ TileSmemGrid<Cfg> sm;
-    field_tile_grid_mixed<Cfg>(sm, srcF, ptsF, W, H, tile % n_tc, tile / n_tc, rows, na, min(TCH, n_tg - j0),
-                               s_begin, s_end, part, pstride);
+    field_tile_grid_mixed<Cfg>(sm, srcF, ptsF, W, H, tile % n_tc, tile / n_tc, rows, na, ks, write_mask,
+                               max(s_begin, kmin), s_end, part, pstride);
 }
 
 }  // namespace ddk

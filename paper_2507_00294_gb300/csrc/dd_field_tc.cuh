@@ -1,0 +1,331 @@
+// dd_field_tc.cuh -- the degree-2 part of the FP32-mixed field on a grid of points as a
+// contraction on the 5th-generation tensor cores.
+//
+// For a grid point (column c, row r) and a visit i whose pair term is on the degree-2
+// exponent series over a whole tile of points (h = rho^2 dq <= 0.04 for every point), the
+// separable form of dd_field_grid.cuh gives
+//   term(r, c; i) = Y_i(r) X_i(c) + B_i(r) A_i(c),
+//   X = 2^(g_1x dx^2 + g_2x dx^4),  A = X (2 ln2 g_2x) dx^2,
+//   Y = 2^(g_0 + g_1x dy^2 + g_2x dy^4),  B = Y dy^2,
+// so the sum over such visits is a matrix product: F(r, c) = sum_i Y(r, i) X(i, c) +
+// B(r, i) A(i, c), M = 128 rows x N = 128 columns per tile, K = visits.  The factors are
+// formed in FP32 exactly as the CUDA-core tile forms them and split into BF16 pieces,
+// X = X_h + X_m + X_l (each piece the round-to-nearest BF16 of what the earlier ones leave,
+// |X - X_h - X_m - X_l| <= 2^-24 |X|); the six products X_h Y_h, X_h Y_m, X_m Y_h, X_h Y_l,
+// X_l Y_h, X_m Y_m keep X Y to about 4 2^-24 relative, and the cross term, at most 3.5e-5
+// of X Y in the degree-2 class, takes one product of the BF16 roundings (2^-7 of itself, at
+// most 2.6e-7 of X Y).  The products accumulate in FP32 in tensor memory (kind::f16,
+// tcgen05.mma issued by one thread), seven MMAs per 16 visits: X_h Y_h into one accumulator
+// and the six small products (at most 2^-7 of it) into a second.  The tensor core's FP32
+// accumulation drops low bits in each MMA (the sums of positive terms come out slightly
+// low); keeping the leading product apart makes that loss one MMA per 16 visits of the
+// chunk instead of seven, and the small products' losses 2^-7 smaller.
+//
+// Work item: one 128 x 128 tile, one snapshot j and a chunk of at most kTcMaxChunk visits of
+// the snapshot's degree-2 prefix.  Persistent CTAs walk the items (item blockIdx.x, then
+// every gridDim.x-th).  Warps 0-7 produce: thread t < 128 forms the factors of row r0 + t,
+// thread 128 + t those of column c0 + t, 16 visits at a time, into one of three shared-memory
+// stages, and arrives on the stage's "full" barrier; lane 0 of warp 8 waits for it, issues
+// the stage's MMAs and commits them to the stage's "empty" barrier, which the producers wait
+// on before they write that stage again -- no CTA-wide barrier inside the item.  After an
+// item's last stage the MMA thread commits to the "done" barrier; the producers then read the
+// accumulators (warp w: rows 32 (w % 4) .., columns 64 (w / 4) ..) and write the FP32 partial
+// sums of the chunk.
+#pragma once
+#include <cstdint>
+
+#include "dd_field_impl.cuh"
+#include "dd_umma.cuh"
+
+namespace ddk {
+
+constexpr int kTcGenThreads = 256;         // warps 0-3: row factors, warps 4-7: column factors
+constexpr int kTcThreads = kTcGenThreads + 32;                 // + warp 8: issues the MMAs
+constexpr int kTcTile = 128;                 // rows = columns of a tile (M = N = 128)
+constexpr int kTcStage = 16;                 // visits per stage: one K step of the BF16 MMA
+constexpr int kTcBufs = 3;                   // stages in flight
+constexpr int kTcMaxChunk = 256;             // visits per work item at most
+constexpr int kTcPieceBytes = kTcTile * kTcStage * 2;          // 4 KB: 128 rows x 16 BF16
+constexpr int kTcBufBytes = 8 * kTcPieceBytes;                 // Y_h Y_m Y_l B | X_h X_m X_l A
+constexpr int kTcCoefBytes = 3 * (kTcMaxChunk / 2) * 16;       // three float4 per visit pair
+constexpr int kTcSmemBytes = kTcBufs * kTcBufBytes + kTcCoefBytes + 128;
+constexpr int kTcCtasPerSm = 2;              // by shared memory (2 x 102 KB) and TMEM (2 x 256 columns)
+constexpr int kTcWaitTries = 1 << 18;        // completion waits: at most about 0.26 s
+constexpr float kTcTwoLn2 = 1.38629436112f;
+// set when a completion wait of the contraction gives up (its partial sums are then NaN)
+static __device__ int g_field_tc_timeout;
+
+// Work item: snapshot (index within the group), chunk q of that snapshot's degree-2
+// prefix, tile (row block * n_tile_cols + column block), end of the chunk's visits.
+struct TcItem {
+    int j, q, tile, v_end;
+    int64_t row_off;         // snapshot j's record row (visit i at rec[row_off + i])
+    int64_t pad;
+};
+static_assert(sizeof(TcItem) == 32, "TcItem layout");
+
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ float2 bf16x2_to_f2(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+// v = h + m + l in BF16 pieces (packed pairs), each the rounding of what the earlier leave;
+// the remainders are exact in FP32
+__device__ __forceinline__ void split3_bf16(float2 v, uint32_t &h, uint32_t &m, uint32_t &l) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    h = bf16x2_rn(v.x, v.y);
+    const float2 r1 = __ffma2_rn(bf16x2_to_f2(h), m1, v);
+    m = bf16x2_rn(r1.x, r1.y);
+    const float2 r2 = __ffma2_rn(bf16x2_to_f2(m), m1, r1);
+    l = bf16x2_rn(r2.x, r2.y);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+// the 256 producer threads only (warps 0-7)
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(kTcGenThreads) : "memory"); }
+
+// The loads of one work item's inputs, issued early (the next item's while the current one
+// runs): the tile's first point and this thread's row or column point, and for thread p below
+// the item's pair count the coordinates and leading coefficients of visits 2p and 2p + 1.
+struct TcPrefetch {
+    float4 org, pt, v[2], r[2];
+};
+__device__ __forceinline__ void tc_prefetch(TcPrefetch &f, const TcItem &it, int chunk, int64_t W, int64_t H,
+                                            int64_t n_tile_cols, const RecF32 *__restrict__ rec,
+                                            const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF, int tid) {
+    const int64_t r0 = (it.tile / n_tile_cols) * (int64_t)kTcTile, c0 = (it.tile % n_tile_cols) * (int64_t)kTcTile;
+    const int t = tid & (kTcTile - 1);
+    f.org = ptsF[r0 * W + c0];
+    f.pt = tid >= kTcTile ? ptsF[r0 * W + min(c0 + t, W - 1)] : ptsF[min(r0 + t, H - 1) * W + c0];
+    const int v0 = it.q * chunk, nv = it.v_end - v0;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int i = 2 * tid + e;
+        if (i < nv) {
+            f.v[e] = srcF[v0 + i];
+            f.r[e] = reinterpret_cast<const float4 *>(rec + it.row_off + v0 + i)[0];
+        }
+    }
+}
+
+// partial[(q * ng + j) * pstride + r W + c] receives chunk q of snapshot j.
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
+field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__restrict__ rec,
+                     const TcItem *__restrict__ items, int n_items, int chunk, int ng, float *__restrict__ partial,
+                     int64_t pstride, const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF,
+                     int withhold_mma) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char *bufs = tc_smem;
+    float4 *cf = reinterpret_cast<float4 *>(tc_smem + kTcBufs * kTcBufBytes);   // [3][kTcMaxChunk / 2]
+    uint64_t *full = reinterpret_cast<uint64_t *>(tc_smem + kTcBufs * kTcBufBytes + kTcCoefBytes);
+    uint64_t *empty = full + kTcBufs;
+    uint64_t *done = empty + kTcBufs;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kGenWarps = kTcGenThreads / 32;
+
+    if (warp == kGenWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(smem_u32(s_tmem)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (lane == 0) {
+            for (int k = 0; k < kTcBufs; ++k) {
+                mbar_init(full + k, kGenWarps);          // one arrival per producer warp
+                mbar_init(empty + k, 1);
+            }
+            mbar_init(done, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;                   // columns [0, 128): X_h Y_h; [128, 256): the rest
+
+    bool ok = true;
+    if (warp == kGenWarps) {
+        // ---- the MMA thread
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc_bf16(kTcTile, kTcTile);
+            int gs = 0;
+            for (int q = blockIdx.x; q < n_items; q += gridDim.x) {
+                const TcItem it = items[q];
+                const int nst = (it.v_end - it.q * chunk + kTcStage - 1) / kTcStage;
+                for (int st = 0; st < nst; ++st) {
+                    const int g = gs + st, b = g % kTcBufs;
+                    ok = mbar_wait_bounded(full + b, (uint32_t)(g / kTcBufs) & 1u, kTcWaitTries) && ok;
+                    tc_fence_after();
+                    if (!withhold_mma) {
+                        // A = row pieces (M = rows), B = column pieces (N = columns); K-major,
+                        // core matrices of 8 rows: SBO 128 bytes, LBO (next 8 visits) 2 KB
+                        const uint32_t base = smem_u32(bufs + b * kTcBufBytes);
+                        auto d = [&](int piece) { return umma_smem_desc(base + piece * kTcPieceBytes, kTcPieceBytes / 2, 128u); };
+                        const int acc = st > 0 ? 1 : 0;
+                        const uint32_t t2 = tmem + (uint32_t)kTcTile;
+                        umma_bf16(tmem, d(0), d(4), idesc, acc);        // Y_h X_h
+                        umma_bf16(t2, d(0), d(5), idesc, acc);          // Y_h X_m
+                        umma_bf16(t2, d(1), d(4), idesc, 1);            // Y_m X_h
+                        umma_bf16(t2, d(0), d(6), idesc, 1);            // Y_h X_l
+                        umma_bf16(t2, d(2), d(4), idesc, 1);            // Y_l X_h
+                        umma_bf16(t2, d(1), d(5), idesc, 1);            // Y_m X_m
+                        umma_bf16(t2, d(3), d(7), idesc, 1);            // B A
+                    }
+                    umma_commit(empty + b);                     // the stage may be rewritten
+                }
+                // DD_FAULT=field_tc_wait: the MMAs are withheld and so is this commit, so
+                // that the producers' wait for the item runs out
+                if (!withhold_mma) umma_commit(done);
+                gs += nst;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- the producers
+        const bool col_side = tid >= kTcTile;              // warp-uniform
+        const int t = tid & (kTcTile - 1);
+        int q = blockIdx.x;
+        TcItem it = items[min(q, n_items - 1)];
+        TcItem nxt = items[min(q + (int)gridDim.x, n_items - 1)];
+        TcPrefetch pf;
+        tc_prefetch(pf, it, chunk, W, H, n_tile_cols, rec, srcF, ptsF, tid);
+        int gs = 0, n_done = 0;
+        for (; q < n_items; q += gridDim.x, ++n_done) {
+            const TcItem nn = items[min(q + 2 * (int)gridDim.x, n_items - 1)];
+            const int64_t r0 = (it.tile / n_tile_cols) * (int64_t)kTcTile;
+            const int64_t c0 = (it.tile % n_tile_cols) * (int64_t)kTcTile;
+            const int v0 = it.q * chunk, nv = it.v_end - v0;
+            const int nst = (nv + kTcStage - 1) / kTcStage;
+            // this thread's row (or column): its offset from the integer grid position
+            // nearest the tile's first point, as an exact integer plus a fraction (as in the
+            // CUDA-core tile); a ragged tile's spare rows and columns repeat the last ones
+            // (not written)
+            const float ox = rintf(pf.org.x), oy = rintf(pf.org.z);
+            float din, dfr;
+            if (col_side) {
+                const float ix = rintf(pf.pt.x);
+                dfr = (pf.pt.x - ix) + pf.pt.y;
+                din = ix - ox;
+            } else {
+                const float iy = rintf(pf.pt.z);
+                dfr = (pf.pt.z - iy) + pf.pt.w;
+                din = iy - oy;
+            }
+            // coefficients of the item's visits, by pairs: (-x, -y), (g_1x, g_2x),
+            // (g_0, 2 ln2 g_2x); the padding to whole stages contributes 0 (g_0 = -inf:
+            // Y = B = 0).  The previous item's readers are done first.
+            producers_sync();
+            if (tid < nst * (kTcStage / 2)) {
+                float vx[2], vy[2], g0[2], g1[2], g2[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    if (2 * tid + e < nv) {
+                        vx[e] = (pf.v[e].x - ox) + pf.v[e].y;    // probe positions are integers
+                        vy[e] = (pf.v[e].z - oy) + pf.v[e].w;
+                        g0[e] = pf.r[e].x; g1[e] = pf.r[e].y; g2[e] = pf.r[e].z;
+                    } else {
+                        vx[e] = vy[e] = 0.0f; g0[e] = -INFINITY; g1[e] = g2[e] = 0.0f;
+                    }
+                }
+                cf[tid] = make_float4(-vx[0], -vx[1], -vy[0], -vy[1]);
+                cf[kTcMaxChunk / 2 + tid] = make_float4(g1[0], g1[1], g2[0], g2[1]);
+                cf[kTcMaxChunk + tid] = make_float4(g0[0], g0[1], kTcTwoLn2 * g2[0], kTcTwoLn2 * g2[1]);
+            }
+            producers_sync();
+            // the next item's inputs, in flight while this item runs
+            if (q + (int)gridDim.x < n_items) tc_prefetch(pf, nxt, chunk, W, H, n_tile_cols, rec, srcF, ptsF, tid);
+            const float2 din2 = f2(din, din), dfr2 = f2(dfr, dfr);
+            for (int st = 0; st < nst; ++st) {
+                const int g = gs + st, b = g % kTcBufs;
+                unsigned char *buf = bufs + b * kTcBufBytes;
+                // the stage's buffer is free once the MMAs of stage g - kTcBufs have completed
+                if (g >= kTcBufs) ok = mbar_wait_bounded(empty + b, (uint32_t)(g / kTcBufs - 1) & 1u, kTcWaitTries) && ok;
+                // factors of 16 visits: K groups of 8 (one 16-byte core-matrix row per piece).
+                // Row: F = Y = 2^(g_0 + g_1x dy^2 + g_2x dy^4), cross piece B = Y dy^2.
+                // Column: F = X = 2^(g_1x dx^2 + g_2x dx^4) (the same roundings as
+                // (g_2x d + g_1x) d), cross piece A = X ((2 ln2 g_2x) dx^2).
+#pragma unroll
+                for (int kg = 0; kg < 2; ++kg) {
+                    uint32_t ph[4], pm[4], pl[4], pc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int p = st * (kTcStage / 2) + kg * 4 + u;
+                        const float4 P0 = cf[p], P1 = cf[kTcMaxChunk / 2 + p], P2 = cf[kTcMaxChunk + p];
+                        const float2 g1 = f2(P1.x, P1.y), g2 = f2(P1.z, P1.w);
+                        const float2 nv2 = col_side ? f2(P0.x, P0.y) : f2(P0.z, P0.w);
+                        const float2 g0 = col_side ? f2(0.0f, 0.0f) : f2(P2.x, P2.y);
+                        const float2 mul = col_side ? f2(P2.z, P2.w) : f2(1.0f, 1.0f);
+                        const float2 dd = __fadd2_rn(__fadd2_rn(din2, nv2), dfr2);
+                        const float2 d2 = __fmul2_rn(dd, dd);
+                        const float2 e = __ffma2_rn(__ffma2_rn(g2, d2, g1), d2, g0);
+                        const float2 F = f2(ex2_approx(e.x), ex2_approx(e.y));
+                        const float2 C = __fmul2_rn(F, __fmul2_rn(mul, d2));
+                        split3_bf16(F, ph[u], pm[u], pl[u]);
+                        pc[u] = bf16x2_rn(C.x, C.y);
+                    }
+                    // piece k at buf + k * 4 KB (rows: 0-3, columns: 4-7); K group kg at
+                    // + kg * 2 KB; row (column) t at + t * 16
+                    constexpr int PW = kTcPieceBytes / 16;             // uint4 per piece
+                    uint4 *const pq = reinterpret_cast<uint4 *>(buf + (col_side ? 4 * kTcPieceBytes : 0) +
+                                                                kg * (kTcPieceBytes / 2) + t * 16);
+                    pq[0 * PW] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                    pq[1 * PW] = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+                    pq[2 * PW] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                    pq[3 * PW] = make_uint4(pc[0], pc[1], pc[2], pc[3]);
+                }
+                // the warp's writes, visible to the tensor core, then one arrival per warp
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full + b);
+            }
+            // the item's MMAs have completed: read the accumulators, write the partial sums
+            const bool fin = mbar_wait_bounded(done, (uint32_t)n_done & 1u, kTcWaitTries);
+            tc_fence_after();
+            const bool item_ok = __all_sync(0xffffffffu, fin && ok);
+            ok = ok && fin;
+            const int quarter = warp & 3, half = warp >> 2;
+            const int64_t r = r0 + 32 * quarter + lane;
+            float *prow = partial + ((int64_t)it.q * ng + it.j) * pstride + r * W + c0;
+            const bool live_r = r < H;
+            const int64_t ncol = min((int64_t)kTcTile, W - c0);
+            const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+                const int cb = 64 * half + 16 * c4;
+                uint32_t v1[16], v2[16];
+                tmem_ld_32x32b<16>(lane_base + (uint32_t)cb, v1);
+                tmem_ld_32x32b<16>(lane_base + (uint32_t)(kTcTile + cb), v2);
+                tmem_ld_wait();
+                if (!live_r) continue;
+                float sv[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    sv[e] = item_ok ? __uint_as_float(v1[e]) + __uint_as_float(v2[e]) : __int_as_float(0x7FC00000);
+                if (cb + 16 <= ncol && (reinterpret_cast<uintptr_t>(prow + cb) & 15) == 0) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        reinterpret_cast<float4 *>(prow + cb)[e] = make_float4(sv[4 * e], sv[4 * e + 1], sv[4 * e + 2], sv[4 * e + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (cb + e < ncol) prow[cb + e] = sv[e];
+                }
+            }
+            // the accumulators are read before the next item's first MMA overwrites them
+            // (that MMA waits for every producer warp's arrival on the next stage)
+            tc_fence_before();
+            gs += nst;
+            it = nxt;
+            nxt = nn;
+        }
+    }
+    if (!ok) atomicExch(&g_field_tc_timeout, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kGenWarps) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
+}
+
+}  // namespace ddk

@@ -4,6 +4,7 @@
 // Scan strategies follow Sec. 1 of Javadi Rad et al. (raster, alternating,
 // interleaved, random, subsampled); the visit order feeds the cumulative sum of
 // Eq. 5, each visit starting when the previous dwell ends (Sec. 2).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -446,6 +447,13 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
             s->Y[(size_t)k] = (double)q;
             s->T[(size_t)k] = s->uniform ? (double)k : s->t_start[(size_t)k] / tref;
             s->TAU[(size_t)k] = s->uniform ? 1.0 : s->tau[(size_t)k] / tref;
+        }
+        if (n > 0) {
+            const auto xr = std::minmax_element(s->X.begin(), s->X.end());
+            const auto yr = std::minmax_element(s->Y.begin(), s->Y.end());
+            s->x_lo = *xr.first; s->x_hi = *xr.second;
+            s->y_lo = *yr.first; s->y_hi = *yr.second;
+            s->tau_max = *std::max_element(s->TAU.begin(), s->TAU.end());
         }
     } catch (const std::bad_alloc &) {
         delete s;

@@ -47,9 +47,11 @@ def test_bench_workload_grid_sampled_and_equal_to_point_list(cuda):
     ref = oracle_pairs(job.scan, pts, job.times, ip, it)
     assert_mixed(gm[it, ip], ref, peak_lower_bound(job.scan, job.times)[it], "grid mixed")
     assert_fp64(g64[it, ip], ref, "grid fp64")
-    # the separable form changes only the FP32 rounding
+    # the separable form and the tensor-core contraction of the older visits (BF16 pieces,
+    # FP32 accumulation in another order) change only the FP32 rounding: both results
+    # within a few 1e-6 of each other
     rel = np.abs(gm - lstm)[lstm > 1e-6 * lstm.max(axis=1, keepdims=True)] / lstm[lstm > 1e-6 * lstm.max(axis=1, keepdims=True)]
-    assert rel.max() <= 2e-6
+    assert rel.max() <= 5e-6
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
