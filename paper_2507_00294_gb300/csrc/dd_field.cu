@@ -81,16 +81,17 @@ __global__ void prep_points_lag_kernel(int nb_lag, int64_t M, double s, double k
         prep_point((int64_t)(blockIdx.x - nb_lag) * blockDim.x + threadIdx.x, xy, g, n, inv_p, X, Y, F);
 }
 
-// out[row[j]][p] = pref * (sum_{q < nq[j]} tpart[(q * n_tg + j) * pstride + p]
+// out[row[j]][p] = pref * (sum_{q < nq[j]} tpart[(trow0[j] + q) * pstride + p]
 //                          + sum_{kb0[j] <= k < nblk[j]} partial[(k * n_tg + j) * pstride + p]):
 // the tensor-core chunks of snapshot j (the older visits), then its visit blocks, in that
 // order (deterministic); four points per thread, so that each load moves 16 bytes or more.
-// kb0 and nq NULL: every block from 0, no tensor-core chunks.
+// kb0 and nq NULL: every block from 0, no tensor-core rows.
 template <typename Part>
 __global__ void reduce_kernel(const Part *__restrict__ partial, const int *__restrict__ nblk_of_snap,
                               const int *__restrict__ kb0_of_snap, const Part *__restrict__ tpart,
-                              const int *__restrict__ nq_of_snap, const int *__restrict__ row, int n_tg,
-                              int64_t n_pts, int64_t pstride, double pref, double *__restrict__ out) {
+                              const int *__restrict__ nq_of_snap, const int *__restrict__ trow0,
+                              const int *__restrict__ row, int n_tg, int64_t n_pts, int64_t pstride, double pref,
+                              double *__restrict__ out) {
     const int j = blockIdx.y;
     const int64_t p0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (p0 >= n_pts) return;
@@ -100,7 +101,7 @@ __global__ void reduce_kernel(const Part *__restrict__ partial, const int *__res
     BlockSum<Part> acc[4];
     for (int k = 0; k < nq; ++k) {
         Part v[4];
-        load4_cg(tpart + ((int64_t)k * n_tg + j) * pstride + p0, v);
+        load4_cg(tpart + ((int64_t)trow0[j] + k) * pstride + p0, v);
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q].add(v[q]);
     }
@@ -159,7 +160,7 @@ struct HostTables {
 // Sizes of the workspace a call needs (the same function drives the carve).
 template <typename Cfg>
 size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out_host, bool pts_host,
-                       int n_t, int64_t n_rec, int nq_max, int64_t n_titems) {
+                       int n_t, int64_t n_rec, int64_t trows, int64_t n_titems) {
     using Rec = typename Cfg::Rec;
     const int nblk_max = (int)((n_src + sb - 1) / sb);
     const int n_chunks = (group + Cfg::kTCH - 1) / Cfg::kTCH;
@@ -170,13 +171,13 @@ size_t workspace_bytes(int64_t n_pts, int64_t n_src, int group, int sb, bool out
     add(2 * (size_t)n_pts * sizeof(double));                  // X, Y in pitch units
     add((size_t)n_pts * sizeof(float4));                      // the same as float-float
     add((size_t)group * sizeof(double));                      // snapshot times
-    add((size_t)group * sizeof(int) * 6);                     // nact, row, nblk, kst, kb0, nq per snapshot
+    add((size_t)group * sizeof(int) * 7);                     // nact, row, nblk, kst, kb0, nq, trow0 per snapshot
     add((size_t)group * sizeof(int64_t));                     // record row offset per snapshot
     add((size_t)n_chunks * nblk_max * sizeof(int2));          // (chunk, block) descriptors
     add((size_t)n_titems * sizeof(ddk::TcItem));              // tensor-core work items
     add((size_t)n_rec * sizeof(Rec));                         // coefficient records
     add((size_t)nblk_max * group * ((n_pts + 3) / 4 * 4) * sizeof(typename Cfg::Real));   // partial sums
-    add((size_t)nq_max * group * ((n_pts + 3) / 4 * 4) * sizeof(float));                  // tensor-core partials
+    add((size_t)trows * ((n_pts + 3) / 4 * 4) * sizeof(float));                           // tensor-core partials
     return b + 256;
 }
 
@@ -247,7 +248,6 @@ int64_t resident_ctas() {
 // start times.  The contraction takes that prefix, the CUDA-core tile the rest.
 struct TcPlan {
     bool on = false;
-    int chunk = ddk::kTcMaxChunk;
     int64_t n_tile_cols = 0, n_tiles = 0;
     std::vector<int> K;          // per snapshot (time order): the contraction's visits [0, K)
 };
@@ -319,20 +319,50 @@ int64_t tc_resident_ctas() {
     return v;
 }
 
-// Visits per tensor-core work item: the candidate (a multiple of the 16-visit stage) with
-// the shortest estimated makespan, whole waves of resident CTAs times (chunk + a fixed
-// cost per item of about three stages for the staging and the epilogue).
-int choose_tc_chunk(const TcPlan &tp, int n_t) {
-    const int64_t slots = std::max<int64_t>(1, tc_resident_ctas());
-    int best = ddk::kTcMaxChunk;
-    int64_t best_cost = INT64_MAX;
-    for (int c = 64; c <= ddk::kTcMaxChunk; c += 64) {
-        int64_t items = 0;
-        for (int j = 0; j < n_t; ++j) items += (int64_t)((tp.K[j] + c - 1) / c) * tp.n_tiles;
-        const int64_t cost = (items + slots - 1) / slots * (c + 48);
-        if (cost < best_cost) { best_cost = cost; best = c; }
+// The tensor-core contraction runs on a side stream of the calling thread, forked from the
+// caller's stream after the coefficients and joined back before the reduce, so that its CTAs
+// fill the SMs the CUDA-core tile kernel leaves idle.  One stream and two events per
+// (thread, device), created on first use (reusing an event is safe: a wait takes the state
+// of the event's latest record when it is issued).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+cudaError_t side_stream(SideStream **out) {
+    thread_local SideStream per_dev[64];
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    SideStream &ss = per_dev[dev];
+    if (!ss.s) {
+        int lo = 0, hi = 0;
+        if ((err = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return err;
+        if ((err = cudaStreamCreateWithPriority(&ss.s, cudaStreamNonBlocking, lo)) != cudaSuccess) return err;
+        if ((err = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return err;
+        if ((err = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return err;
     }
-    return best;
+    *out = &ss;
+    return cudaSuccess;
+}
+
+// Pieces of each snapshot's prefix for one launch over snapshots [g0, g0 + ng): about one
+// work item per resident CTA (every item the same number of 16-visit stages, give or take
+// the rounding), so that the launch is one wave and each CTA writes one partial row per item;
+// and no piece longer than kTcMaxItemStages stages (the accumulation's error budget).
+std::vector<int> tc_pieces(const TcPlan &tp, int g0, int ng, int64_t slots) {
+    std::vector<int> pieces(ng, 0);
+    int64_t total = 0;
+    for (int j = 0; j < ng; ++j) total += (int64_t)((tp.K[g0 + j] + ddk::kTcStage - 1) / ddk::kTcStage) * tp.n_tiles;
+    if (total == 0) return pieces;
+    const int64_t per = std::max<int64_t>(1, (total + std::max<int64_t>(slots, 1) - 1) / std::max<int64_t>(slots, 1));
+    for (int j = 0; j < ng; ++j) {
+        const int64_t S = (tp.K[g0 + j] + ddk::kTcStage - 1) / ddk::kTcStage;
+        if (S > 0) pieces[j] = (int)std::max<int64_t>(1, (S * tp.n_tiles + per / 2) / per / std::max<int64_t>(tp.n_tiles, 1));
+        if (S > 0) pieces[j] = (int)std::min<int64_t>(std::max<int64_t>({(int64_t)pieces[j], 1,
+                                                                        (S + ddk::kTcMaxItemStages - 1) / ddk::kTcMaxItemStages}), S);
+    }
+    return pieces;
 }
 
 // pts_xy_m == NULL: the points are the grid `grid` (row-major, n_pts = W H), formed on
@@ -422,29 +452,26 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     const int n_chunks_max = (group + Cfg::kTCH - 1) / Cfg::kTCH;
     // tensor-core chunks: rows of partial sums per snapshot and work items per group, within
     // the partial-sum budget (else the CUDA-core tile takes every visit)
-    int nq_max = 0;
-    int64_t n_titems_max = 0;
+    int64_t trows_max = 0, n_titems_max = 0;
+    const int64_t tc_slots = tp.on ? std::max<int64_t>(1, tc_resident_ctas()) : 1;
     if (tp.on) {
-        tp.chunk = choose_tc_chunk(tp, n_t);
         for (int g0 = 0; g0 < n_t; g0 += group) {
-            int64_t ni = 0;
-            for (int j = g0; j < std::min(n_t, g0 + group); ++j) {
-                const int nq = (tp.K[j] + tp.chunk - 1) / tp.chunk;
-                nq_max = std::max(nq_max, nq);
-                ni += (int64_t)nq * tp.n_tiles;
-            }
-            n_titems_max = std::max(n_titems_max, ni);
+            const std::vector<int> pc = tc_pieces(tp, g0, std::min(group, n_t - g0), tc_slots);
+            int64_t rows = 0;
+            for (int v : pc) rows += v;
+            trows_max = std::max(trows_max, rows);
+            n_titems_max = std::max(n_titems_max, rows * tp.n_tiles);
         }
-        if ((size_t)nq_max * group * ((n_pts + 3) / 4 * 4) * sizeof(float) > budget || n_titems_max > (int64_t(1) << 24)) {
+        if ((size_t)trows_max * ((n_pts + 3) / 4 * 4) * sizeof(float) > budget || n_titems_max > (int64_t(1) << 24)) {
             tp.on = false;
             std::fill(tp.K.begin(), tp.K.end(), 0);
-            nq_max = 0;
+            trows_max = 0;
             n_titems_max = 0;
         }
     }
 
     const int64_t n_rec = lattice ? M + 1 : (int64_t)group * n_src;
-    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_copy, pts_copy, n_t, n_rec, nq_max,
+    const size_t ws_bytes = workspace_bytes<Cfg>(n_pts, n_src, group, sb, out_copy, pts_copy, n_t, n_rec, trows_max,
                                                  n_titems_max);
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, stream, &st);
@@ -470,12 +497,13 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     double *Y = X + n_pts;
     float4 *PF = cv.take<float4>((size_t)n_pts);
     double *d_t = cv.take<double>(group);
-    int *d_nact = cv.take<int>(6 * (size_t)group);
+    int *d_nact = cv.take<int>(7 * (size_t)group);
     int *d_row = d_nact + group;
     int *d_nblk = d_row + group;
     int *d_kst = d_nblk + group;
     int *d_kb0 = d_kst + group;
     int *d_nq = d_kb0 + group;
+    int *d_trow0 = d_nq + group;
     int64_t *d_roff = cv.take<int64_t>(group);
     int2 *d_desc = cv.take<int2>((size_t)n_chunks_max * nblk_max);
     ddk::TcItem *d_titems = cv.take<ddk::TcItem>((size_t)n_titems_max);
@@ -483,7 +511,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     using Part = typename Cfg::Real;
     const int64_t pstride = (n_pts + 3) / 4 * 4;            // 16-byte aligned partial rows
     Part *d_part = cv.take<Part>((size_t)nblk_max * group * pstride);
-    float *d_tpart = cv.take<float>((size_t)nq_max * group * pstride);
+    float *d_tpart = cv.take<float>((size_t)trows_max * pstride);
 
     if (!lattice) {
         DD_PROFILED("prep_points", stream,
@@ -507,7 +535,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     for (int g0 = 0; g0 < n_t; g0 += group) {
         const int ng = std::min(group, n_t - g0);
         const int n_chunks = (ng + Cfg::kTCH - 1) / Cfg::kTCH;
-        std::vector<int> tabs(6 * (size_t)ng);
+        std::vector<int> tabs(7 * (size_t)ng);
+        const std::vector<int> tpieces = tp.on ? tc_pieces(tp, g0, ng, tc_slots) : std::vector<int>(ng, 0);
         std::vector<double> tg(ng);
         std::vector<int64_t> roff(ng);
         int max_nact = 0;
@@ -517,7 +546,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
             tabs[ng + j] = order[g0 + j];
             tabs[3 * ng + j] = tp.K[g0 + j];                               // kst
             tabs[4 * ng + j] = tp.K[g0 + j] / sb;                          // kb0
-            tabs[5 * ng + j] = (tp.K[g0 + j] + tp.chunk - 1) / tp.chunk;   // nq
+            tabs[5 * ng + j] = tpieces[j];                                 // nq
+            tabs[6 * ng + j] = j > 0 ? tabs[6 * ng + j - 1] + tpieces[j - 1] : 0;   // trow0
             max_nact = std::max(max_nact, nact[g0 + j]);
             // lattice: snapshot t reads lag t - i at rev[M - t + i]; otherwise row j of the
             // per-(snapshot, visit) records
@@ -545,18 +575,23 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                 blocks.push_back({cost, make_int2(c, k)});
             }
         }
-        // tensor-core items: (snapshot, chunk of its prefix, tile), whole chunks first
+        // tensor-core items: piece p of snapshot j's prefix (stages [p S / P, (p + 1) S / P) of
+        // its S 16-visit stages) on each tile, partial row trow0[j] + p; longest first
         std::vector<ddk::TcItem> titems;
         if (tp.on) {
-            for (int pass = 0; pass < 2; ++pass)
-                for (int j = 0; j < ng; ++j) {
-                    const int K = tp.K[g0 + j];
-                    for (int q = 0; q * tp.chunk < K; ++q) {
-                        const int v_end = std::min(K, (q + 1) * tp.chunk);
-                        if ((v_end - q * tp.chunk == tp.chunk) != (pass == 0)) continue;
-                        for (int64_t t = 0; t < tp.n_tiles; ++t) titems.push_back({j, q, (int)t, v_end, roff[j], 0});
-                    }
+            for (int j = 0; j < ng; ++j) {
+                const int K = tp.K[g0 + j], P = tpieces[j];
+                const int64_t S = (K + ddk::kTcStage - 1) / ddk::kTcStage;
+                for (int p = 0; p < P; ++p) {
+                    const int vb = (int)(S * p / P) * ddk::kTcStage;
+                    const int ve = std::min(K, (int)(S * (p + 1) / P) * ddk::kTcStage);
+                    for (int64_t t = 0; t < tp.n_tiles; ++t)
+                        titems.push_back({vb, ve, (int)t, tabs[6 * ng + j] + p, roff[j], 0});
                 }
+            }
+            std::stable_sort(titems.begin(), titems.end(), [](const ddk::TcItem &a, const ddk::TcItem &b) {
+                return a.v_end - a.v_begin > b.v_end - b.v_begin;
+            });
         }
         std::stable_sort(blocks.begin(), blocks.end(),
                          [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
@@ -571,7 +606,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                                                : reinterpret_cast<char *>(d_titems + titems.size()) - d0;
             std::vector<char> img(span);
             std::memcpy(img.data(), tg.data(), ng * sizeof(double));
-            std::memcpy(img.data() + (reinterpret_cast<char *>(d_nact) - d0), tabs.data(), 6 * (size_t)ng * sizeof(int));
+            std::memcpy(img.data() + (reinterpret_cast<char *>(d_nact) - d0), tabs.data(), 7 * (size_t)ng * sizeof(int));
             std::memcpy(img.data() + (reinterpret_cast<char *>(d_roff) - d0), roff.data(), ng * sizeof(int64_t));
             std::memcpy(img.data() + (reinterpret_cast<char *>(d_desc) - d0), it.data(), it.size() * sizeof(int2));
             if (!titems.empty())
@@ -586,22 +621,11 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                         (ddk::coef_kernel<Rec><<<cg, 128, 0, stream>>>(srcT, srcTAU, d_t, d_nact, scan->s, scan->kappa, d_rec, n_src)));
             DD_CUDA_TRY(cudaGetLastError());
         }
-        if constexpr (kMixed) {
-            if (!titems.empty()) {
-                DD_CUDA_TRY(prepare_tc_kernel());
-                // DD_FAULT=field_tc_wait (tests): no MMA is issued, so the completion waits
-                // run out and the kernel reports it (dd_field_check)
-                const int withhold = dd::fault_injected("field_tc_wait") ? 1 : 0;
-                // persistent CTAs: as many as are resident at once, at most one per item
-                const int64_t resident = tc_resident_ctas();
-                const unsigned n_cta = (unsigned)std::min<int64_t>((int64_t)titems.size(),
-                                                                   resident > 0 ? resident : 2 * 148);
-                DD_PROFILED("field_grid_tc", stream,
-                            (ddk::field_grid_tc_kernel<<<n_cta, ddk::kTcThreads, ddk::kTcSmemBytes, stream>>>(
-                                grid.W, grid.H, tp.n_tile_cols, d_rec, d_titems, (int)titems.size(), tp.chunk, ng,
-                                d_tpart, pstride, srcF, PF, withhold)));
-                DD_CUDA_TRY(cudaGetLastError());
-            }
+        // the tensor-core contraction's fork point: after the coefficients
+        SideStream *side = nullptr;
+        if (kMixed && !titems.empty()) {
+            DD_CUDA_TRY(side_stream(&side));
+            DD_CUDA_TRY(cudaEventRecord(side->fork, stream));
         }
         if (!it.empty()) {
             if (grid_tiles) DD_CUDA_TRY((prefer_shared<Cfg, true>()));
@@ -627,11 +651,33 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                 DD_CUDA_TRY(cudaGetLastError());
             }
         }
+        // the contraction on the side stream, submitted after the CUDA-core tile kernel so
+        // that the latter's CTAs are placed first and the contraction's fill what they leave
+        if constexpr (kMixed) {
+            if (side) {
+                DD_CUDA_TRY(prepare_tc_kernel());
+                DD_CUDA_TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
+                // DD_FAULT=field_tc_wait (tests): no MMA is issued, so the completion waits
+                // run out and the kernel reports it (dd_field_check)
+                const int withhold = dd::fault_injected("field_tc_wait") ? 1 : 0;
+                // persistent CTAs: as many as are resident at once, at most one per item
+                const int64_t resident = tc_resident_ctas();
+                const unsigned n_cta = (unsigned)std::min<int64_t>((int64_t)titems.size(),
+                                                                   resident > 0 ? resident : 2 * 148);
+                DD_PROFILED("field_grid_tc", side->s,
+                            (ddk::field_grid_tc_kernel<<<n_cta, ddk::kTcThreads, ddk::kTcSmemBytes, side->s>>>(
+                                grid.W, grid.H, tp.n_tile_cols, d_rec, d_titems, (int)titems.size(), d_tpart, pstride,
+                                srcF, PF, withhold)));
+                DD_CUDA_TRY(cudaGetLastError());
+                DD_CUDA_TRY(cudaEventRecord(side->join, side->s));
+                DD_CUDA_TRY(cudaStreamWaitEvent(stream, side->join, 0));
+            }
+        }
         dim3 rg((unsigned)((n_pts + 1023) / 1024), (unsigned)ng);
         DD_PROFILED("field_reduce", stream,
                     (ddk::reduce_kernel<Part><<<rg, 256, 0, stream>>>(
                         d_part, d_nblk, tp.on ? d_kb0 : nullptr, reinterpret_cast<const Part *>(d_tpart),
-                        tp.on ? d_nq : nullptr, d_row, ng, n_pts, pstride, scan->pref, out_dev)));
+                        tp.on ? d_nq : nullptr, d_trow0, d_row, ng, n_pts, pstride, scan->pref, out_dev)));
         DD_CUDA_TRY(cudaGetLastError());
         keep->items.push_back(std::move(it));
         keep->ints.push_back(std::move(tabs));

@@ -21,16 +21,16 @@
 // low); keeping the leading product apart makes that loss one MMA per 16 visits of the
 // chunk instead of seven, and the small products' losses 2^-7 smaller.
 //
-// Work item: one 128 x 128 tile, one snapshot j and a chunk of at most kTcMaxChunk visits of
-// the snapshot's degree-2 prefix.  Persistent CTAs walk the items (item blockIdx.x, then
-// every gridDim.x-th).  Warps 0-7 produce: thread t < 128 forms the factors of row r0 + t,
+// Work item: one 128 x 128 tile, one snapshot j and a range of the snapshot's degree-2
+// prefix (about one item per resident CTA), staged kTcMaxChunk visits at a time.
+// Persistent CTAs walk the items (item blockIdx.x, then every gridDim.x-th).  Warps 0-7 produce: thread t < 128 forms the factors of row r0 + t,
 // thread 128 + t those of column c0 + t, 16 visits at a time, into one of three shared-memory
 // stages, and arrives on the stage's "full" barrier; lane 0 of warp 8 waits for it, issues
 // the stage's MMAs and commits them to the stage's "empty" barrier, which the producers wait
 // on before they write that stage again -- no CTA-wide barrier inside the item.  After an
 // item's last stage the MMA thread commits to the "done" barrier; the producers then read the
-// accumulators (warp w: rows 32 (w % 4) .., columns 64 (w / 4) ..) and write the FP32 partial
-// sums of the chunk.
+// accumulators (warp w: rows 32 (w % 4) .., columns 64 (w / 4) ..) into shared memory and
+// write the FP32 partial sums of the item as whole rows.
 #pragma once
 #include <cstdint>
 
@@ -44,22 +44,28 @@ constexpr int kTcThreads = kTcGenThreads + 32;                 // + warp 8: issu
 constexpr int kTcTile = 128;                 // rows = columns of a tile (M = N = 128)
 constexpr int kTcStage = 16;                 // visits per stage: one K step of the BF16 MMA
 constexpr int kTcBufs = 3;                   // stages in flight
-constexpr int kTcMaxChunk = 256;             // visits per work item at most
+constexpr int kTcMaxChunk = 256;             // visits per coefficient staging (segment of an item)
+constexpr int kTcScratchStride = kTcTile + 4; // floats per row of the epilogue's transpose
 constexpr int kTcPieceBytes = kTcTile * kTcStage * 2;          // 4 KB: 128 rows x 16 BF16
 constexpr int kTcBufBytes = 8 * kTcPieceBytes;                 // Y_h Y_m Y_l B | X_h X_m X_l A
 constexpr int kTcCoefBytes = 3 * (kTcMaxChunk / 2) * 16;       // three float4 per visit pair
 constexpr int kTcSmemBytes = kTcBufs * kTcBufBytes + kTcCoefBytes + 128;
+constexpr int kTcMaxItemStages = 32;         // stages per item (one partial row) at most: the
+                                             // tensor core's FP32 accumulation drops up to an ulp
+                                             // of the sum per MMA, so a sum takes at most 32
+                                             // leading-product MMAs (<= 32 2^-23 relative)
 constexpr int kTcCtasPerSm = 2;              // by shared memory (2 x 102 KB) and TMEM (2 x 256 columns)
 constexpr int kTcWaitTries = 1 << 18;        // completion waits: at most about 0.26 s
 constexpr float kTcTwoLn2 = 1.38629436112f;
 // set when a completion wait of the contraction gives up (its partial sums are then NaN)
 static __device__ int g_field_tc_timeout;
 
-// Work item: snapshot (index within the group), chunk q of that snapshot's degree-2
-// prefix, tile (row block * n_tile_cols + column block), end of the chunk's visits.
+// Work item: visits [v_begin, v_end) of one snapshot's degree-2 prefix on one tile (row
+// block * n_tile_cols + column block); its sums go to partial row `row`; the snapshot's
+// records start at rec + row_off.
 struct TcItem {
-    int j, q, tile, v_end;
-    int64_t row_off;         // snapshot j's record row (visit i at rec[row_off + i])
+    int v_begin, v_end, tile, row;
+    int64_t row_off;
     int64_t pad;
 };
 static_assert(sizeof(TcItem) == 32, "TcItem layout");
@@ -89,36 +95,34 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // the 256 producer threads only (warps 0-7)
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(kTcGenThreads) : "memory"); }
 
-// The loads of one work item's inputs, issued early (the next item's while the current one
+// The loads of one segment's inputs, issued early (the next segment's while the current one
 // runs): the tile's first point and this thread's row or column point, and for thread p below
-// the item's pair count the coordinates and leading coefficients of visits 2p and 2p + 1.
+// the segment's pair count the coordinates and leading coefficients of its visits 2p, 2p + 1.
 struct TcPrefetch {
     float4 org, pt, v[2], r[2];
 };
-__device__ __forceinline__ void tc_prefetch(TcPrefetch &f, const TcItem &it, int chunk, int64_t W, int64_t H,
+__device__ __forceinline__ void tc_prefetch(TcPrefetch &f, const TcItem &it, int s0, int64_t W, int64_t H,
                                             int64_t n_tile_cols, const RecF32 *__restrict__ rec,
                                             const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF, int tid) {
     const int64_t r0 = (it.tile / n_tile_cols) * (int64_t)kTcTile, c0 = (it.tile % n_tile_cols) * (int64_t)kTcTile;
     const int t = tid & (kTcTile - 1);
     f.org = ptsF[r0 * W + c0];
     f.pt = tid >= kTcTile ? ptsF[r0 * W + min(c0 + t, W - 1)] : ptsF[min(r0 + t, H - 1) * W + c0];
-    const int v0 = it.q * chunk, nv = it.v_end - v0;
+    const int nv = min(it.v_end - s0, kTcMaxChunk);
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int i = 2 * tid + e;
         if (i < nv) {
-            f.v[e] = srcF[v0 + i];
-            f.r[e] = reinterpret_cast<const float4 *>(rec + it.row_off + v0 + i)[0];
+            f.v[e] = srcF[s0 + i];
+            f.r[e] = reinterpret_cast<const float4 *>(rec + it.row_off + s0 + i)[0];
         }
     }
 }
 
-// partial[(q * ng + j) * pstride + r W + c] receives chunk q of snapshot j.
 __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
 field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__restrict__ rec,
-                     const TcItem *__restrict__ items, int n_items, int chunk, int ng, float *__restrict__ partial,
-                     int64_t pstride, const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF,
-                     int withhold_mma) {
+                     const TcItem *__restrict__ items, int n_items, float *__restrict__ partial, int64_t pstride,
+                     const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF, int withhold_mma) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char *bufs = tc_smem;
     float4 *cf = reinterpret_cast<float4 *>(tc_smem + kTcBufs * kTcBufBytes);   // [3][kTcMaxChunk / 2]
@@ -128,6 +132,7 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kGenWarps = kTcGenThreads / 32;
+    static_assert(kTcTile * kTcScratchStride * 4 <= kTcBufs * kTcBufBytes, "epilogue scratch inside the stages");
 
     if (warp == kGenWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(smem_u32(s_tmem)) : "memory");
@@ -154,7 +159,7 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
             int gs = 0;
             for (int q = blockIdx.x; q < n_items; q += gridDim.x) {
                 const TcItem it = items[q];
-                const int nst = (it.v_end - it.q * chunk + kTcStage - 1) / kTcStage;
+                const int nst = (it.v_end - it.v_begin + kTcStage - 1) / kTcStage;
                 for (int st = 0; st < nst; ++st) {
                     const int g = gs + st, b = g % kTcBufs;
                     ok = mbar_wait_bounded(full + b, (uint32_t)(g / kTcBufs) & 1u, kTcWaitTries) && ok;
@@ -187,17 +192,19 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
         // ---- the producers
         const bool col_side = tid >= kTcTile;              // warp-uniform
         const int t = tid & (kTcTile - 1);
+        const int G = (int)gridDim.x;
         int q = blockIdx.x;
         TcItem it = items[min(q, n_items - 1)];
-        TcItem nxt = items[min(q + (int)gridDim.x, n_items - 1)];
+        TcItem nxt = items[min(q + G, n_items - 1)];
+        int s0 = it.v_begin;
         TcPrefetch pf;
-        tc_prefetch(pf, it, chunk, W, H, n_tile_cols, rec, srcF, ptsF, tid);
+        tc_prefetch(pf, it, s0, W, H, n_tile_cols, rec, srcF, ptsF, tid);
         int gs = 0, n_done = 0;
-        for (; q < n_items; q += gridDim.x, ++n_done) {
-            const TcItem nn = items[min(q + 2 * (int)gridDim.x, n_items - 1)];
+        float *const scr = reinterpret_cast<float *>(bufs);
+        while (q < n_items) {
             const int64_t r0 = (it.tile / n_tile_cols) * (int64_t)kTcTile;
             const int64_t c0 = (it.tile % n_tile_cols) * (int64_t)kTcTile;
-            const int v0 = it.q * chunk, nv = it.v_end - v0;
+            const int s1 = min(s0 + kTcMaxChunk, it.v_end), nv = s1 - s0;
             const int nst = (nv + kTcStage - 1) / kTcStage;
             // this thread's row (or column): its offset from the integer grid position
             // nearest the tile's first point, as an exact integer plus a fraction (as in the
@@ -214,9 +221,10 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
                 dfr = (pf.pt.z - iy) + pf.pt.w;
                 din = iy - oy;
             }
-            // coefficients of the item's visits, by pairs: (-x, -y), (g_1x, g_2x),
+            // coefficients of the segment's visits, by pairs: (-x, -y), (g_1x, g_2x),
             // (g_0, 2 ln2 g_2x); the padding to whole stages contributes 0 (g_0 = -inf:
-            // Y = B = 0).  The previous item's readers are done first.
+            // Y = B = 0).  The previous segment's readers (and the previous item's epilogue,
+            // whose scratch is the stage buffers) are done first.
             producers_sync();
             if (tid < nst * (kTcStage / 2)) {
                 float vx[2], vy[2], g0[2], g1[2], g2[2];
@@ -235,8 +243,13 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
                 cf[kTcMaxChunk + tid] = make_float4(g0[0], g0[1], kTcTwoLn2 * g2[0], kTcTwoLn2 * g2[1]);
             }
             producers_sync();
-            // the next item's inputs, in flight while this item runs
-            if (q + (int)gridDim.x < n_items) tc_prefetch(pf, nxt, chunk, W, H, n_tile_cols, rec, srcF, ptsF, tid);
+            // the next segment (of this item, else the next item's first), its inputs in
+            // flight while this one runs
+            const bool last_seg = s1 >= it.v_end;
+            const int nq_ = last_seg ? q + G : q;
+            const TcItem nit = last_seg ? nxt : it;
+            const int ns0 = last_seg ? nit.v_begin : s1;
+            if (nq_ < n_items) tc_prefetch(pf, nit, ns0, W, H, n_tile_cols, rec, srcF, ptsF, tid);
             const float2 din2 = f2(din, din), dfr2 = f2(dfr, dfr);
             for (int st = 0; st < nst; ++st) {
                 const int g = gs + st, b = g % kTcBufs;
@@ -281,45 +294,63 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
                 __syncwarp();
                 if (lane == 0) mbar_arrive(full + b);
             }
-            // the item's MMAs have completed: read the accumulators, write the partial sums
-            const bool fin = mbar_wait_bounded(done, (uint32_t)n_done & 1u, kTcWaitTries);
-            tc_fence_after();
-            const bool item_ok = __all_sync(0xffffffffu, fin && ok);
-            ok = ok && fin;
-            const int quarter = warp & 3, half = warp >> 2;
-            const int64_t r = r0 + 32 * quarter + lane;
-            float *prow = partial + ((int64_t)it.q * ng + it.j) * pstride + r * W + c0;
-            const bool live_r = r < H;
-            const int64_t ncol = min((int64_t)kTcTile, W - c0);
-            const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+            gs += nst;
+            if (last_seg) {
+                // The item's MMAs have completed: the accumulators (warp w: rows 32 (w % 4) ..,
+                // columns 64 (w / 4) ..) go through shared memory (the stage buffers, whose
+                // last readers were those MMAs) and out as whole rows of the partial sums.
+                const bool fin = mbar_wait_bounded(done, (uint32_t)n_done & 1u, kTcWaitTries);
+                tc_fence_after();
+                const bool item_ok = __all_sync(0xffffffffu, fin && ok);
+                ok = ok && fin;
+                const int quarter = warp & 3, half = warp >> 2;
+                const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+                float *const srow = scr + (32 * quarter + lane) * kTcScratchStride;
 #pragma unroll
-            for (int c4 = 0; c4 < 4; ++c4) {
-                const int cb = 64 * half + 16 * c4;
-                uint32_t v1[16], v2[16];
-                tmem_ld_32x32b<16>(lane_base + (uint32_t)cb, v1);
-                tmem_ld_32x32b<16>(lane_base + (uint32_t)(kTcTile + cb), v2);
-                tmem_ld_wait();
-                if (!live_r) continue;
-                float sv[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    sv[e] = item_ok ? __uint_as_float(v1[e]) + __uint_as_float(v2[e]) : __int_as_float(0x7FC00000);
-                if (cb + 16 <= ncol && (reinterpret_cast<uintptr_t>(prow + cb) & 15) == 0) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        reinterpret_cast<float4 *>(prow + cb)[e] = make_float4(sv[4 * e], sv[4 * e + 1], sv[4 * e + 2], sv[4 * e + 3]);
-                } else {
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int cb = 64 * half + 16 * c4;
+                    uint32_t v1[16], v2[16];
+                    tmem_ld_32x32b<16>(lane_base + (uint32_t)cb, v1);
+                    tmem_ld_32x32b<16>(lane_base + (uint32_t)(kTcTile + cb), v2);
+                    tmem_ld_wait();
+                    float sv[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e)
-                        if (cb + e < ncol) prow[cb + e] = sv[e];
+                        sv[e] = item_ok ? __uint_as_float(v1[e]) + __uint_as_float(v2[e]) : __int_as_float(0x7FC00000);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        reinterpret_cast<float4 *>(srow + cb)[e] = make_float4(sv[4 * e], sv[4 * e + 1], sv[4 * e + 2], sv[4 * e + 3]);
                 }
+                // the accumulators are read before the next item's first MMA overwrites them
+                // (that MMA waits for every producer warp's arrival on the next stage)
+                tc_fence_before();
+                producers_sync();
+                // warp w writes rows w, w + 8, ..: lane l the columns 4l .. 4l + 3
+                const int64_t ncol = min((int64_t)kTcTile, W - c0);
+                const bool vec = (W & 3) == 0 && 4 * lane + 4 <= ncol;
+                for (int rr = warp; rr < kTcTile; rr += kGenWarps) {
+                    const int64_t r = r0 + rr;
+                    if (r >= H) break;
+                    const float4 v = reinterpret_cast<const float4 *>(scr + rr * kTcScratchStride)[lane];
+                    float *const dst = partial + (int64_t)it.row * pstride + r * W + c0 + 4 * lane;
+                    if (vec) {
+                        *reinterpret_cast<float4 *>(dst) = v;
+                    } else {
+                        if (4 * lane + 0 < ncol) dst[0] = v.x;
+                        if (4 * lane + 1 < ncol) dst[1] = v.y;
+                        if (4 * lane + 2 < ncol) dst[2] = v.z;
+                        if (4 * lane + 3 < ncol) dst[3] = v.w;
+                    }
+                }
+                ++n_done;
             }
-            // the accumulators are read before the next item's first MMA overwrites them
-            // (that MMA waits for every producer warp's arrival on the next stage)
-            tc_fence_before();
-            gs += nst;
-            it = nxt;
-            nxt = nn;
+            // advance to the next segment; the item record after the next is fetched early
+            if (last_seg) {
+                q += G;
+                it = nxt;
+                nxt = items[min(q + G, n_items - 1)];
+            }
+            s0 = ns0;
         }
     }
     if (!ok) atomicExch(&g_field_tc_timeout, 1);
