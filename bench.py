@@ -220,6 +220,31 @@ def recorded_traffic(kernel):
         return None
 
 
+# BF16 tensor-core peak: the measured cuBLAS burst figure, else the recipe's fallback
+def bf16_peak_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (cuBLAS bf16 burst, MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback (1.9 PFLOP/s bf16)"
+
+
+def tensor_core_line(prof, tc_pairs):
+    """The tensor-core contraction (field_grid_tc): 7 BF16 MMAs of 2 flops per (row, column,
+    visit) triple, i.e. 14 tensor flops per pair-term it sums.  Its event time runs from its
+    launch on the side stream to its end, overlapping the CUDA-core tile kernel (whose CTAs
+    are placed first), so the rate below is a lower bound of what it does alone."""
+    n, ms = prof.get("field_grid_tc", (0, 0.0))
+    if not n or not tc_pairs:
+        return None
+    avg = ms / n
+    peak, note = bf16_peak_tflops()
+    achieved = 14.0 * tc_pairs / (avg / 1e3) / 1e12
+    return {"kernel": "field_grid_tc", "bound": "tensor", "pairs_per_launch": tc_pairs, "flops_per_pair": 14,
+            "avg_launch_ms": avg, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_note": note, "note": "event time overlaps the CUDA-core tile kernel (side stream)"}
+
+
 def cumulant_l2(r):
     """l_2 of the FP32 record's exponent series (half the variance of s under the weight
     r / (1 + r s) on [0, 1]), by a 2000-node midpoint rule: enough to place a pair in the
@@ -236,12 +261,14 @@ def cumulant_l2(r):
     return out
 
 
-def ops_per_pair(job, samples=400_000, seed=5, grid=False):
+def ops_per_pair(job, samples=400_000, seed=5, grid=False, prefix=None):
     """Algorithmic FP32 FLOPs and MUFU operations per pair-term of the field kernel on this
     workload: the cost of the cheapest path that meets the FP32 accuracy target for each
     pair (series degree from that pair's own h, zero when a >= 87; on a grid, the degree-2
     pairs in their separable form, with the cross term where its size 2 g_2x dx^2 dy^2
-    exceeds the 2.5e-7 budget), averaged over seeded pairs."""
+    exceeds the 2.5e-7 budget), averaged over seeded pairs.  prefix[j]: visits of snapshot
+    j that the tensor-core contraction takes (the CUDA-core tile kernel sums the rest; the
+    pairs sampled here are its pairs)."""
     from paper_2507_00294_gb300 import workloads as w
     s = job.scan
     rng = np.random.default_rng(seed)
@@ -250,7 +277,8 @@ def ops_per_pair(job, samples=400_000, seed=5, grid=False):
     it = rng.integers(0, len(job.times), samples)
     t = job.times[it]
     nact = np.searchsorted(ts, t, side="left")
-    i = (rng.random(samples) * nact).astype(np.int64)
+    k0 = np.zeros(samples, np.int64) if prefix is None else np.asarray(prefix, np.int64)[it]
+    i = k0 + (rng.random(samples) * (nact - k0)).astype(np.int64)
     ip = rng.integers(0, len(job.pts_xy), samples)
     g = i                                        # raster: visit k is grid index k
     dx = job.pts_xy[ip, 0] - (g % s.nx) * s.pitch_m
@@ -279,7 +307,7 @@ def ops_per_pair(job, samples=400_000, seed=5, grid=False):
         sep = np.where(cross <= 2.5e-7, GRID_FLOPS_SEP1, GRID_FLOPS_SEP2)
         f = np.where(zero, GRID_FLOPS_ZERO, np.where(d2, sep, f - FLOPS_ZERO + GRID_FLOPS_RHO))
         m = np.where(zero, 0.0, np.where(d2, GRID_MUFU_SEP, m))
-    wgt = nact[np.arange(samples)]               # pairs are sampled per snapshot: weight by n_active
+    wgt = (nact - k0).astype(np.float64)         # pairs are sampled per snapshot: weight by their count
     return (float(np.sum(f * wgt) / np.sum(wgt)), float(np.sum(m * wgt) / np.sum(wgt)),
             float(np.sum(zero * wgt) / np.sum(wgt)))
 
@@ -757,6 +785,11 @@ def run_ours(args):
     out = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
     dose = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
     rank_field_pairs = field_pairs // n_pts * (p1 - p0)     # every point has the same pair count
+    # the split of the rank's field between the tensor-core contraction (the older visits'
+    # degree-2 terms) and the CUDA-core tile kernel (the rest), as the library plans it
+    tc_prefix = b.dd_field_grid_split(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times)
+    rank_tc_pairs = int(tc_prefix.sum()) * (p1 - p0)
+    rank_core_pairs = rank_field_pairs - rank_tc_pairs
 
     # The field and the dose are independent calls: the dose goes on a side stream that forks
     # from the step's stream and joins it again, so that its short kernels run beside the
@@ -804,11 +837,13 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
 
-    # roofline of the dominant kernel (field_grid_mixed), from its own events in the timed region
+    # roofline of the dominant kernel (field_grid_mixed, the CUDA-core tile kernel: the
+    # critical path of the field), from its own events in the timed region, over the pairs it
+    # sums (those the tensor-core contraction leaves)
     fl, fms = prof.get("field_grid_mixed", (0, 0.0))
     avg_ms = fms / max(1, fl)
-    fpp, mpp, culled = ops_per_pair(job, grid=True)
-    rate = rank_field_pairs / (avg_ms / 1e3) if fl else None
+    fpp, mpp, culled = ops_per_pair(job, grid=True, prefix=tc_prefix if world == 1 else None)
+    rate = rank_core_pairs / (avg_ms / 1e3) if fl else None
     traffic = recorded_traffic("field_grid_mixed")
     # the pair term needs FP32 issue and one MUFU ex2: report the pipe this algorithm's mix
     # binds (the larger fraction), with the other beside it
@@ -823,12 +858,13 @@ def run_ours(args):
     bind, other = (mufu, fp32) if (mufu["frac"] or 0) >= (fp32["frac"] or 0) else (fp32, mufu)
     roofline = {"bound": "alu", "kernel": "field_grid_mixed", "pipe": "mufu" if bind is mufu else "fp32",
                 "achieved": bind["achieved"], "peak": bind["peak"], "unit": bind["unit"], "frac": bind["frac"],
-                "traffic": traffic, "avg_launch_ms": avg_ms, "pairs_per_launch": rank_field_pairs,
+                "traffic": traffic, "avg_launch_ms": avg_ms, "pairs_per_launch": rank_core_pairs,
                 "kernel_pairs_per_s": rate, "ops_per_pair": bind["per_pair"], "peak_note": bind["peak_note"],
                 "culled_pair_fraction": round(culled, 5),
                 "culled_note": "pair-terms with a >= 87 (below the FP32 normal range) are counted in the "
-                               "pair-terms but skipped per warp; their share of the workload's pairs",
-                "other_pipe": {"pipe": "fp32" if bind is mufu else "mufu", **other}}
+                               "pair-terms but skipped per warp; their share of this kernel's pairs",
+                "other_pipe": {"pipe": "fp32" if bind is mufu else "mufu", **other},
+                "tensor_core": tensor_core_line(prof, rank_tc_pairs)}
     launches = int(sum(v[0] for v in prof.values()))
     # shares of the summed per-launch event time (the dose's kernels run beside the field's,
     # so their events overlap and the shares do not add up to wall time)
