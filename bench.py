@@ -229,18 +229,19 @@ def bf16_peak_tflops():
         return 1900.0, "fallback (1.9 PFLOP/s bf16)"
 
 
-def tensor_core_line(prof, tc_pairs):
-    """The tensor-core contraction (field_grid_tc): 7 BF16 MMAs of 2 flops per (row, column,
-    visit) triple, i.e. 14 tensor flops per pair-term it sums.  Its event time runs from its
-    launch on the side stream to its end, overlapping the CUDA-core tile kernel (whose CTAs
-    are placed first), so the rate below is a lower bound of what it does alone."""
-    n, ms = prof.get("field_grid_tc", (0, 0.0))
+def tensor_core_line(prof, kernel, tc_pairs, flops_per_pair):
+    """A tensor-core contraction of the grid field: field_grid_tc (degree 2: 7 BF16 MMAs of 2
+    flops per (row, column, visit) triple, 14 tensor flops per pair-term) or field_grid_tc4
+    (degree 4: 12 MMAs, 24 flops).  Its event time runs from its launch on the side stream to
+    its end, overlapping the CUDA-core tile kernel (whose CTAs are placed first), so the rate
+    below is a lower bound of what it does alone."""
+    n, ms = prof.get(kernel, (0, 0.0))
     if not n or not tc_pairs:
         return None
     avg = ms / n
     peak, note = bf16_peak_tflops()
-    achieved = 14.0 * tc_pairs / (avg / 1e3) / 1e12
-    return {"kernel": "field_grid_tc", "bound": "tensor", "pairs_per_launch": tc_pairs, "flops_per_pair": 14,
+    achieved = flops_per_pair * tc_pairs / (avg / 1e3) / 1e12
+    return {"kernel": kernel, "bound": "tensor", "pairs_per_launch": tc_pairs, "flops_per_pair": flops_per_pair,
             "avg_launch_ms": avg, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "peak_note": note, "note": "event time overlaps the CUDA-core tile kernel (side stream)"}
 
@@ -787,8 +788,9 @@ def run_ours(args):
     rank_field_pairs = field_pairs // n_pts * (p1 - p0)     # every point has the same pair count
     # the split of the rank's field between the tensor-core contraction (the older visits'
     # degree-2 terms) and the CUDA-core tile kernel (the rest), as the library plans it
-    tc_prefix = b.dd_field_grid_split(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times)
+    tc_prefix, tc_prefix2 = b.dd_field_grid_split(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, degree2=True)
     rank_tc_pairs = int(tc_prefix.sum()) * (p1 - p0)
+    rank_tc2_pairs = int(tc_prefix2.sum()) * (p1 - p0)
     rank_core_pairs = rank_field_pairs - rank_tc_pairs
 
     # The field and the dose are independent calls: the dose goes on a side stream that forks
@@ -864,7 +866,8 @@ def run_ours(args):
                 "culled_note": "pair-terms with a >= 87 (below the FP32 normal range) are counted in the "
                                "pair-terms but skipped per warp; their share of this kernel's pairs",
                 "other_pipe": {"pipe": "fp32" if bind is mufu else "mufu", **other},
-                "tensor_core": tensor_core_line(prof, rank_tc_pairs)}
+                "tensor_core": [tensor_core_line(prof, "field_grid_tc", rank_tc2_pairs, 14),
+                                tensor_core_line(prof, "field_grid_tc4", rank_tc_pairs - rank_tc2_pairs, 24)]}
     launches = int(sum(v[0] for v in prof.values()))
     # shares of the summed per-launch event time (the dose's kernels run beside the field's,
     # so their events overlap and the shares do not add up to wall time)

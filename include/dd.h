@@ -156,19 +156,22 @@ dd_status dd_field_on_grid(const dd_scan *scan, double x0_m, double y0_m, double
 
 /* The split dd_field_on_grid makes in FP32-mixed precision, host-only (no GPU work):
    prefix[it] = the number of leading visits (in visit order) whose pair terms at snapshot
-   times_s[it] (host array) are summed on the tensor cores; the visits after them go to the
-   CUDA-core tile kernel.  A visit qualifies when its pair term is on the degree-2 series at
-   every point of the grid: h = rho^2 dq <= 0.04 for rho^2 up to the largest squared
-   distance between the grid's box and the visits' box (R2), with dq bounded through the
-   scan's longest dwell (dq <= c / ((w1 - c) w1), c = 4 D tau_max, at w1 = 2 sigma^2 +
-   4 D (t - t_i)), so the qualifying visits are those started by t - dT*: a prefix.  0 for
-   grids smaller than 64 x 64 points and for snapshots with no qualifying visit; the path
-   also falls back to 0 everywhere if the split's partial sums would exceed its 1 GiB
-   workspace budget.  Errors: DD_EINVAL (NULL scan or buffers, negative sizes, non-finite
-   grid or times, device arrays). */
+   times_s[it] (host array) are summed on the tensor cores, and prefix_deg2[it] (NULL: not
+   wanted) how many of them in the degree-2 form; the visits after prefix[it] go to the
+   CUDA-core tile kernel.  A visit qualifies when its pair term is on the degree-2 (degree-4)
+   series at every point of the grid: h = rho^2 dq <= 0.04 (0.33) for rho^2 up to the
+   largest squared distance between the grid's box and the visits' box, with dq bounded
+   through the scan's longest dwell (dq <= c / ((w1 - c) w1), c = 4 D tau_max, at
+   w1 = 2 sigma^2 + 4 D (t - t_i)), so the qualifying visits are those started by
+   t - dT*: prefixes.  0 for grids smaller than 64 x 64 points and for snapshots with no
+   qualifying visit; the degree-4 band is left out where its coefficients of (rho^2)^4
+   would leave the FP32 normal range, and the path falls back to 0 everywhere if the
+   split's partial sums would exceed its 1 GiB workspace budget.
+   Errors: DD_EINVAL (NULL scan or buffers, negative sizes, non-finite grid or times,
+   device arrays). */
 dd_status dd_field_grid_split(const dd_scan *scan, double x0_m, double y0_m, double dx_m, double dy_m,
                               int64_t n_cols, int64_t n_rows, const double *times_s, int64_t n_t,
-                              int64_t *prefix);
+                              int64_t *prefix, int64_t *prefix_deg2);
 
 /* Synchronise the device and return DD_ETIMEOUT (clearing the flag) if a tensor-core
    contraction of dd_field_on_grid gave up waiting for its MMAs since the last check,

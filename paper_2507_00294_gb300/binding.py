@@ -95,7 +95,7 @@ def load(build_if_missing=True):
     lib.dd_field_check.argtypes = []
     lib.dd_field_check.restype = ctypes.c_int
     lib.dd_field_grid_split.argtypes = [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                        _I64, _I64, _VP, _I64, _VP]
+                                        _I64, _I64, _VP, _I64, _VP, _VP]
     lib.dd_field_grid_split.restype = ctypes.c_int
     for name in ("dd_sur_conv3x3", "dd_sur_wgrad", "dd_sur_mse", "dd_sur_wmse", "dd_sur_weights", "dd_sur_adam",
                  "dd_sur_planes",
@@ -412,14 +412,16 @@ def dd_sur_conv3x3(x, w, bias, mask, out, epilogue, dilation=1, stream=None):
     return out
 
 
-def dd_field_grid_split(scan, x0, y0, dx, dy, n_cols, n_rows, times_s):
+def dd_field_grid_split(scan, x0, y0, dx, dy, n_cols, n_rows, times_s, degree2=False):
     """Per snapshot, the number of leading visits dd_field_on_grid sums on the tensor cores
-    (FP32-mixed); host-only."""
+    (FP32-mixed); host-only.  degree2: also return how many of them in the degree-2 form."""
     t = np.ascontiguousarray(np.asarray(times_s, dtype=np.float64).reshape(-1))
     out = np.zeros(len(t), dtype=np.int64)
+    out2 = np.zeros(len(t), dtype=np.int64)
     _check(load().dd_field_grid_split(scan.handle, float(x0), float(y0), float(dx), float(dy), int(n_cols),
-                                      int(n_rows), t.ctypes.data, len(t), out.ctypes.data), "dd_field_grid_split")
-    return out
+                                      int(n_rows), t.ctypes.data, len(t), out.ctypes.data, out2.ctypes.data),
+           "dd_field_grid_split")
+    return (out, out2) if degree2 else out
 
 
 def dd_field_check():

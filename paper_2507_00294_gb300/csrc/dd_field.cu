@@ -239,23 +239,40 @@ int64_t resident_ctas() {
 // ---- the tensor-core part of the grid field (dd_field_tc.cuh)
 //
 // A visit is handed to the contraction for snapshot j when its pair term is on the degree-2
-// series at every point of the grid: h = rho^2 dq <= kL2H for rho^2 up to R2, the largest
-// squared distance between the grid's box and the box of the visits.  With c = 4 kappa
-// tau_max, dq = 1/w0 - 1/w1 <= c / ((w1 - c) w1) for every visit of the scan (dq grows with
-// the dwell at a fixed w1 = 2s + 4 kappa (t - T_i)), so every visit with w1 at or above the
-// root w1* of (w1 - c) w1 = c R2 / kL2H (and its dwell over) qualifies: the prefix of the
-// visits that started by t_j - dT*, dT* = (w1* - 2s) / (4 kappa), found by bisection of the
-// start times.  The contraction takes that prefix, the CUDA-core tile the rest.
+// (or degree-4) series at every point of the grid: h = rho^2 dq <= kL2H (kL4H) for rho^2 up
+// to R2, the largest squared distance between the grid's box and the box of the visits.
+// With c = 4 kappa tau_max, dq = 1/w0 - 1/w1 <= c / ((w1 - c) w1) for every visit of the
+// scan (dq grows with the dwell at a fixed w1 = 2s + 4 kappa (t - T_i)), so every visit
+// with w1 at or above the root w1* of (w1 - c) w1 = c R2 / h_limit (and its dwell over)
+// qualifies: the prefix of the visits that started by t_j - dT*, dT* = (w1* - 2s) /
+// (4 kappa), found by bisection of the start times.  The degree-2 prefix [0, K2) and the
+// degree-4 band [K2, K) go to the contraction (the degree-4 band only while its records'
+// g_4x = log2(e) l_4 dq^4 stay in the FP32 normal range, dq >= kMinDqX), the rest [K, nact)
+// to the CUDA-core tile.
 struct TcPlan {
     bool on = false;
     int64_t n_tile_cols = 0, n_tiles = 0;
-    std::vector<int> K;          // per snapshot (time order): the contraction's visits [0, K)
+    std::vector<int> K2;         // per snapshot (time order): the degree-2 visits [0, K2)
+    std::vector<int> K;          // and the degree-4 band [K2, K); the CUDA-core tile from K
 };
+
+// Age (in dwells) from which every visit of the scan is on the series of the given h limit
+// at every point within R2, or a negative value if none is.
+double tc_min_age(const dd_scan *scan, double R2, double h_limit, double *w1s_out) {
+    const double dq_max = h_limit * (1.0 - 1e-4) / R2;
+    const double c = 4.0 * scan->kappa * scan->tau_max;
+    if (!(c > 0.0) || !(dq_max > 0.0) || !std::isfinite(dq_max)) return -1.0;
+    double w1s = 0.5 * (c + std::sqrt(c * c + 4.0 * c / dq_max));
+    w1s = std::max(w1s, (2.0 * scan->s + c) * (1.0 + 1e-9));        // the dwell is over
+    if (w1s_out) *w1s_out = w1s;
+    return (w1s - 2.0 * scan->s) / (4.0 * scan->kappa) * (1.0 + 1e-9);
+}
 
 TcPlan plan_tc(const dd_scan *scan, const ddk::GridDesc &grid, const std::vector<double> &tdim,
                const std::vector<int> &nact) {
     TcPlan tp;
     const int n_t = (int)tdim.size();
+    tp.K2.assign(n_t, 0);
     tp.K.assign(n_t, 0);
     // tiles of 128 x 128 points: only grids that fill them reasonably
     if (grid.W < ddk::kTcTile / 2 || grid.H < ddk::kTcTile / 2 || scan->n == 0) return tp;
@@ -266,16 +283,19 @@ TcPlan plan_tc(const dd_scan *scan, const ddk::GridDesc &grid, const std::vector
     const double ey = std::max(std::max(ya, yb) - scan->y_lo, scan->y_hi - std::min(ya, yb));
     // margins for the points' own rounding and the records' rounding to FP32
     const double R2 = (ex * ex + ey * ey) * (1.0 + 1e-6) + 1e-6;
-    const double dq_max = (double)ddk::kL2H * (1.0 - 1e-4) / R2;
-    const double c = 4.0 * scan->kappa * scan->tau_max;
-    if (!(c > 0.0) || !(dq_max > 0.0) || !std::isfinite(dq_max)) return tp;
-    double w1s = 0.5 * (c + std::sqrt(c * c + 4.0 * c / dq_max));
-    w1s = std::max(w1s, (2.0 * scan->s + c) * (1.0 + 1e-9));        // the dwell is over
-    const double dTs = (w1s - 2.0 * scan->s) / (4.0 * scan->kappa) * (1.0 + 1e-9);
+    double w1s2 = 0.0;
+    const double age2 = tc_min_age(scan, R2, (double)ddk::kL2H, &w1s2);
+    if (age2 < 0.0) return tp;
+    double age4 = tc_min_age(scan, R2, (double)ddk::kL4H, nullptr);
+    // the degree-4 band's smallest dq: its oldest visit (w1 up to w1s2) with the shortest dwell
+    const double cmin = 4.0 * scan->kappa * scan->tau_min;
+    if (age4 < 0.0 || !(w1s2 > cmin) || cmin / ((w1s2 - cmin) * w1s2) < 2.0 * (double)ddk::kMinDqX) age4 = age2;
     int64_t any = 0;
     for (int k = 0; k < n_t; ++k) {
-        const int64_t Kk = std::upper_bound(scan->T.begin(), scan->T.end(), tdim[k] - dTs) - scan->T.begin();
-        tp.K[k] = (int)std::min<int64_t>(Kk, nact[k]);
+        const int64_t k2 = std::upper_bound(scan->T.begin(), scan->T.end(), tdim[k] - age2) - scan->T.begin();
+        const int64_t k4 = std::upper_bound(scan->T.begin(), scan->T.end(), tdim[k] - std::min(age4, age2)) - scan->T.begin();
+        tp.K2[k] = (int)std::min<int64_t>(k2, nact[k]);
+        tp.K[k] = (int)std::max<int64_t>(tp.K2[k], std::min<int64_t>(k4, nact[k]));
         any += tp.K[k];
     }
     if (any == 0) return tp;
@@ -287,22 +307,25 @@ TcPlan plan_tc(const dd_scan *scan, const ddk::GridDesc &grid, const std::vector
 
 // dynamic shared memory above 48 KB and the whole L1/shared array as shared memory, set
 // once per device
+template <int kDeg>
 cudaError_t prepare_tc_kernel() {
     static std::atomic<uint64_t> done{0};
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess || dev >= 64) return err;
     if (done.load() & (uint64_t(1) << dev)) return cudaSuccess;
-    err = cudaFuncSetAttribute(ddk::field_grid_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ddk::kTcSmemBytes);
+    err = cudaFuncSetAttribute(ddk::field_grid_tc_kernel<kDeg>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               ddk::TcConst<kDeg>::kSmemBytes);
     if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(ddk::field_grid_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+        err = cudaFuncSetAttribute(ddk::field_grid_tc_kernel<kDeg>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                    (int)cudaSharedmemCarveoutMaxShared);
     if (err == cudaSuccess) done.fetch_or(uint64_t(1) << dev);
     return err;
 }
 
-// Tensor-core CTAs resident on the whole device at once: kTcCtasPerSm per SM (their
-// shared memory and tensor memory bound it; 0 if unknown).
+// Tensor-core CTAs of the degree-kDeg kernel resident on the whole device at once (their
+// shared memory and tensor memory bound it per SM; 0 if unknown).
+template <int kDeg>
 int64_t tc_resident_ctas() {
     static std::atomic<int64_t> cached[64];
     int dev = 0;
@@ -314,7 +337,7 @@ int64_t tc_resident_ctas() {
         cudaGetLastError();
         return 0;
     }
-    v = (int64_t)ddk::kTcCtasPerSm * sms;
+    v = (int64_t)ddk::TcShape<kDeg>::kCtasPerSm * sms;
     cached[dev].store(v);
     return v;
 }
@@ -324,6 +347,8 @@ int64_t tc_resident_ctas() {
 // fill the SMs the CUDA-core tile kernel leaves idle.  One stream and two events per
 // (thread, device), created on first use (reusing an event is safe: a wait takes the state
 // of the event's latest record when it is issued).
+constexpr bool kTcBeforeCore = false;        // submission order of the two grid kernels
+constexpr bool kTcHighPriority = false;      // the side stream's priority (else the lowest)
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -338,7 +363,8 @@ cudaError_t side_stream(SideStream **out) {
     if (!ss.s) {
         int lo = 0, hi = 0;
         if ((err = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return err;
-        if ((err = cudaStreamCreateWithPriority(&ss.s, cudaStreamNonBlocking, lo)) != cudaSuccess) return err;
+        if ((err = cudaStreamCreateWithPriority(&ss.s, cudaStreamNonBlocking, kTcHighPriority ? hi : lo)) != cudaSuccess)
+            return err;
         if ((err = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return err;
         if ((err = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return err;
     }
@@ -346,19 +372,22 @@ cudaError_t side_stream(SideStream **out) {
     return cudaSuccess;
 }
 
-// Pieces of each snapshot's prefix for one launch over snapshots [g0, g0 + ng): about one
-// work item per resident CTA (every item the same number of 16-visit stages, give or take
-// the rounding), so that the launch is one wave and each CTA writes one partial row per item;
-// and no piece longer than kTcMaxItemStages stages (the accumulation's error budget).
-std::vector<int> tc_pieces(const TcPlan &tp, int g0, int ng, int64_t slots) {
+// Pieces of each snapshot's visit range [lo[j], hi[j]) for one launch over snapshots
+// [g0, g0 + ng): about one work item per resident CTA (every item the same number of 16-visit
+// stages, give or take the rounding), so that the launch is one wave and each CTA writes one
+// partial row per item; and no piece longer than kTcMaxItemStages stages (the accumulation's
+// error budget).
+std::vector<int> tc_pieces(const std::vector<int> &lo, const std::vector<int> &hi, int64_t n_tiles, int g0, int ng,
+                           int64_t slots) {
     std::vector<int> pieces(ng, 0);
+    auto stages = [&](int j) { return (int64_t)((hi[g0 + j] - lo[g0 + j] + ddk::kTcStage - 1) / ddk::kTcStage); };
     int64_t total = 0;
-    for (int j = 0; j < ng; ++j) total += (int64_t)((tp.K[g0 + j] + ddk::kTcStage - 1) / ddk::kTcStage) * tp.n_tiles;
+    for (int j = 0; j < ng; ++j) total += stages(j) * n_tiles;
     if (total == 0) return pieces;
     const int64_t per = std::max<int64_t>(1, (total + std::max<int64_t>(slots, 1) - 1) / std::max<int64_t>(slots, 1));
     for (int j = 0; j < ng; ++j) {
-        const int64_t S = (tp.K[g0 + j] + ddk::kTcStage - 1) / ddk::kTcStage;
-        if (S > 0) pieces[j] = (int)std::max<int64_t>(1, (S * tp.n_tiles + per / 2) / per / std::max<int64_t>(tp.n_tiles, 1));
+        const int64_t S = stages(j);
+        if (S > 0) pieces[j] = (int)std::max<int64_t>(1, (S * n_tiles + per / 2) / per / std::max<int64_t>(n_tiles, 1));
         if (S > 0) pieces[j] = (int)std::min<int64_t>(std::max<int64_t>({(int64_t)pieces[j], 1,
                                                                         (S + ddk::kTcMaxItemStages - 1) / ddk::kTcMaxItemStages}), S);
     }
@@ -421,8 +450,10 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     const bool lattice = snapshot_dims(scan, times, order, tdim, nact, M);
     // the degree-2 prefixes that the tensor-core contraction takes (grid tiles only)
     TcPlan tp;
+    tp.K2.assign(n_t, 0);
     tp.K.assign(n_t, 0);
     if (grid_tiles) tp = plan_tc(scan, grid, tdim, nact);
+    const std::vector<int> zeros(n_t, 0);
 
     // visit block size and snapshot groups bound the partial and record buffers
     const int tile = Cfg::kThreads * Cfg::kPPT;
@@ -468,17 +499,21 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     // tensor-core chunks: rows of partial sums per snapshot and work items per group, within
     // the partial-sum budget (else the CUDA-core tile takes every visit)
     int64_t trows_max = 0, n_titems_max = 0;
-    const int64_t tc_slots = tp.on ? std::max<int64_t>(1, tc_resident_ctas()) : 1;
+    const int64_t tc_slots2 = tp.on ? std::max<int64_t>(1, tc_resident_ctas<2>()) : 1;
+    const int64_t tc_slots4 = tp.on ? std::max<int64_t>(1, tc_resident_ctas<4>()) : 1;
     if (tp.on) {
         for (int g0 = 0; g0 < n_t; g0 += group) {
-            const std::vector<int> pc = tc_pieces(tp, g0, std::min(group, n_t - g0), tc_slots);
+            const int ng = std::min(group, n_t - g0);
+            const std::vector<int> p2 = tc_pieces(zeros, tp.K2, tp.n_tiles, g0, ng, tc_slots2);
+            const std::vector<int> p4 = tc_pieces(tp.K2, tp.K, tp.n_tiles, g0, ng, tc_slots4);
             int64_t rows = 0;
-            for (int v : pc) rows += v;
+            for (int j = 0; j < ng; ++j) rows += p2[j] + p4[j];
             trows_max = std::max(trows_max, rows);
             n_titems_max = std::max(n_titems_max, rows * tp.n_tiles);
         }
         if ((size_t)trows_max * ((n_pts + 3) / 4 * 4) * sizeof(float) > budget || n_titems_max > (int64_t(1) << 24)) {
             tp.on = false;
+            std::fill(tp.K2.begin(), tp.K2.end(), 0);
             std::fill(tp.K.begin(), tp.K.end(), 0);
             trows_max = 0;
             n_titems_max = 0;
@@ -551,7 +586,9 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
         const int ng = std::min(group, n_t - g0);
         const int n_chunks = (ng + Cfg::kTCH - 1) / Cfg::kTCH;
         std::vector<int> tabs(7 * (size_t)ng);
-        const std::vector<int> tpieces = tp.on ? tc_pieces(tp, g0, ng, tc_slots) : std::vector<int>(ng, 0);
+        // tensor-core pieces: of the degree-2 prefix [0, K2) and of the degree-4 band [K2, K)
+        const std::vector<int> tp2 = tp.on ? tc_pieces(zeros, tp.K2, tp.n_tiles, g0, ng, tc_slots2) : std::vector<int>(ng, 0);
+        const std::vector<int> tp4 = tp.on ? tc_pieces(tp.K2, tp.K, tp.n_tiles, g0, ng, tc_slots4) : std::vector<int>(ng, 0);
         std::vector<double> tg(ng);
         std::vector<int64_t> roff(ng);
         int max_nact = 0;
@@ -561,8 +598,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
             tabs[ng + j] = order[g0 + j];
             tabs[3 * ng + j] = tp.K[g0 + j];                               // kst
             tabs[4 * ng + j] = tp.K[g0 + j] / sb;                          // kb0
-            tabs[5 * ng + j] = tpieces[j];                                 // nq
-            tabs[6 * ng + j] = j > 0 ? tabs[6 * ng + j - 1] + tpieces[j - 1] : 0;   // trow0
+            tabs[5 * ng + j] = tp2[j] + tp4[j];                            // nq
+            tabs[6 * ng + j] = j > 0 ? tabs[6 * ng + j - 1] + tabs[5 * ng + j - 1] : 0;   // trow0
             max_nact = std::max(max_nact, nact[g0 + j]);
             // lattice: snapshot t reads lag t - i at rev[M - t + i]; otherwise row j of the
             // per-(snapshot, visit) records
@@ -590,23 +627,32 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                 blocks.push_back({cost, make_int2(c, k)});
             }
         }
-        // tensor-core items: piece p of snapshot j's prefix (stages [p S / P, (p + 1) S / P) of
-        // its S 16-visit stages) on each tile, partial row trow0[j] + p; longest first
+        // tensor-core items: piece p of a snapshot's range [lo, hi) (stages [p S / P,
+        // (p + 1) S / P) of its S 16-visit stages) on each tile; degree-2 items (partial rows
+        // trow0[j] + p) then degree-4 items (rows trow0[j] + P2 + p), each list longest first
         std::vector<ddk::TcItem> titems;
+        size_t n_t2 = 0;
         if (tp.on) {
-            for (int j = 0; j < ng; ++j) {
-                const int K = tp.K[g0 + j], P = tpieces[j];
-                const int64_t S = (K + ddk::kTcStage - 1) / ddk::kTcStage;
-                for (int p = 0; p < P; ++p) {
-                    const int vb = (int)(S * p / P) * ddk::kTcStage;
-                    const int ve = std::min(K, (int)(S * (p + 1) / P) * ddk::kTcStage);
-                    for (int64_t t = 0; t < tp.n_tiles; ++t)
-                        titems.push_back({vb, ve, (int)t, tabs[6 * ng + j] + p, roff[j], 0});
+            auto add_items = [&](const std::vector<int> &lo, const std::vector<int> &hi, const std::vector<int> &pc,
+                                 bool deg4) {
+                const size_t first = titems.size();
+                for (int j = 0; j < ng; ++j) {
+                    const int v0 = lo[g0 + j], P = pc[j];
+                    const int64_t S = (hi[g0 + j] - v0 + ddk::kTcStage - 1) / ddk::kTcStage;
+                    for (int p = 0; p < P; ++p) {
+                        const int vb = v0 + (int)(S * p / P) * ddk::kTcStage;
+                        const int ve = std::min(hi[g0 + j], v0 + (int)(S * (p + 1) / P) * ddk::kTcStage);
+                        const int row = tabs[6 * ng + j] + (deg4 ? tp2[j] : 0) + p;
+                        for (int64_t t = 0; t < tp.n_tiles; ++t) titems.push_back({vb, ve, (int)t, row, roff[j], 0});
+                    }
                 }
-            }
-            std::stable_sort(titems.begin(), titems.end(), [](const ddk::TcItem &a, const ddk::TcItem &b) {
-                return a.v_end - a.v_begin > b.v_end - b.v_begin;
-            });
+                std::stable_sort(titems.begin() + first, titems.end(), [](const ddk::TcItem &a, const ddk::TcItem &b) {
+                    return a.v_end - a.v_begin > b.v_end - b.v_begin;
+                });
+            };
+            add_items(zeros, tp.K2, tp2, false);
+            n_t2 = titems.size();
+            add_items(tp.K2, tp.K, tp4, true);
         }
         std::stable_sort(blocks.begin(), blocks.end(),
                          [](const std::pair<int64_t, int2> &a, const std::pair<int64_t, int2> &b) { return a.first > b.first; });
@@ -642,6 +688,41 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
             DD_CUDA_TRY(side_stream(&side));
             DD_CUDA_TRY(cudaEventRecord(side->fork, stream));
         }
+        // the contraction on the side stream (after the CUDA-core tile kernel is submitted,
+        // so that the latter's CTAs are placed first and the contraction's fill what they leave)
+        auto launch_tc = [&]() -> cudaError_t {
+            if constexpr (kMixed) {
+                if (side) {
+                    cudaError_t e = cudaStreamWaitEvent(side->s, side->fork, 0);
+                    if (e != cudaSuccess) return e;
+                    // DD_FAULT=field_tc_wait (tests): no MMA is issued, so the completion waits
+                    // run out and the kernel reports it (dd_field_check)
+                    const int withhold = dd::fault_injected("field_tc_wait") ? 1 : 0;
+                    // persistent CTAs: as many as are resident at once, at most one per item
+                    auto launch = [&](auto deg, const ddk::TcItem *items, size_t n_items, int64_t resident,
+                                      const char *name) -> cudaError_t {
+                        constexpr int kDeg = decltype(deg)::value;
+                        if (n_items == 0) return cudaSuccess;
+                        cudaError_t e2 = prepare_tc_kernel<kDeg>();
+                        if (e2 != cudaSuccess) return e2;
+                        const unsigned n_cta = (unsigned)std::min<int64_t>((int64_t)n_items, resident);
+                        DD_PROFILED(name, side->s,
+                                    (ddk::field_grid_tc_kernel<kDeg><<<n_cta, ddk::kTcThreads, ddk::TcConst<kDeg>::kSmemBytes, side->s>>>(
+                                        grid.W, grid.H, tp.n_tile_cols, d_rec, items, (int)n_items, d_tpart, pstride, srcF,
+                                        PF, withhold)));
+                        return cudaGetLastError();
+                    };
+                    if ((e = launch(std::integral_constant<int, 2>(), d_titems, n_t2, tc_slots2, "field_grid_tc")) != cudaSuccess)
+                        return e;
+                    if ((e = launch(std::integral_constant<int, 4>(), d_titems + n_t2, titems.size() - n_t2, tc_slots4,
+                                    "field_grid_tc4")) != cudaSuccess)
+                        return e;
+                    if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return e;
+                }
+            }
+            return cudaSuccess;
+        };
+        if (kTcBeforeCore) DD_CUDA_TRY(launch_tc());
         if (!it.empty()) {
             if (grid_tiles) DD_CUDA_TRY((prefer_shared<Cfg, true>()));
             else DD_CUDA_TRY(prefer_shared<Cfg>());
@@ -666,28 +747,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                 DD_CUDA_TRY(cudaGetLastError());
             }
         }
-        // the contraction on the side stream, submitted after the CUDA-core tile kernel so
-        // that the latter's CTAs are placed first and the contraction's fill what they leave
-        if constexpr (kMixed) {
-            if (side) {
-                DD_CUDA_TRY(prepare_tc_kernel());
-                DD_CUDA_TRY(cudaStreamWaitEvent(side->s, side->fork, 0));
-                // DD_FAULT=field_tc_wait (tests): no MMA is issued, so the completion waits
-                // run out and the kernel reports it (dd_field_check)
-                const int withhold = dd::fault_injected("field_tc_wait") ? 1 : 0;
-                // persistent CTAs: as many as are resident at once, at most one per item
-                const int64_t resident = tc_resident_ctas();
-                const unsigned n_cta = (unsigned)std::min<int64_t>((int64_t)titems.size(),
-                                                                   resident > 0 ? resident : 2 * 148);
-                DD_PROFILED("field_grid_tc", side->s,
-                            (ddk::field_grid_tc_kernel<<<n_cta, ddk::kTcThreads, ddk::kTcSmemBytes, side->s>>>(
-                                grid.W, grid.H, tp.n_tile_cols, d_rec, d_titems, (int)titems.size(), d_tpart, pstride,
-                                srcF, PF, withhold)));
-                DD_CUDA_TRY(cudaGetLastError());
-                DD_CUDA_TRY(cudaEventRecord(side->join, side->s));
-                DD_CUDA_TRY(cudaStreamWaitEvent(stream, side->join, 0));
-            }
-        }
+        if (!kTcBeforeCore) DD_CUDA_TRY(launch_tc());
+        if (side) DD_CUDA_TRY(cudaStreamWaitEvent(stream, side->join, 0));
         dim3 rg((unsigned)((n_pts + 1023) / 1024), (unsigned)ng);
         DD_PROFILED("field_reduce", stream,
                     (ddk::reduce_kernel<Part><<<rg, 256, 0, stream>>>(
@@ -779,7 +840,7 @@ extern "C" dd_status dd_field_check(void) {
 
 extern "C" dd_status dd_field_grid_split(const dd_scan *scan, double x0_m, double y0_m, double dx_m, double dy_m,
                                          int64_t n_cols, int64_t n_rows, const double *times_s, int64_t n_t,
-                                         int64_t *prefix) {
+                                         int64_t *prefix, int64_t *prefix_deg2) {
     dd::clear_error();
     if (!scan) return dd::fail(DD_EINVAL, "dd_field_grid_split: NULL scan");
     if (n_cols < 0 || n_rows < 0 || n_t < 0) return dd::fail(DD_EINVAL, "dd_field_grid_split: negative size");
@@ -787,7 +848,7 @@ extern "C" dd_status dd_field_grid_split(const dd_scan *scan, double x0_m, doubl
         return dd::fail(DD_EINVAL, "dd_field_grid_split: grid origin and spacing must be finite");
     if (n_t == 0) return DD_OK;
     if (!times_s || !prefix) return dd::fail(DD_EINVAL, "dd_field_grid_split: NULL buffer");
-    if (dd::is_device_pointer(times_s) || dd::is_device_pointer(prefix))
+    if (dd::is_device_pointer(times_s) || dd::is_device_pointer(prefix) || (prefix_deg2 && dd::is_device_pointer(prefix_deg2)))
         return dd::fail(DD_EINVAL, "dd_field_grid_split: times and prefix are host arrays");
     std::vector<double> times(times_s, times_s + n_t);
     for (double t : times)
@@ -799,6 +860,9 @@ extern "C" dd_status dd_field_grid_split(const dd_scan *scan, double x0_m, doubl
     ddk::GridDesc g;
     g.x0 = x0_m; g.y0 = y0_m; g.dx = dx_m; g.dy = dy_m; g.W = n_cols; g.H = n_rows;
     const TcPlan tp = n_cols > 0 && n_rows > 0 ? plan_tc(scan, g, tdim, nact) : TcPlan();
-    for (int k = 0; k < (int)n_t; ++k) prefix[order[k]] = tp.on ? tp.K[k] : 0;
+    for (int k = 0; k < (int)n_t; ++k) {
+        prefix[order[k]] = tp.on ? tp.K[k] : 0;
+        if (prefix_deg2) prefix_deg2[order[k]] = tp.on ? tp.K2[k] : 0;
+    }
     return DD_OK;
 }

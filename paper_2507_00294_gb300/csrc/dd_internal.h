@@ -30,7 +30,7 @@ struct dd_scan {
 
     double s = 0, kappa = 0, pref = 0;   // dimensionless Ds, D, and Q0/(4 pi D) [u/m^2]
     std::vector<double> X, Y, T, TAU;    // dimensionless, visit order
-    double x_lo = 0, x_hi = 0, y_lo = 0, y_hi = 0, tau_max = 0;   // their ranges (X, Y) and max (TAU)
+    double x_lo = 0, x_hi = 0, y_lo = 0, y_hi = 0, tau_min = 0, tau_max = 0;   // their ranges
 
     // per device: 4n doubles X | Y | T | TAU, then n float4 (x_hi, x_lo, y_hi, y_lo),
     // uploaded stream-ordered on `home`; `ready` marks the end of the upload for calls on

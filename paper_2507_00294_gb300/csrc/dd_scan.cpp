@@ -453,7 +453,9 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
             const auto yr = std::minmax_element(s->Y.begin(), s->Y.end());
             s->x_lo = *xr.first; s->x_hi = *xr.second;
             s->y_lo = *yr.first; s->y_hi = *yr.second;
-            s->tau_max = *std::max_element(s->TAU.begin(), s->TAU.end());
+            const auto tr = std::minmax_element(s->TAU.begin(), s->TAU.end());
+            s->tau_min = *tr.first;
+            s->tau_max = *tr.second;
         }
     } catch (const std::bad_alloc &) {
         delete s;

@@ -1,9 +1,9 @@
-"""dd_field_grid_split (host-only): the prefix of visits that dd_field_on_grid sums on the
+"""dd_field_grid_split (host-only): the prefixes of visits that dd_field_on_grid sums on the
 tensor cores in FP32-mixed precision.  The contraction relies on every such visit's pair
-term being on the degree-2 exponent series at every grid point (h = rho^2 dq <= 0.04, the
-series classes' limit); these tests evaluate h in FP64 from the oracle's visit list and
-check that, that the prefix is as long as the library's stated bound allows, and the
-simple properties of a prefix."""
+term being on the degree-2 exponent series (h = rho^2 dq <= 0.04) at every grid point, or
+on the degree-4 series (h <= 0.33) for the band after the degree-2 prefix; these tests
+evaluate h in FP64 from the oracle's visit list and check that, that each prefix is as long
+as the library's stated bound allows, and the simple properties of a prefix."""
 import numpy as np
 import pytest
 
@@ -11,7 +11,8 @@ from paper_2507_00294_gb300 import binding as b
 from paper_2507_00294_gb300 import workloads as w
 from parity_util import oracle_problem
 
-L2H = 0.04
+L2H, L4H = 0.04, 0.33
+MIN_DQ = 1e-8            # per pitch^2: the degree-4 coefficients stay in the FP32 normal range
 
 
 def grid_corners(g):
@@ -36,7 +37,8 @@ def visit_geometry(spec, t_dwell):
 
 def check_split(spec, g, times):
     scan = b.Scan(spec)
-    K = b.dd_field_grid_split(scan, *g, times)
+    K, K2 = b.dd_field_grid_split(scan, *g, times, degree2=True)
+    assert np.all(K2 <= K)
     gx, gy = grid_corners(g)
     src, _, _, _ = visit_geometry(spec, 0.0)
     # the largest squared distance between the grid's box and the visits' box
@@ -49,17 +51,21 @@ def check_split(spec, g, times):
         src, started, over, dq = visit_geometry(spec, t)
         n_started = int(started.sum())
         assert 0 <= K[k] <= n_started
-        if K[k] > 0:
-            i = np.arange(K[k])
-            assert np.all(over[i]), "a visit still under the beam in the prefix"
-            # each visit's own farthest grid corner: on the degree-2 series at every point
-            r2 = np.maximum.reduce([(cx - src.xs[i]) ** 2 + (cy - src.ys[i]) ** 2 for cx in gx for cy in gy])
-            assert np.all(r2 * dq[i] <= L2H), "a prefix visit off the degree-2 series"
-        if K[k] < n_started and K[k] > 0:
-            # the first visit after the prefix fails the stated bound (prefix is maximal)
-            j = K[k]
-            w1 = 2 * Ds + 4 * D * (t - src.ts[j])
-            assert (w1 <= c) or (c / ((w1 - c) * w1)) * R2 > L2H * (1 - 1e-3)
+        for n_pre, limit, what in ((K2[k], L2H, "degree-2"), (K[k], L4H, "degree-4")):
+            if n_pre > 0:
+                i = np.arange(n_pre)
+                assert np.all(over[i]), "a visit still under the beam in the prefix"
+                # each visit's own farthest grid corner: on the series at every point
+                r2 = np.maximum.reduce([(cx - src.xs[i]) ** 2 + (cy - src.ys[i]) ** 2 for cx in gx for cy in gy])
+                assert np.all(r2 * dq[i] <= limit), "a prefix visit off the %s series" % what
+            if 0 < n_pre < n_started and (limit == L2H or K[k] > K2[k]):
+                # the first visit after the prefix fails the stated bound (prefix is maximal)
+                j = n_pre
+                w1 = 2 * Ds + 4 * D * (t - src.ts[j])
+                assert (w1 <= c) or (c / ((w1 - c) * w1)) * R2 > limit * (1 - 1e-3)
+        if K[k] > K2[k]:
+            band = np.arange(K2[k], K[k])
+            assert np.all(dq[band] * spec.pitch_m ** 2 >= MIN_DQ)
     return K
 
 

@@ -1,6 +1,6 @@
-"""The tensor-core part of the FP32-mixed grid field (the older visits' degree-2 pair terms
-as a BF16-split matrix product, dd_field_tc.cuh): taken where it applies, and the field
-it gives against the oracle and against the FP64 path."""
+"""The tensor-core part of the FP32-mixed grid field (the older visits' degree-2 and degree-4
+pair terms as BF16-split matrix products, dd_field_tc.cuh): taken where it applies, and the
+field it gives against the oracle and against the FP64 path."""
 import numpy as np
 import pytest
 
@@ -94,8 +94,10 @@ def test_bench_grid_snapshot_groups_and_repeat(cuda):
     p = job.scan.pitch_m
     g = (0.0, 0.0, p / 2, p / 2, 128, 128)
     gm, _ = check_against_oracle_and_fp64(job.scan, g, job.times, 4096, 2, "bench grid")
-    again, _ = on_grid(job.scan, g, job.times, "mixed")
+    again, launched = on_grid(job.scan, g, job.times, "mixed", profile=True)
     np.testing.assert_array_equal(again, gm)
+    # both forms ran: degree 2 (the oldest visits) and degree 4 (the band after them)
+    assert "field_grid_tc" in launched and "field_grid_tc4" in launched
 
 
 def test_grid256_raster_sixteen_tiles(cuda):
