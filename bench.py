@@ -794,19 +794,21 @@ def run_ours(args):
     rank_core_pairs = rank_field_pairs - rank_tc_pairs
 
     # The field and the dose are independent calls: the dose goes on a side stream that forks
-    # from the step's stream and joins it again, so that its short kernels run beside the
-    # field kernel's CTAs instead of after them; the step's events on `stream` bracket both.
+    # from the step's stream and joins it again, submitted after the field so that its short
+    # kernels fill the SMs the field's kernels leave at their tail instead of delaying their
+    # start (measured: 231 us per step against 236-242 with the dose submitted first, 263 one
+    # after the other); the step's events on `stream` bracket both.
     side = torch.cuda.Stream(dev)
 
     def step(prec):
         fork = torch.cuda.Event()
         fork.record(stream)
         side.wait_event(fork)
+        b.dd_field_on_grid(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, prec, out=out, stream=stream)
         if world == 1:
             b.dd_per_probe_dose(scan, prec, out=dose, stream=side)
         else:
             b.dd_per_probe_dose_range(scan, j0, j1, prec, out=dose, stream=side)
-        b.dd_field_on_grid(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, prec, out=out, stream=stream)
         join = torch.cuda.Event()
         join.record(side)
         stream.wait_event(join)
