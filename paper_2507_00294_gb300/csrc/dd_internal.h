@@ -38,6 +38,7 @@ struct dd_scan {
     struct DevCache {
         int device;
         double *src;
+        size_t cap;                      // bytes of the block (a size class of the block cache)
         cudaStream_t home;
         cudaEvent_t ready;
     };

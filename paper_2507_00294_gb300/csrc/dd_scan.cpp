@@ -189,6 +189,49 @@ cudaError_t defer_release(cudaStream_t stream, void *obj, void (*del)(void *)) {
     return err;
 }
 
+// Device blocks of visit caches: a destroyed scan's block (its device synchronised) is kept
+// per device and power-of-two size class for the next scan, up to 1 GiB per device, since a
+// stream-ordered pool allocation of a fresh block took about 66 us of host time per scan.
+static std::mutex g_vcache_mu;
+static std::vector<void *> g_vcache_free[64][48];
+static size_t g_vcache_kept[64];
+constexpr size_t kVCacheKeep = size_t(1) << 30;
+
+static int vcache_class(size_t bytes) {
+    int k = 12;
+    while (k < 47 && (size_t(1) << k) < bytes) ++k;
+    return k;
+}
+
+static cudaError_t vcache_take(int device, size_t bytes, void **p, size_t *cap) {
+    const int k = vcache_class(bytes);
+    *cap = size_t(1) << k;
+    {
+        std::lock_guard<std::mutex> lock(g_vcache_mu);
+        if (!g_vcache_free[device][k].empty()) {
+            *p = g_vcache_free[device][k].back();
+            g_vcache_free[device][k].pop_back();
+            g_vcache_kept[device] -= *cap;
+            return cudaSuccess;
+        }
+    }
+    return cudaMalloc(p, *cap);
+}
+
+// the caller has synchronised the device: no work may still use the block
+static void vcache_give(int device, void *p, size_t cap) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(g_vcache_mu);
+        if (g_vcache_kept[device] + cap <= kVCacheKeep) {
+            g_vcache_free[device][vcache_class(cap)].push_back(p);
+            g_vcache_kept[device] += cap;
+            return;
+        }
+    }
+    cudaFree(p);
+}
+
 const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status *st) {
     int device = 0;
     cudaError_t err = cudaGetDevice(&device);
@@ -207,11 +250,12 @@ const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status
     // written straight into a pinned staging block (a pageable vector when none is free)
     const size_t bytes = 6 * n * sizeof(double);
     void *d = nullptr;
-    err = workspace_alloc(&d, bytes, stream);
+    size_t cap = 0;
+    err = device < 64 ? vcache_take(device, bytes, &d, &cap) : cudaErrorInvalidDevice;
     if (err != cudaSuccess) { *st = fail_cuda(err, "scan visit cache allocation"); cudaGetLastError(); return nullptr; }
     cudaEvent_t ready = nullptr;
     err = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    if (err != cudaSuccess) { cudaFreeAsync(d, stream); *st = fail_cuda(err, "cudaEventCreate"); return nullptr; }
+    if (err != cudaSuccess) { vcache_give(device, d, cap); *st = fail_cuda(err, "cudaEventCreate"); return nullptr; }
     auto *stage = new CallStaging();
     std::vector<double> pageable;
     double *host = static_cast<double *>(stage->stage(bytes));
@@ -237,13 +281,13 @@ const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status
     if (err != cudaSuccess) {
         cudaStreamSynchronize(stream);
         delete stage;
-        cudaFreeAsync(d, stream);
+        vcache_give(device, d, cap);
         cudaEventDestroy(ready);
         *st = fail_cuda(err, "scan visit cache upload");
         return nullptr;
     }
     defer_release(stream, stage, [](void *p) { delete static_cast<CallStaging *>(p); });
-    scan->dev.push_back({device, static_cast<double *>(d), stream, ready});
+    scan->dev.push_back({device, static_cast<double *>(d), cap, stream, ready});
     return static_cast<double *>(d);
 }
 
@@ -492,7 +536,7 @@ void dd_destroy(dd_scan *scan) {
             // no enqueued call may still use the scan (the caller's contract); the device
             // synchronisation makes that hold regardless, and returns at once when idle
             cudaDeviceSynchronize();
-            cudaFreeAsync(c.src, 0);
+            dd::vcache_give(c.device, c.src, c.cap);
             cudaEventDestroy(c.ready);
         }
     }
