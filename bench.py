@@ -959,17 +959,20 @@ def run_ours(args):
 def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, rr, pr, dr):
     """End to end through the public API with page-locked host outputs: scan build (its
     visit list uploaded on first use), the grid field and the dose, D2H of both.  One GPU:
-    the two calls on two streams, each synchronised once per step (with a stream and
-    page-locked buffers the calls leave their copies enqueued).  Several: each rank evaluates its
-    rows and dose targets, the device results are gathered, and rank 0 copies out the
-    whole field and dose."""
+    two steps in flight -- step k's calls are enqueued (field and dose on their own pair
+    of streams, copies into step k's own page-locked buffers) before step k - 1 is
+    synchronised and its scan destroyed, so the host builds the next step while the GPU
+    runs the previous one.  Several: each rank evaluates its rows and dose targets, the
+    device results are gathered, and rank 0 copies out the whole field and dose."""
     import torch
     x0, y0, gdx, gdy, W, H = job.extra["grid"]
     (r0, r1), (p0, p1), (j0, j1) = rr[rank], pr[rank], dr[rank]
-    out_h = torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True)
-    dose_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    e2e_stream = torch.cuda.Stream(dev)
-    e2e_side = torch.cuda.Stream(dev)
+    n_buf = 2 if world == 1 else 1
+    outs_h = [torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True) for _ in range(n_buf)]
+    doses_h = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(n_buf)]
+    out_h, dose_h = outs_h[0], doses_h[0]
+    streams = [(torch.cuda.Stream(dev), torch.cuda.Stream(dev)) for _ in range(n_buf)]
+    e2e_stream = streams[0][0]
     if world > 1:
         out_d = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
         dose_d = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
@@ -977,14 +980,24 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
+    in_flight = None
     for k in range(args.steps):
         s2 = b.Scan(job.scan)
         if world == 1:
+            i = k % n_buf
+            sf, sd = streams[i]
             # the field first (its kernels start while the host prepares the dose), the
             # dose on a second stream beside it, each leaving its copies enqueued
-            b.dd_field_on_grid(s2, x0, y0, gdx, gdy, W, H, times, "mixed", out=out_h.numpy(), stream=e2e_stream)
-            b.dd_per_probe_dose(s2, "mixed", out=dose_h.numpy(), stream=e2e_side)
-            e2e_side.synchronize()
+            b.dd_field_on_grid(s2, x0, y0, gdx, gdy, W, H, times, "mixed", out=outs_h[i].numpy(), stream=sf)
+            b.dd_per_probe_dose(s2, "mixed", out=doses_h[i].numpy(), stream=sd)
+            if in_flight is not None:
+                # the previous step: its results are in its host buffers once its streams are done
+                prev, (pf, pd) = in_flight
+                pf.synchronize()
+                pd.synchronize()
+                prev.close()
+            in_flight = (s2, (sf, sd))
+            continue
         else:
             with torch.cuda.stream(e2e_stream):
                 b.dd_field_on_grid(s2, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, "mixed", out=out_d,
@@ -997,6 +1010,11 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
                     dose_h.copy_(d, non_blocking=True)
         e2e_stream.synchronize()
         s2.close()
+    if in_flight is not None:
+        last, (pf, pd) = in_flight
+        pf.synchronize()
+        pd.synchronize()
+        last.close()
     e2e_ms = (time.perf_counter() - t0) * 1e3
     v, ms, _ = whole_job(pairs_step, args.steps, e2e_ms, dist, dev)
     # host -> device per step and rank: the scan's visit cache (6 doubles per visit) and the
@@ -1004,7 +1022,8 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
     return {"value": v, "unit": UNIT, "h2d_bytes_per_step": int(world * (6 * n * 8 + len(times) * 8)),
             "d2h_bytes_per_step": int(out_h.numel() * 8 + dose_h.numel() * 8),
             "ms_per_step": ms / args.steps,
-            "api": "dd_create_scan + dd_field_on_grid + dd_per_probe_dose (host outputs)"}
+            "api": "dd_create_scan + dd_field_on_grid + dd_per_probe_dose (host outputs)",
+            "in_flight": n_buf}
 
 
 def bench_point_list(b, job, times, scan, dev, stream, flush, field_pairs, reps=10):

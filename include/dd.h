@@ -267,8 +267,11 @@ dd_status dd_batch_info(const dd_batch *batch, int64_t *n_items, int64_t *pair_t
 void dd_batch_destroy(dd_batch *batch);
 
 /* Free a scan and its per-device caches (device caches are freed on their own
-   devices).  NULL, or a handle that was already destroyed, is a no-op.  The scan must
-   not be in use by an enqueued call.
+   devices).  NULL, or a handle that was already destroyed, is a no-op.  Blocks until the
+   work already enqueued by calls on this scan is done: on each stream that such a call
+   used, up to that call's last launch or copy (other work in flight is not waited for),
+   or the whole device once a batch plan was built on the scan (a plan may run on any
+   stream).  The handle must not be passed to a call made after (or during) dd_destroy.
    Testing hook: with the environment variable DD_FAULT=alloc, the field workspace
    allocation reports cudaErrorMemoryAllocation (the call returns DD_ENOMEM). */
 void dd_destroy(dd_scan *scan);

@@ -364,6 +364,7 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
         dd_status st = DD_OK;
         const double *src = dd::device_sources(s, nullptr, &st);
         if (!src) return st;
+        dd::scan_shared(s);                  // the plan may run on any stream
         ddk::BScan &S = sc[(size_t)k];
         S.src = src;
         S.srcF = dd::device_sources_ff(s, nullptr, &st);

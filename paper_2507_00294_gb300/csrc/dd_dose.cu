@@ -358,6 +358,7 @@ dd_status run_dose(const dd_scan *scan, int64_t j0, int64_t j1, double *out, cud
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
+    const dd::ScanUse use{scan, stream};
     const float4 *srcF = dd::device_sources_ff(scan, stream, &st);
     void *ws = nullptr;
     cudaError_t err = dd::workspace_alloc(&ws, bytes, stream);
@@ -429,6 +430,7 @@ dd_status run_dose_general(const dd_scan *scan, int64_t j0, int64_t j1, double *
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
+    const dd::ScanUse use{scan, stream};
     void *ws = nullptr;
     const size_t bytes = (size_t)m * sizeof(double) * (out_host ? 2 : 1) + 512;
     cudaError_t err = dd::workspace_alloc(&ws, bytes, stream);

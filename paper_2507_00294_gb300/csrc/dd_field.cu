@@ -526,6 +526,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     dd_status st = DD_OK;
     const double *src = dd::device_sources(scan, stream, &st);
     if (!src) return st;
+    const dd::ScanUse use{scan, stream};
     const float4 *srcF = dd::device_sources_ff(scan, stream, &st);
     void *ws = nullptr;
     cudaError_t err = dd::fault_injected("alloc") ? cudaErrorMemoryAllocation

@@ -41,6 +41,15 @@ struct dd_scan {
         size_t cap;                      // bytes of the block (a size class of the block cache)
         cudaStream_t home;
         cudaEvent_t ready;
+        // streams whose enqueued work reads the block, each with an event recorded after
+        // its latest such work; any_stream: the block was handed to work that may run on
+        // any stream (a batch plan), so its release waits for the whole device
+        struct Use {
+            cudaStream_t stream;
+            cudaEvent_t done;
+        };
+        std::vector<Use> uses = {};
+        bool any_stream = false;
     };
     mutable std::mutex mu;
     mutable std::vector<DevCache> dev;
@@ -63,6 +72,19 @@ const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status
 // kernels form coordinate differences without FP64 arithmetic: n float4 stored after the
 // FP64 arrays of the same cache (call after device_sources on the same stream).
 const float4 *device_sources_ff(const dd_scan *scan, cudaStream_t stream, dd_status *st);
+
+// The work enqueued so far on `stream` may read the scan's device block on the current
+// device: dd_destroy waits for it before the block is released.  scan_shared: the block
+// was handed to work that may run on any stream (dd_destroy synchronises the device).
+void note_scan_use(const dd_scan *scan, cudaStream_t stream);
+void scan_shared(const dd_scan *scan);
+// Notes the calling function's use of the scan on `stream` when it goes out of scope,
+// on every return path after the device block was obtained.
+struct ScanUse {
+    const dd_scan *scan;
+    cudaStream_t stream;
+    ~ScanUse() { note_scan_use(scan, stream); }
+};
 
 // True if `p` is device-accessible memory of the current device.
 bool is_device_pointer(const void *p);
@@ -145,6 +167,10 @@ bool fault_injected(const char *site);
 // Registry of live scan handles (guards dd_destroy against double frees).
 void register_scan(dd_scan *s);
 bool unregister_scan(dd_scan *s);
+// A destroyed scan kept for its host storage (NULL if none), and the hand-back of a
+// destroyed scan (kept if small enough and the spares are not full, else deleted).
+dd_scan *reuse_scan();
+void recycle_scan(dd_scan *s);
 
 // Kernel timing scope (dd_profile.cpp): records an event pair around the launch
 // made inside the scope when profiling is enabled, nothing otherwise.

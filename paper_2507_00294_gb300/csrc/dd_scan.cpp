@@ -42,6 +42,39 @@ bool fault_injected(const char *site) {
 static std::mutex g_scans_mu;
 static std::unordered_set<dd_scan *> g_scans;
 
+// Destroyed scans kept for their host storage (a few, of bounded size): the next scan of
+// at most that many visits is built in vectors that keep their capacity, instead of pages
+// the allocator handed back to the system and must fault in and zero again (about half the
+// host time of building a 4,096-visit scan).
+static std::mutex g_spare_mu;
+static std::vector<dd_scan *> g_spare;
+constexpr size_t kSpareScans = 4, kSpareBytes = size_t(16) << 20;
+
+static size_t scan_bytes(const dd_scan *s) {
+    return s->visit.capacity() * sizeof(int32_t) +
+           (s->t_start.capacity() + s->tau.capacity() + s->X.capacity() + s->Y.capacity() + s->T.capacity() +
+            s->TAU.capacity()) * sizeof(double);
+}
+
+dd_scan *reuse_scan() {
+    std::lock_guard<std::mutex> lock(g_spare_mu);
+    if (g_spare.empty()) return nullptr;
+    dd_scan *s = g_spare.back();
+    g_spare.pop_back();
+    return s;
+}
+
+void recycle_scan(dd_scan *s) {
+    if (scan_bytes(s) <= kSpareBytes) {
+        std::lock_guard<std::mutex> lock(g_spare_mu);
+        if (g_spare.size() < kSpareScans) {
+            g_spare.push_back(s);
+            return;
+        }
+    }
+    delete s;
+}
+
 void register_scan(dd_scan *s) {
     std::lock_guard<std::mutex> lock(g_scans_mu);
     g_scans.insert(s);
@@ -291,6 +324,41 @@ const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status
     return static_cast<double *>(d);
 }
 
+constexpr size_t kMaxUseStreams = 8;
+
+void note_scan_use(const dd_scan *scan, cudaStream_t stream) {
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) { cudaGetLastError(); return; }
+    std::lock_guard<std::mutex> lock(scan->mu);
+    for (auto &c : scan->dev) {
+        if (c.device != device) continue;
+        if (c.any_stream) return;
+        for (auto &u : c.uses)
+            if (u.stream == stream) {
+                if (cudaEventRecord(u.done, stream) != cudaSuccess) { cudaGetLastError(); c.any_stream = true; }
+                return;
+            }
+        cudaEvent_t ev = nullptr;
+        if (c.uses.size() >= kMaxUseStreams || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ev, stream) != cudaSuccess) {
+            cudaGetLastError();
+            if (ev) cudaEventDestroy(ev);
+            c.any_stream = true;                 // released after a device synchronisation
+            return;
+        }
+        c.uses.push_back({stream, ev});
+        return;
+    }
+}
+
+void scan_shared(const dd_scan *scan) {
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) { cudaGetLastError(); return; }
+    std::lock_guard<std::mutex> lock(scan->mu);
+    for (auto &c : scan->dev)
+        if (c.device == device) c.any_stream = true;
+}
+
 const float4 *device_sources_ff(const dd_scan *scan, cudaStream_t stream, dd_status *st) {
     const double *d = device_sources(scan, stream, st);
     return d ? reinterpret_cast<const float4 *>(d + 4 * scan->n) : nullptr;
@@ -366,10 +434,12 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         return dd::fail(DD_EINVAL, "dd_create_scan: keep_fraction < 1 cannot be combined with a custom order");
 
     const int64_t nx = d->nx, ny = d->ny, ngrid = nx * ny;
-    dd_scan *s = new (std::nothrow) dd_scan();
+    dd_scan *s = dd::reuse_scan();
+    if (!s) s = new (std::nothrow) dd_scan();
     if (!s) return dd::fail(DD_ENOMEM, "dd_create_scan: out of host memory");
     try {
-        std::vector<int32_t> seq;
+        std::vector<int32_t> &seq = s->visit;            // built in place
+        seq.clear();
         switch (d->order) {
         case DD_RASTER:
             seq.resize((size_t)ngrid);
@@ -437,7 +507,7 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         s->keep_fraction = d->keep_fraction;
         s->blank = d->blank_s; s->blank_per_m = d->blank_s_per_m;
         s->n = n;
-        s->visit = seq;
+        const std::vector<int32_t> &vis = s->visit;
         s->t_start.resize((size_t)n);
         s->tau.resize((size_t)n);
         if (d->dwell_per_visit) {
@@ -462,7 +532,7 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
                 s->t_start[(size_t)k] = t;
                 t = t + s->tau[(size_t)k];
                 if (k + 1 == n) break;
-                const int64_t g0 = seq[(size_t)k], g1 = seq[(size_t)k + 1];
+                const int64_t g0 = vis[(size_t)k], g1 = vis[(size_t)k + 1];
                 const int64_t r0 = g0 / nx, r1 = g1 / nx;
                 if (d->flyback_s != 0.0 && r0 != r1) t = t + d->flyback_s;
                 if (travel) {
@@ -483,23 +553,31 @@ dd_status dd_create_scan(const dd_scan_desc *d, dd_scan **out) {
         // the exact quotient (g < 2^26, so the product is off by less than one), instead of
         // an integer division per visit
         const double inv_nx = 1.0 / (double)nx;
+        int64_t c_lo = nx, c_hi = -1, r_lo = ny, r_hi = -1;     // column and row ranges
         for (int64_t k = 0; k < n; ++k) {
-            const int64_t g = seq[(size_t)k];
+            const int64_t g = vis[(size_t)k];
             int64_t q = (int64_t)((double)g * inv_nx), r = g - q * nx;
             if (r < 0) { --q; r += nx; } else if (r >= nx) { ++q; r -= nx; }
             s->X[(size_t)k] = (double)r;
             s->Y[(size_t)k] = (double)q;
-            s->T[(size_t)k] = s->uniform ? (double)k : s->t_start[(size_t)k] / tref;
-            s->TAU[(size_t)k] = s->uniform ? 1.0 : s->tau[(size_t)k] / tref;
+            c_lo = std::min(c_lo, r); c_hi = std::max(c_hi, r);
+            r_lo = std::min(r_lo, q); r_hi = std::max(r_hi, q);
         }
-        if (n > 0) {
-            const auto xr = std::minmax_element(s->X.begin(), s->X.end());
-            const auto yr = std::minmax_element(s->Y.begin(), s->Y.end());
-            s->x_lo = *xr.first; s->x_hi = *xr.second;
-            s->y_lo = *yr.first; s->y_hi = *yr.second;
-            const auto tr = std::minmax_element(s->TAU.begin(), s->TAU.end());
-            s->tau_min = *tr.first;
-            s->tau_max = *tr.second;
+        s->x_lo = (double)c_lo; s->x_hi = (double)c_hi;
+        s->y_lo = (double)r_lo; s->y_hi = (double)r_hi;
+        if (s->uniform) {
+            for (int64_t k = 0; k < n; ++k) s->T[(size_t)k] = (double)k;
+            std::fill(s->TAU.begin(), s->TAU.end(), 1.0);
+            s->tau_min = s->tau_max = 1.0;
+        } else {
+            double t_lo = s->tau[0] / tref, t_hi = t_lo;
+            for (int64_t k = 0; k < n; ++k) {
+                s->T[(size_t)k] = s->t_start[(size_t)k] / tref;
+                const double tk = s->tau[(size_t)k] / tref;
+                s->TAU[(size_t)k] = tk;
+                t_lo = std::min(t_lo, tk); t_hi = std::max(t_hi, tk);
+            }
+            s->tau_min = t_lo; s->tau_max = t_hi;
         }
     } catch (const std::bad_alloc &) {
         delete s;
@@ -533,16 +611,25 @@ void dd_destroy(dd_scan *scan) {
     cudaGetDevice(&prev);
     for (auto &c : scan->dev) {
         if (cudaSetDevice(c.device) == cudaSuccess) {
-            // no enqueued call may still use the scan (the caller's contract); the device
-            // synchronisation makes that hold regardless, and returns at once when idle
-            cudaDeviceSynchronize();
+            // wait for the work that may read the block: the upload and each stream's
+            // latest use, or the whole device when the block may be read from any stream
+            bool waited = !c.any_stream && cudaEventSynchronize(c.ready) == cudaSuccess;
+            for (auto &u : c.uses) {
+                waited = waited && cudaEventSynchronize(u.done) == cudaSuccess;
+                cudaEventDestroy(u.done);
+            }
+            if (!waited) {
+                cudaGetLastError();
+                cudaDeviceSynchronize();
+            }
             dd::vcache_give(c.device, c.src, c.cap);
             cudaEventDestroy(c.ready);
         }
     }
     if (!scan->dev.empty() && prev >= 0) cudaSetDevice(prev);
     cudaGetLastError();
-    delete scan;
+    scan->dev.clear();
+    dd::recycle_scan(scan);
 }
 
 }  // extern "C"

@@ -212,7 +212,7 @@ def field_scales(specs, device):
     return torch.tensor([4 * math.pi * s.D_m2s / s.Q0 for s in specs], dtype=torch.float64, device=device)
 
 
-def split_scan(spec, k=K_EXACT):
+def split_scan(spec, k=None):
     """The scan's first n - k visits and its last k, as two custom-order scans of the same
     grid positions and dwell: (background spec, its snapshot time, near spec, its
     snapshot time).  The background is seen at the scan's end, n dwells; the near scan's
@@ -220,7 +220,7 @@ def split_scan(spec, k=K_EXACT):
     depends on t - t_i only).  Uniform dwell, no dead time (the surrogate's scans)."""
     g = visit_list(spec)
     n = len(g)
-    k = max(1, min(k, n - 1))
+    k = max(1, min(K_EXACT if k is None else k, n - 1))
     kw = dict(order=w.CUSTOM, keep_fraction=1.0, mask=None)
     bg = spec.with_(custom_visit=np.ascontiguousarray(g[:n - k]), **kw)
     near = spec.with_(custom_visit=np.ascontiguousarray(g[n - k:]), **kw)

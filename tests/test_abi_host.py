@@ -40,6 +40,7 @@ def _compare_with_oracle(spec):
     np.testing.assert_array_equal(g, og)
     np.testing.assert_array_equal(t, ts)      # same FP64 recipe on both sides: bit-exact
     np.testing.assert_array_equal(tau, taus)
+    return s
 
 
 @pytest.mark.parametrize("order,stride", [(w.RASTER, 1), (w.SERPENTINE, 1), (w.INTERLEAVED, 4),
@@ -77,6 +78,23 @@ def test_scan_blanker_travel_matches_oracle():
     s = b.Scan(w.ScanSpec(4, 4, order=w.RANDOM, seed=1, blank_s=1e-7))
     _, t, tau = s.visits()
     assert np.all(np.diff(t) >= tau[:-1] * (1 - 1e-12))    # dead time only adds
+
+
+def test_destroyed_scans_storage_reused():
+    """A destroyed scan's host storage is kept for the next scan: scans of growing and
+    shrinking sizes and of every order, each built right after the previous one was
+    destroyed, still match the oracle's visit lists and times exactly."""
+    rng = np.random.default_rng(4)
+    specs = [w.ScanSpec(40, 40), w.ScanSpec(3, 5, order=w.SERPENTINE), w.ScanSpec(64, 64, order=w.RANDOM, seed=9),
+             w.ScanSpec(7, 7, order=w.INTERLEAVED, interleave_stride=2, keep_fraction=0.5, seed=3),
+             w.ScanSpec(30, 20, order=w.SERPENTINE, flyback_s=2e-7),
+             w.ScanSpec(6, 6, order=w.CUSTOM, custom_visit=np.array([35, 0, 7, 7, 14])),
+             w.ScanSpec(12, 12, order=w.RANDOM, seed=5, dwell_per_visit=10 ** rng.uniform(-7, -5, 144)),
+             w.ScanSpec(50, 50, order=w.RASTER, blank_s=1e-7)]
+    for spec in specs + specs[::-1]:
+        s = _compare_with_oracle(spec)
+        assert len(s) == len(s.visits()[0])
+        s.close()
 
 
 def test_scan_rejects_negative_blanker_time():

@@ -138,6 +138,41 @@ def test_pinned_host_buffers_on_a_stream(cuda):
         scan.close()
 
 
+def test_destroy_waits_for_the_scans_enqueued_work(cuda):
+    """dd_destroy right after enqueuing a field and a dose on two streams (page-locked
+    outputs, nothing synchronised): it blocks until that work is done, so a scan of the
+    same size built next -- whose visit list may go into the released device block -- does
+    not change the first scan's results, which equal a synchronous evaluation bit for bit."""
+    import torch
+    job = w.raster_64_supersampled()
+    p = job.scan.pitch_m
+    g = (0.0, 0.0, p / 2, p / 2, 128, 128)
+    times = np.ascontiguousarray(job.times)
+    n = w.n_visits(job.scan)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    other = job.scan.with_(order=w.RANDOM, seed=3, D_m2s=job.scan.D_m2s * 7)
+    for _ in range(3):
+        out = torch.full((len(times), 128 * 128), -1.0, dtype=torch.float64).pin_memory()
+        dose = torch.full((n,), -1.0, dtype=torch.float64).pin_memory()
+        scan = b.Scan(job.scan)
+        b.dd_field_on_grid(scan, *g, times, "mixed", out=out.numpy(), stream=s1)
+        b.dd_per_probe_dose(scan, "mixed", out=dose.numpy(), stream=s2)
+        scan.close()
+        scan2 = b.Scan(other)
+        junk = b.dd_field_on_grid(scan2, *g, times[-2:], "mixed", device=torch.device("cuda", 0))
+        s1.synchronize()
+        s2.synchronize()
+        torch.cuda.synchronize()
+        scan2.close()
+        ref_scan = b.Scan(job.scan)
+        ref = b.dd_field_on_grid(ref_scan, *g, times, "mixed", device=torch.device("cuda", 0)).cpu().numpy()
+        ref_dose = b.dd_per_probe_dose(ref_scan, "mixed", device=torch.device("cuda", 0)).cpu().numpy()
+        ref_scan.close()
+        np.testing.assert_array_equal(out.numpy(), ref)
+        np.testing.assert_array_equal(dose.numpy(), ref_dose)
+        assert np.isfinite(junk.cpu().numpy()).all()
+
+
 def test_deterministic_repeat(cuda):
     job = w.raster_64_supersampled()
     a = gpu_field(job.scan, job.pts_xy, job.times[-4:], "mixed")
