@@ -415,7 +415,7 @@ dd_status run_dose(const dd_scan *scan, int64_t j0, int64_t j1, double *out, cud
     DD_CUDA_TRY(cudaGetLastError());
     if (out_copy)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, stream));
-    DD_CUDA_TRY(cudaFreeAsync(ws, stream));
+    DD_CUDA_TRY(dd::workspace_release(ws, stream));
     DD_CUDA_TRY(dd::defer_release(stream, keep, [](void *p) { delete static_cast<Keep *>(p); }));
     if (dd::host_sync_needed(stream, {out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
@@ -450,7 +450,7 @@ dd_status run_dose_general(const dd_scan *scan, int64_t j0, int64_t j1, double *
     DD_CUDA_TRY(cudaGetLastError());
     if (out_host)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, stream));
-    DD_CUDA_TRY(cudaFreeAsync(ws, stream));
+    DD_CUDA_TRY(dd::workspace_release(ws, stream));
     if (dd::host_sync_needed(stream, {out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;
 }

@@ -763,7 +763,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
     }
     if (out_copy)
         DD_CUDA_TRY(cudaMemcpyAsync(out, out_dev, (size_t)n_t * n_pts * sizeof(double), cudaMemcpyDeviceToHost, stream));
-    DD_CUDA_TRY(cudaFreeAsync(ws, stream));
+    DD_CUDA_TRY(dd::workspace_release(ws, stream));
     DD_CUDA_TRY(dd::defer_release(stream, keep, HostTables::release));
     if (dd::host_sync_needed(stream, {pts_kind, out_kind})) DD_CUDA_TRY(cudaStreamSynchronize(stream));
     return DD_OK;

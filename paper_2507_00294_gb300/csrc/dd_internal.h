@@ -98,11 +98,15 @@ MemKind memory_kind(const void *p);
 // leaves its copies enqueued (the caller synchronises before reading).
 bool host_sync_needed(cudaStream_t stream, std::initializer_list<MemKind> kinds);
 
-// Stream-ordered workspace of a call, from the library's memory pool on the current
-// device.  The pool keeps up to 4 GiB of freed workspace mapped between calls (the
-// default pool returns it to the driver at every synchronisation, and mapping it again
-// costs more than a small call's kernels).  Returns the CUDA error.
+// Stream-ordered workspace of a call on the current device: a released block of the same
+// size class that is free for `stream` (last used on it, or its work done), else a new
+// block from the library's memory pool (which keeps up to 4 GiB of freed memory mapped:
+// the default pool returns it to the driver at every synchronisation).  Returns the CUDA
+// error.
 cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t stream);
+// Hands a workspace back after the work enqueued on `stream` that uses it (an event
+// recorded there marks when another stream may take it).
+cudaError_t workspace_release(void *p, cudaStream_t stream);
 
 // Pinned host staging for the small tables a call uploads (work lists, snapshot
 // tables).  A copy from pageable memory is staged by the driver and can hold the host

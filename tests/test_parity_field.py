@@ -173,6 +173,39 @@ def test_destroy_waits_for_the_scans_enqueued_work(cuda):
         assert np.isfinite(junk.cpu().numpy()).all()
 
 
+def test_calls_in_flight_on_several_streams(cuda):
+    """Six grid fields and doses of different scans enqueued on three stream pairs with no
+    synchronisation between them (workspaces released by one call and taken by the next on
+    the same stream while its predecessor may still run, or on another stream once done):
+    each result equals its own synchronous evaluation bit for bit."""
+    import torch
+    job = w.raster_64_supersampled()
+    p = job.scan.pitch_m
+    g = (0.0, 0.0, p / 2, p / 2, 128, 128)
+    times = np.ascontiguousarray(job.times[::3])
+    specs = [job.scan.with_(D_m2s=job.scan.D_m2s * f) for f in (1.0, 0.3, 3.0)]
+    specs += [job.scan.with_(order=w.SERPENTINE), job.scan.with_(order=w.RANDOM, seed=11), w.ScanSpec(40, 50)]
+    streams = [(torch.cuda.Stream(), torch.cuda.Stream()) for _ in range(3)]
+    runs = []
+    for k, spec in enumerate(specs):
+        sf, sd = streams[k % 3]
+        scan = b.Scan(spec)
+        out = torch.full((len(times), 128 * 128), -1.0, dtype=torch.float64).pin_memory()
+        dose = torch.full((w.n_visits(spec),), -1.0, dtype=torch.float64).pin_memory()
+        b.dd_field_on_grid(scan, *g, times, "mixed", out=out.numpy(), stream=sf)
+        b.dd_per_probe_dose(scan, "mixed", out=dose.numpy(), stream=sd)
+        runs.append((spec, scan, out, dose))
+    torch.cuda.synchronize()
+    for spec, scan, out, dose in runs:
+        scan.close()
+        ref_scan = b.Scan(spec)
+        ref = b.dd_field_on_grid(ref_scan, *g, times, "mixed", device=torch.device("cuda", 0)).cpu().numpy()
+        ref_dose = b.dd_per_probe_dose(ref_scan, "mixed", device=torch.device("cuda", 0)).cpu().numpy()
+        ref_scan.close()
+        np.testing.assert_array_equal(out.numpy(), ref)
+        np.testing.assert_array_equal(dose.numpy(), ref_dose)
+
+
 def test_deterministic_repeat(cuda):
     job = w.raster_64_supersampled()
     a = gpu_field(job.scan, job.pts_xy, job.times[-4:], "mixed")
