@@ -42,19 +42,19 @@ __host__ __device__ inline int64_t dose_blocks(int64_t t1, int lb) {
     return kDoseSplit + (kmax - lb - 1) / lb + 1;
 }
 
+// FP64 dose: PPT = Cfg::kDosePPT targets per thread (strided by the block size), lags
+// outermost, one pair term per (target, lag) at the pair's own series class.
 template <typename Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads)
 dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, int64_t n,
             const typename Cfg::Rec *__restrict__ lagrec, const int2 *__restrict__ items, int lb,
-            typename Cfg::Real *__restrict__ partial, const float4 *__restrict__ srcF) {
+            typename Cfg::Real *__restrict__ partial) {
     using Rec = typename Cfg::Rec;
     using Real = typename Cfg::Real;
+    static_assert(std::is_same<Real, double>::value, "the FP32 dose runs dose_kernel_f32");
     constexpr int NT = Cfg::kThreads, PPT = Cfg::kDosePPT, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
     constexpr int RV = sizeof(Rec) / 16;
-    constexpr bool kF32 = std::is_same<Real, float>::value;
-    static_assert(!kF32 || PPT % 2 == 0, "the FP32 path takes targets in pairs");
-    __shared__ Real s_x[kF32 ? 1 : TILE + LBMAX], s_y[kF32 ? 1 : TILE + LBMAX];   // FP64 path
-    __shared__ float2 s_xy[kF32 ? TILE + LBMAX : 1];                               // FP32 path
+    __shared__ Real s_x[TILE + LBMAX], s_y[TILE + LBMAX];
     __shared__ __align__(16) Rec s_rec[Cfg::kDoseSTILE];
 
     const int2 item = items[blockIdx.x];
@@ -68,18 +68,12 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     // sources needed: i = j - k for j in [t0, t1), k in [k0, k1): i in [t0 - k1 + 1, t1 - k0)
     const int64_t w0 = t0 - k1 + 1;
     const int64_t w1 = t1 - k0;
-    // coordinates relative to the tile's first target: FP32 from the float-float copy on
-    // the FP32 path (no FP64 arithmetic), FP64 otherwise
+    // coordinates relative to the tile's first target
     const double cx = srcX[t0], cy = srcY[t0];
-    const float4 org = kF32 ? srcF[t0] : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = w0 + tid; i < w1; i += NT) {
         const int64_t ic = i < 0 ? 0 : i;                  // i < 0 never used
-        if constexpr (kF32) {
-            s_xy[i - w0] = ff_diff(srcF[ic], org);
-        } else {
-            s_x[i - w0] = (Real)(srcX[ic] - cx);
-            s_y[i - w0] = (Real)(srcY[ic] - cy);
-        }
+        s_x[i - w0] = (Real)(srcX[ic] - cx);
+        s_y[i - w0] = (Real)(srcY[ic] - cy);
     }
     Real px[PPT], py[PPT];
     int64_t jt[PPT];
@@ -87,27 +81,13 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
     for (int q = 0; q < PPT; ++q) {
         jt[q] = t0 + q * NT + tid;
         const int64_t jj = jt[q] < n ? jt[q] : t0;
-        if constexpr (kF32) {
-            const float2 d = ff_diff(srcF[jj], org);
-            px[q] = d.x;
-            py[q] = d.y;
-        } else {
-            px[q] = (Real)(srcX[jj] - cx);
-            py[q] = (Real)(srcY[jj] - cy);
-        }
+        px[q] = (Real)(srcX[jj] - cx);
+        py[q] = (Real)(srcY[jj] - cy);
     }
-    // FP32 (or FP64) sums of up to kFlush lags, added into a compensated running sum
-    // (BlockSum: no FP64 arithmetic on the FP32 path)
     Real acc[PPT];
-    float2 acc2[PPT / 2 > 0 ? PPT / 2 : 1];               // FP32 path: targets (2m, 2m+1)
     BlockSum<Real> tot[PPT];
 #pragma unroll
     for (int q = 0; q < PPT; ++q) acc[q] = 0;
-#pragma unroll
-    for (int m = 0; m < (PPT / 2 > 0 ? PPT / 2 : 1); ++m) acc2[m] = make_float2(0.f, 0.f);
-    // every (target, lag) pair of this item exists: the whole tile lies in [0, n) and its
-    // first target is beyond the block's largest lag
-    const bool full = t0 + TILE <= n && (int64_t)k1 - 1 <= t0;
 
     for (int kk = k0; kk < k1; kk += Cfg::kDoseSTILE) {
         const int cnt = min(Cfg::kDoseSTILE, k1 - kk);
@@ -121,94 +101,188 @@ dose_kernel(const double *__restrict__ srcX, const double *__restrict__ srcY, in
         for (int c = 0; c < cnt; ++c) {
             const int k = kk + c;
             const Rec &R = s_rec[c];
-            if constexpr (std::is_same<Real, float>::value) {
-                // FP32: one exponent-series degree for the whole warp, from the largest h
-                // and the smallest a over its lanes (the same classes as the field kernel)
-                float r2[PPT];
-                bool ok[PPT];
-                bool lo = true;                 // every valid pair of this lane fits degree 2
-                const float dqR = R.dq();
 #pragma unroll
-                for (int m = 0; m < PPT / 2; ++m) {
-                    // targets (2m, 2m+1) of this thread on f32x2: their sources are the visits
-                    // k before them
-                    const int64_t i0 = jt[2 * m] - k, i1 = jt[2 * m + 1] - k;
-                    ok[2 * m] = full || (i0 >= 0 && jt[2 * m] < n);
-                    ok[2 * m + 1] = full || (i1 >= 0 && jt[2 * m + 1] < n);
-                    const float2 sa = ok[2 * m] ? s_xy[i0 - w0] : make_float2(px[2 * m], py[2 * m]);
-                    const float2 sb = ok[2 * m + 1] ? s_xy[i1 - w0] : make_float2(px[2 * m + 1], py[2 * m + 1]);
-                    const float2 dx = __fadd2_rn(make_float2(px[2 * m], px[2 * m + 1]), make_float2(-sa.x, -sb.x));
-                    const float2 dy = __fadd2_rn(make_float2(py[2 * m], py[2 * m + 1]), make_float2(-sa.y, -sb.y));
-                    const float2 q2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-                    r2[2 * m] = q2.x;
-                    r2[2 * m + 1] = q2.y;
-                    lo = lo && (fmaxf(q2.x, q2.y) * dqR <= kL2H);
+            for (int q = 0; q < PPT; ++q) {
+                const int64_t i = jt[q] - k;
+                if (i >= 0 && jt[q] < n) {
+                    const Real dx = px[q] - s_x[i - w0], dy = py[q] - s_y[i - w0];
+                    acc[q] += pair_term(dx * dx + dy * dy, R);
                 }
-                uint32_t cls = kCodeD2;
-                // the common case is settled by one vote; otherwise classify every pair
-                if (!__all_sync(0xffffffffu, lo && dqR >= kMinDqX)) {
-                    cls = kCodeSkip;
+            }
+            if (Cfg::kFlush < Cfg::kDoseSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
 #pragma unroll
-                    for (int q = 0; q < PPT; ++q) {
-                        const uint32_t cq = !ok[q] ? kCodeSkip : series_class(r2[q] * dqR, r2[q] * R.q1(), dqR);
-                        cls = max(cls, cq);
-                    }
-                    cls = __reduce_max_sync(0xffffffffu, cls);
-                }
-                if (cls == kCodeSkip) continue;
-                if (cls == kCodeD2) {
-                    // degree 2 on f32x2 over target pairs; a pair that does not exist gets the
-                    // exponent -inf (term 0)
-                    const float4 v0 = R.v0;                // (g_0, g_1x, g_2x, g_3x)
-                    const float2 g2 = make_float2(v0.z, v0.z), g1 = make_float2(v0.y, v0.y);
-#pragma unroll
-                    for (int m = 0; m < PPT / 2; ++m) {
-                        const float2 r = make_float2(r2[2 * m], r2[2 * m + 1]);
-                        const float2 g0 = make_float2(ok[2 * m] ? v0.x : -INFINITY, ok[2 * m + 1] ? v0.x : -INFINITY);
-                        const float2 g = __ffma2_rn(__ffma2_rn(g2, r, g1), r, g0);
-                        acc2[m] = __fadd2_rn(acc2[m], make_float2(ex2_approx(g.x), ex2_approx(g.y)));
-                    }
-                    continue;
-                }
-#pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    float t;
-                    if (cls == kCodeD4) t = log_term<4>(r2[q], R);
-                    else if (cls == kCodeD8) t = log_term<8>(r2[q], R);
-                    else if (cls == kCodeD12) t = log_term<12>(r2[q], R);
-                    else t = pair_term(r2[q], R);
-                    if (ok[q]) { if (q & 1) acc2[q >> 1].y += t; else acc2[q >> 1].x += t; }
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    const int64_t i = jt[q] - k;
-                    if (i >= 0 && jt[q] < n) {
-                        const Real dx = px[q] - s_x[i - w0], dy = py[q] - s_y[i - w0];
-                        acc[q] += pair_term(dx * dx + dy * dy, R);
-                    }
-                }
-                if (Cfg::kFlush < Cfg::kDoseSTILE && (c % Cfg::kFlush) == Cfg::kFlush - 1) {
-#pragma unroll
-                    for (int q = 0; q < PPT; ++q) { tot[q].add(acc[q]); acc[q] = 0; }
-                }
+                for (int q = 0; q < PPT; ++q) { tot[q].add(acc[q]); acc[q] = 0; }
             }
         }
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-            if constexpr (std::is_same<Real, float>::value) {
-                tot[q].add((q & 1) ? acc2[q >> 1].y : acc2[q >> 1].x);
-            } else {
-                tot[q].add(acc[q]);
-            }
+            tot[q].add(acc[q]);
             acc[q] = 0;
         }
-#pragma unroll
-        for (int m = 0; m < (PPT / 2 > 0 ? PPT / 2 : 1); ++m) acc2[m] = make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int q = 0; q < PPT; ++q)
         if (jt[q] < n) partial[(int64_t)item.y * n + jt[q]] = tot[q].result();
+}
+
+// The lags [kk, kk + cnt) of one staged round of the FP32 dose for this thread's PPT targets
+// (target pairs (2m, 2m + 1) on f32x2).  rel[q]: the target's index in the coordinate
+// window, whose entry rel[q] - k is the source of lag k (always inside the window).
+// kFull: every (target, lag) pair of the item exists; otherwise pair q exists when bit q
+// of live is set (target < n) and rel[q] - k >= lo_idx (source index >= 0).  One exponent-series
+// degree per warp and lag, from the largest h and the smallest a over its lanes (the
+// classes of the field kernel); degree 2, the common case, settled by one vote.
+template <int PPT, bool kFull>
+__device__ __forceinline__ void dose_lags_f32(const RecF32 *s_rec, int cnt, int kk, const float2 *s_xy,
+                                              const float (&px)[PPT], const float (&py)[PPT], const int (&rel)[PPT],
+                                              uint32_t live, int lo_idx, float2 (&acc2)[PPT / 2]) {
+    static_assert(PPT <= 32, "pair flags in one word");
+    for (int c = 0; c < cnt; ++c) {
+        const int k = kk + c;
+        const RecF32 &R = s_rec[c];
+        const float dqR = R.dq();
+        float r2[PPT];
+        // bit q: pair q exists (flags in a word rather than PPT predicates)
+        uint32_t ok = kFull ? (1u << PPT) - 1u : 0u;
+        float rmax = 0.0f;
+#pragma unroll
+        for (int m = 0; m < PPT / 2; ++m) {
+            const int ia = rel[2 * m] - k, ib = rel[2 * m + 1] - k;
+            if (!kFull) {
+                ok |= (((live >> (2 * m)) & 1u) && ia >= lo_idx ? 1u : 0u) << (2 * m);
+                ok |= (((live >> (2 * m + 1)) & 1u) && ib >= lo_idx ? 1u : 0u) << (2 * m + 1);
+            }
+            // a pair that does not exist takes its own target as the source (rho^2 = 0)
+            const float2 sa = ((ok >> (2 * m)) & 1u) ? s_xy[ia] : make_float2(px[2 * m], py[2 * m]);
+            const float2 sb = ((ok >> (2 * m + 1)) & 1u) ? s_xy[ib] : make_float2(px[2 * m + 1], py[2 * m + 1]);
+            const float2 dx = __fadd2_rn(make_float2(px[2 * m], px[2 * m + 1]), make_float2(-sa.x, -sb.x));
+            const float2 dy = __fadd2_rn(make_float2(py[2 * m], py[2 * m + 1]), make_float2(-sa.y, -sb.y));
+            const float2 q2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            r2[2 * m] = q2.x;
+            r2[2 * m + 1] = q2.y;
+            rmax = fmaxf(rmax, fmaxf(q2.x, q2.y));
+        }
+        // use: the pairs whose terms are added.  When the whole warp is on degree 2 (one
+        // vote: every pair's h, culled or not, is in that series' range) every existing
+        // pair; else the class is the largest of the pairs' own classes, and a pair whose
+        // own a is 87 or more (its term below 2e-38) is left out: its h can lie far beyond
+        // the range of the warp's series, whose polynomial would then overflow.
+        uint32_t use = ok;
+        uint32_t cls = kCodeD2;
+        if (!__all_sync(0xffffffffu, rmax * dqR <= kL2H && dqR >= kMinDqX)) {
+            cls = kCodeSkip;
+            use = 0u;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                const uint32_t cq = !((ok >> q) & 1u) ? kCodeSkip : series_class(r2[q] * dqR, r2[q] * R.q1(), dqR);
+                use |= (cq != kCodeSkip ? 1u : 0u) << q;
+                cls = max(cls, cq);
+            }
+            cls = __reduce_max_sync(0xffffffffu, cls);
+        }
+        if (cls == kCodeSkip) continue;
+        if (cls == kCodeD2) {
+            // degree 2 on f32x2 over target pairs; a pair left out gets the exponent -inf
+            // (term 0)
+            const float4 v0 = R.v0;                        // (g_0, g_1x, g_2x, g_3x)
+            const float2 g2 = make_float2(v0.z, v0.z), g1 = make_float2(v0.y, v0.y);
+#pragma unroll
+            for (int m = 0; m < PPT / 2; ++m) {
+                const float2 r = make_float2(r2[2 * m], r2[2 * m + 1]);
+                const float2 g0 = make_float2(((use >> (2 * m)) & 1u) ? v0.x : -INFINITY,
+                                              ((use >> (2 * m + 1)) & 1u) ? v0.x : -INFINITY);
+                const float2 g = __ffma2_rn(__ffma2_rn(g2, r, g1), r, g0);
+                acc2[m] = __fadd2_rn(acc2[m], make_float2(ex2_approx(g.x), ex2_approx(g.y)));
+            }
+            continue;
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            float t;
+            if (cls == kCodeD4) t = log_term<4>(r2[q], R);
+            else if (cls == kCodeD8) t = log_term<8>(r2[q], R);
+            else if (cls == kCodeD12) t = log_term<12>(r2[q], R);
+            else t = pair_term(r2[q], R);
+            if ((use >> q) & 1u) { if (q & 1) acc2[q >> 1].y += t; else acc2[q >> 1].x += t; }
+        }
+    }
+}
+
+// FP32 dose: PPT targets per thread (strided by the block size: a warp's lanes hold
+// consecutive targets), lags outermost, so all lanes of a warp read one lag record (a
+// shared-memory broadcast) while each lane's source is its own.  More targets per thread
+// share each lag's record, vote and loop over more pairs (the large scans take 4); the
+// coordinates are FP32 differences from the float-float copy (no FP64 arithmetic).
+template <typename Cfg, int PPT>
+__global__ void __launch_bounds__(Cfg::kThreads)
+dose_kernel_f32(int64_t n, const RecF32 *__restrict__ lagrec, const int2 *__restrict__ items, int lb,
+                float *__restrict__ partial, const float4 *__restrict__ srcF) {
+    static_assert(std::is_same<typename Cfg::Real, float>::value, "FP32 records and sums");
+    static_assert(PPT % 2 == 0, "the FP32 path takes targets in pairs");
+    constexpr int NT = Cfg::kThreads, TILE = NT * PPT, LBMAX = Cfg::kDoseLB;
+    constexpr int RV = sizeof(RecF32) / 16;
+    __shared__ float2 s_xy[TILE + LBMAX];
+    __shared__ __align__(16) RecF32 s_rec[Cfg::kDoseSTILE];
+
+    const int2 item = items[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int64_t t0 = (int64_t)item.x * TILE;             // first target of the tile
+    const int64_t t1 = min((int64_t)n, t0 + TILE);
+    int64_t kb0, kb1;
+    dose_block_lags(item.y, lb, kb0, kb1);
+    const int k0 = (int)kb0;                               // lags [k0, k1)
+    const int k1 = (int)min(kb1, t1);                      // lag < target index <= t1 - 1
+    // sources needed: i = j - k for j in [t0, t1), k in [k0, k1): the window
+    // [t0 - k1 + 1, t1 - k0), at most TILE + lb - 1 visits
+    const int64_t w0 = t0 - k1 + 1;
+    const int64_t w1 = t1 - k0;
+    const float4 org = srcF[t0];
+    for (int64_t i = w0 + tid; i < w1; i += NT) {
+        const int64_t ic = i < 0 ? 0 : i;                  // i < 0 never used
+        s_xy[i - w0] = ff_diff(srcF[ic], org);
+    }
+    float px[PPT], py[PPT];
+    int rel[PPT];
+    uint32_t live = 0;                                     // bit q: target q < n
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int64_t jt = t0 + q * NT + tid;
+        live |= (jt < n ? 1u : 0u) << q;
+        const float2 d = ff_diff(srcF[jt < n ? jt : t0], org);
+        px[q] = d.x;
+        py[q] = d.y;
+        rel[q] = (int)(jt - w0);
+    }
+    // source index i = w0 + (rel - k) >= 0
+    const int lo_idx = (int)(w0 < 0 ? -w0 : 0);
+    // every (target, lag) pair of this item exists: the whole tile lies in [0, n) and its
+    // first target is beyond the block's largest lag
+    const bool full = t0 + TILE <= n && (int64_t)k1 - 1 <= t0;
+    // FP32 sums of one staged round of lags, added into a compensated running sum
+    float2 acc2[PPT / 2];
+    BlockSum<float> tot[PPT];
+#pragma unroll
+    for (int m = 0; m < PPT / 2; ++m) acc2[m] = make_float2(0.f, 0.f);
+
+    for (int kk = k0; kk < k1; kk += Cfg::kDoseSTILE) {
+        const int cnt = min(Cfg::kDoseSTILE, k1 - kk);
+        __syncthreads();
+        {
+            const float4 *row = reinterpret_cast<const float4 *>(lagrec + kk);
+            float4 *dst = reinterpret_cast<float4 *>(&s_rec[0]);
+            for (int v = tid; v < cnt * RV; v += NT) dst[v] = row[v];
+        }
+        __syncthreads();
+        if (full) dose_lags_f32<PPT, true>(s_rec, cnt, kk, s_xy, px, py, rel, live, lo_idx, acc2);
+        else dose_lags_f32<PPT, false>(s_rec, cnt, kk, s_xy, px, py, rel, live, lo_idx, acc2);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) tot[q].add((q & 1) ? acc2[q >> 1].y : acc2[q >> 1].x);
+#pragma unroll
+        for (int m = 0; m < PPT / 2; ++m) acc2[m] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q)
+        if ((live >> q) & 1u) partial[(int64_t)item.y * n + t0 + q * NT + tid] = tot[q].result();
 }
 
 // Dose for arbitrary visit timing (per-visit dwells, flyback): the pair (i, j) has its
@@ -294,29 +368,61 @@ dose_reduce_kernel(const Part *__restrict__ partial, int64_t n, int64_t j0, int6
 
 namespace {
 
-// Lag block of the dose work items: the largest power-of-two fraction of kDoseLB, down to
-// kDoseLBMin lags, that still gives at least 8 items per SM (the triangle of a few
-// thousand visits is otherwise cut into too few CTAs to fill the GPU).
-template <typename Cfg>
-int dose_lag_block(int64_t n, int64_t tile_lo, int64_t tile_hi) {
-    constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
+int device_sms() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
         cudaGetLastError();
         sms = 1;
     }
+    return sms;
+}
+
+// Work items (target tile, lag block) of the tiles [tile_lo, tile_hi) of `tile` targets.
+int64_t dose_items(int64_t n, int64_t tile_lo, int64_t tile_hi, int tile, int lb) {
+    int64_t items = 0;
+    for (int64_t t = tile_lo; t < tile_hi; ++t) items += ddk::dose_blocks(std::min(n, t * tile + tile), lb);
+    return items;
+}
+
+// Lag block of the dose work items: the largest power-of-two fraction of kDoseLB, down to
+// kDoseLBMin lags, that still gives at least 8 items per SM (the triangle of a few
+// thousand visits is otherwise cut into too few CTAs to fill the GPU).
+template <typename Cfg>
+int dose_lag_block(int64_t n, int64_t j0, int64_t j1, int tile) {
+    const int64_t want = 8 * (int64_t)device_sms();
+    const int64_t tile_lo = j0 / tile, tile_hi = (j1 + tile - 1) / tile;
     int lb = Cfg::kDoseLB;
-    while (lb > Cfg::kDoseLBMin) {
-        int64_t items = 0;
-        for (int64_t t = tile_lo; t < tile_hi; ++t) {
-            const int64_t t1 = std::min(n, t * TILE + TILE);
-            items += ddk::dose_blocks(t1, lb);
-        }
-        if (items >= 8 * (int64_t)sms) break;
-        lb /= 2;
-    }
+    while (lb > Cfg::kDoseLBMin && dose_items(n, tile_lo, tile_hi, tile, lb) < want) lb /= 2;
     return lb;
+}
+
+// Targets per thread of the FP32 dose: kDoseWidePPT when the wide tiles still give at least
+// 8 items per SM at the largest lag block (large scans), else Cfg::kDosePPT.
+constexpr int kDoseWidePPT = 4;
+template <typename Cfg>
+int dose_ppt(int64_t n, int64_t j0, int64_t j1) {
+    if (!std::is_same<typename Cfg::Real, float>::value) return Cfg::kDosePPT;
+    const int tile = Cfg::kThreads * kDoseWidePPT;
+    return dose_items(n, j0 / tile, (j1 + tile - 1) / tile, tile, Cfg::kDoseLB) >= 8 * (int64_t)device_sms()
+               ? kDoseWidePPT : Cfg::kDosePPT;
+}
+
+// One launch of the dose kernel over `count` items: the FP32 kernel at `ppt` targets per
+// thread, or the FP64 kernel.
+template <typename Cfg>
+cudaError_t launch_dose(unsigned count, int ppt, cudaStream_t stream, const double *srcX, const double *srcY,
+                        int64_t n, const typename Cfg::Rec *rec, const int2 *items, int lb,
+                        typename Cfg::Real *part, const float4 *srcF) {
+    if constexpr (std::is_same<typename Cfg::Real, float>::value) {
+        if (ppt == kDoseWidePPT)
+            ddk::dose_kernel_f32<Cfg, kDoseWidePPT><<<count, Cfg::kThreads, 0, stream>>>(n, rec, items, lb, part, srcF);
+        else
+            ddk::dose_kernel_f32<Cfg, Cfg::kDosePPT><<<count, Cfg::kThreads, 0, stream>>>(n, rec, items, lb, part, srcF);
+    } else {
+        ddk::dose_kernel<Cfg><<<count, Cfg::kThreads, 0, stream>>>(srcX, srcY, n, rec, items, lb, part);
+    }
+    return cudaGetLastError();
 }
 
 // Valid (target j, lag k) pairs of a dose work item: targets [t0, t1), lags [k0, k1) with
@@ -338,14 +444,11 @@ dd_status run_dose(const dd_scan *scan, int64_t j0, int64_t j1, double *out, cud
     const dd::MemKind out_kind = dd::memory_kind(out);
     const bool out_host = out_kind != dd::MemKind::Device;
     const bool out_copy = out_host;
-    constexpr int TILE = Cfg::kThreads * Cfg::kDosePPT;
+    const int ppt = dose_ppt<Cfg>(n, j0, j1);
+    const int TILE = Cfg::kThreads * ppt;
     const int64_t tile_lo = j0 / TILE, tile_hi = (j1 + TILE - 1) / TILE;
-    const int lb = dose_lag_block<Cfg>(n, tile_lo, tile_hi);
-    int64_t n_items = 0;
-    for (int64_t t = tile_lo; t < tile_hi; ++t) {
-        const int64_t t1 = std::min(n, t * TILE + TILE);
-        n_items += ddk::dose_blocks(t1, lb);                          // lags 1 .. t1-1
-    }
+    const int lb = dose_lag_block<Cfg>(n, j0, j1, TILE);
+    const int64_t n_items = dose_items(n, tile_lo, tile_hi, TILE, lb);   // lags 1 .. t1-1 per tile
     const int64_t nblk = ddk::dose_blocks(std::min(n, tile_hi * TILE), lb);
     size_t bytes = 0;
     auto add = [&](size_t b) { bytes = ((bytes + 255) & ~size_t(255)) + b; };
@@ -406,9 +509,8 @@ dd_status run_dose(const dd_scan *scan, int64_t j0, int64_t j1, double *out, cud
         for (size_t k = 0; k < its.size(); ++k) keep->items[k] = its[k].second;
         DD_CUDA_TRY(keep->staging.upload(d_items, keep->items.data(), keep->items.size() * sizeof(int2), stream));
         DD_PROFILED(Cfg::kDoseName, stream,
-                    (ddk::dose_kernel<Cfg><<<(unsigned)keep->items.size(), Cfg::kThreads, 0, stream>>>(
-                        src, src + n, n, d_rec, d_items, lb, d_part, srcF)));
-        DD_CUDA_TRY(cudaGetLastError());
+                    DD_CUDA_TRY(launch_dose<Cfg>((unsigned)keep->items.size(), ppt, stream, src, src + n, n, d_rec,
+                                                 d_items, lb, d_part, srcF)));
     }
     DD_PROFILED("dose_reduce", stream,
                 (ddk::dose_reduce_kernel<Part><<<(unsigned)((m + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, j0, j1, TILE, lb, scan->pref, out_dev)));
@@ -605,8 +707,8 @@ dd_status run_dose_noalloc(const dd_scan *scan, double *out, cudaStream_t stream
         ddk::lag_coef_kernel<Rec><<<(unsigned)((n + 31) / 32), 32, 0, stream>>>(n, scan->s, scan->kappa, d_rec);
         DD_CUDA_TRY(cudaGetLastError());
         DD_CUDA_TRY(cudaMemcpyAsync(d_items, flat, (size_t)count * sizeof(int2), cudaMemcpyHostToDevice, stream));
-        ddk::dose_kernel<Cfg><<<(unsigned)count, Cfg::kThreads, 0, stream>>>(d_x, d_y, n, d_rec, d_items, lb, d_part, d_f);
-        DD_CUDA_TRY(cudaGetLastError());
+        DD_CUDA_TRY(launch_dose<Cfg>((unsigned)count, Cfg::kDosePPT, stream, d_x, d_y, n, d_rec, d_items, lb, d_part,
+                                     d_f));
     }
     ddk::dose_reduce_kernel<Part><<<(unsigned)((n + 31) / 32), 32 * ddk::kDoseReduceSplit, 0, stream>>>(d_part, n, 0, n, TILE, lb, scan->pref, out);
     DD_CUDA_TRY(cudaGetLastError());

@@ -252,7 +252,33 @@ def test_grid256_precision_study_sampled(cuda, order, d_index):
     dmx = b.dd_per_probe_dose(scan, "mixed", device=cuda).cpu().numpy()
     assert dmx[0] == 0.0
     assert_mixed(dmx[targets], dref, dref.max(), "dose256 %s mixed" % w.ORDER_NAMES[order])
+    # every target against the FP64 path (itself checked against the oracle above)
+    assert_mixed(dmx, d64, d64.max(), "dose256 %s mixed vs fp64, every target" % w.ORDER_NAMES[order])
     scan.close()
+
+
+@pytest.mark.parametrize("order", [w.RASTER, w.INTERLEAVED, w.SERPENTINE, w.RANDOM])
+def test_grid256_dose_slowest_diffusion_every_target(cuda, order):
+    """The 256x256 dose at the slowest seeded D (D tau / pitch^2 = 7.2e-3), the four orders:
+    every target's FP32-mixed dose within the mixed tolerance of the FP64 path, and seeded
+    targets of both against the oracle.  In random order a warp's targets sit at very
+    different distances from their sources at one lag, so culled pairs (a >= 87) with h far
+    beyond the warp's series range meet that series here."""
+    from parity_util import oracle_dose, oracle_problem
+    spec = w.precision_study(order, 0).scan
+    problem = oracle_problem(spec)
+    n = problem[0].n
+    rng = np.random.default_rng(40 + order)
+    targets = np.unique(np.concatenate([[1, 2, 255, 256, n - 1], rng.choice(np.arange(1, n), 400, replace=False)]))
+    dref = oracle_dose(spec, targets, problem)
+    scan = b.Scan(spec)
+    d64 = b.dd_per_probe_dose(scan, "fp64", device=cuda).cpu().numpy()
+    dmx = b.dd_per_probe_dose(scan, "mixed", device=cuda).cpu().numpy()
+    scan.close()
+    assert np.isfinite(dmx).all() and np.isfinite(d64).all()
+    assert_fp64(d64[targets], dref, "slow dose %s fp64" % w.ORDER_NAMES[order])
+    assert_mixed(dmx[targets], dref, dref.max(), "slow dose %s mixed" % w.ORDER_NAMES[order])
+    assert_mixed(dmx, d64, d64.max(), "slow dose %s mixed vs fp64, every target" % w.ORDER_NAMES[order])
 
 
 def test_allocation_failure_is_reported_and_recoverable(cuda, monkeypatch):
