@@ -202,22 +202,42 @@ def kernel_source_sha(kernel):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
+def recorded_profile(kernel):
+    """The "- key: value" lines of the committed ncu summary, if taken on this source."""
     path = os.path.join(ROOT, "profiles", PROFILED[kernel][0])
     if not os.path.exists(path):
-        return None
+        return {}
     vals = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
     if vals.get("kernel") != kernel or vals.get("source_sha") != kernel_source_sha(kernel):
-        return None
+        return {}
+    return vals
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this source."""
     try:
-        return int(vals["dram_bytes_per_launch"])
+        return int(recorded_profile(kernel)["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def recorded_pipes(kernel):
+    """Pipe and issue utilisation of the committed ncu capture (fractions), if taken on this
+    source: what the kernel keeps busy, beside the algorithmic fraction of the roofline."""
+    vals = recorded_profile(kernel)
+    keys = {"fma_pipe_pct": "fma_pipe", "xu_pipe_pct": "xu_pipe", "issue_active_pct": "issue_active"}
+    try:
+        out = {name: float(vals[k]) / 100.0 for k, name in keys.items()}
+        out["thread_instructions_per_pair"] = float(vals["thread_instructions_per_pair"])
+    except (KeyError, ValueError):
+        return None
+    out["note"] = ("ncu --set full capture of one launch on this source (profiles/%s): pipe busy "
+                   "fractions and issue-slot use per SM sub-partition" % PROFILED[kernel][0])
+    return out
 
 
 # BF16 tensor-core peak: the measured cuBLAS burst figure, else the recipe's fallback
@@ -868,6 +888,7 @@ def run_ours(args):
                 "culled_note": "pair-terms with a >= 87 (below the FP32 normal range) are counted in the "
                                "pair-terms but skipped per warp; their share of this kernel's pairs",
                 "other_pipe": {"pipe": "fp32" if bind is mufu else "mufu", **other},
+                "ncu_capture": recorded_pipes("field_grid_mixed"),
                 "tensor_core": [tensor_core_line(prof, "field_grid_tc", rank_tc2_pairs, 14),
                                 tensor_core_line(prof, "field_grid_tc4", rank_tc_pairs - rank_tc2_pairs, 24)]}
     launches = int(sum(v[0] for v in prof.values()))
