@@ -175,7 +175,9 @@ cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t stream) {
         auto &fl = g_ws_free[device];
         for (size_t i = 0; i < fl.size(); ++i) {
             if (fl[i].cap != cap) continue;
-            if (fl[i].last != stream) {
+            // another stream, or the per-thread default stream (one handle for a different
+            // stream on each host thread): only once the block's last use has completed
+            if (fl[i].last != stream || stream == cudaStreamPerThread) {
                 const cudaError_t q = cudaEventQuery(fl[i].ev);
                 if (q != cudaSuccess) {
                     cudaGetLastError();             // unfinished work is not an error
@@ -432,6 +434,12 @@ void note_scan_use(const dd_scan *scan, cudaStream_t stream) {
     for (auto &c : scan->dev) {
         if (c.device != device) continue;
         if (c.any_stream) return;
+        if (stream == cudaStreamPerThread) {
+            // one handle for a different stream on each host thread: the release waits for
+            // the whole device instead
+            c.any_stream = true;
+            return;
+        }
         for (auto &u : c.uses)
             if (u.stream == stream) {
                 if (cudaEventRecord(u.done, stream) != cudaSuccess) { cudaGetLastError(); c.any_stream = true; }
