@@ -372,14 +372,17 @@ BATCH_FLOPS = np.array([0.25, 2.75, 5.125, 2.0 + 8.0 + 1.0, 2.0 + 17.0 + 1.0, 2.
 BATCH_MUFU = np.array([0.0, 0.125, 0.125, 1.0, 1.0, 1.0, 4.0])
 
 
-def batch_ops_per_pair(jobs, samples=200_000, seed=7):
+def batch_ops_per_pair(jobs, samples=200_000, seed=7, prefix=None):
     """Algorithmic FP32 flops and ex2 per pair-term of the batch grid kernel on the 512-scan
     workload (each pair at the cheapest class its own h allows, degree 2 with the cross term
-    where 2 g_2x dx^2 dy^2 exceeds 2.5e-7), pairs sampled in proportion to each scan's."""
+    where 2 g_2x dx^2 dy^2 exceeds 2.5e-7), pairs sampled in proportion to each scan's.
+    prefix[k]: visits of scan k that the tensor-core contraction takes (the pairs sampled
+    are then the CUDA-core tile kernel's own)."""
     from paper_2507_00294_gb300 import binding as b
     from paper_2507_00294_gb300 import workloads as w
     rng = np.random.default_rng(seed)
-    pairs = np.array([w.n_visits(j.scan) * len(j.pts_xy) for j in jobs], dtype=np.float64)
+    k0 = np.zeros(len(jobs), np.int64) if prefix is None else np.asarray(prefix, np.int64)
+    pairs = np.array([(w.n_visits(j.scan) - k0[k]) * len(j.pts_xy) for k, j in enumerate(jobs)], dtype=np.float64)
     ks = rng.choice(len(jobs), samples, p=pairs / pairs.sum())
     code = np.empty(samples, dtype=np.int64)
     for k in np.unique(ks):
@@ -390,7 +393,7 @@ def batch_ops_per_pair(jobs, samples=200_000, seed=7):
         g = sc.visits()[0].astype(np.int64)
         sc.close()
         nv = len(g)
-        i = rng.integers(0, nv, len(sel))
+        i = rng.integers(k0[k], nv, len(sel))
         ip = rng.integers(0, len(j.pts_xy), len(sel))
         dx = j.pts_xy[ip, 0] / s.pitch_m - g[i] % s.nx
         dy = j.pts_xy[ip, 1] / s.pitch_m - g[i] // s.nx
@@ -569,19 +572,44 @@ def bench_batched(dev, stream, runs=10, rank=0, world=1, dist=None, grid=True):
     plan.close()
     roof = None
     if grid and world == 1:
-        fpp, mpp = batch_ops_per_pair(jobs_all)
-        rate = total_pairs / (ms_total / runs / 1e3)
+        # the plan's split: the tensor-core contraction takes each scan's prefix on the
+        # degree-2 (and then degree-4) series at every point of its grid (grids of at least
+        # 64 x 64 points), the CUDA-core tile kernel the rest
+        k2, k4 = [], []
+        for j in jobs_all:
+            sc = b.Scan(j.scan)
+            K, K2 = b.dd_field_grid_split(sc, 0.0, 0.0, j.scan.pitch_m, j.scan.pitch_m, j.scan.nx, j.scan.ny,
+                                          j.times[:1], degree2=True)
+            sc.close()
+            k2.append(int(K2[0]))
+            k4.append(int(K[0]))
+        npts = np.array([len(j.pts_xy) for j in jobs_all], dtype=np.float64)
+        tc2 = float(np.sum(np.array(k2) * npts))
+        tc4 = float(np.sum((np.array(k4) - np.array(k2)) * npts))
+        core = total_pairs - tc2 - tc4
+        fpp, mpp = batch_ops_per_pair(jobs_all, prefix=k4)
+        t_run = ms_total / runs / 1e3
+        rate = core / t_run
+        bf16, bf16_note = bf16_peak_tflops()
         roof = {"bound": "alu", "kernel": "batch_grid_mixed_32x32", "pipe": "fp32", "achieved": fpp * rate / 1e12,
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fpp * rate / 1e12 / FP32_PEAK_TFLOPS,
-                "ops_per_pair": round(fpp, 3), "mufu_per_pair": round(mpp, 4),
+                "pairs_per_run": core, "ops_per_pair": round(fpp, 3), "mufu_per_pair": round(mpp, 4),
                 "mufu_frac": mpp * rate / 1e12 / MUFU_PEAK_TOPS,
-                "note": "event time of the whole graph (coefficients, kernel, reduce) per run"}
+                "note": "the CUDA-core tile kernel's own pairs over the event time of the whole graph "
+                        "(coefficients, contraction, tile kernel, reduce, one after another): a lower bound "
+                        "of that kernel's rate",
+                "tensor_core": {"pairs_per_run": tc2 + tc4, "degree2_pairs": tc2, "degree4_pairs": tc4,
+                                "flops_per_run": 14 * tc2 + 24 * tc4,
+                                "achieved": (14 * tc2 + 24 * tc4) / t_run / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                                "frac": (14 * tc2 + 24 * tc4) / t_run / 1e12 / bf16, "peak_note": bf16_note,
+                                "note": "over the whole graph's event time: a lower bound"}}
     return {"value": value, "unit": UNIT, "ms_per_run": ms_total / runs, "runs": runs, "roofline": roof,
             "pairs_per_run": total_pairs, "rank_pairs_per_run": info["pairs"], "scans": len(jobs_all),
             "rank_scans": len(jobs), "work_items": info["items"], "tuned_variant": variant,
             "workload": "512 scans, n ~ U{32..128}, D log-U[1e-15,1e-12], "
             "dwell log-U[1e-7,1e-5] s, sigma U[0.05,0.2] nm, keep U[0.1,1], random order, final field on the n x n grid",
-            "points": "each scan's probe grid, dd_batch_create_grid (32 x 32 grid tiles)" if grid
+            "points": "each scan's probe grid, dd_batch_create_grid (older visits of grids >= 64 x 64 on "
+                      "the tensor cores, the rest in 32 x 32 grid tiles)" if grid
                       else "each scan's probe grid as a point list (512-point tiles)",
             "launch": "persistent kernel, atomic work claim, CUDA graph replay" +
                       (", scans split over %d GPUs longest-first, one gather per run" % world if world > 1 else "")}

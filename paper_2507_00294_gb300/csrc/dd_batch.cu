@@ -30,6 +30,7 @@
 #include "dd_coef.cuh"
 #include "dd_e1.cuh"
 #include "dd_field_impl.cuh"
+#include "dd_field_tc.cuh"
 #include "dd_internal.h"
 
 namespace ddk {
@@ -47,6 +48,11 @@ struct BScan {
     // W = 0 for an explicit point list
     double gx0, gy0, gdx, gdy;
     int64_t gW, gH, n_tc;
+    // grid plans in FP32-mixed: visits [0, k_tc) are summed by the tensor-core contraction
+    // into nq_tc FP32 rows of t_stride points at t_off (dd_field_tc.cuh); the CUDA-core tile
+    // kernel takes visits [k_tc, nact), in the blocks [blk0, nblk)
+    int k_tc, nq_tc, blk0;
+    int64_t t_off, t_stride;
 };
 
 __device__ __forceinline__ int find_segment(const int64_t *__restrict__ offs, int n, int64_t g) {
@@ -155,21 +161,24 @@ batch_grid_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items, 
         if (it >= n_items) break;
         const int4 item = items[it];
         const BScan &S = sc[item.x];
-        const int s_begin = item.z * sb;
-        const int s_end = min(s_begin + sb, S.nact);
+        const int s_begin = max(item.z * sb, S.k_tc);
+        const int s_end = min(item.z * sb + sb, S.nact);
         field_tile_bgrid(sm, S.srcF, F + S.pt_off, S.gW, S.gH, item.y % S.n_tc, item.y / S.n_tc,
                          rec + S.rec_off, s_begin, s_end, partial + S.part_off + (int64_t)item.z * S.n_pts);
     }
 }
 
 __global__ void batch_reduce_kernel(const BScan *__restrict__ sc, const int64_t *__restrict__ pt_offs, int n_scans,
-                                    int64_t total, const double *__restrict__ partial, double *__restrict__ out) {
+                                    int64_t total, const double *__restrict__ partial, const float *__restrict__ tpart,
+                                    double *__restrict__ out) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
     const BScan &S = sc[find_segment(pt_offs, n_scans, g)];
     const int64_t p = g - S.pt_off;
     double acc = 0.0;
-    for (int b = 0; b < S.nblk; ++b) acc += partial[S.part_off + (int64_t)b * S.n_pts + p];
+    // the tensor-core rows first, then the CUDA-core blocks from the first one past k_tc
+    for (int q = 0; q < S.nq_tc; ++q) acc += (double)tpart[S.t_off + (int64_t)q * S.t_stride + p];
+    for (int b = S.blk0; b < S.nblk; ++b) acc += partial[S.part_off + (int64_t)b * S.n_pts + p];
     out[g] = S.pref * acc;
 }
 
@@ -205,6 +214,12 @@ struct dd_batch {
     double *d_X = nullptr, *d_Y = nullptr, *d_part = nullptr;
     float4 *d_F = nullptr;
     void *d_rec = nullptr;
+    // tensor-core contraction of grid plans: scan table, work items (degree 2, then
+    // degree 4), their CTA counts and FP32 partial rows
+    ddk::TcScan *d_tcs = nullptr;
+    ddk::TcItem *d_titems = nullptr;
+    int n_t2 = 0, n_t4 = 0, cta_t2 = 0, cta_t4 = 0;
+    float *d_tpart = nullptr;
     double *d_pts = nullptr, *d_out = nullptr;   // staging for host buffers
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -259,6 +274,12 @@ dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cuda
             ddk::batch_coef_kernel<ddk::RecF64><<<nb, 128, 0, st>>>(b->d_sc, b->d_rec_offs, b->n_scans, b->total_rec,
                                                                   (ddk::RecF64 *)b->d_rec);
     }
+    if (b->n_t2 + b->n_t4 > 0) {
+        // the older visits of the larger grids on the tensor cores
+        DD_CUDA_TRY(dd::launch_field_tc(2, b->d_tcs, (const ddk::RecF32 *)b->d_rec, b->d_titems, b->n_t2, b->cta_t2, st));
+        DD_CUDA_TRY(dd::launch_field_tc(4, b->d_tcs, (const ddk::RecF32 *)b->d_rec, b->d_titems + b->n_t2, b->n_t4,
+                                        b->cta_t4, st));
+    }
     if (b->n_items > 0 && b->grid_tiles) {
         ddk::batch_grid_kernel<<<b->grid[0], ddk::kBgThreads, 0, st>>>(b->d_sc, b->d_items, b->n_items, b->d_counter,
                                                                       b->d_F, (const ddk::RecF32 *)b->d_rec, b->sb,
@@ -276,7 +297,8 @@ dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cuda
             else launch_field<ddk::CfgF64>(b, g, st);
         }
     }
-    ddk::batch_reduce_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, b->total_pts, b->d_part, out);
+    ddk::batch_reduce_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, b->total_pts, b->d_part,
+                                                     b->d_tpart, out);
     DD_CUDA_TRY(cudaGetLastError());
     return DD_OK;
 }
@@ -358,6 +380,11 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
     std::vector<ddk::BScan> sc((size_t)n_scans);
     std::vector<int64_t> pt_offs((size_t)n_scans), rec_offs((size_t)n_scans);
     std::vector<std::pair<int64_t, int4>> items;
+    // tensor-core work items (FP32-mixed grid plans): degree 2 and degree 4, each at most
+    // kTcMaxItemStages stages long (the FP32 accumulation's error budget), times the tiles
+    std::vector<std::pair<int64_t, ddk::TcItem>> titems2, titems4;
+    std::vector<ddk::TcScan> tcs((size_t)n_scans, ddk::TcScan{});
+    int64_t tpart_total = 0;
     int64_t rec = 0, part = 0;
     for (int k = 0; k < n_scans; ++k) {
         const dd_scan *s = scans[k];
@@ -386,6 +413,35 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
             S.gW = grid_wh[2 * k]; S.gH = grid_wh[2 * k + 1];
             S.n_tc = (S.gW + ddk::kBgCols - 1) / ddk::kBgCols;
         }
+        S.k_tc = S.nq_tc = 0;
+        S.t_off = S.t_stride = 0;
+        if (b->grid_tiles && S.nact > 0) {
+            int K2 = 0, K = 0;
+            dd::tc_prefixes(s, S.gx0, S.gy0, S.gdx, S.gdy, S.gW, S.gH, S.tdim, S.nact, &K2, &K);
+            if (K > 0) {
+                const int64_t n_tcols = (S.gW + ddk::kTcTile - 1) / ddk::kTcTile;
+                const int n_ttiles = (int)(n_tcols * ((S.gH + ddk::kTcTile - 1) / ddk::kTcTile));
+                constexpr int kPiece = ddk::kTcMaxItemStages * ddk::kTcStage;
+                int row = 0;
+                auto pieces = [&](int lo, int hi, std::vector<std::pair<int64_t, ddk::TcItem>> &list) {
+                    for (int vb = lo; vb < hi; vb += kPiece, ++row) {
+                        const int ve = std::min(hi, vb + kPiece);
+                        for (int t = 0; t < n_ttiles; ++t)
+                            list.push_back({(int64_t)(ve - vb), ddk::TcItem{vb, ve, t, row, S.rec_off, k, 0}});
+                    }
+                };
+                pieces(0, K2, titems2);
+                pieces(K2, K, titems4);
+                S.k_tc = K;
+                S.nq_tc = row;
+                S.t_stride = (S.n_pts + 3) / 4 * 4;             // 16-byte aligned rows
+                S.t_off = tpart_total;
+                tpart_total += (int64_t)row * S.t_stride;
+                // the points and partial rows are filled in once the plan's buffers exist
+                tcs[(size_t)k] = ddk::TcScan{S.gW, S.gH, n_tcols, S.srcF, nullptr, nullptr, S.t_stride};
+            }
+        }
+        S.blk0 = S.k_tc >= S.nact ? S.nblk : S.k_tc / b->sb;
         pt_offs[(size_t)k] = S.pt_off;
         rec_offs[(size_t)k] = rec;
         rec += S.nact;
@@ -393,8 +449,9 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
         // grid tiles of 32 x 32 points (items cost by their valid points), else point tiles
         const int64_t n_tr = b->grid_tiles ? (S.gH + ddk::kBgRows - 1) / ddk::kBgRows : 0;
         const int64_t tiles = S.n_pts == 0 ? 0 : b->grid_tiles ? S.n_tc * n_tr : (S.n_pts + tile - 1) / tile;
-        for (int blk = 0; blk < S.nblk; ++blk) {
-            const int64_t nsrc = std::min<int64_t>(S.nact, (int64_t)(blk + 1) * b->sb) - (int64_t)blk * b->sb;
+        for (int blk = S.blk0; blk < S.nblk; ++blk) {
+            const int64_t nsrc = std::min<int64_t>(S.nact, (int64_t)(blk + 1) * b->sb) -
+                                 std::max<int64_t>((int64_t)blk * b->sb, S.k_tc);
             for (int64_t t = 0; t < tiles; ++t) {
                 int64_t npt;
                 if (b->grid_tiles) {
@@ -410,6 +467,13 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
     }
     std::stable_sort(items.begin(), items.end(),
                      [](const std::pair<int64_t, int4> &x, const std::pair<int64_t, int4> &y) { return x.first > y.first; });
+    auto longest_first = [](const std::pair<int64_t, ddk::TcItem> &x, const std::pair<int64_t, ddk::TcItem> &y) {
+        return x.first > y.first;
+    };
+    std::stable_sort(titems2.begin(), titems2.end(), longest_first);
+    std::stable_sort(titems4.begin(), titems4.end(), longest_first);
+    b->n_t2 = (int)titems2.size();
+    b->n_t4 = (int)titems4.size();
     b->total_pts = pt_offsets[n_scans];
     b->total_rec = rec;
     b->total_part = part;
@@ -426,6 +490,9 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
     const size_t o_f = add((size_t)std::max<int64_t>(1, b->total_pts) * sizeof(float4));
     const size_t o_rec = add((size_t)std::max<int64_t>(1, rec) * rec_size);
     const size_t o_part = add((size_t)std::max<int64_t>(1, part) * sizeof(double));
+    const size_t o_tcs = add(tcs.size() * sizeof(ddk::TcScan));
+    const size_t o_ti = add((size_t)std::max(1, b->n_t2 + b->n_t4) * sizeof(ddk::TcItem));
+    const size_t o_tp = add((size_t)std::max<int64_t>(4, tpart_total) * sizeof(float));
     cudaError_t err = cudaMalloc(&b->ws, bytes);
     if (err != cudaSuccess) {
         cudaGetLastError();
@@ -442,6 +509,25 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
     b->d_F = (float4 *)(base + o_f);
     b->d_rec = base + o_rec;
     b->d_part = (double *)(base + o_part);
+    b->d_tcs = (ddk::TcScan *)(base + o_tcs);
+    b->d_titems = (ddk::TcItem *)(base + o_ti);
+    b->d_tpart = (float *)(base + o_tp);
+    if (b->n_t2 + b->n_t4 > 0) {
+        for (int k = 0; k < n_scans; ++k) {
+            if (sc[(size_t)k].nq_tc == 0) continue;
+            tcs[(size_t)k].ptsF = b->d_F + sc[(size_t)k].pt_off;
+            tcs[(size_t)k].partial = b->d_tpart + sc[(size_t)k].t_off;
+        }
+        std::vector<ddk::TcItem> ti;
+        ti.reserve(titems2.size() + titems4.size());
+        for (auto &x : titems2) ti.push_back(x.second);
+        for (auto &x : titems4) ti.push_back(x.second);
+        DD_CUDA_TRY(cudaMemcpy(b->d_tcs, tcs.data(), tcs.size() * sizeof(ddk::TcScan), cudaMemcpyHostToDevice));
+        DD_CUDA_TRY(cudaMemcpy(b->d_titems, ti.data(), ti.size() * sizeof(ddk::TcItem), cudaMemcpyHostToDevice));
+        DD_CUDA_TRY(dd::prepare_field_tc());
+        b->cta_t2 = (int)std::min<int64_t>(b->n_t2, std::max<int64_t>(1, dd::field_tc_resident(2)));
+        b->cta_t4 = (int)std::min<int64_t>(b->n_t4, std::max<int64_t>(1, dd::field_tc_resident(4)));
+    }
     std::vector<int4> it(items.size());
     for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
     DD_CUDA_TRY(cudaMemcpy(b->d_sc, sc.data(), sc.size() * sizeof(ddk::BScan), cudaMemcpyHostToDevice));

@@ -644,7 +644,7 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                         const int vb = v0 + (int)(S * p / P) * ddk::kTcStage;
                         const int ve = std::min(hi[g0 + j], v0 + (int)(S * (p + 1) / P) * ddk::kTcStage);
                         const int row = tabs[6 * ng + j] + (deg4 ? tp2[j] : 0) + p;
-                        for (int64_t t = 0; t < tp.n_tiles; ++t) titems.push_back({vb, ve, (int)t, row, roff[j], 0});
+                        for (int64_t t = 0; t < tp.n_tiles; ++t) titems.push_back({vb, ve, (int)t, row, roff[j], 0, 0});
                     }
                 }
                 std::stable_sort(titems.begin() + first, titems.end(), [](const ddk::TcItem &a, const ddk::TcItem &b) {
@@ -709,8 +709,8 @@ dd_status run_field(const dd_scan *scan, const double *pts_xy_m, int64_t n_pts, 
                         const unsigned n_cta = (unsigned)std::min<int64_t>((int64_t)n_items, resident);
                         DD_PROFILED(name, side->s,
                                     (ddk::field_grid_tc_kernel<kDeg><<<n_cta, ddk::kTcThreads, ddk::TcConst<kDeg>::kSmemBytes, side->s>>>(
-                                        grid.W, grid.H, tp.n_tile_cols, d_rec, items, (int)n_items, d_tpart, pstride, srcF,
-                                        PF, withhold)));
+                                        ddk::TcScan{grid.W, grid.H, tp.n_tile_cols, srcF, PF, d_tpart, pstride}, nullptr,
+                                        d_rec, items, (int)n_items, withhold)));
                         return cudaGetLastError();
                     };
                     if ((e = launch(std::integral_constant<int, 2>(), d_titems, n_t2, tc_slots2, "field_grid_tc")) != cudaSuccess)
@@ -838,6 +838,43 @@ extern "C" dd_status dd_field_check(void) {
     DD_CUDA_TRY(cudaMemcpyToSymbol(ddk::g_field_tc_timeout, &zero, sizeof(int)));
     return dd::fail(DD_ETIMEOUT, "dd_field_check: a tensor-core contraction of the grid field gave up waiting for its MMAs");
 }
+
+namespace dd {
+
+void tc_prefixes(const dd_scan *scan, double x0, double y0, double dx, double dy, int64_t W, int64_t H, double tdim,
+                 int nact, int *K2, int *K) {
+    *K2 = *K = 0;
+    if (W <= 0 || H <= 0 || nact <= 0) return;
+    ddk::GridDesc g;
+    g.x0 = x0; g.y0 = y0; g.dx = dx; g.dy = dy; g.W = W; g.H = H;
+    const TcPlan tp = plan_tc(scan, g, std::vector<double>{tdim}, std::vector<int>{nact});
+    if (!tp.on) return;
+    *K2 = tp.K2[0];
+    *K = tp.K[0];
+}
+
+cudaError_t prepare_field_tc() {
+    cudaError_t err = prepare_tc_kernel<2>();
+    return err == cudaSuccess ? prepare_tc_kernel<4>() : err;
+}
+
+int64_t field_tc_resident(int deg) { return deg == 2 ? tc_resident_ctas<2>() : tc_resident_ctas<4>(); }
+
+cudaError_t launch_field_tc(int deg, const ddk::TcScan *scans, const ddk::RecF32 *rec, const ddk::TcItem *items,
+                            int n_items, int n_ctas, cudaStream_t stream) {
+    if (n_items <= 0) return cudaSuccess;
+    // (no profiling scope: batch plans capture this launch into a CUDA graph)
+    const ddk::TcScan none{};
+    if (deg == 2)
+        ddk::field_grid_tc_kernel<2><<<(unsigned)n_ctas, ddk::kTcThreads, ddk::TcConst<2>::kSmemBytes, stream>>>(
+            none, scans, rec, items, n_items, 0);
+    else
+        ddk::field_grid_tc_kernel<4><<<(unsigned)n_ctas, ddk::kTcThreads, ddk::TcConst<4>::kSmemBytes, stream>>>(
+            none, scans, rec, items, n_items, 0);
+    return cudaGetLastError();
+}
+
+}  // namespace dd
 
 extern "C" dd_status dd_field_grid_split(const dd_scan *scan, double x0_m, double y0_m, double dx_m, double dy_m,
                                          int64_t n_cols, int64_t n_rows, const double *times_s, int64_t n_t,

@@ -99,9 +99,22 @@ static __device__ int g_field_tc_timeout;
 struct TcItem {
     int v_begin, v_end, tile, row;
     int64_t row_off;
-    int64_t pad;
+    int scan, pad;          // the item's entry in a batch's scan table (0 for one grid)
 };
 static_assert(sizeof(TcItem) == 32, "TcItem layout");
+
+// The grid of points, the visits and the partial rows of the work items: one entry (a
+// kernel argument) for dd_field_on_grid, a table indexed by TcItem::scan for a batch of
+// scans, each on its own grid.  Item `row` writes partial + row * pstride + r W + c.
+struct TcScan {
+    int64_t W, H, n_tile_cols;
+    const float4 *srcF, *ptsF;      // visits and points, float-float in pitch units
+    float *partial;
+    int64_t pstride;                // a multiple of 4 (16-byte aligned rows)
+};
+__device__ __forceinline__ TcScan tc_scan(const TcScan &one, const TcScan *many, const TcItem &it) {
+    return many ? many[it.scan] : one;
+}
 
 __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
     uint32_t r;
@@ -144,10 +157,12 @@ struct TcPrefetch {
     float4 org, pt, v[2], r[2], r1[2];
 };
 template <int kDeg>
-__device__ __forceinline__ void tc_prefetch(TcPrefetch<kDeg> &f, const TcItem &it, int s0, int64_t W, int64_t H,
-                                            int64_t n_tile_cols, const RecF32 *__restrict__ rec,
-                                            const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF, int tid) {
-    const int64_t r0 = (it.tile / n_tile_cols) * (int64_t)kTcTile, c0 = (it.tile % n_tile_cols) * (int64_t)kTcTile;
+__device__ __forceinline__ void tc_prefetch(TcPrefetch<kDeg> &f, const TcItem &it, int s0, const TcScan &S,
+                                            const RecF32 *__restrict__ rec, int tid) {
+    const int64_t W = S.W, H = S.H;
+    const float4 *__restrict__ srcF = S.srcF;
+    const float4 *__restrict__ ptsF = S.ptsF;
+    const int64_t r0 = (it.tile / S.n_tile_cols) * (int64_t)kTcTile, c0 = (it.tile % S.n_tile_cols) * (int64_t)kTcTile;
     const int t = tid & (kTcTile - 1);
     f.org = ptsF[r0 * W + c0];
     f.pt = tid >= kTcTile ? ptsF[r0 * W + min(c0 + t, W - 1)] : ptsF[min(r0 + t, H - 1) * W + c0];
@@ -292,12 +307,11 @@ __device__ __forceinline__ void tc_issue_stage(uint32_t base, uint32_t tmem, int
     }
 }
 
-// partial[row * pstride + r W + c] receives item `row`'s sums.
+// Item `row` of scan table entry S (tc_scan) writes S.partial[row * S.pstride + r W + c].
 template <int kDeg>
 __global__ void __launch_bounds__(kTcThreads, TcShape<kDeg>::kCtasPerSm)
-field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__restrict__ rec,
-                     const TcItem *__restrict__ items, int n_items, float *__restrict__ partial, int64_t pstride,
-                     const float4 *__restrict__ srcF, const float4 *__restrict__ ptsF, int withhold_mma) {
+field_grid_tc_kernel(const TcScan one, const TcScan *__restrict__ many, const RecF32 *__restrict__ rec,
+                     const TcItem *__restrict__ items, int n_items, int withhold_mma) {
     using C = TcConst<kDeg>;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char *bufs = tc_smem;
@@ -359,10 +373,11 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
         TcItem nxt = items[min(q + G, n_items - 1)];
         int s0 = it.v_begin;
         TcPrefetch<kDeg> pf;
-        tc_prefetch<kDeg>(pf, it, s0, W, H, n_tile_cols, rec, srcF, ptsF, tid);
+        tc_prefetch<kDeg>(pf, it, s0, tc_scan(one, many, it), rec, tid);
         int gs = 0, n_done = 0;
         float *const scr = reinterpret_cast<float *>(bufs);
         while (q < n_items) {
+            const int64_t n_tile_cols = tc_scan(one, many, it).n_tile_cols;
             const int64_t r0 = (it.tile / n_tile_cols) * (int64_t)kTcTile;
             const int64_t c0 = (it.tile % n_tile_cols) * (int64_t)kTcTile;
             const int s1 = min(s0 + kTcMaxChunk, it.v_end), nv = s1 - s0;
@@ -393,7 +408,7 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
             const int nq_ = last_seg ? q + G : q;
             const TcItem nit = last_seg ? nxt : it;
             const int ns0 = last_seg ? nit.v_begin : s1;
-            if (nq_ < n_items) tc_prefetch<kDeg>(pf, nit, ns0, W, H, n_tile_cols, rec, srcF, ptsF, tid);
+            if (nq_ < n_items) tc_prefetch<kDeg>(pf, nit, ns0, tc_scan(one, many, nit), rec, tid);
             const float2 din2 = f2(din, din), dfr2 = f2(dfr, dfr);
             for (int st = 0; st < nst; ++st) {
                 const int g = gs + st, b = g % kTcBufs;
@@ -440,13 +455,15 @@ field_grid_tc_kernel(int64_t W, int64_t H, int64_t n_tile_cols, const RecF32 *__
                 tc_fence_before();
                 producers_sync();
                 // warp w writes rows w, w + 8, ..: lane l the columns 4l .. 4l + 3
+                const TcScan S = tc_scan(one, many, it);
+                const int64_t W = S.W, H = S.H;
                 const int64_t ncol = min((int64_t)kTcTile, W - c0);
                 const bool vec = (W & 3) == 0 && 4 * lane + 4 <= ncol;
                 for (int rr = warp; rr < kTcTile; rr += kGenWarps) {
                     const int64_t r = r0 + rr;
                     if (r >= H) break;
                     const float4 v = reinterpret_cast<const float4 *>(scr + rr * kTcScratchStride)[lane];
-                    float *const dst = partial + (int64_t)it.row * pstride + r * W + c0 + 4 * lane;
+                    float *const dst = S.partial + (int64_t)it.row * S.pstride + r * W + c0 + 4 * lane;
                     if (vec) {
                         *reinterpret_cast<float4 *>(dst) = v;
                     } else {

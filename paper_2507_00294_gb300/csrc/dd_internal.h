@@ -55,6 +55,12 @@ struct dd_scan {
     mutable std::vector<DevCache> dev;
 };
 
+namespace ddk {
+struct TcScan;
+struct TcItem;
+struct RecF32;
+}  // namespace ddk
+
 namespace dd {
 
 // Record `msg` as this thread's last error and return `st`.
@@ -72,6 +78,18 @@ const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status
 // kernels form coordinate differences without FP64 arithmetic: n float4 stored after the
 // FP64 arrays of the same cache (call after device_sources on the same stream).
 const float4 *device_sources_ff(const dd_scan *scan, cudaStream_t stream, dd_status *st);
+
+// Tensor-core contraction of grids (dd_field.cu, dd_field_tc.cuh), for batches of scans:
+// the prefixes of one snapshot (visits [0, K2) on the degree-2 series and [K2, K) on the
+// degree-4 series at every point of the W x H grid; both 0 when the grid takes none), the
+// kernels' one-time attributes, the CTAs resident at once, and a launch over work items
+// whose grids, visits and partial rows come from the scan table.
+void tc_prefixes(const dd_scan *scan, double x0, double y0, double dx, double dy, int64_t W, int64_t H, double tdim,
+                 int nact, int *K2, int *K);
+cudaError_t prepare_field_tc();
+int64_t field_tc_resident(int deg);
+cudaError_t launch_field_tc(int deg, const ddk::TcScan *scans, const ddk::RecF32 *rec, const ddk::TcItem *items,
+                            int n_items, int n_ctas, cudaStream_t stream);
 
 // The work enqueued so far on `stream` may read the scan's device block on the current
 // device: dd_destroy waits for it before the block is released.  scan_shared: the block

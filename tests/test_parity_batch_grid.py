@@ -99,3 +99,41 @@ def test_batched_512_scans_grid_against_point_list_and_oracle(cuda):
         ref = oracle_pairs(j.scan, j.pts_xy, j.times, ip, np.zeros(4, int))
         got = gout[offs[k]:offs[k + 1]][ip]
         assert_mixed(got, ref, ref.max(), "grid 512 scan %d" % k)
+
+
+def test_grid_batch_tensor_core_part(cuda):
+    """Scans whose grids reach 64 x 64 points, where the plan sums each scan's older visits
+    on the tensor cores (dd_field_tc.cuh, one table entry per scan) and the rest on the grid
+    tiles: a probe grid, a ragged pitch/2 grid of 2 x 2 tensor-core tiles, an off-lattice
+    grid, during and after the scan; every point within the mixed tolerance of the FP64
+    plan, and seeded points against the oracle."""
+    rng = np.random.default_rng(17)
+    specs, grids, times = [], [], []
+    for k in range(6):
+        n = int(rng.integers(64, 101))
+        s = w.ScanSpec(n, n, D_m2s=float(10 ** rng.uniform(-14, -12)), dwell_s=float(10 ** rng.uniform(-7, -6)),
+                       sigma_m=0.1e-9, order=w.RANDOM, seed=40 + k, keep_fraction=float(rng.uniform(0.3, 1.0)))
+        p = s.pitch_m
+        g = [(0.0, 0.0, p, p, n, n), (0.0, 0.0, p / 2, p / 2, 2 * n + 3, 2 * n - 5),
+             (-0.37 * p, 0.21 * p, 0.7 * p, 0.7 * p, 97, 130)][k % 3]
+        nv = w.n_visits(s)
+        specs.append(s)
+        grids.append(g)
+        times.append([nv * s.dwell_s, (0.7 * nv + 0.5) * s.dwell_s, 4.0 * nv * s.dwell_s][k % 3])
+    times = np.array(times)
+    scans = [b.Scan(s) for s in specs]
+    split = [int(b.dd_field_grid_split(sc, *g, times[k:k + 1])[0]) for k, (sc, g) in enumerate(zip(scans, grids))]
+    assert sum(x > 0 for x in split) >= 4, split          # the contraction takes part
+    plan = b.Batch(scans, None, times, "mixed", grids=grids)
+    out = plan.run(device=cuda).cpu().numpy()
+    np.testing.assert_array_equal(out, plan.run(device=cuda).cpu().numpy())   # graph replay
+    ref64 = b.Batch(scans, None, times, "fp64", grids=grids).run(device=cuda).cpu().numpy()
+    for k, (s, g) in enumerate(zip(specs, grids)):
+        got = out[plan.offsets[k]:plan.offsets[k + 1]]
+        r64 = ref64[plan.offsets[k]:plan.offsets[k + 1]]
+        assert_mixed(got, r64, r64.max(), "tc grid batch scan %d vs fp64" % k)
+        pts = grid_pts(g)
+        ip = rng.integers(0, len(pts), 24)
+        ref = oracle_pairs(s, pts, times[k:k + 1], ip, np.zeros(len(ip), int))
+        assert_fp64(r64[ip], ref, "tc grid batch scan %d fp64" % k)
+        assert_mixed(got[ip], ref, r64.max(), "tc grid batch scan %d" % k)
