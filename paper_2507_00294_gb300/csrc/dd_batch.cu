@@ -170,16 +170,25 @@ batch_grid_kernel(const BScan *__restrict__ sc, const int4 *__restrict__ items, 
 
 __global__ void batch_reduce_kernel(const BScan *__restrict__ sc, const int64_t *__restrict__ pt_offs, int n_scans,
                                     int64_t total, const double *__restrict__ partial, const float *__restrict__ tpart,
-                                    double *__restrict__ out) {
+                                    bool mixed_grid, double *__restrict__ out) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
     const BScan &S = sc[find_segment(pt_offs, n_scans, g)];
     const int64_t p = g - S.pt_off;
-    double acc = 0.0;
-    // the tensor-core rows first, then the CUDA-core blocks from the first one past k_tc
-    for (int q = 0; q < S.nq_tc; ++q) acc += (double)tpart[S.t_off + (int64_t)q * S.t_stride + p];
-    for (int b = S.blk0; b < S.nblk; ++b) acc += partial[S.part_off + (int64_t)b * S.n_pts + p];
-    out[g] = S.pref * acc;
+    // the tensor-core rows first, then the CUDA-core blocks from the first one past k_tc.
+    // Grid plans in FP32-mixed hold FP32 sums (the block sums exactly, in FP64 storage):
+    // a compensated FP32 sum (FP64 arithmetic is 64 times slower on this part); the others
+    // sum in FP64.
+    if (S.nq_tc > 0 || mixed_grid) {
+        BlockSum<float> acc;
+        for (int q = 0; q < S.nq_tc; ++q) acc.add(tpart[S.t_off + (int64_t)q * S.t_stride + p]);
+        for (int b = S.blk0; b < S.nblk; ++b) acc.add((float)partial[S.part_off + (int64_t)b * S.n_pts + p]);
+        out[g] = S.pref * acc.value();
+    } else {
+        double acc = 0.0;
+        for (int b = 0; b < S.nblk; ++b) acc += partial[S.part_off + (int64_t)b * S.n_pts + p];
+        out[g] = S.pref * acc;
+    }
 }
 
 // Kernel variants with the same 512-point tile (so they share one work list).
@@ -222,6 +231,8 @@ struct dd_batch {
     float *d_tpart = nullptr;
     double *d_pts = nullptr, *d_out = nullptr;   // staging for host buffers
     cudaStream_t cap = nullptr;
+    cudaStream_t side = nullptr;        // the graph's second branch (coefficients, contraction)
+    cudaEvent_t ev_fork = nullptr, ev_coef = nullptr, ev_join = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool on_grid = false;               // points formed from per-scan grids (no point buffer)
     bool grid_tiles = false;            // ... and evaluated by the grid tile kernel (FP32-mixed)
@@ -263,23 +274,34 @@ void launch_field(dd_batch *b, int grid, cudaStream_t st) {
 // Enqueue the whole batch evaluation on `st` (used for capture and for tuning).
 dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cudaStream_t st) {
     const unsigned nb_pts = (unsigned)((b->total_pts + 255) / 256);
+    // two branches: the points on `st`, the coefficient records beside them on `side`
+    // (they only read the scans); with the tensor-core contraction, it follows the records
+    // on `side` while the grid tiles run on `st`; both join before the reduce
+    DD_CUDA_TRY(cudaEventRecord(b->ev_fork, st));
+    DD_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
     DD_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st));
     ddk::batch_prep_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, pts, b->total_pts, b->d_X, b->d_Y, b->d_F);
     if (b->total_rec > 0) {
         const unsigned nb = (unsigned)((b->total_rec + 127) / 128);
         if (b->prec == DD_MIXED)
-            ddk::batch_coef_kernel<ddk::RecF32><<<nb, 128, 0, st>>>(b->d_sc, b->d_rec_offs, b->n_scans, b->total_rec,
-                                                                  (ddk::RecF32 *)b->d_rec);
+            ddk::batch_coef_kernel<ddk::RecF32><<<nb, 128, 0, b->side>>>(b->d_sc, b->d_rec_offs, b->n_scans,
+                                                                       b->total_rec, (ddk::RecF32 *)b->d_rec);
         else
-            ddk::batch_coef_kernel<ddk::RecF64><<<nb, 128, 0, st>>>(b->d_sc, b->d_rec_offs, b->n_scans, b->total_rec,
-                                                                  (ddk::RecF64 *)b->d_rec);
+            ddk::batch_coef_kernel<ddk::RecF64><<<nb, 128, 0, b->side>>>(b->d_sc, b->d_rec_offs, b->n_scans,
+                                                                       b->total_rec, (ddk::RecF64 *)b->d_rec);
     }
+    DD_CUDA_TRY(cudaEventRecord(b->ev_coef, b->side));
+    DD_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_coef, 0));
     if (b->n_t2 + b->n_t4 > 0) {
-        // the older visits of the larger grids on the tensor cores
-        DD_CUDA_TRY(dd::launch_field_tc(2, b->d_tcs, (const ddk::RecF32 *)b->d_rec, b->d_titems, b->n_t2, b->cta_t2, st));
+        // the older visits of the larger grids on the tensor cores (after the points)
+        DD_CUDA_TRY(cudaEventRecord(b->ev_fork, st));
+        DD_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+        DD_CUDA_TRY(dd::launch_field_tc(2, b->d_tcs, (const ddk::RecF32 *)b->d_rec, b->d_titems, b->n_t2, b->cta_t2,
+                                        b->side));
         DD_CUDA_TRY(dd::launch_field_tc(4, b->d_tcs, (const ddk::RecF32 *)b->d_rec, b->d_titems + b->n_t2, b->n_t4,
-                                        b->cta_t4, st));
+                                        b->cta_t4, b->side));
     }
+    DD_CUDA_TRY(cudaEventRecord(b->ev_join, b->side));
     if (b->n_items > 0 && b->grid_tiles) {
         ddk::batch_grid_kernel<<<b->grid[0], ddk::kBgThreads, 0, st>>>(b->d_sc, b->d_items, b->n_items, b->d_counter,
                                                                       b->d_F, (const ddk::RecF32 *)b->d_rec, b->sb,
@@ -297,8 +319,9 @@ dd_status enqueue(dd_batch *b, const double *pts, double *out, int variant, cuda
             else launch_field<ddk::CfgF64>(b, g, st);
         }
     }
+    DD_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_join, 0));
     ddk::batch_reduce_kernel<<<nb_pts, 256, 0, st>>>(b->d_sc, b->d_pt_offs, b->n_scans, b->total_pts, b->d_part,
-                                                     b->d_tpart, out);
+                                                     b->d_tpart, b->grid_tiles, out);
     DD_CUDA_TRY(cudaGetLastError());
     return DD_OK;
 }
@@ -535,6 +558,10 @@ dd_status create_plan(const dd_scan *const *scans, int32_t n_scans, const int64_
     DD_CUDA_TRY(cudaMemcpy(b->d_rec_offs, rec_offs.data(), rec_offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     if (!it.empty()) DD_CUDA_TRY(cudaMemcpy(b->d_items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
     DD_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    DD_CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+    DD_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    DD_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_coef, cudaEventDisableTiming));
+    DD_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
     if (b->grid_tiles)
         b->grid = {grid_kernel_ctas(), grid_kernel_ctas(), grid_kernel_ctas(), grid_kernel_ctas()};
     else if (prec == DD_MIXED)
@@ -676,6 +703,10 @@ void dd_batch_destroy(dd_batch *b) {
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_coef) cudaEventDestroy(b->ev_coef);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     cudaFree(b->ws);
     cudaFree(b->d_pts);
     cudaFree(b->d_out);
