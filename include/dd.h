@@ -252,9 +252,12 @@ typedef struct dd_batch dd_batch;
    its field goes to out[off_k + r W_k + c], off_k = sum over the earlier scans of W H.
    dd_batch_run and dd_batch_tune then take pts_xy_m = NULL.  In FP32-mixed precision the
    grid lets tiles of 32 x 32 points split the low-degree pair terms into column and row
-   factors (as dd_field_on_grid does); the result differs from the point-list plan by FP32
-   rounding only.  Errors: DD_EINVAL (sizes, non-finite origin or spacing, more than 2^31
-   points), DD_ENOMEM, DD_ECUDA. */
+   factors (as dd_field_on_grid does), and for grids of at least 64 x 64 points each scan's
+   visits on the degree-2 (then degree-4) series at every point of its grid are summed as
+   matrix products on the tensor cores, the prefixes dd_field_grid_split reports, with the
+   same completion waits and NaN-on-timeout rule as dd_field_on_grid (dd_field_check); the
+   result differs from the point-list plan by FP32 rounding only.  Errors: DD_EINVAL (sizes,
+   non-finite origin or spacing, more than 2^31 points), DD_ENOMEM, DD_ECUDA. */
 dd_status dd_batch_create_grid(const dd_scan *const *scans, int32_t n_scans, const double *grid_xy,
                                const int64_t *grid_wh, const double *times_s, dd_precision prec,
                                dd_batch **out);
