@@ -29,10 +29,12 @@
  *     of the call is page-locked (cudaHostAlloc / cudaHostRegister): then its copies
  *     stay enqueued on `cuda_stream` like its kernels, and the caller synchronises
  *     the stream before reading the outputs or reusing the inputs.
- *   - Device scratch is taken stream-ordered on the call's stream from a memory
- *     pool the library owns per device (freed workspace up to 4 GiB stays mapped
- *     for the next call) and returned with cudaFreeAsync; a scan caches its probe
- *     list per device.
+ *   - Device scratch of a call is handed back with an event recorded on its stream
+ *     and reused by later calls (at once on the same stream, on another once that
+ *     event has completed; up to 8 GiB per device kept); new scratch comes from a
+ *     memory pool the library owns per device (freed memory up to 4 GiB stays
+ *     mapped).  A scan caches its probe list per device, in blocks that destroyed
+ *     scans give back.
  */
 #ifndef DD_H
 #define DD_H

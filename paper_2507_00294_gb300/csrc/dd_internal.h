@@ -69,10 +69,10 @@ dd_status fail_cuda(cudaError_t err, const char *what);
 void clear_error();
 
 // Device copy of the scan's dimensionless visit arrays on the current device, usable by
-// work enqueued on `stream` after this call: created on first use from the library's
-// memory pool and uploaded on `stream` (no host synchronisation); a call on another
-// stream waits for the upload's event.  Returns NULL on failure after recording the
-// error in *st.
+// work enqueued on `stream` after this call: created on first use in a block that a
+// destroyed scan gave back (else a new one) and uploaded on `stream` (no host
+// synchronisation); a call on another stream waits for the upload's event.  Returns NULL
+// on failure after recording the error in *st.
 const double *device_sources(const dd_scan *scan, cudaStream_t stream, dd_status *st);
 // The same visits' X, Y as float-float pairs (hi = fl32(v), lo = fl32(v - hi)), so FP32
 // kernels form coordinate differences without FP64 arithmetic: n float4 stored after the

@@ -323,9 +323,10 @@ cudaError_t defer_release(cudaStream_t stream, void *obj, void (*del)(void *)) {
     return err;
 }
 
-// Device blocks of visit caches: a destroyed scan's block (its device synchronised) is kept
-// per device and power-of-two size class for the next scan, up to 1 GiB per device, since a
-// stream-ordered pool allocation of a fresh block took about 66 us of host time per scan.
+// Device blocks of visit caches: a destroyed scan's block (once the work that read it is
+// done) is kept per device and power-of-two size class for the next scan, up to 1 GiB per
+// device, since a stream-ordered pool allocation of a fresh block took about 66 us of host
+// time per scan.
 static std::mutex g_vcache_mu;
 static std::vector<void *> g_vcache_free[64][48];
 static size_t g_vcache_kept[64];
@@ -352,7 +353,7 @@ static cudaError_t vcache_take(int device, size_t bytes, void **p, size_t *cap) 
     return cudaMalloc(p, *cap);
 }
 
-// the caller has synchronised the device: no work may still use the block
+// the caller has waited for every use of the block (or for the whole device)
 static void vcache_give(int device, void *p, size_t cap) {
     if (!p) return;
     {
