@@ -89,7 +89,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 25 ms, each stamped with the host clock.
+    """nvidia-smi clock / throttle samples every PERIOD_MS (10 ms), each stamped with the host clock.
 
     The timed region of a short run lasts tens of milliseconds, so the sampler is started
     first and the region opens only once a sample has arrived; `mark()` brackets the region
