@@ -339,6 +339,14 @@ dd_status dd_sur_adam(float *param, const float *grad, float *m, float *v, int64
                       void *w_flip_bf16, int32_t cin, int32_t cout, void *cuda_stream);
 dd_status dd_sur_planes(const float *tmap, const float *scal, int32_t B, int32_t H, int32_t W, void *x,
                         void *cuda_stream);
+/* dd_sur_planes_bg: the planes of dd_sur_planes from scal3 [B][3] (standardised log D,
+   standardised log dwell, kappa = D dwell / pitch^2), tmap holding 1 / age (age in dwells
+   at the end of the scan, 1 for the last visit), plus channel 4: the own term of each
+   background visit (age > k_exact) at its position, ln(w1/w0) of Eq. 3/4 with
+   w1 = 2 s + 4 kappa age, w0 = 2 s + 4 kappa (age - 1), s = probe sigma^2 / pitch^2, as
+   (log10 - mu) / sigma, 0 elsewhere; channel 5: 1 on those visits; channels 6..15 zero. */
+dd_status dd_sur_planes_bg(const float *tmap, const float *scal3, float s_dim, int32_t k_exact, float mu,
+                           float sigma, int32_t B, int32_t H, int32_t W, void *x, void *cuda_stream);
 dd_status dd_sur_wmse(const float *pred, const float *target, const float *weight, int64_t n, void *dz,
                       double *block_sums, double *loss_sum, void *cuda_stream);
 dd_status dd_sur_weights(const float *target, int64_t n_maps, int64_t hw, float mu, float sigma, float alpha,

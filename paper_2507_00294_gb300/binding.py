@@ -88,6 +88,8 @@ def load(build_if_missing=True):
     lib.dd_sur_adam.argtypes = [_VP, _VP, _VP, _VP, _I64, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, ctypes.c_float, i32, _VP, _VP, i32, i32, _VP]
     lib.dd_sur_planes.argtypes = [_VP, _VP, i32, i32, i32, _VP, _VP]
+    lib.dd_sur_planes_bg.argtypes = [_VP, _VP, ctypes.c_float, i32, ctypes.c_float, ctypes.c_float, i32, i32, i32,
+                                     _VP, _VP]
     lib.dd_sur_targets.argtypes = [_VP, _VP, _I64, _I64, ctypes.c_double, ctypes.c_float, ctypes.c_float, _VP, _VP]
     lib.dd_sur_fields.argtypes = [_VP, _VP, _I64, _I64, ctypes.c_float, ctypes.c_float, _VP, _VP]
     lib.dd_sur_spot_error.argtypes = [_VP, _VP, _VP, _VP, _VP, i32, i32, i32, ctypes.c_float, ctypes.c_float, _VP, _VP]
@@ -98,7 +100,7 @@ def load(build_if_missing=True):
                                         _I64, _I64, _VP, _I64, _VP, _VP]
     lib.dd_field_grid_split.restype = ctypes.c_int
     for name in ("dd_sur_conv3x3", "dd_sur_wgrad", "dd_sur_mse", "dd_sur_wmse", "dd_sur_weights", "dd_sur_adam",
-                 "dd_sur_planes",
+                 "dd_sur_planes", "dd_sur_planes_bg",
                  "dd_sur_targets", "dd_sur_fields", "dd_sur_spot_error", "dd_sur_check"):
         getattr(lib, name).restype = ctypes.c_int
     lib.dd_profile_enable.argtypes = [ctypes.c_int32]
@@ -458,6 +460,13 @@ def dd_sur_adam(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, w
 def dd_sur_planes(tmap, scal, x, stream=None):
     B, H, W = tmap.shape
     _check(load().dd_sur_planes(_dp(tmap), _dp(scal), B, H, W, _dp(x), _cs(stream, tmap)), "dd_sur_planes")
+    return x
+
+
+def dd_sur_planes_bg(tmap, scal3, s_dim, k_exact, mu, sigma, x, stream=None):
+    B, H, W = tmap.shape
+    _check(load().dd_sur_planes_bg(_dp(tmap), _dp(scal3), s_dim, k_exact, mu, sigma, B, H, W, _dp(x),
+                                   _cs(stream, tmap)), "dd_sur_planes_bg")
     return x
 
 

@@ -517,6 +517,39 @@ __global__ void planes_kernel(const float *__restrict__ tmap, const float *__res
     o[1] = make_uint4(0, 0, 0, 0);
 }
 
+// The planes of planes_kernel, plus channel 4: each background visit's own term at its
+// position (a visit older than k_exact dwells at the end of the scan: ln(w1/w0) of Eq. 3/4,
+// w1 = 2 s + 4 kappa age, w0 = 2 s + 4 kappa (age - 1), as the normalised log10 of the
+// target), and channel 5: the background mask.  scal3[b] = (standardised log D,
+// standardised log dwell, kappa = D dwell / pitch^2).
+__global__ void planes_bg_kernel(const float *__restrict__ tmap, const float *__restrict__ scal3, float s_dim,
+                                 float k_exact, float mu, float inv_sigma, int HW, int64_t n, bf16 *__restrict__ x) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int b = (int)(p / HW);
+    const float t = tmap[p];
+    float own = 0.f, bg = 0.f;
+    if (t > 0.f) {
+        const float age = 1.0f / t;                      // 1 for the last visit
+        if (age > k_exact + 0.5f) {
+            const float kap = scal3[3 * b + 2];
+            const float v = log1pf(4.0f * kap / (2.0f * s_dim + 4.0f * kap * (age - 1.0f)));
+            own = (log10f(v) - mu) * inv_sigma;
+            bg = 1.f;
+        }
+    }
+    __nv_bfloat162 c01 = __floats2bfloat162_rn(t >= 0.f ? t : 0.f, t >= 0.f ? 1.f : 0.f);
+    __nv_bfloat162 c23 = __floats2bfloat162_rn(scal3[3 * b], scal3[3 * b + 1]);
+    __nv_bfloat162 c45 = __floats2bfloat162_rn(own, bg);
+    uint4 z = make_uint4(0, 0, 0, 0);
+    z.x = *reinterpret_cast<uint32_t *>(&c01);
+    z.y = *reinterpret_cast<uint32_t *>(&c23);
+    z.z = *reinterpret_cast<uint32_t *>(&c45);
+    uint4 *o = reinterpret_cast<uint4 *>(x + p * 16);
+    o[0] = z;
+    o[1] = make_uint4(0, 0, 0, 0);
+}
+
 // One CTA per map: peak = max_p psi[m][p] * scale[m], then
 // target[m][p] = (log10(max(psi[m][p] * scale[m], peak * 10^floor_rel)) - mu) * inv_sigma
 __global__ void targets_kernel(const double *__restrict__ psi, const double *__restrict__ scale, int64_t hw,
@@ -812,6 +845,18 @@ dd_status dd_sur_planes(const float *tmap, const float *scal, int32_t B, int32_t
     const int64_t n = (int64_t)B * H * W;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     ddk::planes_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmap, scal, H * W, n, (ddk::bf16 *)x);
+    DD_CUDA_TRY(cudaGetLastError());
+    return DD_OK;
+}
+
+dd_status dd_sur_planes_bg(const float *tmap, const float *scal3, float s_dim, int32_t k_exact, float mu, float sigma,
+                           int32_t B, int32_t H, int32_t W, void *x, void *cuda_stream) {
+    dd::clear_error();
+    if (!tmap || !scal3 || !x || B < 1 || H < 1 || W < 1 || !(s_dim > 0.f) || k_exact < 0 || !(sigma > 0.f))
+        return dd::fail(DD_EINVAL, "dd_sur_planes_bg: bad arguments");
+    const int64_t n = (int64_t)B * H * W;
+    ddk::planes_bg_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(
+        tmap, scal3, s_dim, (float)k_exact, mu, 1.0f / sigma, H * W, n, (ddk::bf16 *)x);
     DD_CUDA_TRY(cudaGetLastError());
     return DD_OK;
 }

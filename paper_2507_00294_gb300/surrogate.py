@@ -1,17 +1,18 @@
 """Learned surrogate of the final damage map, trained on the exact batched path.
 
-A small convolutional network maps four input planes of a scan -- the visit-time map
+A small convolutional network maps six input planes of a scan -- the visit-time map
 (the inverse of each visit's age at the end of the scan, in dwells, where visited), the
-visited mask, standardised log10 D and log10 dwell -- on a 128 x 128 canvas at the probe
-pitch to the log10 of the dimensionless final field (psi * 4 pi D / Q0), floored six
-decades below the map's own peak: values below that floor change a map's relative L2
-error by less than 1e-6, so the loss does not spend capacity on them.  The probe sigma is
-fixed (0.1 nm) for the surrogate's scans: it is not an input plane, and near the last
-visits the field depends on it.  The loss is the squared log error weighted per pixel by
-the pixel's share of the map's squared norm (plus a small uniform part), which to first
-order is the squared relative L2 error of the linear map, the measure the surrogate is
-judged by.  Six 3x3 convolutions, 32 channels, ReLU,
-BF16 activations, FP32 accumulation and FP32 master weights; every layer, the loss, the
+visited mask, standardised log10 D and log10 dwell, and for every background visit its
+own closed-form term at its position (Eq. 3/4, in the target's units) with a mask of those
+visits -- on a 128 x 128 canvas at the probe pitch to the log10 of the dimensionless final
+field (psi * 4 pi D / Q0), floored six decades below the map's own peak: values below that
+floor change a map's relative L2 error by less than 1e-6, so the loss does not spend
+capacity on them.  The probe sigma is fixed (0.1 nm) for the surrogate's scans: it is not
+an input plane, and near the last visits the field depends on it.  The loss is the squared
+log error weighted per pixel by the pixel's share of the map's squared norm (plus a small
+uniform part), which to first order is the squared relative L2 error of the linear map,
+the measure the surrogate is judged by.  Six 3x3 convolutions, 32 channels, ReLU, BF16
+activations, FP32 accumulation and FP32 master weights; every layer, the loss, the
 weight and data gradients and Adam run in the library's CUDA kernels (dd_sur_* in
 include/dd.h).  This module only allocates buffers and sequences those calls.
 
@@ -35,11 +36,12 @@ LAYERS = [(16, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 16)]   # (cin, 
 # dilation of each 3x3 layer: the receptive field grows to 1 + 2 * sum = 127 pixels, the
 # whole canvas, since the final field at a point depends on the whole scan history
 DILATIONS = (1, 2, 4, 8, 16, 32)
-REAL_IN, REAL_OUT = 4, 1
+REAL_IN, REAL_OUT = 6, 1
 FLOOR_REL = -6.0          # target floor: log10 of the fraction of the map's peak
 # fixed affine normalisation of the target log10 field: (log10 psi - MU) / SIGMA
 MU, SIGMA = -3.0, 3.0
 PROBE_SIGMA = 0.1e-9      # probe sigma of every surrogate scan [m]
+S_DIM = (PROBE_SIGMA / w.PITCH) ** 2   # sigma^2 / pitch^2 of the surrogate's scans
 LOSS_ALPHA = 0.9          # share of the loss weight that follows the pixel's squared field
 K_EXACT = 64              # the last visits of a scan, added exactly to the network's background
 
@@ -190,10 +192,11 @@ def canvas_points(spec):
 
 
 def scan_inputs(specs):
-    """Host-side input descriptors: time maps [N, H, W] (-1 unvisited) and scalars [N, 2]."""
+    """Host-side input descriptors: time maps [N, H, W] (-1 unvisited) and scalars [N, 3]
+    (standardised log10 D, standardised log10 dwell, kappa = D dwell / pitch^2)."""
     N = len(specs)
     tmap = np.full((N, CANVAS, CANVAS), -1.0, np.float32)
-    scal = np.zeros((N, 2), np.float32)
+    scal = np.zeros((N, 3), np.float32)
     for k, s in enumerate(specs):
         g = visit_list(s)
         nv = len(g)
@@ -202,8 +205,17 @@ def scan_inputs(specs):
         # visit: 1).  Long after its dwell a visit's own dose falls as 1 / age, and BF16
         # keeps 1 / age to 0.2 % (a log of the age would lose ln(age) times more)
         tmap[k, iy, ix] = (1.0 / (nv - np.arange(nv, dtype=np.float64))).astype(np.float32)
-        scal[k] = [(math.log10(s.D_m2s) + 13.5) / 1.5, math.log10(s.dwell_s) + 6.0]
+        scal[k] = [(math.log10(s.D_m2s) + 13.5) / 1.5, math.log10(s.dwell_s) + 6.0,
+                   s.D_m2s * s.dwell_s / s.pitch_m ** 2]
     return tmap, scal
+
+
+def input_planes(tmap, scal, x):
+    """The network's input planes (BF16 [B,H,W,16]) of a batch: the time map, the visited
+    mask, standardised log D and log dwell, and each background visit's own closed-form
+    term at its position with a mask of those visits (dd_sur_planes_bg)."""
+    b.dd_sur_planes_bg(tmap, scal, S_DIM, K_EXACT, MU, SIGMA, x)
+    return x
 
 
 def field_scales(specs, device):
@@ -299,7 +311,7 @@ def train(net, tmap, scal, target, epochs, batch=32, lr=2e-3, seed=0, log=None, 
         lr_ep = lr * (0.5 * (1 + math.cos(math.pi * ep / max(1, epochs))))
         for s0 in range(0, N - batch + 1, batch):
             idx = torch.from_numpy(order[s0:s0 + batch]).to(tmap.device)
-            b.dd_sur_planes(tmap[idx].contiguous(), scal[idx].contiguous(), net.x)
+            input_planes(tmap[idx].contiguous(), scal[idx].contiguous(), net.x)
             net.forward()
             loss = net.backward(target[idx].contiguous(), None if weight is None else weight[idx].contiguous())
             net.adam(lr_ep)
@@ -319,7 +331,7 @@ def predict(net, tmap, scal, batch=256):
     for s0 in range(0, N, batch):
         B = min(batch, N - s0)
         net.buffers(B)
-        b.dd_sur_planes(tmap[s0:s0 + B].contiguous(), scal[s0:s0 + B].contiguous(), net.x)
+        input_planes(tmap[s0:s0 + B].contiguous(), scal[s0:s0 + B].contiguous(), net.x)
         out[s0:s0 + B] = net.forward()
     return out
 

@@ -196,6 +196,40 @@ def test_adam_and_input_planes(cuda):
     assert np.all(xh[0, ..., 2] == 0.5) and np.all(xh[1, ..., 3] == 2.0) and np.all(xh[..., 4:] == 0)
 
 
+def test_background_planes(cuda):
+    """dd_sur_planes_bg: the first four planes as dd_sur_planes, then each background
+    visit's own term ln(w1/w0) (Eq. 3/4 at rho = 0) in the target's normalised log10 units
+    and the background mask, against the same numbers formed in FP64."""
+    import torch
+    from paper_2507_00294_gb300 import surrogate as sur
+    rng = np.random.default_rng(12)
+    B = 3
+    tmap = np.full((B, 128, 128), -1.0, np.float32)
+    ages = rng.integers(1, 5000, (B, 400))
+    for m in range(B):
+        idx = rng.choice(128 * 128, 400, replace=False)
+        tmap[m].reshape(-1)[idx] = (1.0 / ages[m]).astype(np.float32)
+    kap = np.array([4e-4, 0.24, 40.0], np.float32)
+    scal = np.stack([rng.normal(size=B), rng.normal(size=B), kap], axis=1).astype(np.float32)
+    x = torch.empty((B, 128, 128, 16), dtype=torch.bfloat16, device=cuda)
+    s_dim, k_exact = 0.04, 64
+    b.dd_sur_planes_bg(torch.from_numpy(tmap).to(cuda), torch.from_numpy(scal).to(cuda), s_dim, k_exact,
+                       sur.MU, sur.SIGMA, x)
+    xh = r64(x)
+    x4 = torch.empty_like(x)
+    b.dd_sur_planes(torch.from_numpy(tmap).to(cuda), torch.from_numpy(np.ascontiguousarray(scal[:, :2])).to(cuda), x4)
+    np.testing.assert_array_equal(xh[..., :4], r64(x4)[..., :4])
+    age = np.where(tmap > 0, 1.0 / np.maximum(tmap.astype(np.float64), 1e-30), 0.0)
+    bg = (tmap > 0) & (age > k_exact + 0.5)
+    k = np.broadcast_to(kap.astype(np.float64)[:, None, None], tmap.shape)
+    ref = np.zeros(tmap.shape)
+    own = np.log1p(4 * k[bg] / (2 * s_dim + 4 * k[bg] * (age[bg] - 1)))
+    ref[bg] = (np.log10(own) - sur.MU) / sur.SIGMA
+    assert np.all(xh[..., 5] == bg.astype(np.float64))
+    np.testing.assert_allclose(xh[..., 4], ref, rtol=8e-3, atol=1e-6)
+    assert np.all(xh[..., 6:] == 0)
+
+
 def test_training_reduces_loss_and_fallback_is_exact(cuda):
     from paper_2507_00294_gb300 import surrogate as sur
     specs, tmap, scal, target = sur.build_dataset(96, seed=123, device=cuda)
