@@ -314,7 +314,7 @@ const char *dd_last_error(void);
    dd_sur_weights: w [n_maps*hw] FP32 = alpha hw f_p^2 / sum_q f_q^2 + (1 - alpha) per map,
    f = 10^(target sigma + mu) from normalised targets (alpha in [0, 1]): the squared log
    error weighted so, summed over a map and divided by hw, approximates (relative L2 error of
-   the linear map / ln 10)^2, the measure the surrogate is judged by.
+   the linear map / ln 10)^2, the surrogate's accuracy measure.
    dd_sur_targets: out [n_maps*hw] FP32 = (log10(max(f, peak * 10^floor_rel_log10)) - mu)
    / sigma with f = psi*scale[map] and peak = max of f over the map (floor_rel_log10 < 0):
    the network's normalised target from exact fields psi [n_maps*hw] (u/m^2, FP64) and

@@ -11,7 +11,7 @@ capacity on them.  The probe sigma is fixed (0.1 nm) for the surrogate's scans: 
 an input plane, and near the last visits the field depends on it.  The loss is the squared
 log error weighted per pixel by the pixel's share of the map's squared norm (plus a small
 uniform part), which to first order is the squared relative L2 error of the linear map,
-the measure the surrogate is judged by.  Six 3x3 convolutions, 32 channels, ReLU, BF16
+the surrogate's accuracy measure.  Six 3x3 convolutions, 32 channels, ReLU, BF16
 activations, FP32 accumulation and FP32 master weights; every layer, the loss, the
 weight and data gradients and Adam run in the library's CUDA kernels (dd_sur_* in
 include/dd.h).  This module only allocates buffers and sequences those calls.
