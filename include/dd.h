@@ -53,7 +53,7 @@ typedef enum {
     DD_ENOMEM = -2,     /* host or device allocation failed */
     DD_ECUDA = -3,      /* a CUDA runtime call failed (message names it) */
     DD_ETIMEOUT = -4,   /* a bounded device wait ran out (status word set by a kernel) */
-    DD_ENOTSUP = -5     /* valid request that this build does not implement */
+    DD_ENOTSUP = -5     /* valid request that this library does not implement */
 } dd_status;
 
 /* Scan strategies of Sec. 1: raster; alternating (serpentine); interleaved, which
