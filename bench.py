@@ -823,22 +823,26 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     # The field is evaluated on the job's grid of points (dd_field_on_grid).  Under torchrun
-    # the step is split (strong scaling): each rank evaluates a contiguous range of whole
-    # grid-tile rows at every snapshot and a cost-balanced range of dose targets, then one
-    # all-gather of the output rows (the only collective on the path).
+    # the step is split (strong scaling): each rank keeps the whole grid (the tensor-core
+    # contraction needs at least 64 x 64 points) and evaluates a set of the snapshots dealt
+    # by pair count, and a cost-balanced range of dose targets; one all-gather of the
+    # output rows is the only collective on the path.
     n_pts = len(job.pts_xy)
     x0, y0, gdx, gdy, W, H = job.extra["grid"]
-    rr, dr = shard.row_ranges(H, world), shard.dose_ranges(n, world)
-    pr = [(r0 * W, r1 * W) for r0, r1 in rr]
-    (r0, r1), (p0, p1), (j0, j1) = rr[rank], pr[rank], dr[rank]
-    out = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
+    _, ts_visits, _ = scan.visits()
+    nact_t = np.searchsorted(ts_visits, times, side="left")            # started visits per snapshot
+    sets, dr = shard.snapshot_sets([int(a) * n_pts for a in nact_t], world), shard.dose_ranges(n, world)
+    mine = sets[rank]
+    times_r = np.ascontiguousarray(times[mine])
+    j0, j1 = dr[rank]
+    out = torch.empty((len(mine), n_pts), dtype=torch.float64, device=dev)
     dose = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
-    rank_field_pairs = field_pairs // n_pts * (p1 - p0)     # every point has the same pair count
+    rank_field_pairs = int(nact_t[mine].sum()) * n_pts
     # the split of the rank's field between the tensor-core contraction (the older visits'
     # degree-2 terms) and the CUDA-core tile kernel (the rest), as the library plans it
-    tc_prefix, tc_prefix2 = b.dd_field_grid_split(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, degree2=True)
-    rank_tc_pairs = int(tc_prefix.sum()) * (p1 - p0)
-    rank_tc2_pairs = int(tc_prefix2.sum()) * (p1 - p0)
+    tc_prefix, tc_prefix2 = b.dd_field_grid_split(scan, x0, y0, gdx, gdy, W, H, times_r, degree2=True)
+    rank_tc_pairs = int(tc_prefix.sum()) * n_pts
+    rank_tc2_pairs = int(tc_prefix2.sum()) * n_pts
     rank_core_pairs = rank_field_pairs - rank_tc_pairs
 
     # The field and the dose are independent calls: the dose goes on a side stream that forks
@@ -852,7 +856,8 @@ def run_ours(args):
         fork = torch.cuda.Event()
         fork.record(stream)
         side.wait_event(fork)
-        b.dd_field_on_grid(scan, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, prec, out=out, stream=stream)
+        if len(mine):
+            b.dd_field_on_grid(scan, x0, y0, gdx, gdy, W, H, times_r, prec, out=out, stream=stream)
         if world == 1:
             b.dd_per_probe_dose(scan, prec, out=dose, stream=side)
         else:
@@ -862,7 +867,7 @@ def run_ours(args):
         stream.wait_event(join)
         if world == 1:
             return out, dose
-        return shard.gather_columns(out, pr, rank, dist), shard.gather_vector(dose, dr, rank, dist)
+        return shard.gather_rows(out, sets, rank, dist), shard.gather_vector(dose, dr, rank, dist)
 
     for _ in range(args.warmup):
         step("mixed")
@@ -973,7 +978,7 @@ def run_ours(args):
                             "degree (4 / 8 / 11 / 15 from the pair's own h: D + 1), exp(-a) counted as 15 "
                             "DFMA-equivalents, 60 for a two-E1 pair"}
         line["mixed_over_fp64"] = value / v64
-        line["e2e"] = bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, rr, pr, dr)
+        line["e2e"] = bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, sets, dr)
         if world == 1:
             line["field_point_list"] = bench_point_list(b, job, times, scan, dev, stream, flush, field_pairs)
         line["batched"] = bench_batched(dev, stream, rank=rank, world=world, dist=dist)
@@ -1005,17 +1010,19 @@ def run_ours(args):
     return 0
 
 
-def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, rr, pr, dr):
+def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev, sets, dr):
     """End to end through the public API with page-locked host outputs: scan build (its
     visit list uploaded on first use), the grid field and the dose, D2H of both.  One GPU:
     three steps in flight -- step k's calls are enqueued (field and dose on their own pair
     of streams, copies into step k's own page-locked buffers) before step k - 2 is
     synchronised and its scan destroyed, so the host builds the next steps while the GPU
-    runs the earlier ones.  Several: each rank evaluates its rows and dose targets, the
-    device results are gathered, and rank 0 copies out the whole field and dose."""
+    runs the earlier ones.  Several: each rank evaluates its snapshots and dose targets,
+    the device results are gathered, and rank 0 copies out the whole field and dose."""
     import torch
     x0, y0, gdx, gdy, W, H = job.extra["grid"]
-    (r0, r1), (p0, p1), (j0, j1) = rr[rank], pr[rank], dr[rank]
+    mine = sets[rank]
+    times_r = np.ascontiguousarray(times[mine])
+    j0, j1 = dr[rank]
     n_buf = 3 if world == 1 else 1
     outs_h = [torch.empty((len(times), len(job.pts_xy)), dtype=torch.float64, pin_memory=True) for _ in range(n_buf)]
     doses_h = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(n_buf)]
@@ -1023,7 +1030,7 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
     streams = [(torch.cuda.Stream(dev), torch.cuda.Stream(dev)) for _ in range(n_buf)]
     e2e_stream = streams[0][0]
     if world > 1:
-        out_d = torch.empty((len(times), p1 - p0), dtype=torch.float64, device=dev)
+        out_d = torch.empty((len(mine), len(job.pts_xy)), dtype=torch.float64, device=dev)
         dose_d = torch.empty(j1 - j0, dtype=torch.float64, device=dev)
     in_flight = []
     t0 = None
@@ -1058,10 +1065,10 @@ def bench_e2e(args, b, shard, job, times, n, pairs_step, rank, world, dist, dev,
             continue
         else:
             with torch.cuda.stream(e2e_stream):
-                b.dd_field_on_grid(s2, x0, y0 + r0 * gdy, gdx, gdy, W, r1 - r0, times, "mixed", out=out_d,
-                                   stream=e2e_stream)
+                if len(mine):
+                    b.dd_field_on_grid(s2, x0, y0, gdx, gdy, W, H, times_r, "mixed", out=out_d, stream=e2e_stream)
                 b.dd_per_probe_dose_range(s2, j0, j1, "mixed", out=dose_d, stream=e2e_stream)
-                f = shard.gather_columns(out_d, pr, rank, dist)
+                f = shard.gather_rows(out_d, sets, rank, dist)
                 d = shard.gather_vector(dose_d, dr, rank, dist)
                 if rank == 0:
                     out_h.copy_(f, non_blocking=True)

@@ -6,7 +6,9 @@ snapshot) output and every dwell-start dose is an independent sum, so the same s
 carries over to several GPUs with no exchange inside the computation:
 
   * the field: each rank takes a contiguous range of the evaluation points (whole point
-    tiles of the field kernel, 512 points) for every snapshot;
+    tiles of the field kernel, 512 points) for every snapshot -- or, on a grid of points,
+    a set of the snapshots for every point (each rank keeps the whole grid, which the
+    tensor-core contraction needs: at least 64 x 64 points), dealt by pair count;
   * the dose: each rank takes a contiguous range of target visits; visit j costs about j
     pair terms, so the ranges are cut where the triangle's area is split evenly;
   * a batch of scans: scans are dealt to ranks longest-first (LPT) by pair count.
@@ -36,6 +38,14 @@ def row_ranges(n_rows, world, align=4):
     """Contiguous row ranges [r0, r1) of a point grid per rank, whole blocks of `align`
     rows (the grid tile's height), as even as the blocks allow."""
     return point_ranges(n_rows, world, align)
+
+
+def snapshot_sets(costs, world):
+    """The snapshots of each rank (ascending indices) with about equal total cost
+    (costs[j]: the pair count of snapshot j, its started visits times the points): the
+    longest-processing-time-first deal of lpt_assign, within 4/3 of the best split (a
+    contiguous cut leaves up to half the costliest snapshot's cost of imbalance)."""
+    return lpt_assign(list(costs), world)
 
 
 def dose_ranges(n_visits, world, align=DOSE_TILE):
@@ -80,9 +90,43 @@ def gather_columns(local, ranges, rank, dist):
     return torch.cat([parts[r][:, :ranges[r][1] - ranges[r][0]] for r in range(world)], dim=1)
 
 
+def gather_rows(local, sets, rank, dist):
+    """All-gather of per-rank rows: local [len(sets[rank]), cols], the rows (snapshots)
+    sets[rank] of the output -> [total, cols] on every rank, each rank's rows put back at
+    their indices (blocks padded to the largest set for the collective)."""
+    import torch
+    world = len(sets)
+    cols = local.shape[1]
+    total = sum(len(x) for x in sets)
+    height = max(1, max(len(x) for x in sets))
+    buf = torch.zeros((height, cols), dtype=local.dtype, device=local.device)
+    buf[:local.shape[0]] = local
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf.contiguous())
+    out = torch.empty((total, cols), dtype=local.dtype, device=local.device)
+    for r in range(world):
+        if sets[r]:
+            idx = torch.as_tensor(sets[r], dtype=torch.long, device=local.device)
+            out[idx] = parts[r][:len(sets[r])]
+    return out
+
+
 def gather_vector(local, ranges, rank, dist):
     """All-gather of per-rank pieces of a vector: local [j1 - j0] -> [total] on every rank."""
     return gather_columns(local.reshape(1, -1), ranges, rank, dist)[0]
+
+
+def grid_field_and_dose(rank, world, snapshot_costs, n_visits, field_fn, dose_fn, dist=None):
+    """The same with the field split by snapshots (a grid of points kept whole on every
+    rank): field_fn(snaps) -> [len(snaps), n_pts] tensor of the snapshots `snaps`."""
+    sets = snapshot_sets(snapshot_costs, world)
+    dr = dose_ranges(n_visits, world)
+    j0, j1 = dr[rank]
+    field = field_fn(sets[rank])
+    dose = dose_fn(j0, j1)
+    if dist is None or world == 1:
+        return field, dose
+    return gather_rows(field, sets, rank, dist), gather_vector(dose, dr, rank, dist)
 
 
 def field_and_dose(rank, world, n_pts, n_visits, field_fn, dose_fn, dist=None):

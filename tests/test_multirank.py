@@ -93,6 +93,57 @@ def _split_rank(rank, world, port, out):
     dist.destroy_process_group()
 
 
+def _grid_split_rank(rank, world, port, out):
+    import torch.distributed as dist
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    spec, pts, (src, Ds, D, Q0) = _oracle_problem()
+    tt = np.asarray(SPLIT_TIMES) / spec.dwell_s
+    costs = [int(np.searchsorted(src.ts, t, side="left")) * len(pts) for t in tt]
+
+    def field_fn(snaps):
+        if not snaps:
+            return torch.zeros((0, len(pts)), dtype=torch.float64)
+        return torch.from_numpy(oracle.field(src, Ds, D, Q0, pts[:, 0], pts[:, 1], tt[snaps], threads=1))
+
+    def dose_fn(j0, j1):
+        return torch.from_numpy(oracle.dose(src, Ds, D, Q0, targets=np.arange(j0, j1), threads=1))
+
+    field, dose = shard.grid_field_and_dose(rank, world, costs, src.n, field_fn, dose_fn, dist)
+    out[rank] = (field.numpy(), dose.numpy())
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_snapshot_split_gathered_equals_one_rank(world):
+    """The grid form of the split: every rank keeps all points and takes a set of the
+    snapshots; the rows gathered back in snapshot order equal the one-rank field bit for
+    bit on every rank (and the dose as in the point split)."""
+    import oracle
+    spec, pts, (src, Ds, D, Q0) = _oracle_problem()
+    tt = np.asarray(SPLIT_TIMES) / spec.dwell_s
+    whole_f = oracle.field(src, Ds, D, Q0, pts[:, 0], pts[:, 1], tt)
+    whole_d = oracle.dose(src, Ds, D, Q0)
+    out = _spawn(_grid_split_rank, world)
+    for r in range(world):
+        f, d = out[r]
+        assert f.shape == whole_f.shape and d.shape == whole_d.shape
+        assert np.array_equal(f, whole_f) and np.array_equal(d, whole_d)
+
+
+def test_snapshot_sets_partition_and_balance():
+    costs = [64 * (j + 1) * 16384 for j in range(64)]          # the bench's row snapshots
+    for world in (1, 2, 3, 4, 8, 64, 70):
+        sets = shard.snapshot_sets(costs, world)
+        assert len(sets) == world
+        assert sorted(j for x in sets for j in x) == list(range(len(costs)))
+        assert all(x == sorted(x) for x in sets)
+        if world <= 8:
+            load = [sum(costs[j] for j in x) for x in sets]
+            assert max(load) <= 1.02 * sum(costs) / world
+
+
 @pytest.mark.parametrize("world", [2, 3])
 def test_split_field_and_dose_gathered_equals_one_rank(world):
     """Every rank holds the gathered field and dose, bit for bit equal to the one-rank
