@@ -34,12 +34,6 @@ def point_ranges(n_pts, world, align=POINT_TILE):
     return out
 
 
-def row_ranges(n_rows, world, align=4):
-    """Contiguous row ranges [r0, r1) of a point grid per rank, whole blocks of `align`
-    rows (the grid tile's height), as even as the blocks allow."""
-    return point_ranges(n_rows, world, align)
-
-
 def snapshot_sets(costs, world):
     """The snapshots of each rank (ascending indices) with about equal total cost
     (costs[j]: the pair count of snapshot j, its started visits times the points): the

@@ -73,3 +73,42 @@ def test_dose_ranges_against_the_oracle(cuda, spec):
     with pytest.raises(b.DDError) as e:
         b.dd_per_probe_dose_range(scan, 3, n + 1, "mixed", device=cuda)
     assert e.value.status == b.DD_EINVAL
+
+
+@pytest.mark.parametrize("world", [2, 3, 8])
+def test_grid_snapshot_sets_equal_the_whole_job(cuda, world):
+    """The grid form of the split: each rank keeps the whole 128 x 128 grid of the 64 x 64
+    raster and evaluates the snapshot set the pair-count deal gives it (one call per set,
+    the tensor-core contraction inside every call that reaches it); the sets put back at
+    their indices against the whole job in one call -- FP64 within 1e-12, FP32-mixed
+    within the mixed tolerance of the FP64 field at every point -- and the mixed rows
+    against the oracle on seeded pairs."""
+    job = w.raster_64_supersampled()
+    scan = b.Scan(job.scan)
+    p = job.scan.pitch_m
+    x0, y0, dx, dy, nc, nr = 0.0, 0.0, p / 2, p / 2, 128, 128
+    n_pts = nc * nr
+    assert np.array_equal(job.pts_xy, w.grid_points(128, p / 2))          # the same points, row-major
+    _, ts, _ = scan.visits()
+    nact = np.searchsorted(ts, job.times, side="left")
+    sets = shard.snapshot_sets([int(a) * n_pts for a in nact], world)
+    assert sorted(k for s in sets for k in s) == list(range(len(job.times)))
+
+    def on_grid(times, prec):
+        return b.dd_field_on_grid(scan, x0, y0, dx, dy, nc, nr, np.ascontiguousarray(times), prec,
+                                  device=cuda).cpu().numpy()
+
+    whole64 = on_grid(job.times, "fp64")
+    for prec in ("fp64", "mixed"):
+        split = np.full_like(whole64, np.nan)
+        for s in sets:
+            if s:
+                split[s] = on_grid(job.times[s], prec)
+        assert not np.isnan(split).any()
+        if prec == "fp64":
+            assert_fp64(split, whole64, "snapshot split fp64")
+        else:
+            assert_mixed(split, whole64, whole64.max(axis=1), "snapshot split mixed vs fp64")
+            ip, it = w.sample_pairs(n_pts, len(job.times), 512, seed=world)
+            ref = oracle_pairs(job.scan, job.pts_xy, job.times, ip, it)
+            assert_mixed(split[it, ip], ref, peak_lower_bound(job.scan, job.times)[it], "snapshot split vs oracle")
