@@ -115,11 +115,12 @@ def _grid_split_rank(rank, world, port, out):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 5])
 def test_snapshot_split_gathered_equals_one_rank(world):
     """The grid form of the split: every rank keeps all points and takes a set of the
     snapshots; the rows gathered back in snapshot order equal the one-rank field bit for
-    bit on every rank (and the dose as in the point split)."""
+    bit on every rank (and the dose as in the point split).  Five ranks for four
+    snapshots: one rank takes none and still joins the gather."""
     import oracle
     spec, pts, (src, Ds, D, Q0) = _oracle_problem()
     tt = np.asarray(SPLIT_TIMES) / spec.dwell_s
