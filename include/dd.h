@@ -34,7 +34,10 @@
  *     event has completed; up to 8 GiB per device kept); new scratch comes from a
  *     memory pool the library owns per device (freed memory up to 4 GiB stays
  *     mapped).  A scan caches its probe list per device, in blocks that destroyed
- *     scans give back.
+ *     scans give back.  Streams are told apart by their handles: a stream destroyed
+ *     while calls enqueued on it are still running must not be followed by calls on a
+ *     new stream before that work has completed (the new stream can receive the old
+ *     handle, and scratch released on the old one would be taken at once).
  */
 #ifndef DD_H
 #define DD_H
